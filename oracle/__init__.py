@@ -1,0 +1,11 @@
+"""FP64 CPU oracle for the subset-correlation hot path (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The CUDA library never does, and the two
+share no code: see ``dic_oracle`` for what is computed and which passage of the
+paper each step follows.
+"""
+from .dic_oracle import *  # noqa: F401,F403
+from .dic_oracle import (AFFINE, DEFAULT_PARAMS, N_PARAMS, QUADRATIC, RIGID, Plane,  # noqa: F401
+                         ReferenceSubset, bspline_coefficients, correlate, grid, icgn,
+                         interpolate, seed_search)
