@@ -1,0 +1,198 @@
+/*
+ * libdic: local-subset 2D digital image correlation on one GPU.
+ *
+ * The calls follow the paper's statement of the problem (Hirst et al., "Pyvale",
+ * arXiv 2601.12941, Sec. 2.1, Listing 1): a reference image, a deformed image, a
+ * region of interest, a seed, a subset size and a subset step; the result per
+ * subset is the displacement (u, v), the shape-function parameters, a correlation
+ * coefficient and convergence information (Sec. 4: "correlation coefficient
+ * map", unconverged points optionally NaN).
+ *
+ * Method (all of it runs in this library's CUDA kernels):
+ *   - cubic B-spline interpolation of gray levels at sub-pixel positions (Sec. 2.2);
+ *   - the ZNSSD cost (Eq. 4) minimised per subset over the rigid, affine or
+ *     quadratic shape function (Eq. 5) by inverse-compositional Gauss-Newton;
+ *   - reliability-guided propagation to the four nearest neighbours (Sec. 2.4,
+ *     Fig. 3), run as deterministic frontier waves: every point on the frontier
+ *     is correlated in one launch, starting from the warp of its accepted
+ *     neighbour with the highest correlation coefficient;
+ *   - an integer-pixel ZNCC search gives each seed its starting displacement.
+ *
+ * Conventions shared by every call:
+ *   - Return value: DIC_OK (0) or a negative DIC_E* code; nothing is thrown
+ *     across this interface. dic_last_error() gives the calling thread's last
+ *     message.
+ *   - Images are row-major. A dic_image with on_device = 1 is borrowed: the
+ *     device buffer must stay valid and unchanged until it is replaced or the
+ *     handle is destroyed. Host images (on_device = 0) are copied during the call
+ *     and may be reused as soon as it returns.
+ *   - Result pointers are owned by the handle and stay valid until the next
+ *     dic_correlate or dic_destroy on it.
+ *   - A handle is used by one host thread at a time.
+ */
+#ifndef DIC_H
+#define DIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define DIC_OK 0
+#define DIC_EINVAL (-1)   /* an argument is out of range or inconsistent      */
+#define DIC_ENOMEM (-2)   /* a device or pinned-host allocation failed         */
+#define DIC_ECUDA (-3)    /* a CUDA call failed; see dic_last_error()          */
+#define DIC_ETIMEOUT (-4) /* the wave loop exceeded its bound                  */
+#define DIC_ENOSEED (-5)  /* no seed could start (all out of ROI or rejected)  */
+#define DIC_ESTATE (-6)   /* call made in the wrong order (e.g. no images)     */
+
+/* ---- enumerations -------------------------------------------------------- */
+typedef enum { DIC_U8 = 0, DIC_U16 = 1, DIC_BF16 = 2, DIC_F32 = 3, DIC_F64 = 4 } dic_dtype;
+
+/* Eq. 5: rigid uses p0..p1, affine p0..p5, quadratic p0..p11 (no 1/2 factor):
+ *   x' = x_c + p0 + (1+p2) dx + p3 dy + p6 dx^2 + p7 dx dy + p8 dy^2
+ *   y' = y_c + p1 + p4 dx + (1+p5) dy + p9 dx^2 + p10 dx dy + p11 dy^2
+ * with (dx, dy) the pixel offset from the subset centre (x_c, y_c). */
+typedef enum { DIC_RIGID = 0, DIC_AFFINE = 1, DIC_QUADRATIC = 2 } dic_shape;
+
+/* Sec. 2.2: interpolating cubic B-spline, mirror boundary. */
+typedef enum { DIC_BSPLINE3 = 0 } dic_interp;
+
+/* DIC_MIXED: gray levels kept in their input type, spline coefficients, samples
+ * and sums in FP32, Hessian solve, parameter update and final ZNCC in FP64.
+ * DIC_FP64: FP64 everywhere. */
+typedef enum { DIC_FP64 = 0, DIC_MIXED = 1 } dic_precision;
+
+/* per-point status (dic_results.status) */
+enum {
+  DIC_PT_OK = 0,            /* converged, ZNCC >= zncc_min, in bounds: accepted */
+  DIC_PT_NOT_IN_ROI = 1,    /* part of the S x S subset is outside the ROI mask */
+  DIC_PT_NOT_REACHED = 2,   /* no accepted neighbour ever led to this point     */
+  DIC_PT_OUT_OF_BOUNDS = 3, /* a sample fell outside 1 <= x < W-2, 1 <= y < H-2 */
+  DIC_PT_MAX_ITER = 4,      /* max_iter updates without meeting conv_threshold  */
+  DIC_PT_LOW_ZNCC = 5,      /* converged but ZNCC < zncc_min                    */
+  DIC_PT_SINGULAR = 6,      /* Hessian pivot <= 1e-12 * max diagonal            */
+  DIC_PT_FLAT = 7           /* subset RMS contrast <= 1e-6 * max(|mean|, 1)     */
+};
+
+/* ---- structures ---------------------------------------------------------- */
+typedef struct {
+  const void* data;          /* first pixel                                          */
+  int32_t width, height;     /* pixels                                               */
+  int64_t row_stride_bytes;  /* 0 means width * element size                        */
+  int32_t dtype;             /* dic_dtype                                            */
+  int32_t on_device;         /* 1: device pointer (borrowed); 0: host (copied)      */
+} dic_image;
+
+typedef struct {
+  int32_t max_iter;          /* Sec. 4 default 40                                    */
+  int32_t search_radius;     /* seed search |du|, |dv| <= R (default 8)             */
+  double conv_threshold;     /* Sec. 4 default 0.01, on ||dp|| (see below)          */
+  double zncc_min;           /* Sec. 4 "precision" 0.70, read as the ZNCC cut-off   */
+  int32_t precision;         /* dic_precision (default DIC_MIXED)                   */
+  int32_t nan_unconverged;   /* Sec. 4: 1 sets u, v, p of rejected points to NaN    */
+  int32_t profile;           /* 1: record CUDA-event stage timings (dic_get_timing) */
+  int32_t reserved;
+} dic_params;
+/* ||dp|| = sqrt(dp0^2 + dp1^2 + r^2 (dp2^2+..+dp5^2) + r^4 (dp6^2+..+dp11^2)),
+ * r = (subset_size - 1) / 2; a subset has converged once ||dp|| < conv_threshold. */
+
+typedef struct {
+  int64_t n_points;          /* nx * ny; point q = j * nx + i                        */
+  int32_t nx, ny;            /* grid: x = r + i * step, y = r + j * step             */
+  int32_t n_params;          /* 2, 6 or 12                                           */
+  int32_t n_waves;           /* propagation waves run (seeds are wave 0)             */
+  int64_t n_accepted;        /* points with status DIC_PT_OK                         */
+  const int32_t* x;          /* [n_points] subset centre, pixels                     */
+  const int32_t* y;
+  const double* u;           /* [n_points] p0: displacement at the centre, px        */
+  const double* v;           /* [n_points] p1                                        */
+  const double* p;           /* [n_points][n_params], Eq. 5 parameters               */
+  const float* zncc;         /* [n_points] ZNCC = 1 - ZNSSD/2 at the final p (NaN if none) */
+  const int32_t* iters;      /* [n_points] parameter updates applied                 */
+  const uint8_t* converged;  /* [n_points] 1 if ||dp|| < conv_threshold was met      */
+  const uint8_t* status;     /* [n_points] DIC_PT_*                                  */
+  const int32_t* wave;       /* [n_points] propagation wave, -1 if never attempted   */
+} dic_results;
+
+typedef struct {
+  double prefilter_ms;       /* spline prefilter of the images that changed          */
+  double setup_ms;           /* ROI flags, point reset, seed search                  */
+  double waves_ms;           /* first wave launch to last wave completion            */
+  double icgn_kernel_ms;     /* sum of the wave kernels' own durations               */
+  double seed_kernel_ms;     /* integer ZNCC search kernel                           */
+  int32_t n_wave_launches;   /* wave kernels launched (some may find an empty front) */
+  int32_t n_waves;
+  int64_t n_points_attempted;
+  int64_t sum_sample_passes; /* sum over attempted points of (iters + 1)            */
+} dic_timing;
+
+typedef struct dic_handle dic_handle;
+
+/* ---- calls --------------------------------------------------------------- */
+
+/* Sec. 4 defaults: max_iter 40, conv_threshold 0.01, zncc_min 0.70; search
+ * radius 8; DIC_MIXED; no NaN; no profiling. */
+dic_params dic_default_params(void);
+
+/* Creates a handle for a reference/deformed pair (Sec. 2.1, Listing 1).
+ *   ref, def     : same width and height (>= 8 each); any dic_dtype.
+ *   roi          : NULL (every grid point) or a DIC_U8 mask of the same size,
+ *                  nonzero = inside; a point is used iff its whole S x S subset is.
+ *   subset_size  : odd, 3 <= S <= 61 and S <= min(width, height).
+ *   subset_step  : >= 1.
+ *   shape_fn     : dic_shape. interp: DIC_BSPLINE3.
+ * Allocates every device buffer the correlation needs; host images are copied,
+ * device images borrowed. No kernel runs until dic_correlate.
+ * Errors: DIC_EINVAL, DIC_ENOMEM, DIC_ECUDA. On error *out is NULL. */
+int dic_create(const dic_image* ref, const dic_image* def, const dic_image* roi,
+               int32_t subset_size, int32_t subset_step, int32_t shape_fn, int32_t interp,
+               dic_handle** out);
+
+/* Replaces the parameters (validated: max_iter >= 1, conv_threshold > 0,
+ * -1 <= zncc_min <= 1, 0 <= search_radius <= 256, precision valid). */
+int dic_set_params(dic_handle* h, const dic_params* params);
+int dic_get_params(const dic_handle* h, dic_params* out);
+
+/* Replace the reference or the deformed image (same size and dtype as at
+ * creation). The reference's spline coefficients stay resident across calls
+ * until the reference changes; a sequence replaces only the deformed image. */
+int dic_set_reference(dic_handle* h, const dic_image* ref);
+int dic_set_deformed(dic_handle* h, const dic_image* def);
+
+/* Runs the hot path on cuda_stream (NULL: the legacy default stream): spline
+ * prefilter of whichever image changed, seed search, and every propagation wave
+ * until the front is empty. seeds_xy holds n_seeds (x, y) pixel pairs, each
+ * snapped to the nearest grid point (ties to the lower index); seeds outside the
+ * ROI are skipped. Returns once the results are complete on the device.
+ * Errors: DIC_EINVAL (no seeds), DIC_ENOSEED (no seed inside the ROI or every
+ * seed rejected), DIC_ECUDA, DIC_ETIMEOUT. */
+int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void* cuda_stream);
+
+/* Fills *out with device pointers (on_device = 1) or with pointers to host copies
+ * owned by the handle (on_device = 0; copied during the call). */
+int dic_get_results(dic_handle* h, dic_results* out, int32_t on_device);
+
+/* Device pointer to the spline coefficients of the reference (which = 0) or the
+ * deformed image (which = 1) as computed by the last dic_correlate: height rows of
+ * *ld elements, each element *elem_bytes wide (4: FP32 under DIC_MIXED, 8: FP64).
+ * Owned by the handle; for inspection and tests. DIC_ESTATE before any correlate. */
+int dic_get_coefficients(const dic_handle* h, int32_t which, const void** plane, int64_t* ld,
+                         int32_t* elem_bytes);
+
+/* Stage timings of the last dic_correlate; zeros unless params.profile = 1. */
+int dic_get_timing(const dic_handle* h, dic_timing* out);
+
+/* Frees every buffer of the handle (NULL is ignored). */
+void dic_destroy(dic_handle* h);
+
+/* Thread-local text of the last error on the calling thread ("" if none). */
+const char* dic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIC_H */

@@ -1,0 +1,316 @@
+"""Thin ctypes binding of libdic (include/dic.h): the same calls under the same
+names, with argument marshalling only. Every step of the correlation runs in the
+library's CUDA kernels; there is no Python or CPU fallback, and loading fails
+loudly if the compiled library is missing."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdic.so")
+
+DIC_OK, DIC_EINVAL, DIC_ENOMEM, DIC_ECUDA, DIC_ETIMEOUT, DIC_ENOSEED, DIC_ESTATE = 0, -1, -2, -3, -4, -5, -6
+DIC_U8, DIC_U16, DIC_BF16, DIC_F32, DIC_F64 = range(5)
+DIC_RIGID, DIC_AFFINE, DIC_QUADRATIC = range(3)
+DIC_BSPLINE3 = 0
+DIC_FP64, DIC_MIXED = 0, 1
+(PT_OK, PT_NOT_IN_ROI, PT_NOT_REACHED, PT_OUT_OF_BOUNDS, PT_MAX_ITER, PT_LOW_ZNCC, PT_SINGULAR,
+ PT_FLAT) = range(8)
+SHAPES = {"rigid": DIC_RIGID, "affine": DIC_AFFINE, "quadratic": DIC_QUADRATIC}
+N_PARAMS = {DIC_RIGID: 2, DIC_AFFINE: 6, DIC_QUADRATIC: 12}
+
+# every function declared in include/dic.h
+EXPORTS = ("dic_default_params", "dic_create", "dic_set_params", "dic_get_params",
+           "dic_set_reference", "dic_set_deformed", "dic_correlate", "dic_get_results",
+           "dic_get_coefficients", "dic_get_timing", "dic_destroy", "dic_last_error")
+
+
+class DicImage(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("row_stride_bytes", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("on_device", ctypes.c_int32)]
+
+
+class DicParams(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("search_radius", ctypes.c_int32),
+                ("conv_threshold", ctypes.c_double), ("zncc_min", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("nan_unconverged", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class DicResults(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("n_params", ctypes.c_int32), ("n_waves", ctypes.c_int32),
+                ("n_accepted", ctypes.c_int64),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("p", ctypes.c_void_p), ("zncc", ctypes.c_void_p),
+                ("iters", ctypes.c_void_p), ("converged", ctypes.c_void_p),
+                ("status", ctypes.c_void_p), ("wave", ctypes.c_void_p)]
+
+
+class DicTiming(ctypes.Structure):
+    _fields_ = [("prefilter_ms", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("waves_ms", ctypes.c_double), ("icgn_kernel_ms", ctypes.c_double),
+                ("seed_kernel_ms", ctypes.c_double), ("n_wave_launches", ctypes.c_int32),
+                ("n_waves", ctypes.c_int32), ("n_points_attempted", ctypes.c_int64),
+                ("sum_sample_passes", ctypes.c_int64)]
+
+
+class DicError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__("libdic error %d: %s" % (code, message))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """The compiled library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libdic.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    lib.dic_default_params.argtypes = []
+    lib.dic_default_params.restype = DicParams
+    lib.dic_create.argtypes = [P(DicImage), P(DicImage), P(DicImage), ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_int32, ctypes.c_int32, P(vp)]
+    lib.dic_create.restype = ctypes.c_int
+    lib.dic_set_params.argtypes = [vp, P(DicParams)]
+    lib.dic_set_params.restype = ctypes.c_int
+    lib.dic_get_params.argtypes = [vp, P(DicParams)]
+    lib.dic_get_params.restype = ctypes.c_int
+    lib.dic_set_reference.argtypes = [vp, P(DicImage)]
+    lib.dic_set_reference.restype = ctypes.c_int
+    lib.dic_set_deformed.argtypes = [vp, P(DicImage)]
+    lib.dic_set_deformed.restype = ctypes.c_int
+    lib.dic_correlate.argtypes = [vp, P(ctypes.c_int32), ctypes.c_int32, vp]
+    lib.dic_correlate.restype = ctypes.c_int
+    lib.dic_get_results.argtypes = [vp, P(DicResults), ctypes.c_int32]
+    lib.dic_get_results.restype = ctypes.c_int
+    lib.dic_get_coefficients.argtypes = [vp, ctypes.c_int32, P(vp), P(ctypes.c_int64),
+                                         P(ctypes.c_int32)]
+    lib.dic_get_coefficients.restype = ctypes.c_int
+    lib.dic_get_timing.argtypes = [vp, P(DicTiming)]
+    lib.dic_get_timing.restype = ctypes.c_int
+    lib.dic_destroy.argtypes = [vp]
+    lib.dic_destroy.restype = None
+    lib.dic_last_error.argtypes = []
+    lib.dic_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != DIC_OK:
+        raise DicError(rc, load().dic_last_error().decode(errors="replace"))
+
+
+_NP_DTYPES = {np.dtype(np.uint8): DIC_U8, np.dtype(np.uint16): DIC_U16,
+              np.dtype(np.float32): DIC_F32, np.dtype(np.float64): DIC_F64}
+
+
+def make_image(arr, bf16: bool = False) -> tuple:
+    """dic_image for a 2-D numpy array (host, copied by the library) or a 2-D CUDA
+    tensor (device, borrowed). torch.int16 / uint16 tensors are read as DIC_U16,
+    torch.bfloat16 as DIC_BF16. Returns (image, keep-alive object)."""
+    if isinstance(arr, np.ndarray):
+        if arr.ndim != 2:
+            raise ValueError("images are 2-D")
+        a = arr if arr.strides[1] == arr.itemsize else np.ascontiguousarray(arr)
+        dt = _NP_DTYPES.get(a.dtype)
+        if dt is None:
+            raise ValueError("unsupported image dtype %s" % a.dtype)
+        return DicImage(a.ctypes.data, a.shape[1], a.shape[0], a.strides[0], dt, 0), a
+    import torch
+
+    t = arr
+    if t.dim() != 2 or not t.is_cuda or t.stride(1) != 1:
+        raise ValueError("device images are 2-D CUDA tensors with contiguous rows")
+    kinds = {torch.uint8: DIC_U8, torch.int16: DIC_U16, torch.bfloat16: DIC_BF16,
+             torch.float32: DIC_F32, torch.float64: DIC_F64}
+    if hasattr(torch, "uint16"):
+        kinds[torch.uint16] = DIC_U16
+    dt = kinds.get(t.dtype)
+    if dt is None:
+        raise ValueError("unsupported tensor dtype %s" % t.dtype)
+    return DicImage(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0) * t.element_size(), dt, 1), t
+
+
+def dic_default_params() -> DicParams:
+    return load().dic_default_params()
+
+
+def dic_create(ref, deformed, roi, subset_size, subset_step, shape_fn, interp=DIC_BSPLINE3):
+    lib = load()
+    ri, rk = make_image(ref)
+    di, dk = make_image(deformed)
+    mask = None
+    if roi is not None:
+        if isinstance(roi, np.ndarray):
+            roi = np.ascontiguousarray(roi.astype(np.uint8))
+        mi, mask = make_image(roi)
+    h = ctypes.c_void_p()
+    _check(lib.dic_create(ctypes.byref(ri), ctypes.byref(di), ctypes.byref(mi) if mask is not None else None,
+                          subset_size, subset_step, shape_fn, interp, ctypes.byref(h)))
+    return h, (rk, dk)
+
+
+def dic_set_params(h, params: DicParams):
+    _check(load().dic_set_params(h, ctypes.byref(params)))
+
+
+def dic_get_params(h) -> DicParams:
+    p = DicParams()
+    _check(load().dic_get_params(h, ctypes.byref(p)))
+    return p
+
+
+def dic_set_reference(h, ref):
+    im, keep = make_image(ref)
+    _check(load().dic_set_reference(h, ctypes.byref(im)))
+    return keep
+
+
+def dic_set_deformed(h, deformed):
+    im, keep = make_image(deformed)
+    _check(load().dic_set_deformed(h, ctypes.byref(im)))
+    return keep
+
+
+def dic_correlate(h, seeds, stream_ptr: int = 0):
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).reshape(-1, 2))
+    _check(load().dic_correlate(h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), s.shape[0],
+                                ctypes.c_void_p(stream_ptr)))
+
+
+def _host_array(ptr, count, dtype):
+    if count == 0:
+        return np.zeros(0, dtype)
+    buf = (ctypes.c_char * (count * np.dtype(dtype).itemsize)).from_address(ptr)
+    return np.frombuffer(buf, dtype=dtype, count=count).copy()
+
+
+class _DeviceArray:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = dict(shape=shape, typestr=typestr, data=(ptr, False),
+                                             version=3, strides=None)
+
+
+def dic_get_results(h, on_device: bool = False) -> dict:
+    """Per-point arrays in grid order: numpy copies (host) or zero-copy CUDA tensors
+    viewing the handle's buffers (device; valid until the next correlate/destroy)."""
+    r = DicResults()
+    _check(load().dic_get_results(h, ctypes.byref(r), 1 if on_device else 0))
+    n, npar = r.n_points, r.n_params
+    spec = [("x", np.int32, (n,)), ("y", np.int32, (n,)), ("u", np.float64, (n,)),
+            ("v", np.float64, (n,)), ("p", np.float64, (n, npar)), ("zncc", np.float32, (n,)),
+            ("iters", np.int32, (n,)), ("converged", np.uint8, (n,)), ("status", np.uint8, (n,)),
+            ("wave", np.int32, (n,))]
+    out = dict(n_points=n, nx=r.nx, ny=r.ny, n_params=npar, n_waves=r.n_waves,
+               n_accepted=r.n_accepted)
+    if on_device:
+        import torch
+
+        for name, dt, shape in spec:
+            out[name] = torch.as_tensor(_DeviceArray(getattr(r, name), shape, np.dtype(dt).str),
+                                        device="cuda")
+    else:
+        for name, dt, shape in spec:
+            out[name] = _host_array(getattr(r, name), int(np.prod(shape)), dt).reshape(shape)
+    return out
+
+
+def dic_get_coefficients(h, which: int):
+    """The coefficient plane as a zero-copy CUDA tensor view [height, ld]."""
+    import torch
+
+    ptr = ctypes.c_void_p()
+    ld = ctypes.c_int64()
+    es = ctypes.c_int32()
+    _check(load().dic_get_coefficients(h, which, ctypes.byref(ptr), ctypes.byref(ld), ctypes.byref(es)))
+    return ptr.value, ld.value, es.value
+
+
+def dic_get_timing(h) -> dict:
+    t = DicTiming()
+    _check(load().dic_get_timing(h, ctypes.byref(t)))
+    return {name: getattr(t, name) for name, _ in DicTiming._fields_}
+
+
+def dic_destroy(h):
+    if h is not None and h.value:
+        load().dic_destroy(h)
+
+
+def dic_last_error() -> str:
+    return load().dic_last_error().decode(errors="replace")
+
+
+def params(**kw) -> DicParams:
+    """Default parameters with the given fields replaced (precision may be a string)."""
+    p = dic_default_params()
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = DIC_FP64 if v == "fp64" else DIC_MIXED
+        setattr(p, k, v)
+    return p
+
+
+class Correlation:
+    """One reference/deformed pair on one handle (convenience over the calls above)."""
+
+    def __init__(self, ref, deformed, roi=None, subset_size=21, subset_step=5, shape="affine",
+                 **param_kw):
+        self.shape = SHAPES[shape] if isinstance(shape, str) else shape
+        self.h, self._keep = dic_create(ref, deformed, roi, subset_size, subset_step, self.shape)
+        if param_kw:
+            dic_set_params(self.h, params(**param_kw))
+
+    def set_params(self, **kw):
+        p = dic_get_params(self.h)
+        for k, v in kw.items():
+            if k == "precision" and isinstance(v, str):
+                v = DIC_FP64 if v == "fp64" else DIC_MIXED
+            setattr(p, k, v)
+        dic_set_params(self.h, p)
+
+    def set_reference(self, ref):
+        self._keep = (dic_set_reference(self.h, ref), self._keep[1])
+
+    def set_deformed(self, deformed):
+        self._keep = (self._keep[0], dic_set_deformed(self.h, deformed))
+
+    def run(self, seeds, stream_ptr: int = 0):
+        dic_correlate(self.h, seeds, stream_ptr)
+        return self
+
+    def results(self, on_device=False):
+        return dic_get_results(self.h, on_device)
+
+    def timing(self):
+        return dic_get_timing(self.h)
+
+    def close(self):
+        if self.h is not None:
+            dic_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,706 @@
+// C-ABI of libdic (declared in include/dic.h): handle life cycle, argument
+// checks, device buffers, the wave loop and result export. Every computation of
+// the method runs in the kernels of prefilter.cu, seed.cu and correlate.cu.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "dic_internal.cuh"
+
+using namespace dic;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? DIC_ENOMEM : DIC_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define DIC_CUDA(call, what)                      \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+size_t dtype_size(int dt) {
+  switch (dt) {
+    case DIC_U8: return 1;
+    case DIC_U16: return 2;
+    case DIC_BF16: return 2;
+    case DIC_F32: return 4;
+    case DIC_F64: return 8;
+    default: return 0;
+  }
+}
+
+int nparams_of(int shape) { return shape == DIC_RIGID ? 2 : shape == DIC_AFFINE ? 6 : 12; }
+
+int64_t floor_div(int64_t a, int64_t b) {
+  int64_t q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+
+template <typename P>
+int dev_alloc(P** ptr, size_t count, const char* what) {
+  void* raw = nullptr;
+  cudaError_t e = cudaMalloc(&raw, count * sizeof(P) > 0 ? count * sizeof(P) : 1);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return cuda_fail(e, what);
+  }
+  *ptr = static_cast<P*>(raw);
+  return DIC_OK;
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+}  // namespace
+
+struct dic_handle {
+  int W = 0, H = 0, S = 0, step = 0, r = 0, shape = 0, nparams = 0, nx = 0, ny = 0;
+  int64_t npts = 0;
+  dic_params prm{};
+  int device = 0;
+  // images: borrowed device pointers or owned copies
+  GrayPlane ref{}, def{};
+  void* ref_owned = nullptr;
+  void* def_owned = nullptr;
+  int ref_dtype = 0, def_dtype = 0;
+  bool ref_dirty = true, def_dirty = true;
+  // ROI flags per point (NULL: all in)
+  uint8_t* roi_ok = nullptr;
+  // spline coefficient planes in the working precision
+  void* c_ref = nullptr;
+  void* c_def = nullptr;
+  int64_t ldc = 0;
+  int plane_prec = -1;
+  // per-point state
+  int32_t* x = nullptr;
+  int32_t* y = nullptr;
+  double* u = nullptr;
+  double* v = nullptr;
+  double* p = nullptr;
+  float* zncc = nullptr;
+  double* zncc64 = nullptr;
+  int32_t* iters = nullptr;
+  int32_t* wave = nullptr;
+  uint8_t* conv = nullptr;
+  uint8_t* status = nullptr;
+  // frontier
+  int32_t* front[2] = {nullptr, nullptr};
+  int32_t* counters = nullptr;
+  int32_t* wave_sizes = nullptr;
+  int32_t* h_counters = nullptr;  // pinned, [kBatchSlots][kNumCounters]
+  // seeds
+  int32_t* seed_xy = nullptr;
+  int32_t* seed_q = nullptr;
+  double* seed_scores = nullptr;
+  size_t seed_cap = 0, score_cap = 0;
+  // host copies of the results
+  void* h_res = nullptr;
+  size_t h_res_bytes = 0;
+  // last run
+  int n_waves = 0;
+  int64_t n_accepted = 0;
+  dic_timing timing{};
+  std::vector<cudaEvent_t> events;       // stage boundaries
+  std::vector<cudaEvent_t> wave_events;  // two per wave kernel when profiling
+  cudaEvent_t batch_ev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+constexpr int kBatchSlots = 2;
+constexpr int kAccepted = 6;  // counters slot holding the accepted-point count
+
+int check_image(const dic_image* im, const char* name) {
+  if (!im) return fail(DIC_EINVAL, "%s image is NULL", name);
+  if (!im->data) return fail(DIC_EINVAL, "%s image has no data", name);
+  if (dtype_size(im->dtype) == 0) return fail(DIC_EINVAL, "%s image has an unknown dtype %d", name, im->dtype);
+  if (im->width < 8 || im->height < 8)
+    return fail(DIC_EINVAL, "%s image is %dx%d; at least 8x8 is needed", name, im->width, im->height);
+  const int64_t min_stride = static_cast<int64_t>(im->width) * dtype_size(im->dtype);
+  if (im->row_stride_bytes != 0 && im->row_stride_bytes < min_stride)
+    return fail(DIC_EINVAL, "%s image row stride %lld is below width * element size", name,
+                static_cast<long long>(im->row_stride_bytes));
+  return DIC_OK;
+}
+
+// Adopts a device image or copies a host image into an owned device buffer.
+int bind_image(const dic_image* im, GrayPlane* plane, void** owned, int* dtype_out) {
+  const size_t es = dtype_size(im->dtype);
+  const int64_t stride = im->row_stride_bytes ? im->row_stride_bytes : im->width * static_cast<int64_t>(es);
+  const size_t row_bytes = static_cast<size_t>(im->width) * es;
+  if (im->on_device) {
+    plane->data = im->data;
+    plane->stride = stride;
+  } else {
+    if (!*owned) {
+      int rc = dev_alloc(reinterpret_cast<uint8_t**>(owned), row_bytes * im->height, "image buffer");
+      if (rc) return rc;
+    }
+    DIC_CUDA(cudaMemcpy2D(*owned, row_bytes, im->data, stride, row_bytes, im->height,
+                          cudaMemcpyHostToDevice),
+             "image upload");
+    plane->data = *owned;
+    plane->stride = static_cast<int64_t>(row_bytes);
+  }
+  plane->dtype = im->dtype;
+  *dtype_out = im->dtype;
+  return DIC_OK;
+}
+
+void free_planes(dic_handle* h) {
+  dev_free(h->c_ref);
+  dev_free(h->c_def);
+  h->c_ref = h->c_def = nullptr;
+  h->plane_prec = -1;
+}
+
+int ensure_planes(dic_handle* h) {
+  const int prec = h->prm.precision;
+  if (h->plane_prec == prec) return DIC_OK;
+  free_planes(h);
+  const size_t es = prec == DIC_FP64 ? sizeof(double) : sizeof(float);
+  h->ldc = (h->W + 31) & ~31;
+  const size_t bytes = es * static_cast<size_t>(h->ldc) * h->H;
+  int rc = dev_alloc(reinterpret_cast<uint8_t**>(&h->c_ref), bytes, "reference coefficients");
+  if (rc) return rc;
+  rc = dev_alloc(reinterpret_cast<uint8_t**>(&h->c_def), bytes, "deformed coefficients");
+  if (rc) return rc;
+  h->plane_prec = prec;
+  h->ref_dirty = h->def_dirty = true;
+  return DIC_OK;
+}
+
+cudaEvent_t pool_event(std::vector<cudaEvent_t>& pool, size_t i) {
+  while (pool.size() <= i) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    pool.push_back(e);
+  }
+  return pool[i];
+}
+
+cudaEvent_t event_at(dic_handle* h, size_t i) { return pool_event(h->events, i); }
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+  return ms;
+}
+
+template <typename T>
+int prefilter(dic_handle* h, const GrayPlane& src, void* dst, cudaStream_t s) {
+  PrefilterArgs<T> a{src, h->W, h->H, static_cast<T*>(dst), h->ldc};
+  DIC_CUDA(launch_prefilter<T>(a, s), "prefilter launch");
+  return DIC_OK;
+}
+
+PointArrays point_arrays(dic_handle* h) {
+  PointArrays pa{};
+  pa.n = h->npts;
+  pa.nx = h->nx;
+  pa.ny = h->ny;
+  pa.u = h->u;
+  pa.v = h->v;
+  pa.p = h->p;
+  pa.zncc = h->zncc;
+  pa.zncc64 = h->zncc64;
+  pa.iters = h->iters;
+  pa.converged = h->conv;
+  pa.status = h->status;
+  pa.wave = h->wave;
+  return pa;
+}
+
+void choose_bands(int S, int* bands, int* band_h) {
+  for (int hgt = 1; hgt <= S; ++hgt) {
+    const int b = (S + hgt - 1) / hgt;
+    if (S * b <= kThreads) {
+      *bands = b;
+      *band_h = hgt;
+      return;
+    }
+  }
+  *bands = 1;
+  *band_h = S;
+}
+
+template <typename T>
+int run_waves(dic_handle* h, cudaStream_t s) {
+  WaveArgs<T> a{};
+  a.W = h->W;
+  a.H = h->H;
+  a.ref_gray = h->ref;
+  a.c_ref = static_cast<const T*>(h->c_ref);
+  a.c_def = static_cast<const T*>(h->c_def);
+  a.ldc = h->ldc;
+  a.S = h->S;
+  a.r = h->r;
+  a.step = h->step;
+  a.nx = h->nx;
+  a.ny = h->ny;
+  choose_bands(h->S, &a.bands, &a.band_h);
+  const int side = h->S + 12;
+  a.win_cap = side * side;
+  a.pts = point_arrays(h);
+  a.roi_ok = h->roi_ok;
+  a.counters = h->counters;
+  a.wave_sizes = h->wave_sizes;
+  a.max_iter = h->prm.max_iter;
+  a.conv_threshold = h->prm.conv_threshold;
+  a.zncc_min = h->prm.zncc_min;
+
+  int sms = 0;
+  DIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "device query");
+  const size_t smem = wave_smem_bytes<T>(h->S, a.win_cap);
+  const int per_sm = wave_blocks_per_sm<T>(h->nparams, smem);
+  const int grid = sms * per_sm;
+
+  const bool prof = h->prm.profile != 0;
+  const int64_t max_waves = h->npts + 2;
+  int64_t launched = 0;
+  int batch = 4;
+  int pending_slot = -1;
+  int64_t pending_end = 0;
+  int slot = 0;
+  cudaEvent_t* batch_ev = h->batch_ev;
+  for (int i = 0; i < kBatchSlots; ++i)
+    if (!batch_ev[i] && cudaEventCreateWithFlags(&batch_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      return fail(DIC_ECUDA, "event creation failed");
+  bool done = false;
+  while (!done) {
+    if (launched + batch > max_waves) return fail(DIC_ETIMEOUT, "wave loop exceeded %lld waves", (long long)max_waves);
+    for (int b = 0; b < batch; ++b) {
+      const int64_t k = launched + b;
+      a.k = static_cast<int>(k);
+      a.cur = h->front[k & 1];
+      a.next = h->front[(k + 1) & 1];
+      if (prof) {
+        cudaEvent_t e0 = pool_event(h->wave_events, 2 * k), e1 = pool_event(h->wave_events, 2 * k + 1);
+        if (!e0 || !e1) return fail(DIC_ECUDA, "event creation failed");
+        cudaEventRecord(e0, s);
+        DIC_CUDA(launch_wave<T>(a, h->nparams, grid, s), "wave launch");
+        cudaEventRecord(e1, s);
+      } else {
+        DIC_CUDA(launch_wave<T>(a, h->nparams, grid, s), "wave launch");
+      }
+    }
+    launched += batch;
+    int32_t* hc = h->h_counters + slot * kNumCounters;
+    DIC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(int32_t) * kNumCounters, cudaMemcpyDeviceToHost, s),
+             "counter read-back");
+    DIC_CUDA(cudaEventRecord(batch_ev[slot], s), "event record");
+    if (pending_slot >= 0) {
+      DIC_CUDA(cudaEventSynchronize(batch_ev[pending_slot]), "wave batch wait");
+      const int32_t* pc = h->h_counters + pending_slot * kNumCounters;
+      if (pc[kCount + pending_end % 3] == 0) done = true;
+    }
+    pending_slot = slot;
+    pending_end = launched;
+    slot = (slot + 1) % kBatchSlots;
+    if (batch < 32) batch *= 2;
+  }
+  DIC_CUDA(cudaStreamSynchronize(s), "wave loop");
+  // last non-empty wave
+  std::vector<int32_t> sizes(static_cast<size_t>(launched));
+  DIC_CUDA(cudaMemcpy(sizes.data(), h->wave_sizes, sizeof(int32_t) * launched, cudaMemcpyDeviceToHost),
+           "wave sizes");
+  int nw = 0;
+  int64_t attempted = 0;
+  for (int64_t k = 0; k < launched; ++k)
+    if (sizes[k] > 0) {
+      nw = static_cast<int>(k) + 1;
+      attempted += sizes[k];
+    }
+  h->n_waves = nw;
+  h->timing.n_wave_launches = static_cast<int>(launched);
+  h->timing.n_waves = nw;
+  h->timing.n_points_attempted = attempted;
+  if (prof) {
+    double sum = 0.0;
+    for (int64_t k = 0; k < launched; ++k)
+      sum += elapsed(h->wave_events[2 * k], h->wave_events[2 * k + 1]);
+    h->timing.icgn_kernel_ms = sum;
+  }
+  return DIC_OK;
+}
+
+int alloc_points(dic_handle* h) {
+  const size_t n = static_cast<size_t>(h->npts);
+  int rc;
+  if ((rc = dev_alloc(&h->x, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->y, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->u, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->v, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->p, n * h->nparams, "points"))) return rc;
+  if ((rc = dev_alloc(&h->zncc, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->zncc64, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->iters, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->wave, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->conv, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->status, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->front[0], n + 1, "frontier"))) return rc;
+  if ((rc = dev_alloc(&h->front[1], n + 1, "frontier"))) return rc;
+  if ((rc = dev_alloc(&h->counters, kNumCounters, "counters"))) return rc;
+  if ((rc = dev_alloc(&h->wave_sizes, n + 2, "wave sizes"))) return rc;
+  void* pinned = nullptr;
+  DIC_CUDA(cudaMallocHost(&pinned, sizeof(int32_t) * kNumCounters * kBatchSlots), "pinned counters");
+  h->h_counters = static_cast<int32_t*>(pinned);
+  std::vector<int32_t> gx(n), gy(n);
+  for (size_t q = 0; q < n; ++q) {
+    gx[q] = h->r + static_cast<int32_t>(q % h->nx) * h->step;
+    gy[q] = h->r + static_cast<int32_t>(q / h->nx) * h->step;
+  }
+  DIC_CUDA(cudaMemcpy(h->x, gx.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice), "grid upload");
+  DIC_CUDA(cudaMemcpy(h->y, gy.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice), "grid upload");
+  return DIC_OK;
+}
+
+void release(dic_handle* h) {
+  if (!h) return;
+  free_planes(h);
+  dev_free(h->ref_owned);
+  dev_free(h->def_owned);
+  dev_free(h->roi_ok);
+  void* ptrs[] = {h->x,     h->y,        h->u,    h->v,      h->p,          h->zncc,
+                  h->zncc64, h->iters,   h->wave, h->conv,   h->status,     h->front[0],
+                  h->front[1], h->counters, h->wave_sizes, h->seed_xy, h->seed_q, h->seed_scores};
+  for (void* q : ptrs) dev_free(q);
+  if (h->h_counters) cudaFreeHost(h->h_counters);
+  if (h->h_res) cudaFreeHost(h->h_res);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->wave_events) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->batch_ev)
+    if (e) cudaEventDestroy(e);
+  delete h;
+}
+
+int validate_params(const dic_params* p) {
+  if (!p) return fail(DIC_EINVAL, "params is NULL");
+  if (p->max_iter < 1 || p->max_iter > 100000) return fail(DIC_EINVAL, "max_iter %d out of range", p->max_iter);
+  if (!(p->conv_threshold > 0.0)) return fail(DIC_EINVAL, "conv_threshold must be > 0");
+  if (!(p->zncc_min >= -1.0 && p->zncc_min <= 1.0)) return fail(DIC_EINVAL, "zncc_min must be in [-1, 1]");
+  if (p->search_radius < 0 || p->search_radius > 256)
+    return fail(DIC_EINVAL, "search_radius %d out of range", p->search_radius);
+  if (p->precision != DIC_FP64 && p->precision != DIC_MIXED)
+    return fail(DIC_EINVAL, "unknown precision %d", p->precision);
+  return DIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dic_params dic_default_params(void) {
+  dic_params p{};
+  p.max_iter = 40;
+  p.search_radius = 8;
+  p.conv_threshold = 0.01;
+  p.zncc_min = 0.70;
+  p.precision = DIC_MIXED;
+  p.nan_unconverged = 0;
+  p.profile = 0;
+  p.reserved = 0;
+  return p;
+}
+
+const char* dic_last_error(void) { return g_last_error.c_str(); }
+
+int dic_create(const dic_image* ref, const dic_image* def, const dic_image* roi, int32_t subset_size,
+               int32_t subset_step, int32_t shape_fn, int32_t interp, dic_handle** out) {
+  g_last_error.clear();
+  if (!out) return fail(DIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc;
+  if ((rc = check_image(ref, "reference"))) return rc;
+  if ((rc = check_image(def, "deformed"))) return rc;
+  if (ref->width != def->width || ref->height != def->height)
+    return fail(DIC_EINVAL, "reference %dx%d and deformed %dx%d differ in size", ref->width, ref->height,
+                def->width, def->height);
+  if (subset_size < 3 || subset_size > kMaxSubset || subset_size % 2 == 0)
+    return fail(DIC_EINVAL, "subset_size %d must be odd and in [3, %d]", subset_size, kMaxSubset);
+  if (subset_size > ref->width || subset_size > ref->height)
+    return fail(DIC_EINVAL, "subset_size %d exceeds the image", subset_size);
+  if (subset_step < 1) return fail(DIC_EINVAL, "subset_step %d must be >= 1", subset_step);
+  if (shape_fn != DIC_RIGID && shape_fn != DIC_AFFINE && shape_fn != DIC_QUADRATIC)
+    return fail(DIC_EINVAL, "unknown shape function %d", shape_fn);
+  if (interp != DIC_BSPLINE3) return fail(DIC_EINVAL, "unknown interpolation %d", interp);
+  if (roi) {
+    if ((rc = check_image(roi, "roi"))) return rc;
+    if (roi->dtype != DIC_U8) return fail(DIC_EINVAL, "roi mask must be DIC_U8");
+    if (roi->width != ref->width || roi->height != ref->height)
+      return fail(DIC_EINVAL, "roi mask size differs from the images");
+  }
+  dic_handle* h = new (std::nothrow) dic_handle();
+  if (!h) return fail(DIC_ENOMEM, "handle allocation");
+  cudaGetDevice(&h->device);
+  h->W = ref->width;
+  h->H = ref->height;
+  h->S = subset_size;
+  h->r = (subset_size - 1) / 2;
+  h->step = subset_step;
+  h->shape = shape_fn;
+  h->nparams = nparams_of(shape_fn);
+  h->nx = (h->W - 1 - 2 * h->r) / h->step + 1;
+  h->ny = (h->H - 1 - 2 * h->r) / h->step + 1;
+  h->npts = static_cast<int64_t>(h->nx) * h->ny;
+  h->prm = dic_default_params();
+  if ((rc = bind_image(ref, &h->ref, &h->ref_owned, &h->ref_dtype)) ||
+      (rc = bind_image(def, &h->def, &h->def_owned, &h->def_dtype)) || (rc = alloc_points(h))) {
+    release(h);
+    return rc;
+  }
+  if (roi) {
+    GrayPlane mask{};
+    void* owned = nullptr;
+    int dt = 0;
+    if ((rc = dev_alloc(&h->roi_ok, static_cast<size_t>(h->npts), "roi flags")) ||
+        (rc = bind_image(roi, &mask, &owned, &dt))) {
+      dev_free(owned);
+      release(h);
+      return rc;
+    }
+    RoiArgs ra{mask, h->S, h->r, h->step, h->nx, h->ny, h->roi_ok};
+    cudaError_t e = launch_roi_flags(ra, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    dev_free(owned);
+    if (e != cudaSuccess) {
+      release(h);
+      return cuda_fail(e, "roi flags");
+    }
+  }
+  *out = h;
+  return DIC_OK;
+}
+
+int dic_set_params(dic_handle* h, const dic_params* params) {
+  if (!h) return fail(DIC_EINVAL, "handle is NULL");
+  int rc = validate_params(params);
+  if (rc) return rc;
+  h->prm = *params;
+  return DIC_OK;
+}
+
+int dic_get_params(const dic_handle* h, dic_params* out) {
+  if (!h || !out) return fail(DIC_EINVAL, "NULL argument");
+  *out = h->prm;
+  return DIC_OK;
+}
+
+static int replace_image(dic_handle* h, const dic_image* im, bool is_ref) {
+  if (!h) return fail(DIC_EINVAL, "handle is NULL");
+  int rc = check_image(im, is_ref ? "reference" : "deformed");
+  if (rc) return rc;
+  if (im->width != h->W || im->height != h->H)
+    return fail(DIC_EINVAL, "image is %dx%d, the handle holds %dx%d", im->width, im->height, h->W, h->H);
+  const int old_dtype = is_ref ? h->ref_dtype : h->def_dtype;
+  void** owned = is_ref ? &h->ref_owned : &h->def_owned;
+  if (!im->on_device && *owned && dtype_size(im->dtype) != dtype_size(old_dtype)) {
+    dev_free(*owned);
+    *owned = nullptr;
+  }
+  if (is_ref) {
+    rc = bind_image(im, &h->ref, owned, &h->ref_dtype);
+    h->ref_dirty = true;
+  } else {
+    rc = bind_image(im, &h->def, owned, &h->def_dtype);
+    h->def_dirty = true;
+  }
+  return rc;
+}
+
+int dic_set_reference(dic_handle* h, const dic_image* ref) { return replace_image(h, ref, true); }
+int dic_set_deformed(dic_handle* h, const dic_image* def) { return replace_image(h, def, false); }
+
+int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void* cuda_stream) {
+  if (!h) return fail(DIC_EINVAL, "handle is NULL");
+  g_last_error.clear();
+  if (!seeds_xy || n_seeds < 1) return fail(DIC_EINVAL, "at least one seed is needed");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int rc = ensure_planes(h);
+  if (rc) return rc;
+  h->timing = dic_timing{};
+  const bool prof = h->prm.profile != 0;
+  const bool fp64 = h->prm.precision == DIC_FP64;
+  // events: 0 start, 1 after prefilter, 2 after setup, 3 after seed scores, 4 end
+  for (int i = 0; i < 5; ++i)
+    if (!event_at(h, i)) return fail(DIC_ECUDA, "event creation failed");
+  if (prof) cudaEventRecord(h->events[0], s);
+
+  if (h->ref_dirty) {
+    rc = fp64 ? prefilter<double>(h, h->ref, h->c_ref, s) : prefilter<float>(h, h->ref, h->c_ref, s);
+    if (rc) return rc;
+    h->ref_dirty = false;
+  }
+  if (h->def_dirty) {
+    rc = fp64 ? prefilter<double>(h, h->def, h->c_def, s) : prefilter<float>(h, h->def, h->c_def, s);
+    if (rc) return rc;
+    h->def_dirty = false;
+  }
+  if (prof) cudaEventRecord(h->events[1], s);
+
+  // seeds: snap to the nearest grid point (ties to the lower index)
+  std::vector<int32_t> centres(2 * static_cast<size_t>(n_seeds)), qs(static_cast<size_t>(n_seeds));
+  for (int i = 0; i < n_seeds; ++i) {
+    int64_t gi = floor_div(2 * (static_cast<int64_t>(seeds_xy[2 * i]) - h->r) + h->step - 1, 2 * h->step);
+    int64_t gj = floor_div(2 * (static_cast<int64_t>(seeds_xy[2 * i + 1]) - h->r) + h->step - 1, 2 * h->step);
+    gi = gi < 0 ? 0 : (gi > h->nx - 1 ? h->nx - 1 : gi);
+    gj = gj < 0 ? 0 : (gj > h->ny - 1 ? h->ny - 1 : gj);
+    qs[i] = static_cast<int32_t>(gj * h->nx + gi);
+    centres[2 * i] = h->r + static_cast<int32_t>(gi) * h->step;
+    centres[2 * i + 1] = h->r + static_cast<int32_t>(gj) * h->step;
+  }
+  const int R = h->prm.search_radius;
+  const size_t side = 2 * static_cast<size_t>(R) + 1;
+  if (static_cast<size_t>(n_seeds) > h->seed_cap) {
+    dev_free(h->seed_xy);
+    dev_free(h->seed_q);
+    h->seed_xy = h->seed_q = nullptr;
+    h->seed_cap = 0;
+    if ((rc = dev_alloc(&h->seed_xy, 2 * static_cast<size_t>(n_seeds), "seeds")) ||
+        (rc = dev_alloc(&h->seed_q, static_cast<size_t>(n_seeds), "seeds")))
+      return rc;
+    h->seed_cap = n_seeds;
+  }
+  if (n_seeds * side * side > h->score_cap) {
+    dev_free(h->seed_scores);
+    h->seed_scores = nullptr;
+    h->score_cap = 0;
+    if ((rc = dev_alloc(&h->seed_scores, n_seeds * side * side, "seed scores"))) return rc;
+    h->score_cap = n_seeds * side * side;
+  }
+  DIC_CUDA(cudaMemcpyAsync(h->seed_xy, centres.data(), centres.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, s), "seed upload");
+  DIC_CUDA(cudaMemcpyAsync(h->seed_q, qs.data(), qs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+           "seed upload");
+  PointArrays pa = point_arrays(h);
+  DIC_CUDA(launch_reset_points(pa, h->nparams, h->roi_ok, s), "point reset");
+  DIC_CUDA(cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * kNumCounters, s), "counter reset");
+  if (prof) cudaEventRecord(h->events[2], s);
+  SeedArgs sa{h->ref, h->def, h->W, h->H, h->S, R, n_seeds, h->seed_xy, h->seed_scores};
+  DIC_CUDA(launch_seed_scores(sa, s), "seed search");
+  if (prof) cudaEventRecord(h->events[3], s);
+  SeedCommitArgs ca{n_seeds, R, h->nparams, h->seed_q, h->seed_scores, h->p, h->status,
+                    h->wave, h->front[0], h->counters, h->roi_ok};
+  DIC_CUDA(launch_seed_commit(ca, s), "seed commit");
+
+  cudaEvent_t w0 = event_at(h, 5), w1 = event_at(h, 6);
+  if (!w0 || !w1) return fail(DIC_ECUDA, "event creation failed");
+  if (prof) cudaEventRecord(w0, s);
+  rc = fp64 ? run_waves<double>(h, s) : run_waves<float>(h, s);
+  if (rc) return rc;
+  if (prof) cudaEventRecord(w1, s);
+  DIC_CUDA(cudaMemsetAsync(h->counters + kAccepted, 0, sizeof(int32_t), s), "counter reset");
+  DIC_CUDA(launch_finalize_points(pa, h->nparams, h->prm.nan_unconverged, h->counters + kAccepted, s),
+           "finalize");
+  if (prof) cudaEventRecord(h->events[4], s);
+  DIC_CUDA(cudaMemcpyAsync(h->h_counters, h->counters, sizeof(int32_t) * kNumCounters,
+                           cudaMemcpyDeviceToHost, s), "counter read-back");
+  DIC_CUDA(cudaStreamSynchronize(s), "correlate");
+  const int64_t accepted = h->h_counters[kAccepted];
+  h->n_accepted = accepted;
+  if (prof) {
+    h->timing.prefilter_ms = elapsed(h->events[0], h->events[1]);
+    h->timing.setup_ms = elapsed(h->events[1], h->events[3]);
+    h->timing.seed_kernel_ms = elapsed(h->events[2], h->events[3]);
+    h->timing.waves_ms = elapsed(w0, w1);
+  }
+  if (accepted == 0) return fail(DIC_ENOSEED, "no seed was accepted");
+  return DIC_OK;
+}
+
+int dic_get_results(dic_handle* h, dic_results* out, int32_t on_device) {
+  if (!h || !out) return fail(DIC_EINVAL, "NULL argument");
+  const size_t n = static_cast<size_t>(h->npts);
+  out->n_points = h->npts;
+  out->nx = h->nx;
+  out->ny = h->ny;
+  out->n_params = h->nparams;
+  out->n_waves = h->n_waves;
+  out->n_accepted = h->n_accepted;
+  if (on_device) {
+    out->x = h->x;
+    out->y = h->y;
+    out->u = h->u;
+    out->v = h->v;
+    out->p = h->p;
+    out->zncc = h->zncc;
+    out->iters = h->iters;
+    out->converged = h->conv;
+    out->status = h->status;
+    out->wave = h->wave;
+    return DIC_OK;
+  }
+  const size_t bytes = n * (4 + 4 + 8 + 8 + 8 * h->nparams + 4 + 4 + 1 + 1 + 4) + 256;
+  if (h->h_res_bytes < bytes) {
+    if (h->h_res) cudaFreeHost(h->h_res);
+    h->h_res = nullptr;
+    h->h_res_bytes = 0;
+    DIC_CUDA(cudaMallocHost(&h->h_res, bytes), "pinned result buffer");
+    h->h_res_bytes = bytes;
+  }
+  char* base = static_cast<char*>(h->h_res);
+  size_t off = 0;
+  auto take = [&](const void* src, size_t len) -> void* {
+    void* dst = base + off;
+    off += (len + 15) & ~static_cast<size_t>(15);
+    cudaMemcpyAsync(dst, src, len, cudaMemcpyDeviceToHost, 0);
+    return dst;
+  };
+  out->p = static_cast<const double*>(take(h->p, n * 8 * h->nparams));
+  out->u = static_cast<const double*>(take(h->u, n * 8));
+  out->v = static_cast<const double*>(take(h->v, n * 8));
+  out->x = static_cast<const int32_t*>(take(h->x, n * 4));
+  out->y = static_cast<const int32_t*>(take(h->y, n * 4));
+  out->zncc = static_cast<const float*>(take(h->zncc, n * 4));
+  out->iters = static_cast<const int32_t*>(take(h->iters, n * 4));
+  out->wave = static_cast<const int32_t*>(take(h->wave, n * 4));
+  out->converged = static_cast<const uint8_t*>(take(h->conv, n));
+  out->status = static_cast<const uint8_t*>(take(h->status, n));
+  DIC_CUDA(cudaStreamSynchronize(0), "result read-back");
+  return DIC_OK;
+}
+
+int dic_get_coefficients(const dic_handle* h, int32_t which, const void** plane, int64_t* ld,
+                         int32_t* elem_bytes) {
+  if (!h || !plane || !ld || !elem_bytes) return fail(DIC_EINVAL, "NULL argument");
+  if (which != 0 && which != 1) return fail(DIC_EINVAL, "which must be 0 or 1");
+  if (h->plane_prec < 0 || (which == 0 ? h->ref_dirty : h->def_dirty))
+    return fail(DIC_ESTATE, "coefficients are computed by dic_correlate");
+  *plane = which == 0 ? h->c_ref : h->c_def;
+  *ld = h->ldc;
+  *elem_bytes = h->plane_prec == DIC_FP64 ? 8 : 4;
+  return DIC_OK;
+}
+
+int dic_get_timing(const dic_handle* h, dic_timing* out) {
+  if (!h || !out) return fail(DIC_EINVAL, "NULL argument");
+  *out = h->timing;
+  return DIC_OK;
+}
+
+void dic_destroy(dic_handle* h) { release(h); }
+
+}  // extern "C"

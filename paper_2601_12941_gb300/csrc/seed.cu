@@ -1,0 +1,163 @@
+// Integer-pixel seed search: for every seed, the ZNCC between the reference subset
+// and the deformed subset shifted by each integer offset (du, dv), |du|, |dv| <= R,
+// whose pixels all lie inside the deformed image. Integer gray levels are summed
+// exactly in 64-bit integers and normalised once in FP64:
+//     C = (N Sfg - Sf Sg) / sqrt((N Sff - Sf^2) (N Sgg - Sg^2)),
+// so ranking ties are decided on exact values. The best offset (larger C, then
+// smaller |du|+|dv|, then smaller dv, then smaller du) starts the seed's IC-GN
+// (Sec. 2.2 leaves the initial estimate to an FFT stage; a brute-force integer
+// search gives the same integer start for a seed).
+#include <math.h>
+
+#include "dic_internal.cuh"
+
+namespace dic {
+namespace {
+
+constexpr double kNoScore = -2.0;    // offset not usable (out of the image or flat)
+constexpr double kFlatRef = -3.0;    // the reference subset itself is flat
+
+__device__ __forceinline__ bool integer_gray(int dtype) { return dtype == DIC_U8 || dtype == DIC_U16; }
+
+// grid (2R+1, n_seeds): block y = seed, block x = dv + R; threads stride over du
+__global__ void __launch_bounds__(128) seed_scores_kernel(SeedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = blockIdx.y;
+  const int dv = static_cast<int>(blockIdx.x) - a.R;
+  const int S = a.S, r = (a.S - 1) / 2, N = S * S;
+  const int xc = a.seed_xy[2 * s], yc = a.seed_xy[2 * s + 1];
+  const int side = 2 * a.R + 1;
+  double* out = a.scores + static_cast<int64_t>(s) * side * side + (dv + a.R) * side;
+  const bool exact = integer_gray(a.ref.dtype) && integer_gray(a.def.dtype);
+
+  if (exact) {
+    int32_t* f = reinterpret_cast<int32_t*>(smem_raw);
+    for (int e = threadIdx.x; e < N; e += blockDim.x)
+      f[e] = static_cast<int32_t>(load_gray<float>(a.ref, xc - r + e % S, yc - r + e / S));
+    __syncthreads();
+    int64_t Sf = 0, Sff = 0;
+    for (int e = 0; e < N; ++e) {
+      Sf += f[e];
+      Sff += static_cast<int64_t>(f[e]) * f[e];
+    }
+    const int64_t Df = static_cast<int64_t>(N) * Sff - Sf * Sf;
+    for (int du = threadIdx.x - a.R; du <= a.R; du += blockDim.x) {
+      const int x0 = xc + du - r, y0 = yc + dv - r;
+      double score = kNoScore;
+      if (Df == 0) {
+        score = kFlatRef;
+      } else if (x0 >= 0 && y0 >= 0 && x0 + S <= a.W && y0 + S <= a.H) {
+        int64_t Sg = 0, Sgg = 0, Sfg = 0;
+        for (int yy = 0; yy < S; ++yy) {
+          for (int xx = 0; xx < S; ++xx) {
+            const int64_t g = static_cast<int64_t>(load_gray<float>(a.def, x0 + xx, y0 + yy));
+            Sg += g;
+            Sgg += g * g;
+            Sfg += g * f[yy * S + xx];
+          }
+        }
+        const int64_t Dg = static_cast<int64_t>(N) * Sgg - Sg * Sg;
+        if (Dg != 0) {
+          const int64_t num = static_cast<int64_t>(N) * Sfg - Sf * Sg;
+          score = static_cast<double>(num) /
+                  sqrt(static_cast<double>(Df) * static_cast<double>(Dg));
+        }
+      }
+      out[du + a.R] = score;
+    }
+  } else {
+    double* f = reinterpret_cast<double*>(smem_raw);
+    for (int e = threadIdx.x; e < N; e += blockDim.x)
+      f[e] = load_gray<double>(a.ref, xc - r + e % S, yc - r + e / S);
+    __syncthreads();
+    double Sf = 0.0, Sff = 0.0;
+    for (int e = 0; e < N; ++e) {
+      Sf += f[e];
+      Sff += f[e] * f[e];
+    }
+    const double Df = N * Sff - Sf * Sf;
+    for (int du = threadIdx.x - a.R; du <= a.R; du += blockDim.x) {
+      const int x0 = xc + du - r, y0 = yc + dv - r;
+      double score = kNoScore;
+      if (!(Df > 0.0)) {
+        score = kFlatRef;
+      } else if (x0 >= 0 && y0 >= 0 && x0 + S <= a.W && y0 + S <= a.H) {
+        double Sg = 0.0, Sgg = 0.0, Sfg = 0.0;
+        for (int yy = 0; yy < S; ++yy)
+          for (int xx = 0; xx < S; ++xx) {
+            const double g = load_gray<double>(a.def, x0 + xx, y0 + yy);
+            Sg += g;
+            Sgg += g * g;
+            Sfg += g * f[yy * S + xx];
+          }
+        const double Dg = N * Sgg - Sg * Sg;
+        if (Dg > 0.0) score = (N * Sfg - Sf * Sg) / sqrt(Df * Dg);
+      }
+      out[du + a.R] = score;
+    }
+  }
+}
+
+// one thread: seeds in the order given, duplicates and out-of-ROI seeds skipped
+__global__ void seed_commit_kernel(SeedCommitArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int side = 2 * a.R + 1;
+  int count = 0;
+  for (int s = 0; s < a.n_seeds; ++s) {
+    const int q = a.seed_q[s];
+    if (a.roi_ok && !a.roi_ok[q]) continue;
+    if (a.wave[q] >= 0) continue;
+    a.wave[q] = 0;
+    const double* sc = a.scores + static_cast<int64_t>(s) * side * side;
+    int best = -1;
+    double bc = 0.0;
+    int bkey = 0;
+    bool flat = false;
+    for (int e = 0; e < side * side; ++e) {
+      const double c = sc[e];
+      if (c == kFlatRef) flat = true;
+      if (c < -1.5) continue;
+      const int du = e % side - a.R, dv = e / side - a.R;
+      // larger C, then smaller |du|+|dv|, then smaller dv, then smaller du
+      const int key = ((abs(du) + abs(dv)) * (side + 1) + (dv + a.R)) * (side + 1) + (du + a.R);
+      if (best < 0 || c > bc || (c == bc && key < bkey)) {
+        best = e;
+        bc = c;
+        bkey = key;
+      }
+    }
+    if (best < 0) {
+      a.status[q] = flat ? DIC_PT_FLAT : DIC_PT_OUT_OF_BOUNDS;
+      continue;
+    }
+    double* p = a.p + static_cast<int64_t>(q) * a.nparams;
+    for (int c = 0; c < a.nparams; ++c) p[c] = 0.0;
+    p[0] = static_cast<double>(best % side - a.R);
+    p[1] = static_cast<double>(best / side - a.R);
+    a.frontier0[count++] = q;
+  }
+  a.counters[kCount + 0] = count;
+  a.counters[kCount + 1] = 0;
+  a.counters[kCount + 2] = 0;
+  a.counters[kWork + 0] = 0;
+  a.counters[kWork + 1] = 0;
+  a.counters[kWork + 2] = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_seed_scores(const SeedArgs& a, cudaStream_t s) {
+  const bool exact = (a.ref.dtype == DIC_U8 || a.ref.dtype == DIC_U16) &&
+                     (a.def.dtype == DIC_U8 || a.def.dtype == DIC_U16);
+  const size_t smem = static_cast<size_t>(a.S) * a.S * (exact ? sizeof(int32_t) : sizeof(double));
+  dim3 grid(2 * a.R + 1, a.n_seeds);
+  seed_scores_kernel<<<grid, 128, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_commit(const SeedCommitArgs& a, cudaStream_t s) {
+  seed_commit_kernel<<<1, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dic

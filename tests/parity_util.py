@@ -1,0 +1,79 @@
+"""Shared helpers of the GPU-versus-oracle parity tests."""
+import numpy as np
+
+import oracle
+from oracle import dic_oracle as O
+
+# per-point tolerances on accepted points: displacement (px) and the other parameters
+TOL_UV = 1e-3
+TOL_P = 1e-5
+# controls of the parity runs: the oracle converges tightly; the FP32 path stops at
+# 1e-4 (its rounding floor is ~1e-6), which leaves well under the tolerances above
+ORACLE_PARAMS = dict(conv_threshold=1e-8, max_iter=100)
+GPU_PARAMS = {"fp64": dict(conv_threshold=1e-8, max_iter=100),
+              "mixed": dict(conv_threshold=1e-4, max_iter=100)}
+
+
+def borderline(ora, W, H, S, zncc_min=0.70, max_iter=100):
+    """Points whose accept/reject decision may legitimately flip under rounding:
+    oracle ZNCC within 1e-4 of the cut-off, iteration count within 2 of the
+    maximum, or the warped subset within 1 px of the sampling bounds."""
+    n = len(ora["status"])
+    out = np.zeros(n, bool)
+    z = ora["zncc"]
+    out |= np.isfinite(z) & (np.abs(z - zncc_min) < 1e-4)
+    out |= ora["iters"] >= max_iter - 2
+    dx, dy = O.local_coordinates(S)
+    for q in range(n):
+        if ora["wave"][q] < 0:
+            continue
+        wx, wy = O.warp(ora["p"][q], dx, dy)
+        x = ora["x"][q] + wx
+        y = ora["y"][q] + wy
+        margin = min((x - 1).min(), (W - 2 - x).min(), (y - 1).min(), (H - 2 - y).min())
+        if abs(margin) < 1.0:
+            out[q] = True
+    return out
+
+
+def compare(gpu, ora, W, H, S, zncc_min=0.70, max_iter=100, tol_uv=TOL_UV, tol_p=TOL_P):
+    """Asserts parity; returns a dict of error statistics for the report."""
+    st_g = np.asarray(gpu["status"]).astype(np.int64)
+    st_o = np.asarray(ora["status"]).astype(np.int64)
+    bl = borderline(ora, W, H, S, zncc_min, max_iter)
+    # a borderline flip can change which points the front reaches; those downstream
+    # points are exempt only if every path to them passes a flipped point
+    flipped = bl & ((st_g == 0) != (st_o == 0))
+    assert flipped.sum() <= 2, "%d borderline points flipped acceptance" % flipped.sum()
+    exempt = bl.copy()
+    if flipped.any():
+        exempt |= _downstream(ora, gpu, flipped)
+    mism = (st_g != st_o) & ~exempt
+    assert not mism.any(), "status differs at %d non-borderline points, e.g. q=%s gpu=%s oracle=%s" % (
+        mism.sum(), np.flatnonzero(mism)[:5], st_g[mism][:5], st_o[mism][:5])
+    wave_mism = (np.asarray(gpu["wave"]) != np.asarray(ora["wave"])) & ~exempt
+    assert not wave_mism.any(), "wave index differs at %d points" % wave_mism.sum()
+    both = (st_g == 0) & (st_o == 0)
+    pg = np.asarray(gpu["p"])[both]
+    po = np.asarray(ora["p"])[both]
+    e_uv = np.abs(pg[:, :2] - po[:, :2]).max() if both.any() else 0.0
+    e_p = np.abs(pg[:, 2:] - po[:, 2:]).max() if both.any() and pg.shape[1] > 2 else 0.0
+    assert e_uv <= tol_uv, "max |du|,|dv| = %.3g px > %.3g" % (e_uv, tol_uv)
+    assert e_p <= tol_p, "max |dp_2..| = %.3g > %.3g" % (e_p, tol_p)
+    zg = np.asarray(gpu["zncc"], dtype=np.float64)[both]
+    zo = ora["zncc"][both]
+    return dict(points=len(st_o), accepted=int(both.sum()), borderline=int(bl.sum()),
+                max_uv=float(e_uv), mean_uv=float(np.abs(pg[:, :2] - po[:, :2]).mean()) if both.any() else 0.0,
+                max_p=float(e_p), max_zncc=float(np.abs(zg - zo).max()) if both.any() else 0.0)
+
+
+def _downstream(ora, gpu, flipped):
+    """Points that either side reached only after a flipped point."""
+    wo, wg = np.asarray(ora["wave"]), np.asarray(gpu["wave"])
+    k = min(wo[flipped].min(), wg[flipped].min()) if flipped.any() else 0
+    return (wo > k) | (wg > k)
+
+
+def oracle_point(refp, defp, xc, yc, S, shape, p_init, params):
+    """One subset through the oracle (from an initial guess the oracle chose)."""
+    return O.icgn(refp, defp, xc, yc, S, shape, p_init, params)

@@ -1,0 +1,83 @@
+"""The C-ABI library loads on a machine without a GPU and exports exactly the
+calls that include/dic.h declares; host-side argument checks answer before any
+CUDA call. No compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2601_12941_gb300 import binding, build
+
+    build.build()
+    return binding.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "dic.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"\b(dic_[a-z_]+)\s*\(", text))
+
+
+def test_header_and_binding_agree():
+    from paper_2601_12941_gb300 import binding
+
+    assert _declared() == set(binding.EXPORTS)
+
+
+def test_library_exports_every_declared_call(lib):
+    so = os.path.join(ROOT, "paper_2601_12941_gb300", "libdic.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (dic_\w+)", out))
+    assert _declared() <= exported
+    for name in _declared():
+        assert hasattr(lib, name)
+
+
+def test_default_params_are_the_papers(lib):
+    from paper_2601_12941_gb300 import binding
+
+    p = binding.dic_default_params()
+    assert (p.max_iter, p.conv_threshold, p.zncc_min) == (40, 0.01, 0.70)
+    assert p.precision == binding.DIC_MIXED and p.nan_unconverged == 0
+
+
+def test_invalid_arguments_fail_before_any_device_work(lib):
+    from paper_2601_12941_gb300 import binding as B
+
+    img = np.zeros((64, 64), np.uint8)
+    ri, _ = B.make_image(img)
+    h = ctypes.c_void_p()
+    # even subset size, zero step, unknown shape, mismatched sizes, NULL image
+    assert lib.dic_create(ctypes.byref(ri), ctypes.byref(ri), None, 20, 5, 1, 0, ctypes.byref(h)) == B.DIC_EINVAL
+    assert b"odd" in lib.dic_last_error()
+    assert lib.dic_create(ctypes.byref(ri), ctypes.byref(ri), None, 21, 0, 1, 0, ctypes.byref(h)) == B.DIC_EINVAL
+    assert lib.dic_create(ctypes.byref(ri), ctypes.byref(ri), None, 21, 5, 7, 0, ctypes.byref(h)) == B.DIC_EINVAL
+    small, _ = B.make_image(np.zeros((32, 40), np.uint8))
+    assert lib.dic_create(ctypes.byref(ri), ctypes.byref(small), None, 21, 5, 1, 0, ctypes.byref(h)) == B.DIC_EINVAL
+    assert lib.dic_create(None, ctypes.byref(ri), None, 21, 5, 1, 0, ctypes.byref(h)) == B.DIC_EINVAL
+    assert lib.dic_create(ctypes.byref(ri), ctypes.byref(ri), None, 63, 5, 1, 0, ctypes.byref(h)) == B.DIC_EINVAL
+    assert h.value is None
+    # parameter validation on a NULL handle
+    p = B.dic_default_params()
+    assert lib.dic_set_params(None, ctypes.byref(p)) == B.DIC_EINVAL
+    assert lib.dic_correlate(None, None, 0, None) == B.DIC_EINVAL
+
+
+def test_loading_fails_loudly_without_the_library(tmp_path):
+    from paper_2601_12941_gb300 import binding
+
+    with pytest.raises(ImportError):
+        binding._lib_saved = binding._lib
+        try:
+            binding._lib = None
+            binding.load(str(tmp_path / "missing.so"))
+        finally:
+            binding._lib = binding._lib_saved
