@@ -1,6 +1,8 @@
 // C-ABI of libdic (declared in include/dic.h): handle life cycle, argument
 // checks, device buffers, the wave loop and result export. Every computation of
 // the method runs in the kernels of prefilter.cu, seed.cu and correlate.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -89,6 +91,11 @@ struct dic_handle {
   bool ref_dirty = true, def_dirty = true;
   // ROI flags per point (NULL: all in)
   uint8_t* roi_ok = nullptr;
+  // TMA descriptors of the reference coefficients, deformed coefficients and
+  // reference gray plane (valid when the matching flag is set)
+  CUtensorMap maps[3];
+  int maps_ok[3] = {0, 0, 0};
+  int maps_prec = -1;
   // spline coefficient planes in the working precision
   void* c_ref = nullptr;
   void* c_def = nullptr;
@@ -101,7 +108,7 @@ struct dic_handle {
   double* v = nullptr;
   double* p = nullptr;
   float* zncc = nullptr;
-  double* zncc64 = nullptr;
+  int64_t* accept = nullptr;
   int32_t* iters = nullptr;
   int32_t* wave = nullptr;
   uint8_t* conv = nullptr;
@@ -131,7 +138,47 @@ struct dic_handle {
 namespace {
 
 constexpr int kBatchSlots = 2;
-constexpr int kAccepted = 6;  // counters slot holding the accepted-point count
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2-D tiled tensor map of a row-major plane; false when the driver call is
+// unavailable or the plane breaks a TMA rule (16-byte aligned base and pitch).
+bool encode_plane(CUtensorMap* map, CUtensorMapDataType type, const void* base, int W, int H,
+                  int64_t pitch_bytes, int box_w, int box_h) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !base) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (pitch_bytes & 15) != 0) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch_bytes)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h)};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, type, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+CUtensorMapDataType gray_map_type(int dtype) {
+  switch (dtype) {
+    case DIC_U8: return CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    case DIC_U16: return CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    case DIC_BF16: return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    case DIC_F32: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    default: return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  }
+}
 
 int check_image(const dic_image* im, const char* name) {
   if (!im) return fail(DIC_EINVAL, "%s image is NULL", name);
@@ -155,15 +202,16 @@ int bind_image(const dic_image* im, GrayPlane* plane, void** owned, int* dtype_o
     plane->data = im->data;
     plane->stride = stride;
   } else {
+    // owned copies get a 128-byte row pitch so that tiles can be loaded by TMA
+    const size_t pitch = (row_bytes + 127) & ~static_cast<size_t>(127);
     if (!*owned) {
-      int rc = dev_alloc(reinterpret_cast<uint8_t**>(owned), row_bytes * im->height, "image buffer");
+      int rc = dev_alloc(reinterpret_cast<uint8_t**>(owned), pitch * im->height, "image buffer");
       if (rc) return rc;
     }
-    DIC_CUDA(cudaMemcpy2D(*owned, row_bytes, im->data, stride, row_bytes, im->height,
-                          cudaMemcpyHostToDevice),
+    DIC_CUDA(cudaMemcpy2D(*owned, pitch, im->data, stride, row_bytes, im->height, cudaMemcpyHostToDevice),
              "image upload");
     plane->data = *owned;
-    plane->stride = static_cast<int64_t>(row_bytes);
+    plane->stride = static_cast<int64_t>(pitch);
   }
   plane->dtype = im->dtype;
   *dtype_out = im->dtype;
@@ -226,7 +274,7 @@ PointArrays point_arrays(dic_handle* h) {
   pa.v = h->v;
   pa.p = h->p;
   pa.zncc = h->zncc;
-  pa.zncc64 = h->zncc64;
+  pa.accept = h->accept;
   pa.iters = h->iters;
   pa.converged = h->conv;
   pa.status = h->status;
@@ -237,7 +285,7 @@ PointArrays point_arrays(dic_handle* h) {
 void choose_bands(int S, int* bands, int* band_h) {
   for (int hgt = 1; hgt <= S; ++hgt) {
     const int b = (S + hgt - 1) / hgt;
-    if (S * b <= kThreads) {
+    if (S * b <= kWaveThreads) {
       *bands = b;
       *band_h = hgt;
       return;
@@ -262,8 +310,17 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   a.nx = h->nx;
   a.ny = h->ny;
   choose_bands(h->S, &a.bands, &a.band_h);
-  const int side = h->S + 12;
-  a.win_cap = side * side;
+  a.tiles = wave_tiles<T>(h->S, h->ref.dtype);
+  {
+    const CUtensorMapDataType ct = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const int64_t cp = h->ldc * static_cast<int64_t>(sizeof(T));
+    h->maps_ok[0] = encode_plane(&h->maps[0], ct, h->c_ref, h->W, h->H, cp, a.tiles.bxc, a.tiles.byc);
+    h->maps_ok[1] = encode_plane(&h->maps[1], ct, h->c_def, h->W, h->H, cp, a.tiles.bxc, a.tiles.byc);
+    h->maps_ok[2] = encode_plane(&h->maps[2], gray_map_type(h->ref.dtype), h->ref.data, h->W, h->H,
+                                 h->ref.stride, a.tiles.bxg, h->S);
+    a.tiles.coef_tma = h->maps_ok[0] && h->maps_ok[1];
+    a.tiles.gray_tma = h->maps_ok[2];
+  }
   a.pts = point_arrays(h);
   a.roi_ok = h->roi_ok;
   a.counters = h->counters;
@@ -274,7 +331,7 @@ int run_waves(dic_handle* h, cudaStream_t s) {
 
   int sms = 0;
   DIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "device query");
-  const size_t smem = wave_smem_bytes<T>(h->S, a.win_cap);
+  const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
   const int per_sm = wave_blocks_per_sm<T>(h->nparams, smem);
   const int grid = sms * per_sm;
 
@@ -301,10 +358,10 @@ int run_waves(dic_handle* h, cudaStream_t s) {
         cudaEvent_t e0 = pool_event(h->wave_events, 2 * k), e1 = pool_event(h->wave_events, 2 * k + 1);
         if (!e0 || !e1) return fail(DIC_ECUDA, "event creation failed");
         cudaEventRecord(e0, s);
-        DIC_CUDA(launch_wave<T>(a, h->nparams, grid, s), "wave launch");
+        DIC_CUDA(launch_wave<T>(a, a.tiles, h->maps, h->nparams, grid, s), "wave launch");
         cudaEventRecord(e1, s);
       } else {
-        DIC_CUDA(launch_wave<T>(a, h->nparams, grid, s), "wave launch");
+        DIC_CUDA(launch_wave<T>(a, a.tiles, h->maps, h->nparams, grid, s), "wave launch");
       }
     }
     launched += batch;
@@ -356,7 +413,7 @@ int alloc_points(dic_handle* h) {
   if ((rc = dev_alloc(&h->v, n, "points"))) return rc;
   if ((rc = dev_alloc(&h->p, n * h->nparams, "points"))) return rc;
   if ((rc = dev_alloc(&h->zncc, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->zncc64, n, "points"))) return rc;
+  if ((rc = dev_alloc(&h->accept, n, "points"))) return rc;
   if ((rc = dev_alloc(&h->iters, n, "points"))) return rc;
   if ((rc = dev_alloc(&h->wave, n, "points"))) return rc;
   if ((rc = dev_alloc(&h->conv, n, "points"))) return rc;
@@ -385,7 +442,7 @@ void release(dic_handle* h) {
   dev_free(h->def_owned);
   dev_free(h->roi_ok);
   void* ptrs[] = {h->x,     h->y,        h->u,    h->v,      h->p,          h->zncc,
-                  h->zncc64, h->iters,   h->wave, h->conv,   h->status,     h->front[0],
+                  h->accept, h->iters,   h->wave, h->conv,   h->status,     h->front[0],
                   h->front[1], h->counters, h->wave_sizes, h->seed_xy, h->seed_q, h->seed_scores};
   for (void* q : ptrs) dev_free(q);
   if (h->h_counters) cudaFreeHost(h->h_counters);
@@ -621,6 +678,7 @@ int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void*
   DIC_CUDA(cudaStreamSynchronize(s), "correlate");
   const int64_t accepted = h->h_counters[kAccepted];
   h->n_accepted = accepted;
+  if (h->h_counters[kError]) return fail(DIC_ETIMEOUT, "a tile load did not complete in time");
   if (prof) {
     h->timing.prefilter_ms = elapsed(h->events[0], h->events[1]);
     h->timing.setup_ms = elapsed(h->events[1], h->events[3]);

@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include "dic_internal.cuh"
+#include "tma.cuh"
 
 namespace dic {
 namespace {
@@ -53,50 +54,6 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-template <typename T>
-__device__ __forceinline__ int floor_int(T x);
-template <>
-__device__ __forceinline__ int floor_int<float>(float x) { return __float2int_rd(x); }
-template <>
-__device__ __forceinline__ int floor_int<double>(double x) { return __double2int_rd(x); }
-
-// Cholesky of the SPD n x n matrix in A (row-major), L written to L.
-// Returns false when a pivot is <= 1e-12 * max diagonal.
-template <int N>
-__device__ bool cholesky(const double* A, double* L) {
-  double dmax = 0.0;
-  for (int k = 0; k < N; ++k) dmax = fmax(dmax, fabs(A[k * N + k]));
-  const double tol = 1e-12 * dmax;
-  for (int k = 0; k < N; ++k) {
-    double d = A[k * N + k];
-    for (int m = 0; m < k; ++m) d -= L[k * N + m] * L[k * N + m];
-    if (!(d > tol)) return false;
-    const double lkk = sqrt(d);
-    L[k * N + k] = lkk;
-    for (int i = k + 1; i < N; ++i) {
-      double s = A[i * N + k];
-      for (int m = 0; m < k; ++m) s -= L[i * N + m] * L[k * N + m];
-      L[i * N + k] = s / lkk;
-    }
-  }
-  return true;
-}
-
-template <int N>
-__device__ void cholesky_solve(const double* L, const double* b, double* x) {
-  double y[N];
-  for (int i = 0; i < N; ++i) {
-    double s = b[i];
-    for (int m = 0; m < i; ++m) s -= L[i * N + m] * y[m];
-    y[i] = s / L[i * N + i];
-  }
-  for (int i = N - 1; i >= 0; --i) {
-    double s = y[i];
-    for (int m = i + 1; m < N; ++m) s -= L[m * N + i] * x[m];
-    x[i] = s / L[i * N + i];
-  }
 }
 
 // Solves A^T Z^T = R^T for two right-hand rows (6 x 6, partial pivoting), i.e. Z = R A^-1.
@@ -172,46 +129,62 @@ __device__ void quad_monomial_matrix(const double* p, double (&A)[6][6]) {
   A[5][0] = 0.0; A[5][1] = 0.0; A[5][2] = 0.0; A[5][3] = 0.0; A[5][4] = 0.0; A[5][5] = 1.0;
 }
 
-// p <- W(W^-1(.; dp); p). Rigid and affine are exact; quadratic takes the x' and
-// y' rows of A(p) A(dp)^-1 (second-order monomial representation of the warps).
-template <int NP>
-__device__ void compose_inverse(double* p, const double* dp) {
+// p <- W(W^-1(.; dp); p) for the quadratic warp: the x' and y' rows of
+// A(p) A(dp)^-1 (second-order monomial representation of the two warps).
+__device__ __noinline__ void compose_quadratic(double* p, const double* dp) {
+  double Ap[6][6], Ad[6][6];
+  quad_monomial_matrix(p, Ap);
+  quad_monomial_matrix(dp, Ad);
+  double R[2][6];
+  for (int j = 0; j < 6; ++j) {
+    R[0][j] = Ap[3][j];
+    R[1][j] = Ap[4][j];
+  }
+  rows_times_inverse6(Ad, R);
+  p[6] = R[0][0]; p[7] = R[0][1]; p[8] = R[0][2]; p[2] = R[0][3] - 1.0; p[3] = R[0][4]; p[0] = R[0][5];
+  p[9] = R[1][0]; p[10] = R[1][1]; p[11] = R[1][2]; p[4] = R[1][3]; p[5] = R[1][4] - 1.0; p[1] = R[1][5];
+}
+
+// p <- W(W^-1(.; dp); p) in the working precision C. Rigid: p - dp. Affine, exact:
+// with A = I + [[p2, p3], [p4, p5]], F = [[dp2, dp3], [dp4, dp5]] and
+// E = (I + F)^-1 - I = -(I + F)^-1 F, the new linear part is A + A E and the new
+// translation t - (A + A E) dt; only the small increments A E and -(A + A E) dt
+// are formed, so p keeps the full precision of C. Quadratic: compose_quadratic.
+template <typename C, int NP>
+__device__ void compose_inverse(C* p, const C* dp) {
   if (NP == 2) {
     p[0] -= dp[0];
     p[1] -= dp[1];
   } else if (NP == 6) {
-    const double a = 1.0 + dp[2], b = dp[3], c = dp[4], d = 1.0 + dp[5];
-    const double det = a * d - b * c;
-    const double ia = d / det, ib = -b / det, ic = -c / det, id = a / det;
-    const double it0 = -(ia * dp[0] + ib * dp[1]), it1 = -(ic * dp[0] + id * dp[1]);
-    const double A = 1.0 + p[2], B = p[3], C = p[4], Dd = 1.0 + p[5];
-    const double n00 = A * ia + B * ic, n01 = A * ib + B * id;
-    const double n10 = C * ia + Dd * ic, n11 = C * ib + Dd * id;
-    const double t0 = A * it0 + B * it1 + p[0], t1 = C * it0 + Dd * it1 + p[1];
-    p[0] = t0;
-    p[1] = t1;
-    p[2] = n00 - 1.0;
-    p[3] = n01;
-    p[4] = n10;
-    p[5] = n11 - 1.0;
+    const C d2 = dp[2], d3 = dp[3], d4 = dp[4], d5 = dp[5];
+    const C det = (C(1) + d2) * (C(1) + d5) - d3 * d4;
+    const C i00 = (C(1) + d5) / det, i01 = -d3 / det, i10 = -d4 / det, i11 = (C(1) + d2) / det;
+    const C e00 = -(i00 * d2 + i01 * d4), e01 = -(i00 * d3 + i01 * d5);
+    const C e10 = -(i10 * d2 + i11 * d4), e11 = -(i10 * d3 + i11 * d5);
+    const C a00 = C(1) + p[2], a01 = p[3], a10 = p[4], a11 = C(1) + p[5];
+    const C g00 = a00 * e00 + a01 * e10, g01 = a00 * e01 + a01 * e11;
+    const C g10 = a10 * e00 + a11 * e10, g11 = a10 * e01 + a11 * e11;
+    const C n00 = a00 + g00, n01 = a01 + g01, n10 = a10 + g10, n11 = a11 + g11;
+    p[0] -= n00 * dp[0] + n01 * dp[1];
+    p[1] -= n10 * dp[0] + n11 * dp[1];
+    p[2] += g00;
+    p[3] += g01;
+    p[4] += g10;
+    p[5] += g11;
   } else {
-    double Ap[6][6], Ad[6][6];
-    quad_monomial_matrix(p, Ap);
-    quad_monomial_matrix(dp, Ad);
-    double R[2][6];
-    for (int j = 0; j < 6; ++j) {
-      R[0][j] = Ap[3][j];
-      R[1][j] = Ap[4][j];
+    double pd[kMaxParams], dd[kMaxParams];
+    for (int c = 0; c < 12; ++c) {
+      pd[c] = static_cast<double>(p[c]);
+      dd[c] = static_cast<double>(dp[c]);
     }
-    rows_times_inverse6(Ad, R);
-    p[6] = R[0][0]; p[7] = R[0][1]; p[8] = R[0][2]; p[2] = R[0][3] - 1.0; p[3] = R[0][4]; p[0] = R[0][5];
-    p[9] = R[1][0]; p[10] = R[1][1]; p[11] = R[1][2]; p[4] = R[1][3]; p[5] = R[1][4] - 1.0; p[1] = R[1][5];
+    compose_quadratic(pd, dd);
+    for (int c = 0; c < 12; ++c) p[c] = static_cast<C>(pd[c]);
   }
 }
 
 // neighbour warp re-expanded about a centre offset (ddx, ddy) from it
-template <int NP>
-__device__ void transfer_warp(const double* pn, double ddx, double ddy, double* p) {
+template <typename C, int NP>
+__device__ void transfer_warp(const C* pn, C ddx, C ddy, C* p) {
   for (int c = 0; c < NP; ++c) p[c] = pn[c];
   if (NP >= 6) {
     p[0] = pn[0] + pn[2] * ddx + pn[3] * ddy;
@@ -220,57 +193,406 @@ __device__ void transfer_warp(const double* pn, double ddx, double ddy, double* 
   if (NP >= 12) {
     p[0] += pn[6] * ddx * ddx + pn[7] * ddx * ddy + pn[8] * ddy * ddy;
     p[1] += pn[9] * ddx * ddx + pn[10] * ddx * ddy + pn[11] * ddy * ddy;
-    p[2] = pn[2] + 2.0 * pn[6] * ddx + pn[7] * ddy;
-    p[3] = pn[3] + pn[7] * ddx + 2.0 * pn[8] * ddy;
-    p[4] = pn[4] + 2.0 * pn[9] * ddx + pn[10] * ddy;
-    p[5] = pn[5] + pn[10] * ddx + 2.0 * pn[11] * ddy;
+    p[2] = pn[2] + C(2) * pn[6] * ddx + pn[7] * ddy;
+    p[3] = pn[3] + pn[7] * ddx + C(2) * pn[8] * ddy;
+    p[4] = pn[4] + C(2) * pn[9] * ddx + pn[10] * ddy;
+    p[5] = pn[5] + pn[10] * ddx + C(2) * pn[11] * ddy;
   }
 }
 
-template <int NP>
-__device__ double update_norm(const double* dp, double r) {
-  double s = dp[0] * dp[0] + dp[1] * dp[1];
-  if (NP >= 6) s += r * r * (dp[2] * dp[2] + dp[3] * dp[3] + dp[4] * dp[4] + dp[5] * dp[5]);
-  if (NP >= 12) {
-    double q = 0.0;
-    for (int c = 6; c < 12; ++c) q += dp[c] * dp[c];
-    s += r * r * r * r * q;
-  }
-  return sqrt(s);
+template <typename C>
+__device__ __forceinline__ bool is_flat(C delta, C mean, int count) {
+  return delta / sqrt(static_cast<C>(count)) <= C(1e-6) * fmax(fabs(mean), C(1));
 }
 
-__device__ __forceinline__ bool is_flat(double delta, double mean, int count) {
-  return delta / sqrt(static_cast<double>(count)) <= 1e-6 * fmax(fabs(mean), 1.0);
+// Gray level at subset column c, row r of a staged gray tile (row pitch in bytes).
+template <typename T>
+__device__ __forceinline__ T tile_gray(const unsigned char* tile, int pitch, int dtype, int c, int r) {
+  const unsigned char* row = tile + r * pitch;
+  switch (dtype) {
+    case DIC_U8:
+      return static_cast<T>(row[c]);
+    case DIC_U16:
+      return static_cast<T>(reinterpret_cast<const uint16_t*>(row)[c]);
+    case DIC_BF16:
+      return static_cast<T>(__uint_as_float(static_cast<uint32_t>(reinterpret_cast<const uint16_t*>(row)[c]) << 16));
+    case DIC_F32:
+      return static_cast<T>(reinterpret_cast<const float*>(row)[c]);
+    default:
+      return static_cast<T>(reinterpret_cast<const double*>(row)[c]);
+  }
 }
 
 struct Window {
-  int x0, y0, w, h;
+  int x0, y0, w, h;   // origin in the image, row pitch and rows in shared memory
 };
 
+// Per-block state of the point being correlated; C is the working precision
+// (float on the mixed path, double on the FP64 path).
+template <typename C, int NP>
+struct PointState {
+  double H[NP * NP];        // Gauss-Newton Hessian (FP64)
+  double X[NP * NP];        // its inverse as computed in C (FP64 copy)
+  double bvec[NP];          // right-hand side of the FP64 solve, then its residual
+  double dvec[NP];          // first FP64 solution
+  C p[kMaxParams];          // current warp
+  C dp[kMaxParams];         // last update
+  C sdf[NP];                // sum SD (f - f_m)
+  C sds[NP];                // sum SD
+  C mu;                     // mean of f' = f - f0 (f0: reference gray level at the centre)
+  C delta_f;                // ||f - f_m||
+  C f0;
+  double zncc;
+  int q, item, ctl, iters, status, converged, stage;
+  Window win, next;
+};
+
+// Warp-parallel Gauss-Jordan inverse of the SPD matrix H (row-major, N x N) in the
+// precision V: lane j < N carries column j of H, lane N + j column j of the
+// identity. No row exchanges: the pivots of an SPD matrix are positive and equal
+// the LDL^T pivots. Returns the smallest pivot divided by the largest diagonal
+// entry (<= 0 when a pivot is not positive); X receives the inverse.
+template <typename V, int N>
+__device__ double invert_spd_warp(const double* H, double* X, int lane) {
+  V col[N];
+  const bool mine = lane < 2 * N;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    col[i] = !mine ? V(0) : (lane < N ? static_cast<V>(H[i * N + lane]) : (i == lane - N ? V(1) : V(0)));
+  double dmax = 0.0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) dmax = fmax(dmax, fabs(H[k * N + k]));
+  V pmin = V(1e30);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const V piv = __shfl_sync(0xffffffffu, col[k], k);
+    pmin = piv < pmin ? piv : pmin;
+    if (!(piv > V(0))) return 0.0;
+    col[k] = col[k] / piv;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (i == k) continue;
+      const V f = __shfl_sync(0xffffffffu, col[i], k);
+      col[i] -= f * col[k];
+    }
+  }
+  if (mine && lane >= N) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) X[i * N + (lane - N)] = static_cast<double>(col[i]);
+  }
+  return dmax > 0.0 ? static_cast<double>(pmin) / dmax : 0.0;
+}
+
+// Coefficients under the warped subset: [x0, x1] x [y0, y1] holds the 4 x 4 support of
+// every sample, from a bound on the warped offsets (0.05 px slack covers the
+// evaluation of the positions), clamped to the image. False for a non-finite or
+// absurd warp, or when nothing of the support lies in the image.
+template <typename C, int NP>
+__device__ bool needed_range(const C* p, int xc, int yc, int r, int W, int H, int* x0, int* x1, int* y0,
+                             int* y1) {
+  float ex, ey;
+  const float rf = static_cast<float>(r);
+  const float q0 = static_cast<float>(p[0]), q1 = static_cast<float>(p[1]);
+  if (NP >= 6) {
+    ex = rf * (fabsf(1.0f + static_cast<float>(p[2])) + fabsf(static_cast<float>(p[3])));
+    ey = rf * (fabsf(static_cast<float>(p[4])) + fabsf(1.0f + static_cast<float>(p[5])));
+  } else {
+    ex = ey = rf;
+  }
+  if (NP >= 12) {
+    ex += rf * rf * (fabsf(static_cast<float>(p[6])) + fabsf(static_cast<float>(p[7])) +
+                     fabsf(static_cast<float>(p[8])));
+    ey += rf * rf * (fabsf(static_cast<float>(p[9])) + fabsf(static_cast<float>(p[10])) +
+                     fabsf(static_cast<float>(p[11])));
+  }
+  ex += 0.05f;
+  ey += 0.05f;
+  if (!(fabsf(q0) < 1e6f && fabsf(q1) < 1e6f && ex < 1e6f && ey < 1e6f)) return false;
+  *x0 = max(xc + static_cast<int>(floorf(q0 - ex)) - 1, 0);
+  *x1 = min(xc + static_cast<int>(floorf(q0 + ex)) + 2, W - 1);
+  *y0 = max(yc + static_cast<int>(floorf(q1 - ey)) - 1, 0);
+  *y1 = min(yc + static_cast<int>(floorf(q1 + ey)) + 2, H - 1);
+  return *x1 >= *x0 && *y1 >= *y0;
+}
+
+// Lane 0: the window for sampling at st.p. stage 0: the staged window holds it;
+// 1: load st.next by TMA (a bxc x byc box, x rounded down to the TMA alignment);
+// 3: copy st.next cooperatively (pitch = its width); 2: too large for shared
+// memory, samples read the global plane.
+template <typename C, int NP>
+__device__ void plan_window(PointState<C, NP>& st, int xc, int yc, int r, int W, int H,
+                            const WaveTiles& t, int xalign) {
+  int x0, x1, y0, y1;
+  if (!needed_range<C, NP>(st.p, xc, yc, r, W, H, &x0, &x1, &y0, &y1)) {
+    st.stage = 2;
+    return;
+  }
+  const Window& cw = st.win;
+  if (cw.w > 0 && x0 >= cw.x0 && y0 >= cw.y0 && x1 < cw.x0 + cw.w && y1 < cw.y0 + cw.h) {
+    st.stage = 0;
+    return;
+  }
+  const int nw = x1 - x0 + 1, nh = y1 - y0 + 1;
+  if (t.coef_tma && nw + xalign - 1 <= t.bxc && nh <= t.byc) {
+    // centre the needed range in the box so the next iterations reuse it
+    int bx = x0 - (t.bxc - nw - (xalign - 1)) / 2;
+    bx -= ((bx % xalign) + xalign) % xalign;
+    if (bx + t.bxc - 1 < x1) bx += xalign;
+    const int by = y0 - (t.byc - nh) / 2;
+    st.next = Window{bx, by, t.bxc, t.byc};
+    st.stage = 1;
+    return;
+  }
+  if (static_cast<int64_t>(nw) * nh <= static_cast<int64_t>(t.bxc) * t.byc) {
+    st.next = Window{x0, y0, nw, nh};
+    st.stage = 3;
+    return;
+  }
+  st.stage = 2;
+}
+
+// Warp 0 after the reference reduction: mean and contrast of f, the Hessian and
+// its inverse. out: [H moments (3 NMOM), sum SD f', sum SD, sum f', sum f'^2].
+// The inverse is formed in C; in FP32 a pivot below 1e-5 of the largest diagonal
+// entry (too ill-conditioned for FP32) switches to the FP64 inverse. Sets st.ctl:
+// 0 ok, 3 flat, 4 singular (a pivot <= 1e-12 of the largest diagonal entry).
+template <typename C, int NP, int NMOM, int M2>
+__device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int lane) {
+  const C sf = out[3 * NMOM + 2 * NP];
+  const C sff = out[3 * NMOM + 2 * NP + 1];
+  const C mu = sf / static_cast<C>(N);
+  const C df = sqrt(fmax(sff - sf * mu, C(0)));
+  if (is_flat<C>(df, mu + st.f0, N)) {
+    if (lane == 0) st.ctl = 3;
+    return;
+  }
+  for (int e = lane; e < NP * NP; e += 32) {
+    const int ca = e / NP, cb = e % NP;
+    const int tt = sd_t(ca) + sd_t(cb);
+    st.H[e] = static_cast<double>(out[tt * NMOM + mono(sd_i(ca) + sd_i(cb), sd_j(ca) + sd_j(cb), M2)]);
+  }
+  __syncwarp();
+  double ratio = invert_spd_warp<C, NP>(st.H, st.X, lane);
+  if (sizeof(C) < sizeof(double) && ratio < 1e-5) ratio = invert_spd_warp<double, NP>(st.H, st.X, lane);
+  if (lane < NP) {
+    st.sds[lane] = out[3 * NMOM + NP + lane];
+    st.sdf[lane] = out[3 * NMOM + lane] - mu * out[3 * NMOM + NP + lane];   // sum SD (f' - mu)
+  }
+  if (lane == 0) {
+    st.mu = mu;
+    st.delta_f = df;
+    st.ctl = ratio > 1e-12 ? 0 : 4;
+  }
+  __syncwarp();
+}
+
+// Warp 0 after an iteration's reduction. out: [sum g', sum g'^2, sum SD g', bad].
+// b = sum SD (f - f_m) - (df/dg) sum SD (g - g_m), one component per lane. The
+// solve H dp = -b is done in FP64: dp0 = -X b, then one refinement step
+// dp = dp0 - X (b + H dp0) with X the inverse formed in C. Lane 0 composes
+// p <- p o dp^-1. Returns (on every lane) 0 continue, 1 converged, 2 flat,
+// 5 out of bounds.
+template <typename C, int NP>
+__device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C r, C thr2, int lane) {
+  if (out[2 + NP] > C(0.5)) return 5;
+  const C nu = out[0] / static_cast<C>(N);          // mean of g' = g - f0
+  const C dg = sqrt(fmax(out[1] - out[0] * nu, C(0)));
+  if (is_flat<C>(dg, nu + st.f0, N)) return 2;
+  const C ratio = st.delta_f / dg;
+  double bc = 0.0;
+  if (lane < NP) bc = static_cast<double>(st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]));
+  if (lane < NP) st.bvec[lane] = bc;
+  __syncwarp();
+  double d0 = 0.0;
+  if (lane < NP) {
+#pragma unroll
+    for (int m = 0; m < NP; ++m) d0 -= st.X[lane * NP + m] * st.bvec[m];
+    st.dvec[lane] = d0;
+  }
+  __syncwarp();
+  double res = bc;
+  if (lane < NP) {
+#pragma unroll
+    for (int m = 0; m < NP; ++m) res += st.H[lane * NP + m] * st.dvec[m];
+  }
+  __syncwarp();
+  if (lane < NP) st.bvec[lane] = res;
+  __syncwarp();
+  double dpc = d0;
+  if (lane < NP) {
+#pragma unroll
+    for (int m = 0; m < NP; ++m) dpc -= st.X[lane * NP + m] * st.bvec[m];
+  }
+  const C d = static_cast<C>(dpc);
+  if (lane < NP) st.dp[lane] = d;
+  // ||dp||^2 with weights 1, r^2, r^4 on the rigid, affine and quadratic terms
+  const C wgt = lane < 2 ? C(1) : (lane < 6 ? r * r : r * r * r * r);
+  C n2 = lane < NP ? wgt * d * d : C(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  __syncwarp();
+  if (lane == 0) compose_inverse<C, NP>(st.p, st.dp);
+  __syncwarp();
+  return n2 < thr2 ? 1 : 0;
+}
+
+// Sums over one thread's column of subset pixels at the warp given by
+// (ax, bx, cxq; ay, by, cyq): x = ax + dy (bx + cxq dy), y = ay + dy (by + cyq dy)
+// relative to the centre. The support of a sample at (ix + tx, iy + ty) starts at
+// base + iy * ld + ix (row iy - 1, column ix - 1 of the plane). Consecutive rows of
+// a column usually step one coefficient row down with the same ix, so the four
+// rows of the support stay in registers (rotated by the 4-way unrolled loop) and
+// only the new row is loaded; anything else reloads all four.
+// FINAL = false: acc = [sum g', sum g'^2, sum fx g' dy^j (j <= D), sum fy g' dy^j]
+// FINAL = true:  acc = [sum g', sum g'^2, sum f' g']
+template <typename T, int D, bool FINAL>
+__device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld, T ax, T bx, T cxq,
+                                              T ay, T by, T cyq, T xlo, T xhi, T ylo, T yhi, T f0,
+                                              int row0, int row1, int r, int S, int col,
+                                              const unsigned char* gtile, int gpitch, int gdtype,
+                                              const T* s_fx, const T* s_fy, T* acc, T& bad) {
+  T c0[4], c1[4], c2[4], c3[4];
+  int pix_ix = -0x40000000, pix_iy = -0x40000000;
+  auto step = [&](T (&A)[4], T (&B)[4], T (&Cc)[4], T (&Dn)[4], int row) {
+    const T dyv = static_cast<T>(row - r);
+    const T xl = ax + dyv * (bx + cxq * dyv);
+    const T yl = ay + dyv * (by + cyq * dyv);
+    if (!(xl >= xlo && xl < xhi && yl >= ylo && yl < yhi)) {
+      bad += T(1);
+      pix_ix = -0x40000000;
+      return;
+    }
+    const T xf = floor(xl), yf = floor(yl);
+    const int ix = static_cast<int>(xf), iy = static_cast<int>(yf);
+    const T* b = base + (iy * ld + ix);
+    if (!(ix == pix_ix && iy == pix_iy + 1)) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        A[k] = b[k];
+        B[k] = b[ld + k];
+        Cc[k] = b[2 * ld + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Dn[k] = b[3 * ld + k];
+    pix_ix = ix;
+    pix_iy = iy;
+    T wx0, wx1, wx2, wx3, wy0, wy1, wy2, wy3;
+    bspline_weights6<T>(xl - xf, wx0, wx1, wx2, wx3);
+    bspline_weights6<T>(yl - yf, wy0, wy1, wy2, wy3);
+    const T r0 = wx0 * A[0] + wx1 * A[1] + wx2 * A[2] + wx3 * A[3];
+    const T r1 = wx0 * B[0] + wx1 * B[1] + wx2 * B[2] + wx3 * B[3];
+    const T r2 = wx0 * Cc[0] + wx1 * Cc[1] + wx2 * Cc[2] + wx3 * Cc[3];
+    const T r3 = wx0 * Dn[0] + wx1 * Dn[1] + wx2 * Dn[2] + wx3 * Dn[3];
+    const T gp = (wy0 * r0 + wy1 * r1 + wy2 * r2 + wy3 * r3) * (T(1) / T(36)) - f0;
+    acc[0] += gp;
+    acc[1] += gp * gp;
+    if (FINAL) {
+      acc[2] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
+    } else {
+      const int pix = row * S + col;
+      const T gxv = gp * s_fx[pix], gyv = gp * s_fy[pix];
+      T dyp = T(1);
+#pragma unroll
+      for (int j = 0; j <= D; ++j) {
+        acc[2 + j] += gxv * dyp;
+        acc[2 + D + 1 + j] += gyv * dyp;
+        dyp *= dyv;
+      }
+    }
+  };
+  for (int row = row0; row < row1; row += 4) {
+    step(c0, c1, c2, c3, row);
+    if (row + 1 < row1) step(c1, c2, c3, c0, row + 1);
+    if (row + 2 < row1) step(c2, c3, c0, c1, row + 2);
+    if (row + 3 < row1) step(c3, c0, c1, c2, row + 3);
+  }
+}
+
+// The rare path (window too large for shared memory): every sample reads its
+// 4 x 4 support from the global plane; a plain loop, light on registers.
+template <typename T, int D, bool FINAL>
+__device__ __forceinline__ void sample_column_global(const T* __restrict__ base, int64_t ld, T ax,
+                                                     T bx, T cxq, T ay, T by, T cyq, T xlo, T xhi,
+                                                     T ylo, T yhi, T f0, int row0, int row1, int r,
+                                                     int S, int col, const unsigned char* gtile,
+                                                     int gpitch, int gdtype, const T* s_fx,
+                                                     const T* s_fy, T* acc, T& bad) {
+  for (int row = row0; row < row1; ++row) {
+    const T dyv = static_cast<T>(row - r);
+    const T xl = ax + dyv * (bx + cxq * dyv);
+    const T yl = ay + dyv * (by + cyq * dyv);
+    if (!(xl >= xlo && xl < xhi && yl >= ylo && yl < yhi)) {
+      bad += T(1);
+      continue;
+    }
+    const T xf = floor(xl), yf = floor(yl);
+    const T* b = base + (static_cast<int64_t>(yf) * ld + static_cast<int64_t>(xf));
+    T wx0, wx1, wx2, wx3, wy0, wy1, wy2, wy3;
+    bspline_weights6<T>(xl - xf, wx0, wx1, wx2, wx3);
+    bspline_weights6<T>(yl - yf, wy0, wy1, wy2, wy3);
+    T g = T(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T* rj = b + j * ld;
+      const T wy = j == 0 ? wy0 : j == 1 ? wy1 : j == 2 ? wy2 : wy3;
+      g += wy * (wx0 * rj[0] + wx1 * rj[1] + wx2 * rj[2] + wx3 * rj[3]);
+    }
+    const T gp = g * (T(1) / T(36)) - f0;
+    acc[0] += gp;
+    acc[1] += gp * gp;
+    if (FINAL) {
+      acc[2] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
+    } else {
+      const int pix = row * S + col;
+      const T gxv = gp * s_fx[pix], gyv = gp * s_fy[pix];
+      T dyp = T(1);
+#pragma unroll
+      for (int j = 0; j <= D; ++j) {
+        acc[2 + j] += gxv * dyp;
+        acc[2 + D + 1 + j] += gyv * dyp;
+        dyp *= dyv;
+      }
+    }
+  }
+}
+
+// resident blocks per SM the register budget is sized for
+template <typename T>
+struct WaveOccupancy;
+template <>
+struct WaveOccupancy<float> { static constexpr int kBlocks = 7; };
+template <>
+struct WaveOccupancy<double> { static constexpr int kBlocks = 4; };
+
 template <typename T, int NP>
-__global__ void __launch_bounds__(kThreads, 2) wave_kernel(WaveArgs<T> a) {
+__global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
+    wave_kernel(WaveArgs<T> a, const __grid_constant__ CUtensorMap tm_cref,
+                const __grid_constant__ CUtensorMap tm_cdef, const __grid_constant__ CUtensorMap tm_gray) {
+  using C = T;  // working precision of the per-point control arithmetic
   constexpr int D = Shape<NP>::D;
   constexpr int M2 = 2 * D;
   constexpr int NMOM = (M2 + 1) * (M2 + 2) / 2;
-  constexpr int NV_PRE = 3 * NMOM + 2 * NP + 2;  // H moments, sum SD fbar, sum SD, sum fbar^2, sum fbar
-  constexpr int NV_IT = 2 + NP;                  // sum g', sum g'^2, sum SD g'
+  constexpr int NV_PRE = 3 * NMOM + 2 * NP + 2;  // H moments, sum SD f', sum SD, sum f', sum f'^2
+  constexpr int NV_IT = 3 + NP;                  // sum g', sum g'^2, sum SD g', bad samples
+  constexpr int NV_FIN = 4;                      // sum g', sum g'^2, sum f' g', bad samples
+  constexpr int NACC = 2 + 2 * (D + 1);
+  constexpr int XALIGN = 16 / static_cast<int>(sizeof(T));   // TMA x alignment of the coefficient planes
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const WaveTiles& tl = a.tiles;
   const int S = a.S, r = a.r, N = S * S;
-  const int SS = (N + 3) & ~3;
-  T* s_fbar = reinterpret_cast<T*>(smem_raw);
-  T* s_fx = s_fbar + SS;
-  T* s_fy = s_fx + SS;
-  T* s_win = s_fy + SS;
+  T* s_fx = reinterpret_cast<T*>(smem_raw + tl.off_fx);
+  T* s_fy = reinterpret_cast<T*>(smem_raw + tl.off_fy);
+  T* s_win = reinterpret_cast<T*>(smem_raw + tl.off_win);
+  unsigned char* s_gray = smem_raw + tl.off_gray;
+  const int gdt = a.ref_gray.dtype;
+  const int gpitch = tl.bxg * tl.gray_es;
 
-  __shared__ double s_red[kWarps * NV_PRE];
-  __shared__ double s_out[NV_PRE];
-  __shared__ double s_p[kMaxParams];
-  __shared__ double s_L[NP * NP];
-  __shared__ double s_sdf[NP], s_sds[NP];
-  __shared__ double s_fm, s_df, s_sumfbar;
-  __shared__ int s_item, s_ctl;
-  __shared__ Window s_win_box;
+  __shared__ T s_part[kWaveWarps][NV_PRE];
+  __shared__ C s_out[NV_PRE];
+  __shared__ PointState<C, NP> st;
+  __shared__ __align__(8) uint64_t s_bar;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int cur = a.k % 3, nxt = (a.k + 1) % 3, old = (a.k + 2) % 3;
@@ -280,8 +602,23 @@ __global__ void __launch_bounds__(kThreads, 2) wave_kernel(WaveArgs<T> a) {
     a.wave_sizes[a.k] = a.counters[kCount + cur];
   }
   const int n_front = a.counters[kCount + cur];
+  if (tid == 0) mbar_init(&s_bar, 1);
+  __syncthreads();
+  uint32_t bar_phase = 0;
+  // every thread waits for the pending TMA transaction; a lost wait ends the block
+  auto tma_wait = [&]() -> bool {
+    const bool ok = mbar_wait_bounded(&s_bar, bar_phase);
+    bar_phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(&a.counters[kError], 1);
+        mbar_wait_bounded(&s_bar, bar_phase ^ 1u);   // let a late copy land before leaving
+      }
+      return false;
+    }
+    return true;
+  };
 
-  // this thread's pixels
   const int col = tid % S;
   const int band = tid / S;
   const int row0 = band < a.bands ? band * a.band_h : S;
@@ -292,410 +629,371 @@ __global__ void __launch_bounds__(kThreads, 2) wave_kernel(WaveArgs<T> a) {
 #pragma unroll
   for (int i = 1; i <= M2; ++i) dxp[i] = dxp[i - 1] * dxv;
 
-  // block-wide sum of per-thread values, written to s_out[0..NV) in FP64
-  auto reduce_store = [&](int idx, int nv, T v) {
+  // warp partial of entry idx of a reduction vector
+  auto part = [&](int idx, T v) {
     v = warp_sum(v);
-    if (lane == 0) s_red[warp * nv + idx] = static_cast<double>(v);
+    if (lane == 0) s_part[warp][idx] = v;
   };
-  auto reduce_finish = [&](int nv) {
-    __syncthreads();
-    for (int i = tid; i < nv; i += kThreads) {
-      double s = 0.0;
-      for (int w = 0; w < kWarps; ++w) s += s_red[w * nv + i];
-      s_out[i] = s;
+  // warp 0: cross-warp sums into s_out[0..nv)
+  auto gather = [&](int nv) {
+    for (int i = lane; i < nv; i += 32) {
+      C sacc = C(0);
+#pragma unroll
+      for (int w = 0; w < kWaveWarps; ++w) sacc += s_part[w][i];
+      s_out[i] = sacc;
     }
-    __syncthreads();
+    __syncwarp();
   };
 
   for (;;) {
-    if (tid == 0) s_item = atomicAdd(&a.counters[kWork + cur], 1);
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= n_front) break;
-    const int q = a.cur[item];
-    const int gi = q % a.nx, gj = q / a.nx;
-    const int xc = r + gi * a.step, yc = r + gj * a.step;
-
-    // ---- 1. starting warp
-    if (tid == 0) {
-      double p[kMaxParams];
-      if (a.k == 0) {
-        for (int c = 0; c < NP; ++c) p[c] = a.pts.p[static_cast<int64_t>(q) * NP + c];
-      } else {
+    // ---- 1. next point and its starting warp (warp 0)
+    if (warp == 0) {
+      int item = 0;
+      if (lane == 0) item = atomicAdd(&a.counters[kWork + cur], 1);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (item < n_front) {
+        const int q = a.cur[item];
+        const int gi = q % a.nx, gj = q / a.nx;
         int best = -1;
-        double bz = 0.0;
-        int nbs[4] = {gi > 0 ? q - 1 : -1, gi < a.nx - 1 ? q + 1 : -1, gj > 0 ? q - a.nx : -1,
-                      gj < a.ny - 1 ? q + a.nx : -1};
-        for (int m = 0; m < 4; ++m) {
-          const int nb = nbs[m];
-          if (nb < 0) continue;
-          const int wv = a.pts.wave[nb];
-          if (wv < 0 || wv >= a.k || a.pts.status[nb] != DIC_PT_OK) continue;
-          const double z = a.pts.zncc64[nb];
-          if (best < 0 || z > bz || (z == bz && nb < best)) {
-            best = nb;
-            bz = z;
-          }
-        }
-        if (best >= 0) {
-          const int bi = best % a.nx, bj = best / a.nx;
-          transfer_warp<NP>(a.pts.p + static_cast<int64_t>(best) * NP,
-                            static_cast<double>((gi - bi) * a.step),
-                            static_cast<double>((gj - bj) * a.step), p);
+        if (a.k == 0) {
+          best = q;
         } else {
-          for (int c = 0; c < NP; ++c) p[c] = 0.0;
-        }
-      }
-      for (int c = 0; c < NP; ++c) s_p[c] = p[c];
-      s_win_box.w = 0;  // no window staged yet
-    }
-
-    // ---- 2. reference subset: gray levels and spline gradients
-    T sf = T(0);
-    for (int row = row0; row < row1; ++row) {
-      const int64_t x = xc + col - r, y = yc + row - r;
-      const int pix = row * S + col;
-      const T f = load_gray<T>(a.ref_gray, x, y);
-      s_fbar[pix] = f;
-      sf += f;
-      const int64_t xm = x > 0 ? x - 1 : 1, xp = x < a.W - 1 ? x + 1 : a.W - 2;
-      const int64_t ym = y > 0 ? y - 1 : 1, yp = y < a.H - 1 ? y + 1 : a.H - 2;
-      const T* cm = a.c_ref + ym * a.ldc;
-      const T* c0 = a.c_ref + y * a.ldc;
-      const T* cp = a.c_ref + yp * a.ldc;
-      // exact derivative of the reference spline at the pixel: (-1/2, 0, 1/2) (x) (1, 4, 1)/6
-      const T gxm = cm[xp] - cm[xm], gx0 = c0[xp] - c0[xm], gxp = cp[xp] - cp[xm];
-      const T gym = cp[xm] - cm[xm], gy0 = cp[x] - cm[x], gyp = cp[xp] - cm[xp];
-      s_fx[pix] = (gxm + T(4) * gx0 + gxp) * (T(1) / T(12));
-      s_fy[pix] = (gym + T(4) * gy0 + gyp) * (T(1) / T(12));
-    }
-    reduce_store(0, 1, sf);
-    reduce_finish(1);
-    if (tid == 0) s_fm = s_out[0] / N;
-    __syncthreads();
-    const double fm = s_fm;
-
-    T A[3][M2 + 1], Bf[2][D + 1], Bs[2][D + 1];
-    T sfb2 = T(0), sfb = T(0);
-#pragma unroll
-    for (int j = 0; j <= M2; ++j) A[0][j] = A[1][j] = A[2][j] = T(0);
-#pragma unroll
-    for (int j = 0; j <= D; ++j) Bf[0][j] = Bf[1][j] = Bs[0][j] = Bs[1][j] = T(0);
-    for (int row = row0; row < row1; ++row) {
-      const int pix = row * S + col;
-      const T fb = static_cast<T>(static_cast<double>(s_fbar[pix]) - fm);
-      s_fbar[pix] = fb;
-      const T fx = s_fx[pix], fy = s_fy[pix];
-      const T dyv = static_cast<T>(row - r);
-      T dyp[M2 + 1];
-      dyp[0] = T(1);
-#pragma unroll
-      for (int j = 1; j <= M2; ++j) dyp[j] = dyp[j - 1] * dyv;
-      const T wxx = fx * fx, wxy = fx * fy, wyy = fy * fy;
-#pragma unroll
-      for (int j = 0; j <= M2; ++j) {
-        A[0][j] += wxx * dyp[j];
-        A[1][j] += wxy * dyp[j];
-        A[2][j] += wyy * dyp[j];
-      }
-      const T fxb = fx * fb, fyb = fy * fb;
-#pragma unroll
-      for (int j = 0; j <= D; ++j) {
-        Bf[0][j] += fxb * dyp[j];
-        Bf[1][j] += fyb * dyp[j];
-        Bs[0][j] += fx * dyp[j];
-        Bs[1][j] += fy * dyp[j];
-      }
-      sfb2 += fb * fb;
-      sfb += fb;
-    }
-#pragma unroll
-    for (int tt = 0; tt < 3; ++tt)
-#pragma unroll
-      for (int j = 0; j <= M2; ++j)
-#pragma unroll
-        for (int i = 0; i + j <= M2; ++i) reduce_store(tt * NMOM + mono(i, j, M2), NV_PRE, dxp[i] * A[tt][j]);
-#pragma unroll
-    for (int c = 0; c < NP; ++c) {
-      reduce_store(3 * NMOM + c, NV_PRE, dxp[sd_i(c)] * Bf[sd_t(c)][sd_j(c)]);
-      reduce_store(3 * NMOM + NP + c, NV_PRE, dxp[sd_i(c)] * Bs[sd_t(c)][sd_j(c)]);
-    }
-    reduce_store(3 * NMOM + 2 * NP, NV_PRE, sfb2);
-    reduce_store(3 * NMOM + 2 * NP + 1, NV_PRE, sfb);
-    reduce_finish(NV_PRE);
-
-    if (tid == 0) {
-      int ctl = 0;
-      s_df = sqrt(fmax(s_out[3 * NMOM + 2 * NP], 0.0));
-      s_sumfbar = s_out[3 * NMOM + 2 * NP + 1];
-      if (is_flat(s_df, fm, N)) {
-        ctl = 3;
-      } else {
-        double Hm[NP * NP];
-        for (int ca = 0; ca < NP; ++ca)
-          for (int cb = 0; cb < NP; ++cb) {
-            const int tt = sd_t(ca) + sd_t(cb);
-            Hm[ca * NP + cb] = s_out[tt * NMOM + mono(sd_i(ca) + sd_i(cb), sd_j(ca) + sd_j(cb), M2)];
+          // the accepted neighbour from an earlier wave with the highest ZNCC
+          // (ties to the lower index); lanes 0-3 look at left, right, up, down
+          int nb = -1;
+          if (lane == 0 && gi > 0) nb = q - 1;
+          if (lane == 1 && gi < a.nx - 1) nb = q + 1;
+          if (lane == 2 && gj > 0) nb = q - a.nx;
+          if (lane == 3 && gj < a.ny - 1) nb = q + a.nx;
+          float z = -3.0f;
+          int cand = 0x7fffffff;
+          if (nb >= 0) {
+            const int64_t rec = a.pts.accept[nb];
+            if (rec >= 0 && static_cast<int>(rec >> 32) < a.k) {
+              z = __int_as_float(static_cast<int>(rec & 0xffffffffLL));
+              cand = nb;
+            }
           }
-        if (!cholesky<NP>(Hm, s_L)) ctl = 4;
-        for (int c = 0; c < NP; ++c) {
-          s_sdf[c] = s_out[3 * NMOM + c];
-          s_sds[c] = s_out[3 * NMOM + NP + c];
+#pragma unroll
+          for (int o = 1; o <= 2; o <<= 1) {
+            const float oz = __shfl_xor_sync(0xffffffffu, z, o);
+            const int oc = __shfl_xor_sync(0xffffffffu, cand, o);
+            if (oz > z || (oz == z && oc < cand)) {
+              z = oz;
+              cand = oc;
+            }
+          }
+          best = __shfl_sync(0xffffffffu, cand, 0);
+          if (best == 0x7fffffff) best = -1;
+        }
+        if (lane < NP)
+          st.dp[lane] = best >= 0 ? static_cast<C>(a.pts.p[static_cast<int64_t>(best) * NP + lane]) : C(0);
+        __syncwarp();
+        if (lane == 0) {
+          if (a.k > 0 && best >= 0)
+            transfer_warp<C, NP>(st.dp, static_cast<C>((gi - best % a.nx) * a.step),
+                                 static_cast<C>((gj - best / a.nx) * a.step), st.p);
+          else
+            for (int c = 0; c < NP; ++c) st.p[c] = st.dp[c];
+          st.q = q;
+          st.win.w = 0;
+          st.iters = 0;
+          st.converged = 0;
+          st.zncc = nan("");
+          st.status = DIC_PT_MAX_ITER;
         }
       }
-      s_ctl = ctl;
+      if (lane == 0) st.item = item;
     }
     __syncthreads();
+    if (st.item >= n_front) break;
+    const int q = st.q;
+    const int xc = r + (q % a.nx) * a.step, yc = r + (q / a.nx) * a.step;
 
-    // ---- 3. IC-GN iterations
-    int status = DIC_PT_MAX_ITER;
-    int iters = 0;
-    bool converged = false;
-    bool stopped = false;  // out of bounds or flat during the iterations
-    double zncc = nan("");
-    if (s_ctl == 3) {
-      status = DIC_PT_FLAT;
-      stopped = true;
-    } else if (s_ctl == 4) {
-      status = DIC_PT_SINGULAR;
-      stopped = true;
-    }
-    const T fmT = static_cast<T>(fm);
-    const T xlo = static_cast<T>(1 - xc), xhi = static_cast<T>(a.W - 2 - xc);
-    const T ylo = static_cast<T>(1 - yc), yhi = static_cast<T>(a.H - 2 - yc);
-
-    // Stage (if needed) the coefficients under the warped subset; returns whether
-    // the shared window is usable (else samples read the global plane).
-    auto stage_window = [&]() -> bool {
-      double p[kMaxParams];
-      for (int c = 0; c < NP; ++c) p[c] = s_p[c];
-      double ex = 0.0, ey = 0.0;
-      if (NP >= 6) {
-        ex = r * (fabs(1.0 + p[2]) + fabs(p[3]));
-        ey = r * (fabs(p[4]) + fabs(1.0 + p[5]));
+    // ---- 2. reference subset: its gray tile and the reference coefficients
+    //         around it, staged in shared memory (TMA where the planes allow)
+    const int rx0 = xc - r - 1, ry0 = yc - r - 1;                  // coefficient window origin
+    const int rxa = rx0 - (((rx0 % XALIGN) + XALIGN) % XALIGN);    // TMA-aligned column
+    const int gxa = (xc - r) - (((xc - r) * tl.gray_es) % 16) / tl.gray_es;   // gray tile column
+    {
+      if (tid == 0 && (tl.coef_tma || tl.gray_tma)) {
+        fence_proxy_async_shared();
+        uint32_t bytes = 0;
+        if (tl.coef_tma) bytes += static_cast<uint32_t>(tl.bxc * tl.byc * sizeof(T));
+        if (tl.gray_tma) bytes += static_cast<uint32_t>(tl.bxg * S * tl.gray_es);
+        mbar_arrive_expect_tx(&s_bar, bytes);
+        if (tl.coef_tma) tma_load_2d(s_win, &tm_cref, rxa, ry0, &s_bar);
+        if (tl.gray_tma) tma_load_2d(s_gray, &tm_gray, gxa, yc - r, &s_bar);
+      }
+      if (!tl.coef_tma) {
+        for (int row = warp; row < S + 2; row += kWaveWarps) {
+          const int gy = mirror_near(ry0 + row, a.H);
+          const T* src = a.c_ref + static_cast<int64_t>(gy) * a.ldc;
+          T* dst = s_win + row * tl.bxc + (rx0 - rxa);
+          for (int c = lane; c < S + 2; c += 32) dst[c] = src[mirror_near(rx0 + c, a.W)];
+        }
+      }
+      if (!tl.gray_tma) {
+        const int es = tl.gray_es;
+        for (int row = warp; row < S; row += kWaveWarps) {
+          const unsigned char* src = static_cast<const unsigned char*>(a.ref_gray.data) +
+                                     static_cast<int64_t>(yc - r + row) * a.ref_gray.stride +
+                                     static_cast<int64_t>(gxa) * es;
+          unsigned char* dst = s_gray + row * gpitch;
+          for (int c = lane; c < (S + (xc - r - gxa)) * es; c += 32) dst[c] = src[c];
+        }
+      }
+      if (tl.coef_tma || tl.gray_tma) {
+        if (!tma_wait()) return;
       } else {
-        ex = ey = r;
+        __syncthreads();
       }
-      if (NP >= 12) {
-        ex += static_cast<double>(r) * r * (fabs(p[6]) + fabs(p[7]) + fabs(p[8]));
-        ey += static_cast<double>(r) * r * (fabs(p[9]) + fabs(p[10]) + fabs(p[11]));
-      }
-      ex += 0.01;
-      ey += 0.01;
-      const double cx = xc + p[0], cy = yc + p[1];
-      if (!(fabs(p[0]) < 1e6 && fabs(p[1]) < 1e6 && ex < 1e6 && ey < 1e6)) return false;
-      int nx0 = static_cast<int>(floor(cx - ex)) - 1, nx1 = static_cast<int>(floor(cx + ex)) + 2;
-      int ny0 = static_cast<int>(floor(cy - ey)) - 1, ny1 = static_cast<int>(floor(cy + ey)) + 2;
-      nx0 = max(nx0, 0);
-      ny0 = max(ny0, 0);
-      nx1 = min(nx1, a.W - 1);
-      ny1 = min(ny1, a.H - 1);
-      if (nx1 < nx0 || ny1 < ny0) return false;  // wholly outside: every sample is out of bounds
-      const Window cw = s_win_box;
-      if (cw.w > 0 && nx0 >= cw.x0 && ny0 >= cw.y0 && nx1 < cw.x0 + cw.w && ny1 < cw.y0 + cw.h)
-        return true;
-      constexpr int kMargin = 2;
-      int wx0 = max(nx0 - kMargin, 0), wy0 = max(ny0 - kMargin, 0);
-      int wx1 = min(nx1 + kMargin, a.W - 1), wy1 = min(ny1 + kMargin, a.H - 1);
-      if (static_cast<int64_t>(wx1 - wx0 + 1) * (wy1 - wy0 + 1) > a.win_cap) {
-        wx0 = nx0;
-        wy0 = ny0;
-        wx1 = nx1;
-        wy1 = ny1;
-        if (static_cast<int64_t>(wx1 - wx0 + 1) * (wy1 - wy0 + 1) > a.win_cap) return false;
-      }
-      const int ww = wx1 - wx0 + 1, wh = wy1 - wy0 + 1;
-      __syncthreads();  // everyone has finished with the previous window
-      for (int row = warp; row < wh; row += kWarps) {
-        const T* src = a.c_def + static_cast<int64_t>(wy0 + row) * a.ldc + wx0;
-        T* dst = s_win + row * ww;
-        for (int c = lane; c < ww; c += 32) dst[c] = src[c];
-      }
-      if (tid == 0) s_win_box = Window{wx0, wy0, ww, wh};
-      __syncthreads();
-      return true;
-    };
-
-    // Sum over this thread's pixels at the current p. MODE 0: sum g', sum g'^2 and the
-    // SD moments; MODE 1: sum g', sum g'^2, sum fbar g'. Returns false if a sample is
-    // out of bounds.
-    auto sample_pass = [&](int mode, T* acc) -> bool {
-      const bool use_win = stage_window();
-      const Window w = s_win_box;
-      T p[kMaxParams];
-      for (int c = 0; c < NP; ++c) p[c] = static_cast<T>(s_p[c]);
-      // positions relative to the centre: x = ax + dy (bx + cxq dy), y = ay + dy (by + cyq dy)
-      T ax = p[0] + dxv, ay = p[1], bx = T(0), by = T(1), cxq = T(0), cyq = T(0);
-      if (NP >= 6) {
-        ax += p[2] * dxv;
-        ay += p[4] * dxv;
-        bx = p[3];
-        by = T(1) + p[5];
-      }
-      if (NP >= 12) {
-        ax += p[6] * dxv * dxv;
-        ay += p[9] * dxv * dxv;
-        bx += p[7] * dxv;
-        by += p[10] * dxv;
-        cxq = p[8];
-        cyq = p[11];
-      }
-      const int offx = xc - 1 - w.x0, offy = yc - 1 - w.y0;
-      bool bad = false;
-      for (int row = row0; row < row1; ++row) {
-        const T dyv = static_cast<T>(row - r);
-        const T xl = ax + dyv * (bx + cxq * dyv);
-        const T yl = ay + dyv * (by + cyq * dyv);
-        if (!(xl >= xlo && xl < xhi && yl >= ylo && yl < yhi)) {
-          bad = true;
-          continue;
-        }
-        const int ix = floor_int<T>(xl), iy = floor_int<T>(yl);
-        const T tx = xl - static_cast<T>(ix), ty = yl - static_cast<T>(iy);
-        T wx0, wx1, wx2, wx3, wy0, wy1, wy2, wy3;
-        bspline_weights<T>(tx, wx0, wx1, wx2, wx3);
-        bspline_weights<T>(ty, wy0, wy1, wy2, wy3);
-        const T* b;
-        int64_t ld;
-        if (use_win) {
-          b = s_win + (offy + iy) * w.w + (offx + ix);
-          ld = w.w;
-        } else {
-          b = a.c_def + static_cast<int64_t>(yc + iy - 1) * a.ldc + (xc + ix - 1);
-          ld = a.ldc;
-        }
-        const T r0 = wx0 * b[0] + wx1 * b[1] + wx2 * b[2] + wx3 * b[3];
-        const T* b1 = b + ld;
-        const T r1 = wx0 * b1[0] + wx1 * b1[1] + wx2 * b1[2] + wx3 * b1[3];
-        const T* b2 = b1 + ld;
-        const T r2 = wx0 * b2[0] + wx1 * b2[1] + wx2 * b2[2] + wx3 * b2[3];
-        const T* b3 = b2 + ld;
-        const T r3 = wx0 * b3[0] + wx1 * b3[1] + wx2 * b3[2] + wx3 * b3[3];
-        const T g = wy0 * r0 + wy1 * r1 + wy2 * r2 + wy3 * r3;
-        const T gp = g - fmT;
-        const int pix = row * S + col;
-        acc[0] += gp;
-        acc[1] += gp * gp;
-        if (mode == 0) {
-          const T gx = gp * s_fx[pix], gy = gp * s_fy[pix];
-          T dyp = T(1);
-#pragma unroll
-          for (int j = 0; j <= D; ++j) {
-            acc[2 + j] += gx * dyp;
-            acc[2 + D + 1 + j] += gy * dyp;
-            dyp *= dyv;
-          }
-        } else {
-          acc[2] += gp * s_fbar[pix];
-        }
-      }
-      return !__syncthreads_or(bad);
-    };
-
-    if (!stopped) {
-      for (int it = 0; it < a.max_iter; ++it) {
-        T acc[2 + 2 * (D + 1)];
-#pragma unroll
-        for (int e = 0; e < 2 + 2 * (D + 1); ++e) acc[e] = T(0);
-        if (!sample_pass(0, acc)) {
-          status = DIC_PT_OUT_OF_BOUNDS;
-          stopped = true;
-          break;
-        }
-        reduce_store(0, NV_IT, acc[0]);
-        reduce_store(1, NV_IT, acc[1]);
-#pragma unroll
-        for (int c = 0; c < NP; ++c)
-          reduce_store(2 + c, NV_IT, dxp[sd_i(c)] * acc[2 + sd_t(c) * (D + 1) + sd_j(c)]);
-        reduce_finish(NV_IT);
-        if (tid == 0) {
-          int ctl = 0;
-          const double gm = s_out[0] / N;  // mean of g - f_m
-          const double dg = sqrt(fmax(s_out[1] - N * gm * gm, 0.0));
-          if (is_flat(dg, gm + static_cast<double>(fmT), N)) {
-            ctl = 2;
-          } else {
-            const double ratio = s_df / dg;
-            double b[NP], x[NP], dp[NP];
-            for (int c = 0; c < NP; ++c) b[c] = s_sdf[c] - ratio * (s_out[2 + c] - gm * s_sds[c]);
-            cholesky_solve<NP>(s_L, b, x);
-            for (int c = 0; c < NP; ++c) dp[c] = -x[c];
-            double p[kMaxParams];
-            for (int c = 0; c < NP; ++c) p[c] = s_p[c];
-            compose_inverse<NP>(p, dp);
-            for (int c = 0; c < NP; ++c) s_p[c] = p[c];
-            if (update_norm<NP>(dp, static_cast<double>(r)) < a.conv_threshold) ctl = 1;
-          }
-          s_ctl = ctl;
+      // mirror the coefficient rows and columns that fall outside the image
+      if (tl.coef_tma && (rx0 < 0 || ry0 < 0 || rx0 + S + 2 > a.W || ry0 + S + 2 > a.H)) {
+        T* w0 = s_win + (rx0 - rxa);
+        for (int e = tid; e < S + 2; e += kWaveThreads) {
+          if (rx0 < 0) w0[e * tl.bxc + 0] = w0[e * tl.bxc + 2];
+          if (rx0 + S + 2 > a.W) w0[e * tl.bxc + S + 1] = w0[e * tl.bxc + S - 1];
         }
         __syncthreads();
-        const int ctl = s_ctl;
-        if (ctl == 2) {
-          status = DIC_PT_FLAT;
-          stopped = true;
-          break;
+        for (int e = tid; e < S + 2; e += kWaveThreads) {
+          if (ry0 < 0) w0[e] = w0[2 * tl.bxc + e];
+          if (ry0 + S + 2 > a.H) w0[(S + 1) * tl.bxc + e] = w0[(S - 1) * tl.bxc + e];
         }
-        ++iters;
-        if (ctl == 1) {
-          converged = true;
-          break;
-        }
+        __syncthreads();
       }
     }
-
-    // ---- 4. ZNCC at the final p, and the decision
-    if (!stopped) {
-      T acc[3] = {T(0), T(0), T(0)};
-      if (!sample_pass(1, acc)) {
-        status = DIC_PT_OUT_OF_BOUNDS;
-      } else {
-        reduce_store(0, 3, acc[0]);
-        reduce_store(1, 3, acc[1]);
-        reduce_store(2, 3, acc[2]);
-        reduce_finish(3);
-        const double gm = s_out[0] / N;
-        const double dg = sqrt(fmax(s_out[1] - N * gm * gm, 0.0));
-        if (is_flat(dg, gm + static_cast<double>(fmT), N)) {
-          status = DIC_PT_FLAT;
-        } else {
-          zncc = (s_out[2] - gm * s_sumfbar) / (s_df * dg);
-          if (!converged)
-            status = DIC_PT_MAX_ITER;
-          else if (zncc < a.zncc_min)
-            status = DIC_PT_LOW_ZNCC;
-          else
-            status = DIC_PT_OK;
+    const unsigned char* gtile = s_gray + (xc - r - gxa) * tl.gray_es;   // column 0 of the subset
+    if (tid == 0) st.f0 = tile_gray<C>(gtile, gpitch, gdt, r, r);
+    {
+      const T* wref = s_win + (rx0 - rxa);
+      const T f0 = tile_gray<T>(gtile, gpitch, gdt, r, r);
+      T A[3][M2 + 1], Bf[2][D + 1], Bs[2][D + 1];
+      T sf = T(0), sff = T(0);
+#pragma unroll
+      for (int j = 0; j <= M2; ++j) A[0][j] = A[1][j] = A[2][j] = T(0);
+#pragma unroll
+      for (int j = 0; j <= D; ++j) Bf[0][j] = Bf[1][j] = Bs[0][j] = Bs[1][j] = T(0);
+      for (int row = row0; row < row1; ++row) {
+        const int pix = row * S + col;
+        // exact derivative of the reference spline at the pixel:
+        // (-1/2, 0, 1/2) along one axis times (1, 4, 1)/6 along the other
+        const T* cm = wref + row * tl.bxc + col;     // row above, column left
+        const T* c0 = cm + tl.bxc;
+        const T* cp = c0 + tl.bxc;
+        const T fx = ((cm[2] - cm[0]) + T(4) * (c0[2] - c0[0]) + (cp[2] - cp[0])) * (T(1) / T(12));
+        const T fy = ((cp[0] - cm[0]) + T(4) * (cp[1] - cm[1]) + (cp[2] - cm[2])) * (T(1) / T(12));
+        s_fx[pix] = fx;
+        s_fy[pix] = fy;
+        const T fp = tile_gray<T>(gtile, gpitch, gdt, col, row) - f0;
+        sf += fp;
+        sff += fp * fp;
+        const T dyv = static_cast<T>(row - r);
+        T dyp[M2 + 1];
+        dyp[0] = T(1);
+#pragma unroll
+        for (int j = 1; j <= M2; ++j) dyp[j] = dyp[j - 1] * dyv;
+        const T wxx = fx * fx, wxy = fx * fy, wyy = fy * fy;
+#pragma unroll
+        for (int j = 0; j <= M2; ++j) {
+          A[0][j] += wxx * dyp[j];
+          A[1][j] += wxy * dyp[j];
+          A[2][j] += wyy * dyp[j];
+        }
+        const T fxb = fx * fp, fyb = fy * fp;
+#pragma unroll
+        for (int j = 0; j <= D; ++j) {
+          Bf[0][j] += fxb * dyp[j];
+          Bf[1][j] += fyb * dyp[j];
+          Bs[0][j] += fx * dyp[j];
+          Bs[1][j] += fy * dyp[j];
         }
       }
+#pragma unroll
+      for (int tt = 0; tt < 3; ++tt)
+#pragma unroll
+        for (int j = 0; j <= M2; ++j)
+#pragma unroll
+          for (int i = 0; i + j <= M2; ++i) part(tt * NMOM + mono(i, j, M2), dxp[i] * A[tt][j]);
+#pragma unroll
+      for (int c = 0; c < NP; ++c) {
+        part(3 * NMOM + c, dxp[sd_i(c)] * Bf[sd_t(c)][sd_j(c)]);
+        part(3 * NMOM + NP + c, dxp[sd_i(c)] * Bs[sd_t(c)][sd_j(c)]);
+      }
+      part(3 * NMOM + 2 * NP, sf);
+      part(3 * NMOM + 2 * NP + 1, sff);
     }
-
-    // ---- 5. results and claims
-    if (tid == 0) {
-      double* pq = a.pts.p + static_cast<int64_t>(q) * NP;
-      for (int c = 0; c < NP; ++c) pq[c] = s_p[c];
-      a.pts.u[q] = s_p[0];
-      a.pts.v[q] = s_p[1];
-      a.pts.zncc[q] = static_cast<float>(zncc);
-      a.pts.zncc64[q] = zncc;
-      a.pts.iters[q] = iters;
-      a.pts.converged[q] = converged ? 1 : 0;
-      a.pts.status[q] = static_cast<uint8_t>(status);
-      if (status == DIC_PT_OK) {
-        int nbs[4] = {gi > 0 ? q - 1 : -1, gi < a.nx - 1 ? q + 1 : -1, gj > 0 ? q - a.nx : -1,
-                      gj < a.ny - 1 ? q + a.nx : -1};
-        for (int m = 0; m < 4; ++m) {
-          const int nb = nbs[m];
-          if (nb < 0) continue;
-          if (a.roi_ok && !a.roi_ok[nb]) continue;
-          if (atomicCAS(&a.pts.wave[nb], -1, a.k + 1) == -1) {
-            const int pos = atomicAdd(&a.counters[kCount + nxt], 1);
-            a.next[pos] = nb;
-          }
-        }
+    __syncthreads();
+    if (warp == 0) {
+      gather(NV_PRE);
+      finish_reference<C, NP, NMOM, M2>(st, s_out, N, lane);
+      if (lane == 0) {
+        if (st.ctl == 0)
+          plan_window<C, NP>(st, xc, yc, r, a.W, a.H, tl, XALIGN);
+        else
+          st.status = st.ctl == 3 ? DIC_PT_FLAT : DIC_PT_SINGULAR;
       }
     }
     __syncthreads();
+
+    // ---- 3. IC-GN iterations, then 4. the final ZNCC pass
+    const T xlo = static_cast<T>(1 - xc), xhi = static_cast<T>(a.W - 2 - xc);
+    const T ylo = static_cast<T>(1 - yc), yhi = static_cast<T>(a.H - 2 - yc);
+    const C thr2 = static_cast<C>(a.conv_threshold * a.conv_threshold);
+    bool running = st.ctl == 0;
+    bool final_pass = false;
+    while (running) {
+      // stage the window that lane 0 planned (st is only written between barriers)
+      const int stage = st.stage;
+      const Window w = (stage == 1 || stage == 3) ? st.next : st.win;
+      if (stage == 1) {
+        if (tid == 0) {
+          fence_proxy_async_shared();
+          mbar_arrive_expect_tx(&s_bar, static_cast<uint32_t>(tl.bxc * tl.byc * sizeof(T)));
+          tma_load_2d(s_win, &tm_cdef, w.x0, w.y0, &s_bar);
+        }
+        if (!tma_wait()) return;
+      } else if (stage == 3) {
+        for (int row = warp; row < w.h; row += kWaveWarps) {
+          const T* src = a.c_def + static_cast<int64_t>(w.y0 + row) * a.ldc + w.x0;
+          T* dst = s_win + row * w.w;
+          for (int c = lane; c < w.w; c += 32) dst[c] = src[c];
+        }
+        __syncthreads();
+      }
+      const T* pw = st.p;
+      T ax = pw[0] + dxv, ay = pw[1], bx = T(0), by = T(1), cxq = T(0), cyq = T(0);
+      if (NP >= 6) {
+        ax += pw[2] * dxv;
+        ay += pw[4] * dxv;
+        bx = pw[3];
+        by = T(1) + pw[5];
+      }
+      if (NP >= 12) {
+        ax += pw[6] * dxv * dxv;
+        ay += pw[9] * dxv * dxv;
+        bx += pw[7] * dxv;
+        by += pw[10] * dxv;
+        cxq = pw[8];
+        cyq = pw[11];
+      }
+      const T f0 = st.f0;
+      T acc[NACC];
+#pragma unroll
+      for (int e = 0; e < NACC; ++e) acc[e] = T(0);
+      T bad = T(0);
+      if (stage != 2) {
+        const T* base = s_win + (yc - 1 - w.y0) * w.w + (xc - 1 - w.x0);
+        if (!final_pass)
+          sample_column<T, D, false>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0,
+                                     row1, r, S, col, gtile, gpitch, gdt, s_fx, s_fy, acc, bad);
+        else
+          sample_column<T, D, true>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0,
+                                    row1, r, S, col, gtile, gpitch, gdt, s_fx, s_fy, acc, bad);
+      } else {
+        const T* base = a.c_def + static_cast<int64_t>(yc - 1) * a.ldc + (xc - 1);
+        if (!final_pass)
+          sample_column_global<T, D, false>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi,
+                                            f0, row0, row1, r, S, col, gtile, gpitch, gdt, s_fx, s_fy,
+                                            acc, bad);
+        else
+          sample_column_global<T, D, true>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi,
+                                           f0, row0, row1, r, S, col, gtile, gpitch, gdt, s_fx, s_fy,
+                                           acc, bad);
+      }
+      if (!final_pass) {
+        part(0, acc[0]);
+        part(1, acc[1]);
+#pragma unroll
+        for (int c = 0; c < NP; ++c) part(2 + c, dxp[sd_i(c)] * acc[2 + sd_t(c) * (D + 1) + sd_j(c)]);
+        part(2 + NP, bad);
+      } else {
+        part(0, acc[0]);
+        part(1, acc[1]);
+        part(2, acc[2]);
+        part(3, bad);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        gather(final_pass ? NV_FIN : NV_IT);
+        if (lane == 0 && (st.stage == 1 || st.stage == 3)) st.win = st.next;
+        if (!final_pass) {
+          const int ctl = gauss_newton_update<C, NP>(st, s_out, N, static_cast<C>(r), thr2, lane);
+          if (lane == 0) {
+            if (ctl == 5) {
+              st.status = DIC_PT_OUT_OF_BOUNDS;
+              st.ctl = 5;
+            } else if (ctl == 2) {
+              st.status = DIC_PT_FLAT;
+              st.ctl = 2;
+            } else {
+              st.iters += 1;
+              if (ctl == 1) st.converged = 1;
+              st.ctl = (ctl == 1 || st.iters >= a.max_iter) ? 6 : 0;   // 6: go to the final pass
+              plan_window<C, NP>(st, xc, yc, r, a.W, a.H, tl, XALIGN);
+            }
+          }
+        } else if (lane == 0) {
+          // FP64 normalisation of the final correlation coefficient
+          const double sg = s_out[0], sgg = s_out[1], sfg = s_out[2];
+          const double nu = sg / N;
+          const double dg = sqrt(fmax(sgg - sg * nu, 0.0));
+          if (s_out[3] > C(0.5)) {
+            st.status = DIC_PT_OUT_OF_BOUNDS;
+          } else if (is_flat<double>(dg, nu + static_cast<double>(st.f0), N)) {
+            st.status = DIC_PT_FLAT;
+          } else {
+            // sum (f - f_m)(g - g_m) = sum f' g' - mu sum g'
+            st.zncc = (sfg - static_cast<double>(st.mu) * sg) / (static_cast<double>(st.delta_f) * dg);
+            if (!st.converged)
+              st.status = DIC_PT_MAX_ITER;
+            else if (st.zncc < a.zncc_min)
+              st.status = DIC_PT_LOW_ZNCC;
+            else
+              st.status = DIC_PT_OK;
+          }
+          st.ctl = 7;
+        }
+      }
+      __syncthreads();
+      const int ctl = st.ctl;
+      if (ctl == 6) {
+        final_pass = true;
+      } else if (ctl != 0) {
+        running = false;
+      }
+    }
+
+    // ---- 5. results and claims (warp 0)
+    if (warp == 0) {
+      const int status = st.status;
+      if (lane < NP) a.pts.p[static_cast<int64_t>(q) * NP + lane] = static_cast<double>(st.p[lane]);
+      if (lane == 0) {
+        a.pts.u[q] = static_cast<double>(st.p[0]);
+        a.pts.v[q] = static_cast<double>(st.p[1]);
+        a.pts.zncc[q] = static_cast<float>(st.zncc);
+        a.pts.accept[q] = status == DIC_PT_OK
+                              ? (static_cast<int64_t>(a.k) << 32) |
+                                    static_cast<int64_t>(static_cast<uint32_t>(__float_as_int(static_cast<float>(st.zncc))))
+                              : -1;
+        a.pts.iters[q] = st.iters;
+        a.pts.converged[q] = static_cast<uint8_t>(st.converged);
+        a.pts.status[q] = static_cast<uint8_t>(status);
+      }
+      if (status == DIC_PT_OK && lane < 4) {
+        const int gi = q % a.nx, gj = q / a.nx;
+        int nb = -1;
+        if (lane == 0 && gi > 0) nb = q - 1;
+        if (lane == 1 && gi < a.nx - 1) nb = q + 1;
+        if (lane == 2 && gj > 0) nb = q - a.nx;
+        if (lane == 3 && gj < a.ny - 1) nb = q + a.nx;
+        if (nb >= 0 && (a.roi_ok == nullptr || a.roi_ok[nb]) &&
+            atomicCAS(&a.pts.wave[nb], -1, a.k + 1) == -1) {
+          const int pos = atomicAdd(&a.counters[kCount + nxt], 1);
+          a.next[pos] = nb;
+        }
+      }
+    }
   }
 }
 
@@ -724,7 +1022,7 @@ __global__ void reset_points_kernel(PointArrays pa, int nparams, const uint8_t* 
     pa.v[q] = 0.0;
     for (int c = 0; c < nparams; ++c) pa.p[q * nparams + c] = 0.0;
     pa.zncc[q] = nanf("");
-    pa.zncc64[q] = nan("");
+    pa.accept[q] = -1;
     pa.iters[q] = 0;
     pa.converged[q] = 0;
     pa.status[q] = (roi_ok && !roi_ok[q]) ? DIC_PT_NOT_IN_ROI : DIC_PT_NOT_REACHED;
@@ -751,27 +1049,24 @@ __global__ void finalize_points_kernel(PointArrays pa, int nparams, int nan_reje
 }
 
 template <typename T, int NP>
-cudaError_t launch_wave_np(const WaveArgs<T>& a, int grid, cudaStream_t s) {
-  const size_t smem = wave_smem_bytes<T>(a.S, a.win_cap);
+cudaError_t launch_wave_np(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
+  const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
   static size_t configured = 0;
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(wave_kernel<T, NP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(wave_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  wave_kernel<T, NP><<<grid, kThreads, smem, s>>>(a);
+  wave_kernel<T, NP><<<grid, kWaveThreads, smem, s>>>(a, maps[0], maps[1], maps[2]);
   return cudaGetLastError();
 }
 
 template <typename T, int NP>
 int blocks_per_sm_np(size_t smem) {
-  cudaFuncSetAttribute(wave_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(smem));
+  cudaFuncSetAttribute(wave_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<T, NP>, kThreads, smem) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<T, NP>, kWaveThreads, smem) != cudaSuccess)
     return 1;
   return nb > 0 ? nb : 1;
 }
@@ -779,20 +1074,36 @@ int blocks_per_sm_np(size_t smem) {
 }  // namespace
 
 template <typename T>
-size_t wave_smem_bytes(int S, int win_cap) {
-  const size_t SS = (static_cast<size_t>(S) * S + 3) & ~static_cast<size_t>(3);
-  return (3 * SS + static_cast<size_t>(win_cap)) * sizeof(T);
+WaveTiles wave_tiles(int S, int gray_dtype) {
+  WaveTiles t{};
+  const int xalign = 16 / static_cast<int>(sizeof(T));
+  t.bxc = ((S + 12 + xalign - 1) / xalign) * xalign;
+  t.byc = S + 9;
+  static const int es_of[5] = {1, 2, 2, 4, 8};
+  t.gray_es = es_of[gray_dtype];
+  const int galign = 16 / t.gray_es;
+  t.bxg = ((S + galign - 1 + galign - 1) / galign) * galign;
+  const int SS = ((S * S + 31) / 32) * 32;
+  auto al = [](int x) { return (x + 127) & ~127; };
+  t.off_fx = 0;
+  t.off_fy = al(t.off_fx + SS * static_cast<int>(sizeof(T)));
+  t.off_win = al(t.off_fy + SS * static_cast<int>(sizeof(T)));
+  t.off_gray = al(t.off_win + t.bxc * t.byc * static_cast<int>(sizeof(T)));
+  t.smem_bytes = al(t.off_gray + t.bxg * S * t.gray_es);
+  return t;
 }
 
 template <typename T>
-cudaError_t launch_wave(const WaveArgs<T>& a, int nparams, int grid, cudaStream_t s) {
+cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensorMap* maps, int nparams,
+                        int grid, cudaStream_t s) {
+  (void)t;
   switch (nparams) {
     case 2:
-      return launch_wave_np<T, 2>(a, grid, s);
+      return launch_wave_np<T, 2>(a, maps, grid, s);
     case 6:
-      return launch_wave_np<T, 6>(a, grid, s);
+      return launch_wave_np<T, 6>(a, maps, grid, s);
     default:
-      return launch_wave_np<T, 12>(a, grid, s);
+      return launch_wave_np<T, 12>(a, maps, grid, s);
   }
 }
 
@@ -831,10 +1142,12 @@ cudaError_t launch_finalize_points(const PointArrays& pa, int nparams, int nan_r
   return cudaGetLastError();
 }
 
-template size_t wave_smem_bytes<float>(int, int);
-template size_t wave_smem_bytes<double>(int, int);
-template cudaError_t launch_wave<float>(const WaveArgs<float>&, int, int, cudaStream_t);
-template cudaError_t launch_wave<double>(const WaveArgs<double>&, int, int, cudaStream_t);
+template WaveTiles wave_tiles<float>(int, int);
+template WaveTiles wave_tiles<double>(int, int);
+template cudaError_t launch_wave<float>(const WaveArgs<float>&, const WaveTiles&, const CUtensorMap*, int, int,
+                                        cudaStream_t);
+template cudaError_t launch_wave<double>(const WaveArgs<double>&, const WaveTiles&, const CUtensorMap*, int, int,
+                                         cudaStream_t);
 template int wave_blocks_per_sm<float>(int, size_t);
 template int wave_blocks_per_sm<double>(int, size_t);
 

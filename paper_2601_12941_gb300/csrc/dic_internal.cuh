@@ -2,6 +2,7 @@
 // small device helpers the kernels share. Nothing here is part of the C-ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -9,13 +10,15 @@
 
 namespace dic {
 
-constexpr int kThreads = 256;        // threads per block of the subset kernels
-constexpr int kWarps = kThreads / 32;
+constexpr int kThreads = 256;        // threads per block of the image kernels
+constexpr int kWaveThreads = 128;    // threads per block of the subset (wave) kernel
+constexpr int kWaveWarps = kWaveThreads / 32;
 constexpr int kMaxSubset = 61;       // largest odd subset side supported
 constexpr int kMaxParams = 12;
 
-// device counters: frontier sizes and work cursors, each triple-buffered by wave
-enum { kCount = 0, kWork = 3, kNumCounters = 8 };
+// device counters: frontier sizes and work cursors, each triple-buffered by wave;
+// the accepted-point total; an error flag (a bounded wait ran out)
+enum { kCount = 0, kWork = 3, kAccepted = 6, kError = 7, kNumCounters = 8 };
 
 // Gray-level plane as given by the caller (borrowed or owned).
 struct GrayPlane {
@@ -51,6 +54,12 @@ __host__ __device__ __forceinline__ int64_t mirror_index(int64_t k, int64_t n) {
   return m < n ? m : period - m;
 }
 
+// Mirror of an index that lies at most n - 1 outside [0, n) (n >= 2).
+__host__ __device__ __forceinline__ int mirror_near(int k, int n) {
+  k = k < 0 ? -k : k;
+  return k > n - 1 ? 2 * (n - 1) - k : k;
+}
+
 // Cubic B-spline weights for the four knots around x = i + t, t in [0, 1):
 // knots i-1, i, i+1, i+2 get beta(t+1), beta(t), beta(1-t), beta(2-t).
 template <typename T>
@@ -63,6 +72,19 @@ __device__ __forceinline__ void bspline_weights(T t, T& w0, T& w1, T& w2, T& w3)
   w3 = t3 * one_sixth;
   w1 = T(0.5) * t3 - t2 + T(2) / T(3);
   w2 = T(1) - w0 - w1 - w3;
+}
+
+// Six times those weights: 6 beta(t+1) = s^3, 6 beta(t) = t^2 (3t - 6) + 4,
+// 6 beta(1-t) = s^2 (3s - 6) + 4, 6 beta(2-t) = t^3, s = 1 - t; a sample is
+// sum w_y w_x c / 36.
+template <typename T>
+__device__ __forceinline__ void bspline_weights6(T t, T& w0, T& w1, T& w2, T& w3) {
+  const T s = T(1) - t;
+  const T t2 = t * t, s2 = s * s;
+  w3 = t2 * t;
+  w0 = s2 * s;
+  w1 = t2 * (T(3) * t - T(6)) + T(4);
+  w2 = s2 * (T(3) * s - T(6)) + T(4);
 }
 
 // ---------------------------------------------------------------- prefilter
@@ -110,7 +132,8 @@ struct PointArrays {
   double* v;
   double* p;         // [n][nparams]
   float* zncc;
-  double* zncc64;    // ranks neighbours for the initial guess
+  int64_t* accept;   // (wave << 32) | ZNCC float bits of accepted points, else -1:
+                     // one load tells a neighbour's wave, acceptance and rank
   int32_t* iters;
   uint8_t* converged;
   uint8_t* status;
@@ -129,6 +152,18 @@ cudaError_t launch_finalize_points(const PointArrays& pa, int nparams, int nan_r
                                    int32_t* accepted, cudaStream_t s);
 
 // ---------------------------------------------------------------- waves
+// Shared-memory tiles of the wave kernel: the coefficient window (bxc x byc
+// elements, also the TMA box of the coefficient planes), the reference gray tile
+// (bxg x S elements of gray_es bytes, the TMA box of the gray plane) and where
+// each region starts in dynamic shared memory (128-byte aligned).
+struct WaveTiles {
+  int bxc, byc;
+  int bxg, gray_es;
+  int coef_tma, gray_tma;    // 1: tiles arrive by TMA; 0: cooperative copies
+  int off_fx, off_fy, off_win, off_gray;
+  int smem_bytes;
+};
+
 template <typename T>
 struct WaveArgs {
   // image geometry and planes
@@ -140,7 +175,8 @@ struct WaveArgs {
   // subset grid
   int S, r, step, nx, ny;
   int bands, band_h;         // thread t < S*bands: column t % S, rows band_h*(t/S) ...
-  int win_cap;               // coefficient-window capacity in elements
+                             // (S * bands <= kWaveThreads)
+  WaveTiles tiles;
   // per-point state
   PointArrays pts;
   const uint8_t* roi_ok;     // NULL: all in ROI
@@ -157,10 +193,11 @@ struct WaveArgs {
 };
 
 template <typename T>
-size_t wave_smem_bytes(int S, int win_cap);
+WaveTiles wave_tiles(int S, int gray_dtype);
 
 template <typename T>
-cudaError_t launch_wave(const WaveArgs<T>& a, int nparams, int grid, cudaStream_t s);
+cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensorMap* maps, int nparams,
+                        int grid, cudaStream_t s);
 
 template <typename T>
 int wave_blocks_per_sm(int nparams, size_t smem);

@@ -198,3 +198,18 @@ def test_flat_image_and_seed_errors(pkg):
         c.run([])
     assert e.value.code == -1
     c.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_large_strain_uses_global_fallback_and_matches_oracle(pkg, precision):
+    """35% stretch: the warped 21 x 21 subset spans more coefficients than the
+    shared-memory window holds, so samples read the global plane."""
+    W, H = 160, 150
+    fld = synth.affine_field(W, H, u0=0.6, v0=-0.4, exx=0.35, eyy=0.3)
+    ref, dfm = _pair(W, H, fld, dtype="f32", seed=77)
+    prm = dict(ORACLE_PARAMS, search_radius=3)
+    ora = _oracle("strain160", ref, dfm, None, 21, 6, "affine", [(80, 75)], prm)
+    gpu = _run(pkg, ref, dfm, None, 21, 6, "affine", [(80, 75)], precision, search_radius=3)
+    stats = compare(gpu, ora, W, H, 21)
+    assert stats["accepted"] >= 4
+    print(precision, stats)
