@@ -185,6 +185,56 @@ int dic_get_coefficients(const dic_handle* h, int32_t which, const void** plane,
 /* Stage timings of the last dic_correlate; zeros unless params.profile = 1. */
 int dic_get_timing(const dic_handle* h, dic_timing* out);
 
+/* ---- allocation-free correlation (the paper has no counterpart) ----------
+ *
+ * For callers that must not allocate device memory when they correlate: code
+ * running inside an allocator's own callback, a real-time loop that cannot take
+ * the driver's allocation locks, or a host that gives all device memory to its
+ * own pool. dic_correlate_static runs the same kernels as dic_correlate (spline
+ * prefilter, seed search, propagation waves) on caller-owned device images and
+ * writes caller-owned device outputs; every intermediate buffer lives in one
+ * file-scope device array of this library (about 10 MiB, held by every GPU that
+ * loads the library until the process exits). It calls no cudaMalloc, cudaFree
+ * or other allocating routine.
+ *
+ * Limits (larger problems return DIC_EINVAL and a message saying which):
+ *   H * (W rounded up to 32) <= DIC_STATIC_MAX_PIXELS, grid points <=
+ *   DIC_STATIC_MAX_POINTS, n_seeds <= DIC_STATIC_MAX_SEEDS, search_radius <=
+ *   DIC_STATIC_MAX_RADIUS; precision must be DIC_MIXED; no ROI (every grid point).
+ * Shared state: all calls in the process use the same array and it keeps the
+ * last call's contents (every call clears what must start from zero). Calls that
+ * overlap on the GPU (other streams or host threads) race on it: serialise them.
+ * The first call on each device looks up the array's device address and caches
+ * it; make that first call before any stream capture.
+ * Arguments: ref, def: device images (on_device = 1), same size and dtype;
+ * subset_size, subset_step, shape_fn, params, seeds_xy, n_seeds as for
+ * dic_create / dic_correlate; out: device arrays of n_points = nx * ny entries
+ * (p: n_points * n_params doubles) in grid order, n_accepted an optional host
+ * pointer; errbuf (optional, errlen bytes) receives the message of a failure.
+ * Returns once the outputs are complete. Errors: DIC_EINVAL, DIC_ENOSEED,
+ * DIC_ECUDA, DIC_ETIMEOUT. */
+#define DIC_STATIC_MAX_PIXELS 1048576
+#define DIC_STATIC_MAX_POINTS 65536
+#define DIC_STATIC_MAX_SEEDS 16
+#define DIC_STATIC_MAX_RADIUS 32
+
+typedef struct {
+  double* u;
+  double* v;
+  double* p;
+  float* zncc;
+  int32_t* iters;
+  uint8_t* converged;
+  uint8_t* status;
+  int32_t* wave;
+  int64_t* n_accepted;       /* host, optional */
+} dic_static_outputs;
+
+int dic_correlate_static(const dic_image* ref, const dic_image* def, int32_t subset_size,
+                         int32_t subset_step, int32_t shape_fn, const dic_params* params,
+                         const int32_t* seeds_xy, int32_t n_seeds, const dic_static_outputs* out,
+                         void* cuda_stream, char* errbuf, int32_t errlen);
+
 /* Frees every buffer of the handle (NULL is ignored). */
 void dic_destroy(dic_handle* h);
 

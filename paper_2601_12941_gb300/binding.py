@@ -25,7 +25,8 @@ N_PARAMS = {DIC_RIGID: 2, DIC_AFFINE: 6, DIC_QUADRATIC: 12}
 # every function declared in include/dic.h
 EXPORTS = ("dic_default_params", "dic_create", "dic_set_params", "dic_get_params",
            "dic_set_reference", "dic_set_deformed", "dic_correlate", "dic_get_results",
-           "dic_get_coefficients", "dic_get_timing", "dic_destroy", "dic_last_error")
+           "dic_get_coefficients", "dic_get_timing", "dic_destroy", "dic_last_error",
+           "dic_correlate_static")
 
 
 class DicImage(ctypes.Structure):
@@ -57,6 +58,12 @@ class DicTiming(ctypes.Structure):
                 ("seed_kernel_ms", ctypes.c_double), ("n_wave_launches", ctypes.c_int32),
                 ("n_waves", ctypes.c_int32), ("n_points_attempted", ctypes.c_int64),
                 ("sum_sample_passes", ctypes.c_int64)]
+
+
+class DicStaticOutputs(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("zncc", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("converged", ctypes.c_void_p),
+                ("status", ctypes.c_void_p), ("wave", ctypes.c_void_p), ("n_accepted", ctypes.c_void_p)]
 
 
 class DicError(RuntimeError):
@@ -104,6 +111,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dic_destroy.restype = None
     lib.dic_last_error.argtypes = []
     lib.dic_last_error.restype = ctypes.c_char_p
+    lib.dic_correlate_static.argtypes = [P(DicImage), P(DicImage), ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, P(DicParams), P(ctypes.c_int32), ctypes.c_int32,
+                                         P(DicStaticOutputs), vp, ctypes.c_char_p, ctypes.c_int32]
+    lib.dic_correlate_static.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -252,6 +263,26 @@ def dic_destroy(h):
 
 def dic_last_error() -> str:
     return load().dic_last_error().decode(errors="replace")
+
+
+def dic_correlate_static(ref, deformed, subset_size, subset_step, shape_fn, prm: DicParams, seeds,
+                         out: dict, stream_ptr: int = 0) -> int:
+    """Allocation-free correlation into caller-owned CUDA tensors ``out`` (keys u, v,
+    p, zncc, iters, converged, status, wave); returns the accepted-point count."""
+    ri, rk = make_image(ref)
+    di, dk = make_image(deformed)
+    s = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).reshape(-1, 2))
+    acc = ctypes.c_int64(0)
+    o = DicStaticOutputs(*[out[k].data_ptr() for k in ("u", "v", "p", "zncc", "iters", "converged",
+                                                         "status", "wave")],
+                         ctypes.cast(ctypes.byref(acc), ctypes.c_void_p))
+    err = ctypes.create_string_buffer(512)
+    rc = load().dic_correlate_static(ctypes.byref(ri), ctypes.byref(di), subset_size, subset_step, shape_fn,
+                                     ctypes.byref(prm), s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     s.shape[0], ctypes.byref(o), ctypes.c_void_p(stream_ptr), err, 512)
+    if rc != DIC_OK:
+        raise DicError(rc, err.value.decode(errors="replace"))
+    return acc.value
 
 
 def params(**kw) -> DicParams:
