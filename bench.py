@@ -119,6 +119,43 @@ def dist_setup(args):
     return world, rank, local
 
 
+class Ranks:
+    """Host-side aggregation over the replicas of a multi-GPU run (one process per
+    GPU, each correlating its own pair): a barrier, the slowest rank's time and the
+    sum of the work. `dist` is torch.distributed or None; `device` holds the
+    reduction buffers (cuda for NCCL, cpu for gloo)."""
+
+    def __init__(self, dist=None, device="cpu"):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, self.dist.ReduceOp.MAX) if self.dist is not None else float(x)
+
+    def sum(self, x):
+        return self._reduce(x, self.dist.ReduceOp.SUM) if self.dist is not None else float(x)
+
+
+def aggregate(ranks, local_ms_per_step, local_accepted):
+    """(ms_per_step, value): the slowest rank's time per step and the points all
+    ranks accepted per second of that time (weak scaling)."""
+    ms = ranks.max(local_ms_per_step)
+    return ms, ranks.sum(local_accepted) / (ms / 1e3)
+
+
 def run_ours(args):
     import torch
 
@@ -142,24 +179,14 @@ def run_ours(args):
     seeds = list(w.seeds)
     nparams = P.N_PARAMS[P.SHAPES[w.shape]]
 
+    ranks = Ranks(dist, "cuda")
+
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        ranks.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    max_over_ranks = ranks.max
+    sum_over_ranks = ranks.sum
 
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
@@ -203,8 +230,7 @@ def run_ours(args):
     accepted = int(res["n_accepted"])
     attempted = int((res["wave"] >= 0).sum())
     flops = algorithmic_flops(res["iters"], res["status"], res["wave"], w.subset_size, nparams)
-    ms_per_step = max_over_ranks(total_ms / args.steps)
-    value = sum_over_ranks(accepted) / (ms_per_step / 1e3)
+    ms_per_step, value = aggregate(ranks, total_ms / args.steps, accepted)
     kern_avg = kern_ms / args.steps
     achieved = flops / (kern_avg / 1e3) / 1e12
     tm = c.timing()
@@ -246,6 +272,11 @@ def run_ours(args):
     if not args.no_e2e:
         out["e2e"] = e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_ranks)
     c.close()
+    del ref, dfm
+    torch.cuda.empty_cache()
+
+    if args.seq_frames > 0:
+        out["sequence"] = sequence_leg(args, stream)
 
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
@@ -284,6 +315,51 @@ def e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_
     return {"value": sum_over_ranks(int(r["n_accepted"])) / el, "unit": UNIT,
             "ms_per_step": el * 1e3, "h2d_bytes_per_step": int(nref.nbytes + ndef.nbytes),
             "d2h_bytes_per_step": int(d2h), "points": n}
+
+
+def sequence_leg(args, stream):
+    """Frames of the incremental uniaxial sequence (4096 x 3000 u16, strain ramping
+    to 2e-2 over 200 frames, 1% noise), subset 21, step 10, affine: frame 1 from the
+    seed, every later frame from the previous frame's field (dic_correlate_sequence)
+    against the resident frame-0 reference. Per-frame latency covers the deformed
+    prefilter and every wave; frames are rendered outside the timed region."""
+    import torch
+
+    import paper_2601_12941_gb300 as P
+    import synth
+    from synth import workloads as wl
+
+    n = args.seq_frames
+    w0 = wl.sequence_frame(1)
+    ref = torch.empty((w0.height, w0.width), dtype=torch.int16, device="cuda")
+    dfm = torch.empty_like(ref)
+    synth.render_gpu(w0.ref, ref)
+    synth.render_gpu(w0.deformed, dfm)
+    c = P.Correlation(ref, dfm, None, w0.subset_size, w0.subset_step, w0.shape, precision="mixed",
+                      search_radius=w0.search_radius, profile=0)
+    c.run(list(w0.seeds), stream.cuda_stream)
+    lat, acc = [], []
+    for k in range(2, n + 1):
+        synth.render_gpu(wl.sequence_frame(k).deformed, dfm)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c.set_deformed(dfm)
+        c.run_next(stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+        acc.append(c.results(on_device=True)["n_accepted"])
+    r = c.results()
+    c.close()
+    lat = np.array(lat)
+    return {"frames": n, "size": [w0.width, w0.height], "subset": w0.subset_size, "step": w0.subset_step,
+            "shape": w0.shape, "points_per_frame": int(r["n_points"]),
+            "accepted_last_frame": int(r["n_accepted"]),
+            "frame_ms_p50": float(np.percentile(lat, 50)), "frame_ms_p99": float(np.percentile(lat, 99)),
+            "points_per_s": float(np.sum(acc) / (np.sum(lat) / 1e3)),
+            "note": "frame 1 from the seed (not timed); frames 2..%d timed" % n}
 
 
 def cpu_baseline(w, seconds):
@@ -352,6 +428,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--seq-frames", type=int, default=200,
+                    help="frames of the 4096 x 3000 sequence leg (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -171,6 +171,16 @@ int dic_set_deformed(dic_handle* h, const dic_image* def);
  * seed rejected), DIC_ECUDA, DIC_ETIMEOUT. */
 int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void* cuda_stream);
 
+/* Next frame of a sequence (Sec. 2.1: several deformed images against one
+ * reference): correlates the handle's current deformed image (set it with
+ * dic_set_deformed) against the resident reference, starting every point that the
+ * previous correlation on this handle accepted from its previous warp, all in
+ * wave 0; the other points are reached by propagation as in dic_correlate. The
+ * reference coefficients are reused unless the reference changed. Same outputs
+ * and errors as dic_correlate; DIC_ESTATE without an earlier correlation or after
+ * a precision change. */
+int dic_correlate_sequence(dic_handle* h, void* cuda_stream);
+
 /* Fills *out with device pointers (on_device = 1) or with pointers to host copies
  * owned by the handle (on_device = 0; copied during the call). */
 int dic_get_results(dic_handle* h, dic_results* out, int32_t on_device);

@@ -7,5 +7,5 @@ paper each step follows.
 """
 from .dic_oracle import *  # noqa: F401,F403
 from .dic_oracle import (AFFINE, DEFAULT_PARAMS, N_PARAMS, QUADRATIC, RIGID, Plane,  # noqa: F401
-                         ReferenceSubset, bspline_coefficients, correlate, grid, icgn,
+                         ReferenceSubset, bspline_coefficients, correlate, correlate_sequence, grid, icgn,
                          interpolate, seed_search)

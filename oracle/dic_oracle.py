@@ -57,6 +57,9 @@ Readings taken where the paper is silent (all of them, in one place):
       4-neighbour of a point accepted in wave k. Each point is attempted once, from
       the warp of its accepted neighbour (earlier waves) with the highest ZNCC
       (ties to the lower index), re-expanded about the new centre.
+  R11 Sequences (one reference, many deformed images, Sec. 2.1): frame k starts
+      every point accepted in frame k-1 from its frame k-1 warp, all in wave 0;
+      the remaining points are reached by propagation as in R10.
 """
 from __future__ import annotations
 
@@ -511,6 +514,24 @@ def correlate(ref, deformed, roi, subset_size, subset_step, shape, seeds, params
     """Whole-image correlation by waves (reading R10). Returns a dict of per-point
     arrays in grid order (q = j * nx + i): x, y, u, v, p, zncc, iters, converged,
     status, wave; plus nx, ny."""
+    return _propagate(ref, deformed, roi, subset_size, subset_step, shape, params, progress,
+                      seeds=seeds)
+
+
+def correlate_sequence(ref, deformed, roi, subset_size, subset_step, shape, previous, params=None,
+                       progress=None):
+    """One frame of a sequence against the same reference (Sec. 2.1: one result per
+    deformed image). Reading R11: wave 0 is every point accepted in the previous
+    frame's result `previous`, each starting from its previous warp; the other
+    points are reached by propagation exactly as in correlate()."""
+    starts = {int(q): np.asarray(previous["p"][q], dtype=np.float64)
+              for q in np.flatnonzero(np.asarray(previous["status"]) == OK)}
+    return _propagate(ref, deformed, roi, subset_size, subset_step, shape, params, progress,
+                      starts=starts)
+
+
+def _propagate(ref, deformed, roi, subset_size, subset_step, shape, params, progress, seeds=None,
+               starts=None):
     prm = dict(DEFAULT_PARAMS)
     if params:
         prm.update(params)
@@ -534,23 +555,31 @@ def correlate(ref, deformed, roi, subset_size, subset_step, shape, seeds, params
     py = np.repeat(ys, nx)
 
     current = []
-    for (sx, sy) in seeds:
-        i, j = snap_seed(sx, sy, W, H, subset_size, subset_step)
-        q = j * nx + i
-        if inroi[q] and wave[q] < 0:
-            wave[q] = 0
-            current.append(q)
+    if seeds is not None:
+        for (sx, sy) in seeds:
+            i, j = snap_seed(sx, sy, W, H, subset_size, subset_step)
+            q = j * nx + i
+            if inroi[q] and wave[q] < 0:
+                wave[q] = 0
+                current.append(q)
+    else:
+        for q in sorted(starts):
+            if inroi[q]:
+                wave[q] = 0
+                current.append(q)
     k = 0
     while current:
         for q in current:
             xc, yc = int(px[q]), int(py[q])
-            if k == 0:
+            if k == 0 and seeds is not None:
                 found = seed_search(ref, deformed, xc, yc, subset_size, int(prm["search_radius"]))
                 if found is None:
                     status[q] = OUT_OF_BOUNDS
                     continue
                 p0 = np.zeros(n)
                 p0[0], p0[1] = found[0], found[1]
+            elif k == 0:
+                p0 = starts[q]
             else:
                 best = None
                 for nb in _neighbours(q, nx, ny):

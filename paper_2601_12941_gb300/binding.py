@@ -26,7 +26,7 @@ N_PARAMS = {DIC_RIGID: 2, DIC_AFFINE: 6, DIC_QUADRATIC: 12}
 EXPORTS = ("dic_default_params", "dic_create", "dic_set_params", "dic_get_params",
            "dic_set_reference", "dic_set_deformed", "dic_correlate", "dic_get_results",
            "dic_get_coefficients", "dic_get_timing", "dic_destroy", "dic_last_error",
-           "dic_correlate_static")
+           "dic_correlate_static", "dic_correlate_sequence")
 
 
 class DicImage(ctypes.Structure):
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dic_set_deformed.restype = ctypes.c_int
     lib.dic_correlate.argtypes = [vp, P(ctypes.c_int32), ctypes.c_int32, vp]
     lib.dic_correlate.restype = ctypes.c_int
+    lib.dic_correlate_sequence.argtypes = [vp, vp]
+    lib.dic_correlate_sequence.restype = ctypes.c_int
     lib.dic_get_results.argtypes = [vp, P(DicResults), ctypes.c_int32]
     lib.dic_get_results.restype = ctypes.c_int
     lib.dic_get_coefficients.argtypes = [vp, ctypes.c_int32, P(vp), P(ctypes.c_int64),
@@ -200,6 +202,10 @@ def dic_correlate(h, seeds, stream_ptr: int = 0):
     s = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).reshape(-1, 2))
     _check(load().dic_correlate(h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), s.shape[0],
                                 ctypes.c_void_p(stream_ptr)))
+
+
+def dic_correlate_sequence(h, stream_ptr: int = 0):
+    _check(load().dic_correlate_sequence(h, ctypes.c_void_p(stream_ptr)))
 
 
 def _host_array(ptr, count, dtype):
@@ -321,6 +327,11 @@ class Correlation:
 
     def run(self, seeds, stream_ptr: int = 0):
         dic_correlate(self.h, seeds, stream_ptr)
+        return self
+
+    def run_next(self, stream_ptr: int = 0):
+        """Next frame: the current deformed image, started from the last result."""
+        dic_correlate_sequence(self.h, stream_ptr)
         return self
 
     def results(self, on_device=False):

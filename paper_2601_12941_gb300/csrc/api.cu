@@ -121,12 +121,14 @@ struct dic_handle {
   // seeds
   int32_t* seed_xy = nullptr;
   int32_t* seed_q = nullptr;
+  int32_t* seed_best = nullptr;
   double* seed_scores = nullptr;
   size_t seed_cap = 0, score_cap = 0;
   // host copies of the results
   void* h_res = nullptr;
   size_t h_res_bytes = 0;
   // last run
+  bool has_results = false;
   int n_waves = 0;
   int64_t n_accepted = 0;
   dic_timing timing{};
@@ -443,7 +445,7 @@ void release(dic_handle* h) {
   dev_free(h->roi_ok);
   void* ptrs[] = {h->x,     h->y,        h->u,    h->v,      h->p,          h->zncc,
                   h->accept, h->iters,   h->wave, h->conv,   h->status,     h->front[0],
-                  h->front[1], h->counters, h->wave_sizes, h->seed_xy, h->seed_q, h->seed_scores};
+                  h->front[1], h->counters, h->wave_sizes, h->seed_xy, h->seed_q, h->seed_best, h->seed_scores};
   for (void* q : ptrs) dev_free(q);
   if (h->h_counters) cudaFreeHost(h->h_counters);
   if (h->h_res) cudaFreeHost(h->h_res);
@@ -463,6 +465,39 @@ int validate_params(const dic_params* p) {
     return fail(DIC_EINVAL, "search_radius %d out of range", p->search_radius);
   if (p->precision != DIC_FP64 && p->precision != DIC_MIXED)
     return fail(DIC_EINVAL, "unknown precision %d", p->precision);
+  return DIC_OK;
+}
+
+// The wave loop and everything after it, shared by dic_correlate and
+// dic_correlate_sequence (wave 0 is already in front[0] and the counters).
+int finish_run(dic_handle* h, cudaStream_t s) {
+  const bool prof = h->prm.profile != 0;
+  const bool fp64 = h->prm.precision == DIC_FP64;
+  cudaEvent_t w0 = event_at(h, 5), w1 = event_at(h, 6);
+  if (!w0 || !w1) return fail(DIC_ECUDA, "event creation failed");
+  if (prof) cudaEventRecord(w0, s);
+  int rc = fp64 ? run_waves<double>(h, s) : run_waves<float>(h, s);
+  if (rc) return rc;
+  if (prof) cudaEventRecord(w1, s);
+  PointArrays pa = point_arrays(h);
+  DIC_CUDA(cudaMemsetAsync(h->counters + kAccepted, 0, sizeof(int32_t), s), "counter reset");
+  DIC_CUDA(launch_finalize_points(pa, h->nparams, h->prm.nan_unconverged, h->counters + kAccepted, s),
+           "finalize");
+  if (prof) cudaEventRecord(h->events[4], s);
+  DIC_CUDA(cudaMemcpyAsync(h->h_counters, h->counters, sizeof(int32_t) * kNumCounters,
+                           cudaMemcpyDeviceToHost, s), "counter read-back");
+  DIC_CUDA(cudaStreamSynchronize(s), "correlate");
+  const int64_t accepted = h->h_counters[kAccepted];
+  h->n_accepted = accepted;
+  h->has_results = true;
+  if (h->h_counters[kError]) return fail(DIC_ETIMEOUT, "a tile load did not complete in time");
+  if (prof) {
+    h->timing.prefilter_ms = elapsed(h->events[0], h->events[1]);
+    h->timing.setup_ms = elapsed(h->events[1], h->events[3]);
+    h->timing.seed_kernel_ms = elapsed(h->events[2], h->events[3]);
+    h->timing.waves_ms = elapsed(w0, w1);
+  }
+  if (accepted == 0) return fail(DIC_ENOSEED, "no point was accepted");
   return DIC_OK;
 }
 
@@ -634,10 +669,12 @@ int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void*
   if (static_cast<size_t>(n_seeds) > h->seed_cap) {
     dev_free(h->seed_xy);
     dev_free(h->seed_q);
-    h->seed_xy = h->seed_q = nullptr;
+    dev_free(h->seed_best);
+    h->seed_xy = h->seed_q = h->seed_best = nullptr;
     h->seed_cap = 0;
     if ((rc = dev_alloc(&h->seed_xy, 2 * static_cast<size_t>(n_seeds), "seeds")) ||
-        (rc = dev_alloc(&h->seed_q, static_cast<size_t>(n_seeds), "seeds")))
+        (rc = dev_alloc(&h->seed_q, static_cast<size_t>(n_seeds), "seeds")) ||
+        (rc = dev_alloc(&h->seed_best, static_cast<size_t>(n_seeds), "seeds")))
       return rc;
     h->seed_cap = n_seeds;
   }
@@ -659,34 +696,44 @@ int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void*
   SeedArgs sa{h->ref, h->def, h->W, h->H, h->S, R, n_seeds, h->seed_xy, h->seed_scores};
   DIC_CUDA(launch_seed_scores(sa, s), "seed search");
   if (prof) cudaEventRecord(h->events[3], s);
-  SeedCommitArgs ca{n_seeds, R, h->nparams, h->seed_q, h->seed_scores, h->p, h->status,
+  SeedCommitArgs ca{n_seeds, R, h->nparams, h->seed_q, h->seed_scores, h->seed_best, h->p, h->status,
                     h->wave, h->front[0], h->counters, h->roi_ok};
   DIC_CUDA(launch_seed_commit(ca, s), "seed commit");
 
-  cudaEvent_t w0 = event_at(h, 5), w1 = event_at(h, 6);
-  if (!w0 || !w1) return fail(DIC_ECUDA, "event creation failed");
-  if (prof) cudaEventRecord(w0, s);
-  rc = fp64 ? run_waves<double>(h, s) : run_waves<float>(h, s);
-  if (rc) return rc;
-  if (prof) cudaEventRecord(w1, s);
-  DIC_CUDA(cudaMemsetAsync(h->counters + kAccepted, 0, sizeof(int32_t), s), "counter reset");
-  DIC_CUDA(launch_finalize_points(pa, h->nparams, h->prm.nan_unconverged, h->counters + kAccepted, s),
-           "finalize");
-  if (prof) cudaEventRecord(h->events[4], s);
-  DIC_CUDA(cudaMemcpyAsync(h->h_counters, h->counters, sizeof(int32_t) * kNumCounters,
-                           cudaMemcpyDeviceToHost, s), "counter read-back");
-  DIC_CUDA(cudaStreamSynchronize(s), "correlate");
-  const int64_t accepted = h->h_counters[kAccepted];
-  h->n_accepted = accepted;
-  if (h->h_counters[kError]) return fail(DIC_ETIMEOUT, "a tile load did not complete in time");
-  if (prof) {
-    h->timing.prefilter_ms = elapsed(h->events[0], h->events[1]);
-    h->timing.setup_ms = elapsed(h->events[1], h->events[3]);
-    h->timing.seed_kernel_ms = elapsed(h->events[2], h->events[3]);
-    h->timing.waves_ms = elapsed(w0, w1);
+  return finish_run(h, s);
+}
+
+int dic_correlate_sequence(dic_handle* h, void* cuda_stream) {
+  if (!h) return fail(DIC_EINVAL, "handle is NULL");
+  g_last_error.clear();
+  if (!h->has_results) return fail(DIC_ESTATE, "dic_correlate_sequence needs an earlier correlation");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (h->plane_prec != h->prm.precision)
+    return fail(DIC_ESTATE, "the precision changed since the last correlation; correlate with seeds");
+  h->timing = dic_timing{};
+  const bool prof = h->prm.profile != 0;
+  const bool fp64 = h->prm.precision == DIC_FP64;
+  for (int i = 0; i < 5; ++i)
+    if (!event_at(h, i)) return fail(DIC_ECUDA, "event creation failed");
+  if (prof) cudaEventRecord(h->events[0], s);
+  int rc = DIC_OK;
+  if (h->ref_dirty) {
+    rc = fp64 ? prefilter<double>(h, h->ref, h->c_ref, s) : prefilter<float>(h, h->ref, h->c_ref, s);
+    if (rc) return rc;
+    h->ref_dirty = false;
   }
-  if (accepted == 0) return fail(DIC_ENOSEED, "no seed was accepted");
-  return DIC_OK;
+  if (h->def_dirty) {
+    rc = fp64 ? prefilter<double>(h, h->def, h->c_def, s) : prefilter<float>(h, h->def, h->c_def, s);
+    if (rc) return rc;
+    h->def_dirty = false;
+  }
+  if (prof) cudaEventRecord(h->events[1], s);
+  PointArrays pa = point_arrays(h);
+  DIC_CUDA(cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * kNumCounters, s), "counter reset");
+  if (prof) cudaEventRecord(h->events[2], s);
+  DIC_CUDA(launch_sequence_reset(pa, h->nparams, h->roi_ok, h->front[0], h->counters, s), "sequence reset");
+  if (prof) cudaEventRecord(h->events[3], s);
+  return finish_run(h, s);
 }
 
 int dic_get_results(dic_handle* h, dic_results* out, int32_t on_device) {

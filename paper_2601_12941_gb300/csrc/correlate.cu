@@ -157,8 +157,8 @@ __device__ void compose_inverse(C* p, const C* dp) {
     p[1] -= dp[1];
   } else if (NP == 6) {
     const C d2 = dp[2], d3 = dp[3], d4 = dp[4], d5 = dp[5];
-    const C det = (C(1) + d2) * (C(1) + d5) - d3 * d4;
-    const C i00 = (C(1) + d5) / det, i01 = -d3 / det, i10 = -d4 / det, i11 = (C(1) + d2) / det;
+    const C inv = C(1) / ((C(1) + d2) * (C(1) + d5) - d3 * d4);
+    const C i00 = (C(1) + d5) * inv, i01 = -d3 * inv, i10 = -d4 * inv, i11 = (C(1) + d2) * inv;
     const C e00 = -(i00 * d2 + i01 * d4), e01 = -(i00 * d3 + i01 * d5);
     const C e10 = -(i10 * d2 + i11 * d4), e11 = -(i10 * d3 + i11 * d5);
     const C a00 = C(1) + p[2], a01 = p[3], a10 = p[4], a11 = C(1) + p[5];
@@ -395,10 +395,12 @@ __device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int
 template <typename C, int NP>
 __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C r, C thr2, int lane) {
   if (out[2 + NP] > C(0.5)) return 5;
-  const C nu = out[0] / static_cast<C>(N);          // mean of g' = g - f0
-  const C dg = sqrt(fmax(out[1] - out[0] * nu, C(0)));
-  if (is_flat<C>(dg, nu + st.f0, N)) return 2;
-  const C ratio = st.delta_f / dg;
+  const C nu = out[0] * (C(1) / static_cast<C>(N));  // mean of g' = g - f0
+  const C dg2 = fmax(out[1] - out[0] * nu, C(0));
+  // flat: dg / sqrt(N) <= 1e-6 max(|mean|, 1), compared squared
+  const C gm = fmax(fabs(nu + st.f0), C(1));
+  if (dg2 <= C(1e-12) * static_cast<C>(N) * gm * gm) return 2;
+  const C ratio = st.delta_f * rsqrt(dg2);
   double bc = 0.0;
   if (lane < NP) bc = static_cast<double>(st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]));
   if (lane < NP) st.bvec[lane] = bc;
@@ -1030,6 +1032,29 @@ __global__ void reset_points_kernel(PointArrays pa, int nparams, const uint8_t* 
   }
 }
 
+// Next frame of a sequence: every point accepted in the previous run joins wave 0
+// and keeps its warp as the start; every other point is reset as for a new pair.
+__global__ void sequence_reset_kernel(PointArrays pa, int nparams, const uint8_t* roi_ok,
+                                      int32_t* front0, int32_t* counters) {
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < pa.n;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const bool in_roi = !(roi_ok && !roi_ok[q]);
+    const bool keep = in_roi && pa.status[q] == DIC_PT_OK;
+    if (!keep) {
+      pa.u[q] = 0.0;
+      pa.v[q] = 0.0;
+      for (int c = 0; c < nparams; ++c) pa.p[q * nparams + c] = 0.0;
+    }
+    pa.zncc[q] = nanf("");
+    pa.accept[q] = -1;
+    pa.iters[q] = 0;
+    pa.converged[q] = 0;
+    pa.status[q] = in_roi ? DIC_PT_NOT_REACHED : DIC_PT_NOT_IN_ROI;
+    pa.wave[q] = keep ? 0 : -1;
+    if (keep) front0[atomicAdd(&counters[kCount + 0], 1)] = static_cast<int32_t>(q);
+  }
+}
+
 __global__ void finalize_points_kernel(PointArrays pa, int nparams, int nan_rejected,
                                        int32_t* accepted) {
   int count = 0;
@@ -1131,6 +1156,14 @@ cudaError_t launch_reset_points(const PointArrays& pa, int nparams, const uint8_
   const int64_t blocks = (pa.n + 255) / 256;
   reset_points_kernel<<<static_cast<unsigned>(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(
       pa, nparams, roi_ok);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sequence_reset(const PointArrays& pa, int nparams, const uint8_t* roi_ok,
+                                  int32_t* front0, int32_t* counters, cudaStream_t s) {
+  const int64_t blocks = (pa.n + 255) / 256;
+  sequence_reset_kernel<<<static_cast<unsigned>(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(
+      pa, nparams, roi_ok, front0, counters);
   return cudaGetLastError();
 }
 

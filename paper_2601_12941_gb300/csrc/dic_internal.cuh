@@ -115,6 +115,7 @@ struct SeedCommitArgs {
   int n_seeds, R, nparams;
   const int32_t* seed_q;     // [n_seeds] point index of each snapped seed
   const double* scores;
+  int32_t* best;             // [n_seeds] scratch: best offset index per seed
   double* p;                 // [n_points][nparams]
   uint8_t* status;
   int32_t* wave;
@@ -150,6 +151,10 @@ cudaError_t launch_reset_points(const PointArrays& pa, int nparams, const uint8_
                                 cudaStream_t s);
 cudaError_t launch_finalize_points(const PointArrays& pa, int nparams, int nan_rejected,
                                    int32_t* accepted, cudaStream_t s);
+// wave 0 of a sequence frame: the points the previous run accepted, keeping their warps
+// (counters must be zero; counters[kCount] receives the size of front0)
+cudaError_t launch_sequence_reset(const PointArrays& pa, int nparams, const uint8_t* roi_ok,
+                                  int32_t* front0, int32_t* counters, cudaStream_t s);
 
 // ---------------------------------------------------------------- waves
 // Shared-memory tiles of the wave kernel: the coefficient window (bxc x byc

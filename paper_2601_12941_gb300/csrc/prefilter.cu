@@ -44,9 +44,20 @@ Taps<T> make_taps() {
   return t;
 }
 
+// outputs per thread along the filtered axis: each thread loads one run of
+// G + 2K inputs and produces G outputs from it
+template <typename T>
+struct OutputsPerThread;
+template <>
+struct OutputsPerThread<float> { static constexpr int kValue = 4; };
+template <>
+struct OutputsPerThread<double> { static constexpr int kValue = 2; };
+
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads) prefilter_kernel(PrefilterArgs<T> a, Taps<T> taps) {
+  constexpr int G = OutputsPerThread<T>::kValue;
   constexpr int IX = kTile + 2 * K;  // staged input tile width (and height)
+  constexpr int RUN = G + 2 * K;     // inputs behind G outputs
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* in = reinterpret_cast<T*>(smem_raw);  // [IX][IX]
   T* mid = in + IX * IX;                   // [IX][kTile] after the x pass
@@ -54,33 +65,53 @@ __global__ void __launch_bounds__(kThreads) prefilter_kernel(PrefilterArgs<T> a,
   const int64_t y0 = static_cast<int64_t>(blockIdx.y) * kTile;
   const int tid = threadIdx.x;
 
-  for (int e = tid; e < IX * IX; e += kThreads) {
-    const int iy = e / IX, ix = e % IX;
-    const int64_t gx = mirror_index(x0 - K + ix, a.W);
-    const int64_t gy = mirror_index(y0 - K + iy, a.H);
-    in[e] = load_gray<T>(a.src, gx, gy);
+  const bool inside = x0 - K >= 0 && y0 - K >= 0 && x0 + kTile + K <= a.W && y0 + kTile + K <= a.H;
+  if (inside) {
+    for (int e = tid; e < IX * IX; e += kThreads) {
+      const int iy = e / IX, ix = e % IX;
+      in[e] = load_gray<T>(a.src, x0 - K + ix, y0 - K + iy);
+    }
+  } else {
+    for (int e = tid; e < IX * IX; e += kThreads) {
+      const int iy = e / IX, ix = e % IX;
+      in[e] = load_gray<T>(a.src, mirror_index(x0 - K + ix, a.W), mirror_index(y0 - K + iy, a.H));
+    }
   }
   __syncthreads();
 
-  for (int e = tid; e < IX * kTile; e += kThreads) {
-    const int iy = e / kTile, c = e % kTile;
-    const T* row = in + iy * IX + c + K;
-    T acc = taps.h[0] * row[0];
+  // x pass: every staged row, G consecutive outputs per item
+  for (int e = tid; e < IX * (kTile / G); e += kThreads) {
+    const int iy = e / (kTile / G), c0 = (e % (kTile / G)) * G;
+    const T* row = in + iy * IX + c0;
+    T v[RUN];
 #pragma unroll
-    for (int m = 1; m <= K; ++m) acc += taps.h[m] * (row[-m] + row[m]);
-    mid[e] = acc;
+    for (int j = 0; j < RUN; ++j) v[j] = row[j];
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      T acc = taps.h[0] * v[m + K];
+#pragma unroll
+      for (int k = 1; k <= K; ++k) acc += taps.h[k] * (v[m + K - k] + v[m + K + k]);
+      mid[iy * kTile + c0 + m] = acc;
+    }
   }
   __syncthreads();
 
-  for (int e = tid; e < kTile * kTile; e += kThreads) {
-    const int r = e / kTile, c = e % kTile;
-    const int64_t gx = x0 + c, gy = y0 + r;
-    if (gx >= a.W || gy >= a.H) continue;
-    const T* col = mid + (r + K) * kTile + c;
-    T acc = taps.h[0] * col[0];
+  // y pass: G consecutive output rows of one column per item
+  for (int e = tid; e < kTile * (kTile / G); e += kThreads) {
+    const int c = e % kTile, r0 = (e / kTile) * G;
+    const T* colp = mid + r0 * kTile + c;
+    T v[RUN];
 #pragma unroll
-    for (int m = 1; m <= K; ++m) acc += taps.h[m] * (col[-m * kTile] + col[m * kTile]);
-    a.coef[gy * a.ldc + gx] = acc;
+    for (int j = 0; j < RUN; ++j) v[j] = colp[j * kTile];
+    const int64_t gx = x0 + c;
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      T acc = taps.h[0] * v[m + K];
+#pragma unroll
+      for (int k = 1; k <= K; ++k) acc += taps.h[k] * (v[m + K - k] + v[m + K + k]);
+      const int64_t gy = y0 + r0 + m;
+      if (gx < a.W && gy < a.H) a.coef[gy * a.ldc + gx] = acc;
+    }
   }
 }
 

@@ -98,6 +98,61 @@ __global__ void __launch_bounds__(128) seed_scores_kernel(SeedArgs a) {
   }
 }
 
+// one block per seed: the best offset (larger C, then smaller |du|+|dv|, then
+// smaller dv, then smaller du) into best[s]; -1 if no offset is usable, -2 if the
+// reference subset is flat
+__global__ void __launch_bounds__(256) seed_best_kernel(SeedCommitArgs a) {
+  const int s = blockIdx.x;
+  const int side = 2 * a.R + 1;
+  const double* sc = a.scores + static_cast<int64_t>(s) * side * side;
+  double bc = 0.0;
+  int bkey = 0x7fffffff, be = -1, flat = 0;
+  for (int e = threadIdx.x; e < side * side; e += blockDim.x) {
+    const double c = sc[e];
+    if (c == kFlatRef) flat = 1;
+    if (c < -1.5) continue;
+    const int du = e % side - a.R, dv = e / side - a.R;
+    const int key = ((abs(du) + abs(dv)) * (side + 1) + (dv + a.R)) * (side + 1) + (du + a.R);
+    if (be < 0 || c > bc || (c == bc && key < bkey)) {
+      be = e;
+      bc = c;
+      bkey = key;
+    }
+  }
+  __shared__ double s_c[8];
+  __shared__ int s_k[8], s_e[8], s_f[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    const double oc = __shfl_xor_sync(0xffffffffu, bc, o);
+    const int ok = __shfl_xor_sync(0xffffffffu, bkey, o);
+    const int oe = __shfl_xor_sync(0xffffffffu, be, o);
+    flat |= __shfl_xor_sync(0xffffffffu, flat, o);
+    if (oe >= 0 && (be < 0 || oc > bc || (oc == bc && ok < bkey))) {
+      bc = oc;
+      bkey = ok;
+      be = oe;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_c[warp] = bc;
+    s_k[warp] = bkey;
+    s_e[warp] = be;
+    s_f[warp] = flat;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < static_cast<int>(blockDim.x / 32); ++w) {
+      flat |= s_f[w];
+      if (s_e[w] >= 0 && (be < 0 || s_c[w] > bc || (s_c[w] == bc && s_k[w] < bkey))) {
+        bc = s_c[w];
+        bkey = s_k[w];
+        be = s_e[w];
+      }
+    }
+    a.best[s] = be >= 0 ? be : (flat ? -2 : -1);
+  }
+}
+
 // one thread: seeds in the order given, duplicates and out-of-ROI seeds skipped
 __global__ void seed_commit_kernel(SeedCommitArgs a) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -108,26 +163,9 @@ __global__ void seed_commit_kernel(SeedCommitArgs a) {
     if (a.roi_ok && !a.roi_ok[q]) continue;
     if (a.wave[q] >= 0) continue;
     a.wave[q] = 0;
-    const double* sc = a.scores + static_cast<int64_t>(s) * side * side;
-    int best = -1;
-    double bc = 0.0;
-    int bkey = 0;
-    bool flat = false;
-    for (int e = 0; e < side * side; ++e) {
-      const double c = sc[e];
-      if (c == kFlatRef) flat = true;
-      if (c < -1.5) continue;
-      const int du = e % side - a.R, dv = e / side - a.R;
-      // larger C, then smaller |du|+|dv|, then smaller dv, then smaller du
-      const int key = ((abs(du) + abs(dv)) * (side + 1) + (dv + a.R)) * (side + 1) + (du + a.R);
-      if (best < 0 || c > bc || (c == bc && key < bkey)) {
-        best = e;
-        bc = c;
-        bkey = key;
-      }
-    }
+    const int best = a.best[s];
     if (best < 0) {
-      a.status[q] = flat ? DIC_PT_FLAT : DIC_PT_OUT_OF_BOUNDS;
+      a.status[q] = best == -2 ? DIC_PT_FLAT : DIC_PT_OUT_OF_BOUNDS;
       continue;
     }
     double* p = a.p + static_cast<int64_t>(q) * a.nparams;
@@ -156,6 +194,7 @@ cudaError_t launch_seed_scores(const SeedArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_seed_commit(const SeedCommitArgs& a, cudaStream_t s) {
+  seed_best_kernel<<<a.n_seeds, 256, 0, s>>>(a);
   seed_commit_kernel<<<1, 32, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -41,7 +41,7 @@ constexpr size_t kScratchBytes = 2 * kPlaneBytes                               /
                                  + 2 * align_up(sizeof(int32_t) * kPointsPlus)  // frontier lists
                                  + align_up(sizeof(int32_t) * kPointsPlus)      // wave sizes
                                  + align_up(sizeof(int32_t) * kNumCounters)     // counters
-                                 + align_up(sizeof(int32_t) * 3 * DIC_STATIC_MAX_SEEDS)   // seed centres, indices
+                                 + align_up(sizeof(int32_t) * 4 * DIC_STATIC_MAX_SEEDS)   // seed centres, indices, best
                                  + align_up(sizeof(double) * DIC_STATIC_MAX_SEEDS * kSide * kSide);
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
@@ -201,11 +201,12 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   int32_t* front1 = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kPointsPlus));
   int32_t* wave_sizes = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kPointsPlus));
   int32_t* counters = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * kNumCounters));
-  int32_t* seed_buf = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 3 * DIC_STATIC_MAX_SEEDS));
+  int32_t* seed_buf = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * 4 * DIC_STATIC_MAX_SEEDS));
   double* scores = reinterpret_cast<double*>(take(sizeof(double) * DIC_STATIC_MAX_SEEDS * kSide * kSide));
   if (off > kScratchBytes) return sfail(DIC_EINVAL, "scratch layout exceeds the static array");
   int32_t* seed_xy = seed_buf;
   int32_t* seed_q = seed_buf + 2 * DIC_STATIC_MAX_SEEDS;
+  int32_t* seed_best = seed_buf + 3 * DIC_STATIC_MAX_SEEDS;
 
   // ---- spline coefficients of both images
   GrayPlane gref{ref->data, ref->row_stride_bytes ? ref->row_stride_bytes : static_cast<int64_t>(W * es),
@@ -247,8 +248,8 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   const int R = params->search_radius;
   SCUDA(launch_seed_scores(SeedArgs{gref, gdef, W, H, subset_size, R, n_seeds, seed_xy, scores}, s),
         "seed search");
-  SCUDA(launch_seed_commit(SeedCommitArgs{n_seeds, R, nparams, seed_q, scores, out->p, out->status, out->wave,
-                                          front0, counters, nullptr},
+  SCUDA(launch_seed_commit(SeedCommitArgs{n_seeds, R, nparams, seed_q, scores, seed_best, out->p, out->status,
+                                          out->wave, front0, counters, nullptr},
                            s),
         "seed commit");
 
