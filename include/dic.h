@@ -28,7 +28,8 @@
  *     and may be reused as soon as it returns.
  *   - Result pointers are owned by the handle and stay valid until the next
  *     dic_correlate or dic_destroy on it.
- *   - A handle is used by one host thread at a time.
+ *   - A handle is used by one host thread at a time. Different handles may be
+ *     used at the same time from different host threads, each on its own stream.
  */
 #ifndef DIC_H
 #define DIC_H
@@ -182,7 +183,9 @@ int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void*
 int dic_correlate_sequence(dic_handle* h, void* cuda_stream);
 
 /* Fills *out with device pointers (on_device = 1) or with pointers to host copies
- * owned by the handle (on_device = 0; copied during the call). */
+ * owned by the handle (on_device = 0; copied during the call, ordered on the
+ * stream of the last correlation). DIC_ESTATE before the first correlation and
+ * after dic_set_subsets. */
 int dic_get_results(dic_handle* h, dic_results* out, int32_t on_device);
 
 /* Device pointer to the spline coefficients of the reference (which = 0) or the
@@ -194,6 +197,47 @@ int dic_get_coefficients(const dic_handle* h, int32_t which, const void** plane,
 
 /* Stage timings of the last dic_correlate; zeros unless params.profile = 1. */
 int dic_get_timing(const dic_handle* h, dic_timing* out);
+
+/* ---- serving support (the paper has no counterpart) ----------------------
+ *
+ * A server that keeps one handle per reference image answers later jobs on the
+ * same reference without uploading or prefiltering it again, whatever their
+ * subset settings, and admits jobs against a device-memory budget. */
+
+/* Re-grids a handle for another subset size, step, shape function or ROI (the
+ * arguments and checks of dic_create) and keeps its images and the reference's
+ * spline coefficients resident. Per-point arrays are reused when large enough,
+ * re-allocated otherwise. The previous results and the sequence state are
+ * dropped: dic_get_results and dic_correlate_sequence give DIC_ESTATE until the
+ * next dic_correlate. Errors: DIC_EINVAL (the handle is unchanged); DIC_ENOMEM
+ * or DIC_ECUDA (the handle keeps its images but has no grid, and dic_correlate
+ * gives DIC_ESTATE, until a later dic_set_subsets succeeds). */
+int dic_set_subsets(dic_handle* h, const dic_image* roi, int32_t subset_size, int32_t subset_step,
+                    int32_t shape_fn);
+
+/* Device bytes that dic_create with these arguments followed by one dic_correlate
+ * with n_seeds seeds requests: owned copies of host images (on_device = 0, rows
+ * padded to 128 bytes), the two coefficient planes in params' precision, the
+ * per-point arrays, the ROI flags when has_roi, and the seed-search buffers. Only
+ * width, height, dtype and on_device of ref and def are read (data may be NULL).
+ * Not included: the driver's rounding of each allocation to its granularity, and
+ * the transient copy of the ROI mask while flags are computed. Errors: DIC_EINVAL. */
+int dic_estimate_device_bytes(const dic_image* ref, const dic_image* def, int32_t has_roi,
+                              int32_t subset_size, int32_t subset_step, int32_t shape_fn,
+                              const dic_params* params, int32_t n_seeds, int64_t* bytes);
+
+/* Device bytes that h holds after dic_set_subsets with these settings,
+ * dic_set_deformed(def) and one dic_correlate with n_seeds seeds: the reference
+ * copy and, at an unchanged precision, the coefficient planes are kept, and
+ * every other buffer keeps its current capacity unless the new settings need
+ * more. Only width, height, dtype and on_device of def are read. Errors:
+ * DIC_EINVAL. */
+int dic_estimate_regrid_bytes(const dic_handle* h, const dic_image* def, int32_t has_roi,
+                              int32_t subset_size, int32_t subset_step, int32_t shape_fn,
+                              const dic_params* params, int32_t n_seeds, int64_t* bytes);
+
+/* Device bytes the handle holds now: the requested sizes of its live allocations. */
+int dic_get_device_bytes(const dic_handle* h, int64_t* bytes);
 
 /* ---- allocation-free correlation (the paper has no counterpart) ----------
  *

@@ -26,7 +26,8 @@ N_PARAMS = {DIC_RIGID: 2, DIC_AFFINE: 6, DIC_QUADRATIC: 12}
 EXPORTS = ("dic_default_params", "dic_create", "dic_set_params", "dic_get_params",
            "dic_set_reference", "dic_set_deformed", "dic_correlate", "dic_get_results",
            "dic_get_coefficients", "dic_get_timing", "dic_destroy", "dic_last_error",
-           "dic_correlate_static", "dic_correlate_sequence")
+           "dic_correlate_static", "dic_correlate_sequence", "dic_set_subsets",
+           "dic_estimate_device_bytes", "dic_estimate_regrid_bytes", "dic_get_device_bytes")
 
 
 class DicImage(ctypes.Structure):
@@ -117,6 +118,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                          ctypes.c_int32, P(DicParams), P(ctypes.c_int32), ctypes.c_int32,
                                          P(DicStaticOutputs), vp, ctypes.c_char_p, ctypes.c_int32]
     lib.dic_correlate_static.restype = ctypes.c_int
+    lib.dic_set_subsets.argtypes = [vp, P(DicImage), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    lib.dic_set_subsets.restype = ctypes.c_int
+    lib.dic_estimate_device_bytes.argtypes = [P(DicImage), P(DicImage), ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_int32, P(DicParams), ctypes.c_int32,
+                                              P(ctypes.c_int64)]
+    lib.dic_estimate_device_bytes.restype = ctypes.c_int
+    lib.dic_estimate_regrid_bytes.argtypes = [vp, P(DicImage), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, P(DicParams), ctypes.c_int32, P(ctypes.c_int64)]
+    lib.dic_estimate_regrid_bytes.restype = ctypes.c_int
+    lib.dic_get_device_bytes.argtypes = [vp, P(ctypes.c_int64)]
+    lib.dic_get_device_bytes.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -147,13 +159,7 @@ def make_image(arr, bf16: bool = False) -> tuple:
     t = arr
     if t.dim() != 2 or not t.is_cuda or t.stride(1) != 1:
         raise ValueError("device images are 2-D CUDA tensors with contiguous rows")
-    kinds = {torch.uint8: DIC_U8, torch.int16: DIC_U16, torch.bfloat16: DIC_BF16,
-             torch.float32: DIC_F32, torch.float64: DIC_F64}
-    if hasattr(torch, "uint16"):
-        kinds[torch.uint16] = DIC_U16
-    dt = kinds.get(t.dtype)
-    if dt is None:
-        raise ValueError("unsupported tensor dtype %s" % t.dtype)
+    dt = image_dtype_code(t)
     return DicImage(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0) * t.element_size(), dt, 1), t
 
 
@@ -165,15 +171,71 @@ def dic_create(ref, deformed, roi, subset_size, subset_step, shape_fn, interp=DI
     lib = load()
     ri, rk = make_image(ref)
     di, dk = make_image(deformed)
-    mask = None
-    if roi is not None:
-        if isinstance(roi, np.ndarray):
-            roi = np.ascontiguousarray(roi.astype(np.uint8))
-        mi, mask = make_image(roi)
+    mi, mask = _roi_image(roi)
     h = ctypes.c_void_p()
     _check(lib.dic_create(ctypes.byref(ri), ctypes.byref(di), ctypes.byref(mi) if mask is not None else None,
                           subset_size, subset_step, shape_fn, interp, ctypes.byref(h)))
     return h, (rk, dk)
+
+
+def _roi_image(roi):
+    if roi is None:
+        return None, None
+    if isinstance(roi, np.ndarray):
+        roi = np.ascontiguousarray(roi.astype(np.uint8))
+    return make_image(roi)
+
+
+def dic_set_subsets(h, roi, subset_size, subset_step, shape_fn):
+    mi, keep = _roi_image(roi)
+    _check(load().dic_set_subsets(h, ctypes.byref(mi) if mi is not None else None, subset_size, subset_step,
+                                  shape_fn))
+
+
+def image_desc(width, height, dtype, on_device) -> DicImage:
+    """A dic_image that describes an image without data (for dic_estimate_device_bytes)."""
+    return DicImage(None, width, height, 0, dtype, 1 if on_device else 0)
+
+
+def image_dtype_code(arr) -> int:
+    """The dic_dtype of a numpy array or CUDA tensor, as make_image reads it."""
+    if isinstance(arr, np.ndarray):
+        dt = _NP_DTYPES.get(arr.dtype)
+        if dt is None:
+            raise ValueError("unsupported image dtype %s" % arr.dtype)
+        return dt
+    import torch
+
+    kinds = {torch.uint8: DIC_U8, torch.int16: DIC_U16, torch.bfloat16: DIC_BF16,
+             torch.float32: DIC_F32, torch.float64: DIC_F64}
+    if hasattr(torch, "uint16"):
+        kinds[torch.uint16] = DIC_U16
+    if arr.dtype not in kinds:
+        raise ValueError("unsupported tensor dtype %s" % arr.dtype)
+    return kinds[arr.dtype]
+
+
+def dic_estimate_device_bytes(ref: DicImage, deformed: DicImage, has_roi, subset_size, subset_step, shape_fn,
+                              prm: DicParams, n_seeds) -> int:
+    out = ctypes.c_int64(0)
+    _check(load().dic_estimate_device_bytes(ctypes.byref(ref), ctypes.byref(deformed), 1 if has_roi else 0,
+                                            subset_size, subset_step, shape_fn, ctypes.byref(prm), n_seeds,
+                                            ctypes.byref(out)))
+    return out.value
+
+
+def dic_estimate_regrid_bytes(h, deformed: DicImage, has_roi, subset_size, subset_step, shape_fn,
+                              prm: DicParams, n_seeds) -> int:
+    out = ctypes.c_int64(0)
+    _check(load().dic_estimate_regrid_bytes(h, ctypes.byref(deformed), 1 if has_roi else 0, subset_size,
+                                            subset_step, shape_fn, ctypes.byref(prm), n_seeds, ctypes.byref(out)))
+    return out.value
+
+
+def dic_get_device_bytes(h) -> int:
+    out = ctypes.c_int64(0)
+    _check(load().dic_get_device_bytes(h, ctypes.byref(out)))
+    return out.value
 
 
 def dic_set_params(h, params: DicParams):
@@ -324,6 +386,15 @@ class Correlation:
 
     def set_deformed(self, deformed):
         self._keep = (self._keep[0], dic_set_deformed(self.h, deformed))
+
+    def set_subsets(self, subset_size, subset_step, shape, roi=None):
+        """Re-grid for other subset settings; the reference stays resident."""
+        shape = SHAPES[shape] if isinstance(shape, str) else shape
+        dic_set_subsets(self.h, roi, subset_size, subset_step, shape)
+        self.shape = shape
+
+    def device_bytes(self) -> int:
+        return dic_get_device_bytes(self.h)
 
     def run(self, seeds, stream_ptr: int = 0):
         dic_correlate(self.h, seeds, stream_ptr)

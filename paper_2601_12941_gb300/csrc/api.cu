@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "dic_internal.cuh"
@@ -127,6 +128,15 @@ struct dic_handle {
   // host copies of the results
   void* h_res = nullptr;
   size_t h_res_bytes = 0;
+  // device allocations owned by the handle and their requested sizes
+  std::unordered_map<void*, size_t> allocs;
+  int64_t device_bytes = 0;
+  // capacity of the per-point arrays (points; elements of p)
+  int64_t pts_cap = 0;
+  int64_t p_cap = 0;
+  bool grid_ok = false;
+  // stream of the last correlation (result read-back is ordered on it)
+  cudaStream_t last_stream = nullptr;
   // last run
   bool has_results = false;
   int n_waves = 0;
@@ -141,18 +151,40 @@ namespace {
 
 constexpr int kBatchSlots = 2;
 
+// Device allocation owned by a handle: counted in device_bytes until hfree.
+template <typename P>
+int halloc(dic_handle* h, P** ptr, size_t count, const char* what) {
+  int rc = dev_alloc(ptr, count, what);
+  if (rc) return rc;
+  const size_t bytes = count * sizeof(P) > 0 ? count * sizeof(P) : 1;
+  h->allocs[static_cast<void*>(*ptr)] = bytes;
+  h->device_bytes += static_cast<int64_t>(bytes);
+  return DIC_OK;
+}
+
+template <typename P>
+void hfree(dic_handle* h, P*& ptr) {
+  if (!ptr) return;
+  auto it = h->allocs.find(static_cast<void*>(ptr));
+  if (it != h->allocs.end()) {
+    h->device_bytes -= static_cast<int64_t>(it->second);
+    h->allocs.erase(it);
+  }
+  dev_free(ptr);
+  ptr = nullptr;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // initialised once, thread-safely, on first use
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -195,8 +227,15 @@ int check_image(const dic_image* im, const char* name) {
   return DIC_OK;
 }
 
-// Adopts a device image or copies a host image into an owned device buffer.
-int bind_image(const dic_image* im, GrayPlane* plane, void** owned, int* dtype_out) {
+// owned image copies get a 128-byte row pitch so that tiles can be loaded by TMA
+size_t owned_pitch(const dic_image* im) {
+  const size_t row_bytes = static_cast<size_t>(im->width) * dtype_size(im->dtype);
+  return (row_bytes + 127) & ~static_cast<size_t>(127);
+}
+
+// Adopts a device image or copies a host image into a device buffer; the buffer
+// is tracked by the handle when h is given, else the caller frees it.
+int bind_image(dic_handle* h, const dic_image* im, GrayPlane* plane, void** owned, int* dtype_out) {
   const size_t es = dtype_size(im->dtype);
   const int64_t stride = im->row_stride_bytes ? im->row_stride_bytes : im->width * static_cast<int64_t>(es);
   const size_t row_bytes = static_cast<size_t>(im->width) * es;
@@ -204,11 +243,13 @@ int bind_image(const dic_image* im, GrayPlane* plane, void** owned, int* dtype_o
     plane->data = im->data;
     plane->stride = stride;
   } else {
-    // owned copies get a 128-byte row pitch so that tiles can be loaded by TMA
-    const size_t pitch = (row_bytes + 127) & ~static_cast<size_t>(127);
+    const size_t pitch = owned_pitch(im);
     if (!*owned) {
-      int rc = dev_alloc(reinterpret_cast<uint8_t**>(owned), pitch * im->height, "image buffer");
+      uint8_t* buf = nullptr;
+      int rc = h ? halloc(h, &buf, pitch * im->height, "image buffer")
+                 : dev_alloc(&buf, pitch * im->height, "image buffer");
       if (rc) return rc;
+      *owned = buf;
     }
     DIC_CUDA(cudaMemcpy2D(*owned, pitch, im->data, stride, row_bytes, im->height, cudaMemcpyHostToDevice),
              "image upload");
@@ -221,9 +262,8 @@ int bind_image(const dic_image* im, GrayPlane* plane, void** owned, int* dtype_o
 }
 
 void free_planes(dic_handle* h) {
-  dev_free(h->c_ref);
-  dev_free(h->c_def);
-  h->c_ref = h->c_def = nullptr;
+  hfree(h, h->c_ref);
+  hfree(h, h->c_def);
   h->plane_prec = -1;
 }
 
@@ -234,10 +274,14 @@ int ensure_planes(dic_handle* h) {
   const size_t es = prec == DIC_FP64 ? sizeof(double) : sizeof(float);
   h->ldc = (h->W + 31) & ~31;
   const size_t bytes = es * static_cast<size_t>(h->ldc) * h->H;
-  int rc = dev_alloc(reinterpret_cast<uint8_t**>(&h->c_ref), bytes, "reference coefficients");
+  uint8_t* cr = nullptr;
+  uint8_t* cd = nullptr;
+  int rc = halloc(h, &cr, bytes, "reference coefficients");
   if (rc) return rc;
-  rc = dev_alloc(reinterpret_cast<uint8_t**>(&h->c_def), bytes, "deformed coefficients");
+  h->c_ref = cr;
+  rc = halloc(h, &cd, bytes, "deformed coefficients");
   if (rc) return rc;
+  h->c_def = cd;
   h->plane_prec = prec;
   h->ref_dirty = h->def_dirty = true;
   return DIC_OK;
@@ -381,11 +425,11 @@ int run_waves(dic_handle* h, cudaStream_t s) {
     slot = (slot + 1) % kBatchSlots;
     if (batch < 32) batch *= 2;
   }
-  DIC_CUDA(cudaStreamSynchronize(s), "wave loop");
   // last non-empty wave
   std::vector<int32_t> sizes(static_cast<size_t>(launched));
-  DIC_CUDA(cudaMemcpy(sizes.data(), h->wave_sizes, sizeof(int32_t) * launched, cudaMemcpyDeviceToHost),
+  DIC_CUDA(cudaMemcpyAsync(sizes.data(), h->wave_sizes, sizeof(int32_t) * launched, cudaMemcpyDeviceToHost, s),
            "wave sizes");
+  DIC_CUDA(cudaStreamSynchronize(s), "wave loop");
   int nw = 0;
   int64_t attempted = 0;
   for (int64_t k = 0; k < launched; ++k)
@@ -406,54 +450,160 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   return DIC_OK;
 }
 
-int alloc_points(dic_handle* h) {
+void free_points(dic_handle* h) {
+  hfree(h, h->x);
+  hfree(h, h->y);
+  hfree(h, h->u);
+  hfree(h, h->v);
+  hfree(h, h->zncc);
+  hfree(h, h->accept);
+  hfree(h, h->iters);
+  hfree(h, h->wave);
+  hfree(h, h->conv);
+  hfree(h, h->status);
+  hfree(h, h->front[0]);
+  hfree(h, h->front[1]);
+  hfree(h, h->wave_sizes);
+  h->pts_cap = 0;
+}
+
+// Per-point arrays for the current grid (kept when large enough) and the subset
+// centres written on the device.
+int size_points(dic_handle* h) {
   const size_t n = static_cast<size_t>(h->npts);
   int rc;
-  if ((rc = dev_alloc(&h->x, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->y, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->u, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->v, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->p, n * h->nparams, "points"))) return rc;
-  if ((rc = dev_alloc(&h->zncc, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->accept, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->iters, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->wave, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->conv, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->status, n, "points"))) return rc;
-  if ((rc = dev_alloc(&h->front[0], n + 1, "frontier"))) return rc;
-  if ((rc = dev_alloc(&h->front[1], n + 1, "frontier"))) return rc;
-  if ((rc = dev_alloc(&h->counters, kNumCounters, "counters"))) return rc;
-  if ((rc = dev_alloc(&h->wave_sizes, n + 2, "wave sizes"))) return rc;
-  void* pinned = nullptr;
-  DIC_CUDA(cudaMallocHost(&pinned, sizeof(int32_t) * kNumCounters * kBatchSlots), "pinned counters");
-  h->h_counters = static_cast<int32_t*>(pinned);
-  std::vector<int32_t> gx(n), gy(n);
-  for (size_t q = 0; q < n; ++q) {
-    gx[q] = h->r + static_cast<int32_t>(q % h->nx) * h->step;
-    gy[q] = h->r + static_cast<int32_t>(q / h->nx) * h->step;
+  if (h->npts > h->pts_cap) {
+    free_points(h);
+    if ((rc = halloc(h, &h->x, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->y, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->u, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->v, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->zncc, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->accept, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->iters, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->wave, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->conv, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->status, n, "points"))) return rc;
+    if ((rc = halloc(h, &h->front[0], n + 1, "frontier"))) return rc;
+    if ((rc = halloc(h, &h->front[1], n + 1, "frontier"))) return rc;
+    if ((rc = halloc(h, &h->wave_sizes, n + 2, "wave sizes"))) return rc;
+    h->pts_cap = h->npts;
   }
-  DIC_CUDA(cudaMemcpy(h->x, gx.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice), "grid upload");
-  DIC_CUDA(cudaMemcpy(h->y, gy.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice), "grid upload");
+  const int64_t np = h->npts * h->nparams;
+  if (np > h->p_cap) {
+    hfree(h, h->p);
+    h->p_cap = 0;
+    if ((rc = halloc(h, &h->p, static_cast<size_t>(np), "points"))) return rc;
+    h->p_cap = np;
+  }
+  if (!h->counters && (rc = halloc(h, &h->counters, kNumCounters, "counters"))) return rc;
+  if (!h->h_counters) {
+    void* pinned = nullptr;
+    DIC_CUDA(cudaMallocHost(&pinned, sizeof(int32_t) * kNumCounters * kBatchSlots), "pinned counters");
+    h->h_counters = static_cast<int32_t*>(pinned);
+  }
+  DIC_CUDA(launch_grid_points(h->x, h->y, h->r, h->step, h->nx, h->npts, 0), "grid");
+  DIC_CUDA(cudaStreamSynchronize(0), "grid");
   return DIC_OK;
 }
 
-void release(dic_handle* h) {
-  if (!h) return;
-  free_planes(h);
-  dev_free(h->ref_owned);
-  dev_free(h->def_owned);
-  dev_free(h->roi_ok);
-  void* ptrs[] = {h->x,     h->y,        h->u,    h->v,      h->p,          h->zncc,
-                  h->accept, h->iters,   h->wave, h->conv,   h->status,     h->front[0],
-                  h->front[1], h->counters, h->wave_sizes, h->seed_xy, h->seed_q, h->seed_best, h->seed_scores};
-  for (void* q : ptrs) dev_free(q);
-  if (h->h_counters) cudaFreeHost(h->h_counters);
-  if (h->h_res) cudaFreeHost(h->h_res);
-  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-  for (cudaEvent_t e : h->wave_events) cudaEventDestroy(e);
-  for (cudaEvent_t e : h->batch_ev)
-    if (e) cudaEventDestroy(e);
-  delete h;
+// Subset geometry checks shared by dic_create and dic_set_subsets.
+int check_subsets(int W, int H, const dic_image* roi, int32_t subset_size, int32_t subset_step,
+                  int32_t shape_fn) {
+  if (subset_size < 3 || subset_size > kMaxSubset || subset_size % 2 == 0)
+    return fail(DIC_EINVAL, "subset_size %d must be odd and in [3, %d]", subset_size, kMaxSubset);
+  if (subset_size > W || subset_size > H) return fail(DIC_EINVAL, "subset_size %d exceeds the image", subset_size);
+  if (subset_step < 1) return fail(DIC_EINVAL, "subset_step %d must be >= 1", subset_step);
+  if (shape_fn != DIC_RIGID && shape_fn != DIC_AFFINE && shape_fn != DIC_QUADRATIC)
+    return fail(DIC_EINVAL, "unknown shape function %d", shape_fn);
+  if (roi) {
+    int rc = check_image(roi, "roi");
+    if (rc) return rc;
+    if (roi->dtype != DIC_U8) return fail(DIC_EINVAL, "roi mask must be DIC_U8");
+    if (roi->width != W || roi->height != H) return fail(DIC_EINVAL, "roi mask size differs from the images");
+  }
+  return DIC_OK;
+}
+
+// Grid, per-point arrays and ROI flags for (subset_size, subset_step, shape_fn);
+// the images and coefficient planes are kept.
+int configure_subsets(dic_handle* h, const dic_image* roi, int32_t subset_size, int32_t subset_step,
+                      int32_t shape_fn) {
+  h->grid_ok = false;
+  h->has_results = false;
+  h->n_waves = 0;
+  h->n_accepted = 0;
+  h->S = subset_size;
+  h->r = (subset_size - 1) / 2;
+  h->step = subset_step;
+  h->shape = shape_fn;
+  h->nparams = nparams_of(shape_fn);
+  h->nx = (h->W - 1 - 2 * h->r) / h->step + 1;
+  h->ny = (h->H - 1 - 2 * h->r) / h->step + 1;
+  h->npts = static_cast<int64_t>(h->nx) * h->ny;
+  int rc = size_points(h);
+  if (rc) return rc;
+  hfree(h, h->roi_ok);
+  if (roi) {
+    GrayPlane mask{};
+    void* owned = nullptr;
+    int dt = 0;
+    if ((rc = halloc(h, &h->roi_ok, static_cast<size_t>(h->npts), "roi flags")) ||
+        (rc = bind_image(nullptr, roi, &mask, &owned, &dt))) {
+      dev_free(owned);
+      return rc;
+    }
+    RoiArgs ra{mask, h->S, h->r, h->step, h->nx, h->ny, h->roi_ok};
+    cudaError_t e = launch_roi_flags(ra, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    dev_free(owned);
+    if (e != cudaSuccess) return cuda_fail(e, "roi flags");
+  }
+  h->grid_ok = true;
+  return DIC_OK;
+}
+
+// Device bytes a handle holds after one correlation with these settings: the sum
+// of halloc sizes. With cur given, the handle is re-gridded rather than created:
+// the reference copy is kept, and every array keeps its capacity unless it is too
+// small, the same rules as configure_subsets, replace_image and dic_correlate.
+int64_t footprint(const dic_handle* cur, const dic_image* ref, const dic_image* def, bool roi, int S, int step,
+                  int shape, int precision, int n_seeds, int R) {
+  const int64_t W = ref->width, H = ref->height;
+  const int r = (S - 1) / 2;
+  const int64_t n = ((W - 1 - 2 * r) / step + 1) * ((H - 1 - 2 * r) / step + 1);
+  const int64_t np = nparams_of(shape);
+  const int64_t ldc = (W + 31) & ~static_cast<int64_t>(31);
+  const int64_t side = 2 * static_cast<int64_t>(R) + 1;
+  const int64_t plane_bytes = 2 * (precision == DIC_FP64 ? 8 : 4) * ldc * H;
+  const int64_t per_point = 4 + 4 + 8 + 8 + 4 + 8 + 4 + 4 + 1 + 1;  // x y u v zncc accept iters wave conv status
+  auto points_bytes = [&](int64_t m) { return m * per_point + 2 * 4 * (m + 1) + 4 * (m + 2); };
+  auto owned_bytes = [&](const dic_handle* h, const void* owned) -> int64_t {
+    auto it = h->allocs.find(const_cast<void*>(owned));
+    return it == h->allocs.end() ? 0 : static_cast<int64_t>(it->second);
+  };
+  int64_t b = 4 * kNumCounters + (roi ? n : 0);
+  if (!cur) {
+    if (!ref->on_device) b += static_cast<int64_t>(owned_pitch(ref)) * H;
+    if (!def->on_device) b += static_cast<int64_t>(owned_pitch(def)) * H;
+    b += plane_bytes + points_bytes(n) + 8 * n * np;
+    b += static_cast<int64_t>(n_seeds) * (8 + 4 + 4) + 8 * n_seeds * side * side;
+    return b;
+  }
+  b += cur->ref_owned ? owned_bytes(cur, cur->ref_owned) : 0;
+  if (!def->on_device)
+    b += (cur->def_owned && dtype_size(def->dtype) == dtype_size(cur->def_dtype))
+             ? owned_bytes(cur, cur->def_owned)
+             : static_cast<int64_t>(owned_pitch(def)) * H;
+  b += cur->plane_prec == precision ? owned_bytes(cur, cur->c_ref) + owned_bytes(cur, cur->c_def) : plane_bytes;
+  b += points_bytes(n > cur->pts_cap ? n : cur->pts_cap);
+  b += 8 * (n * np > cur->p_cap ? n * np : cur->p_cap);
+  const int64_t sc = static_cast<int64_t>(n_seeds) > static_cast<int64_t>(cur->seed_cap)
+                         ? n_seeds : static_cast<int64_t>(cur->seed_cap);
+  const int64_t scores = n_seeds * side * side > static_cast<int64_t>(cur->score_cap)
+                             ? n_seeds * side * side : static_cast<int64_t>(cur->score_cap);
+  b += sc * (8 + 4 + 4) + 8 * scores;
+  return b;
 }
 
 int validate_params(const dic_params* p) {
@@ -467,6 +617,35 @@ int validate_params(const dic_params* p) {
     return fail(DIC_EINVAL, "unknown precision %d", p->precision);
   return DIC_OK;
 }
+
+int check_estimate_args(const dic_image* ref, const dic_image* def, int32_t subset_size, int32_t subset_step,
+                        int32_t shape_fn, const dic_params* params, int32_t n_seeds) {
+  if (!ref || !def || !params) return fail(DIC_EINVAL, "NULL argument");
+  if (dtype_size(ref->dtype) == 0 || dtype_size(def->dtype) == 0) return fail(DIC_EINVAL, "unknown image dtype");
+  if (ref->width != def->width || ref->height != def->height)
+    return fail(DIC_EINVAL, "reference %dx%d and deformed %dx%d differ in size", ref->width, ref->height,
+                def->width, def->height);
+  if (ref->width < 8 || ref->height < 8) return fail(DIC_EINVAL, "images must be at least 8x8");
+  int rc = check_subsets(ref->width, ref->height, nullptr, subset_size, subset_step, shape_fn);
+  if (rc) return rc;
+  if ((rc = validate_params(params))) return rc;
+  if (n_seeds < 1) return fail(DIC_EINVAL, "at least one seed is needed");
+  return DIC_OK;
+}
+
+void release(dic_handle* h) {
+  if (!h) return;
+  for (auto& kv : h->allocs) dev_free(kv.first);
+  h->allocs.clear();
+  if (h->h_counters) cudaFreeHost(h->h_counters);
+  if (h->h_res) cudaFreeHost(h->h_res);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->wave_events) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->batch_ev)
+    if (e) cudaEventDestroy(e);
+  delete h;
+}
+
 
 // The wave loop and everything after it, shared by dic_correlate and
 // dic_correlate_sequence (wave 0 is already in front[0] and the counters).
@@ -531,59 +710,65 @@ int dic_create(const dic_image* ref, const dic_image* def, const dic_image* roi,
   if (ref->width != def->width || ref->height != def->height)
     return fail(DIC_EINVAL, "reference %dx%d and deformed %dx%d differ in size", ref->width, ref->height,
                 def->width, def->height);
-  if (subset_size < 3 || subset_size > kMaxSubset || subset_size % 2 == 0)
-    return fail(DIC_EINVAL, "subset_size %d must be odd and in [3, %d]", subset_size, kMaxSubset);
-  if (subset_size > ref->width || subset_size > ref->height)
-    return fail(DIC_EINVAL, "subset_size %d exceeds the image", subset_size);
-  if (subset_step < 1) return fail(DIC_EINVAL, "subset_step %d must be >= 1", subset_step);
-  if (shape_fn != DIC_RIGID && shape_fn != DIC_AFFINE && shape_fn != DIC_QUADRATIC)
-    return fail(DIC_EINVAL, "unknown shape function %d", shape_fn);
+  if ((rc = check_subsets(ref->width, ref->height, roi, subset_size, subset_step, shape_fn))) return rc;
   if (interp != DIC_BSPLINE3) return fail(DIC_EINVAL, "unknown interpolation %d", interp);
-  if (roi) {
-    if ((rc = check_image(roi, "roi"))) return rc;
-    if (roi->dtype != DIC_U8) return fail(DIC_EINVAL, "roi mask must be DIC_U8");
-    if (roi->width != ref->width || roi->height != ref->height)
-      return fail(DIC_EINVAL, "roi mask size differs from the images");
-  }
   dic_handle* h = new (std::nothrow) dic_handle();
   if (!h) return fail(DIC_ENOMEM, "handle allocation");
   cudaGetDevice(&h->device);
   h->W = ref->width;
   h->H = ref->height;
-  h->S = subset_size;
-  h->r = (subset_size - 1) / 2;
-  h->step = subset_step;
-  h->shape = shape_fn;
-  h->nparams = nparams_of(shape_fn);
-  h->nx = (h->W - 1 - 2 * h->r) / h->step + 1;
-  h->ny = (h->H - 1 - 2 * h->r) / h->step + 1;
-  h->npts = static_cast<int64_t>(h->nx) * h->ny;
   h->prm = dic_default_params();
-  if ((rc = bind_image(ref, &h->ref, &h->ref_owned, &h->ref_dtype)) ||
-      (rc = bind_image(def, &h->def, &h->def_owned, &h->def_dtype)) || (rc = alloc_points(h))) {
+  if ((rc = bind_image(h, ref, &h->ref, &h->ref_owned, &h->ref_dtype)) ||
+      (rc = bind_image(h, def, &h->def, &h->def_owned, &h->def_dtype)) ||
+      (rc = configure_subsets(h, roi, subset_size, subset_step, shape_fn))) {
     release(h);
     return rc;
   }
-  if (roi) {
-    GrayPlane mask{};
-    void* owned = nullptr;
-    int dt = 0;
-    if ((rc = dev_alloc(&h->roi_ok, static_cast<size_t>(h->npts), "roi flags")) ||
-        (rc = bind_image(roi, &mask, &owned, &dt))) {
-      dev_free(owned);
-      release(h);
-      return rc;
-    }
-    RoiArgs ra{mask, h->S, h->r, h->step, h->nx, h->ny, h->roi_ok};
-    cudaError_t e = launch_roi_flags(ra, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    dev_free(owned);
-    if (e != cudaSuccess) {
-      release(h);
-      return cuda_fail(e, "roi flags");
-    }
-  }
   *out = h;
+  return DIC_OK;
+}
+
+int dic_set_subsets(dic_handle* h, const dic_image* roi, int32_t subset_size, int32_t subset_step,
+                    int32_t shape_fn) {
+  if (!h) return fail(DIC_EINVAL, "handle is NULL");
+  g_last_error.clear();
+  int rc = check_subsets(h->W, h->H, roi, subset_size, subset_step, shape_fn);
+  if (rc) return rc;
+  return configure_subsets(h, roi, subset_size, subset_step, shape_fn);
+}
+
+int dic_estimate_device_bytes(const dic_image* ref, const dic_image* def, int32_t has_roi, int32_t subset_size,
+                              int32_t subset_step, int32_t shape_fn, const dic_params* params, int32_t n_seeds,
+                              int64_t* bytes) {
+  g_last_error.clear();
+  if (!bytes) return fail(DIC_EINVAL, "NULL argument");
+  int rc = check_estimate_args(ref, def, subset_size, subset_step, shape_fn, params, n_seeds);
+  if (rc) return rc;
+  *bytes = footprint(nullptr, ref, def, has_roi != 0, subset_size, subset_step, shape_fn, params->precision,
+                     n_seeds, params->search_radius);
+  return DIC_OK;
+}
+
+int dic_estimate_regrid_bytes(const dic_handle* h, const dic_image* def, int32_t has_roi, int32_t subset_size,
+                              int32_t subset_step, int32_t shape_fn, const dic_params* params, int32_t n_seeds,
+                              int64_t* bytes) {
+  g_last_error.clear();
+  if (!h || !bytes) return fail(DIC_EINVAL, "NULL argument");
+  dic_image ref{};
+  ref.width = h->W;
+  ref.height = h->H;
+  ref.dtype = h->ref_dtype;
+  ref.on_device = h->ref_owned ? 0 : 1;
+  int rc = check_estimate_args(&ref, def, subset_size, subset_step, shape_fn, params, n_seeds);
+  if (rc) return rc;
+  *bytes = footprint(h, &ref, def, has_roi != 0, subset_size, subset_step, shape_fn, params->precision, n_seeds,
+                     params->search_radius);
+  return DIC_OK;
+}
+
+int dic_get_device_bytes(const dic_handle* h, int64_t* bytes) {
+  if (!h || !bytes) return fail(DIC_EINVAL, "NULL argument");
+  *bytes = h->device_bytes;
   return DIC_OK;
 }
 
@@ -609,15 +794,13 @@ static int replace_image(dic_handle* h, const dic_image* im, bool is_ref) {
     return fail(DIC_EINVAL, "image is %dx%d, the handle holds %dx%d", im->width, im->height, h->W, h->H);
   const int old_dtype = is_ref ? h->ref_dtype : h->def_dtype;
   void** owned = is_ref ? &h->ref_owned : &h->def_owned;
-  if (!im->on_device && *owned && dtype_size(im->dtype) != dtype_size(old_dtype)) {
-    dev_free(*owned);
-    *owned = nullptr;
-  }
+  // an owned copy that no longer fits (or is no longer used) is released
+  if (*owned && (im->on_device || dtype_size(im->dtype) != dtype_size(old_dtype))) hfree(h, *owned);
   if (is_ref) {
-    rc = bind_image(im, &h->ref, owned, &h->ref_dtype);
+    rc = bind_image(h, im, &h->ref, owned, &h->ref_dtype);
     h->ref_dirty = true;
   } else {
-    rc = bind_image(im, &h->def, owned, &h->def_dtype);
+    rc = bind_image(h, im, &h->def, owned, &h->def_dtype);
     h->def_dirty = true;
   }
   return rc;
@@ -630,7 +813,9 @@ int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void*
   if (!h) return fail(DIC_EINVAL, "handle is NULL");
   g_last_error.clear();
   if (!seeds_xy || n_seeds < 1) return fail(DIC_EINVAL, "at least one seed is needed");
+  if (!h->grid_ok) return fail(DIC_ESTATE, "the handle has no subset grid; call dic_set_subsets");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = s;
   int rc = ensure_planes(h);
   if (rc) return rc;
   h->timing = dic_timing{};
@@ -667,22 +852,20 @@ int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void*
   const int R = h->prm.search_radius;
   const size_t side = 2 * static_cast<size_t>(R) + 1;
   if (static_cast<size_t>(n_seeds) > h->seed_cap) {
-    dev_free(h->seed_xy);
-    dev_free(h->seed_q);
-    dev_free(h->seed_best);
-    h->seed_xy = h->seed_q = h->seed_best = nullptr;
+    hfree(h, h->seed_xy);
+    hfree(h, h->seed_q);
+    hfree(h, h->seed_best);
     h->seed_cap = 0;
-    if ((rc = dev_alloc(&h->seed_xy, 2 * static_cast<size_t>(n_seeds), "seeds")) ||
-        (rc = dev_alloc(&h->seed_q, static_cast<size_t>(n_seeds), "seeds")) ||
-        (rc = dev_alloc(&h->seed_best, static_cast<size_t>(n_seeds), "seeds")))
+    if ((rc = halloc(h, &h->seed_xy, 2 * static_cast<size_t>(n_seeds), "seeds")) ||
+        (rc = halloc(h, &h->seed_q, static_cast<size_t>(n_seeds), "seeds")) ||
+        (rc = halloc(h, &h->seed_best, static_cast<size_t>(n_seeds), "seeds")))
       return rc;
     h->seed_cap = n_seeds;
   }
   if (n_seeds * side * side > h->score_cap) {
-    dev_free(h->seed_scores);
-    h->seed_scores = nullptr;
+    hfree(h, h->seed_scores);
     h->score_cap = 0;
-    if ((rc = dev_alloc(&h->seed_scores, n_seeds * side * side, "seed scores"))) return rc;
+    if ((rc = halloc(h, &h->seed_scores, n_seeds * side * side, "seed scores"))) return rc;
     h->score_cap = n_seeds * side * side;
   }
   DIC_CUDA(cudaMemcpyAsync(h->seed_xy, centres.data(), centres.size() * sizeof(int32_t),
@@ -708,6 +891,7 @@ int dic_correlate_sequence(dic_handle* h, void* cuda_stream) {
   g_last_error.clear();
   if (!h->has_results) return fail(DIC_ESTATE, "dic_correlate_sequence needs an earlier correlation");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = s;
   if (h->plane_prec != h->prm.precision)
     return fail(DIC_ESTATE, "the precision changed since the last correlation; correlate with seeds");
   h->timing = dic_timing{};
@@ -738,6 +922,7 @@ int dic_correlate_sequence(dic_handle* h, void* cuda_stream) {
 
 int dic_get_results(dic_handle* h, dic_results* out, int32_t on_device) {
   if (!h || !out) return fail(DIC_EINVAL, "NULL argument");
+  if (!h->has_results) return fail(DIC_ESTATE, "no correlation since the handle was created or re-gridded");
   const size_t n = static_cast<size_t>(h->npts);
   out->n_points = h->npts;
   out->nx = h->nx;
@@ -771,7 +956,7 @@ int dic_get_results(dic_handle* h, dic_results* out, int32_t on_device) {
   auto take = [&](const void* src, size_t len) -> void* {
     void* dst = base + off;
     off += (len + 15) & ~static_cast<size_t>(15);
-    cudaMemcpyAsync(dst, src, len, cudaMemcpyDeviceToHost, 0);
+    cudaMemcpyAsync(dst, src, len, cudaMemcpyDeviceToHost, h->last_stream);
     return dst;
   };
   out->p = static_cast<const double*>(take(h->p, n * 8 * h->nparams));
@@ -784,7 +969,7 @@ int dic_get_results(dic_handle* h, dic_results* out, int32_t on_device) {
   out->wave = static_cast<const int32_t*>(take(h->wave, n * 4));
   out->converged = static_cast<const uint8_t*>(take(h->conv, n));
   out->status = static_cast<const uint8_t*>(take(h->status, n));
-  DIC_CUDA(cudaStreamSynchronize(0), "result read-back");
+  DIC_CUDA(cudaStreamSynchronize(h->last_stream), "result read-back");
   return DIC_OK;
 }
 

@@ -1017,6 +1017,14 @@ __global__ void roi_flags_kernel(RoiArgs a) {
   }
 }
 
+__global__ void grid_points_kernel(int32_t* x, int32_t* y, int r, int step, int nx, int64_t n) {
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < n;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    x[q] = r + static_cast<int32_t>(q % nx) * step;
+    y[q] = r + static_cast<int32_t>(q / nx) * step;
+  }
+}
+
 __global__ void reset_points_kernel(PointArrays pa, int nparams, const uint8_t* roi_ok) {
   for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < pa.n;
        q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -1073,23 +1081,37 @@ __global__ void finalize_points_kernel(PointArrays pa, int nparams, int nan_reje
   if ((threadIdx.x & 31) == 0 && count) atomicAdd(accepted, count);
 }
 
+// Raises the kernel's dynamic shared-memory limit to the device's opt-in limit
+// less its static shared memory, once per instantiation (thread-safe); the
+// largest tile set (S = 61, FP64 coefficients, 8-byte gray) stays below it.
+template <typename T, int NP>
+cudaError_t configure_wave_smem() {
+  static const cudaError_t result = []() {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, wave_kernel<T, NP>);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(wave_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               optin - static_cast<int>(fa.sharedSizeBytes));
+    return e;
+  }();
+  return result;
+}
+
 template <typename T, int NP>
 cudaError_t launch_wave_np(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
   const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(wave_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  const cudaError_t configured = configure_wave_smem<T, NP>();
+  if (configured != cudaSuccess) return configured;
   wave_kernel<T, NP><<<grid, kWaveThreads, smem, s>>>(a, maps[0], maps[1], maps[2]);
   return cudaGetLastError();
 }
 
 template <typename T, int NP>
 int blocks_per_sm_np(size_t smem) {
-  cudaFuncSetAttribute(wave_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (configure_wave_smem<T, NP>() != cudaSuccess) return 1;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<T, NP>, kWaveThreads, smem) != cudaSuccess)
     return 1;
@@ -1148,6 +1170,12 @@ cudaError_t launch_roi_flags(const RoiArgs& a, cudaStream_t s) {
   const int64_t n = static_cast<int64_t>(a.nx) * a.ny;
   const int64_t blocks = (n * 32 + 255) / 256;
   roi_flags_kernel<<<static_cast<unsigned>(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_points(int32_t* x, int32_t* y, int r, int step, int nx, int64_t n, cudaStream_t s) {
+  const int64_t blocks = (n + 255) / 256;
+  grid_points_kernel<<<static_cast<unsigned>(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(x, y, r, step, nx, n);
   return cudaGetLastError();
 }
 

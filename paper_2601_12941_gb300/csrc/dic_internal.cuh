@@ -147,6 +147,8 @@ struct RoiArgs {
   uint8_t* roi_ok;   // [n_points]
 };
 cudaError_t launch_roi_flags(const RoiArgs& a, cudaStream_t s);
+// subset centres of the grid in point order: x = r + (q % nx) step, y = r + (q / nx) step
+cudaError_t launch_grid_points(int32_t* x, int32_t* y, int r, int step, int nx, int64_t n, cudaStream_t s);
 cudaError_t launch_reset_points(const PointArrays& pa, int nparams, const uint8_t* roi_ok,
                                 cudaStream_t s);
 cudaError_t launch_finalize_points(const PointArrays& pa, int nparams, int nan_rejected,

@@ -122,14 +122,9 @@ cudaError_t launch_prefilter(const PrefilterArgs<T>& a, cudaStream_t s) {
   constexpr int K = taps_radius<T>();
   constexpr int IX = kTile + 2 * K;
   const size_t smem = sizeof(T) * static_cast<size_t>(IX * IX + IX * kTile);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(prefilter_kernel<T, K>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      prefilter_kernel<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (configured != cudaSuccess) return configured;
   static const Taps<T> taps = make_taps<T>();
   dim3 grid((a.W + kTile - 1) / kTile, (a.H + kTile - 1) / kTile);
   prefilter_kernel<T, K><<<grid, kThreads, smem, s>>>(a, taps);

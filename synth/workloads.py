@@ -9,6 +9,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, replace
 
+import numpy as np
+
 from . import ImageSpec, Speckle, affine_field, sine_field, FIELD_AFFINE
 
 SEED_BASE = 12941
@@ -93,6 +95,49 @@ def sequence_frame(k, n_frames=200, width=4096, height=3000, subset_size=21, sha
     dfm = ImageSpec(sp, field=fld, gray_max=G, noise=0.01 * G, noise_tag=1000 + k)
     return Workload("sequence_%dx%d_u16_f%d" % (width, height, k), width, height, "u16", ref, dfm,
                     subset_size, 10, shape, ((width // 2, height // 2),), 8)
+
+
+@dataclass(frozen=True)
+class ServingJob:
+    """One request of a serving stream: a pair of a pooled reference and its own
+    deformed image, with the job's own subset settings."""
+    index: int
+    arrival_s: float
+    ref_index: int
+    workload: Workload
+
+
+def serving_stream(n_jobs=500, rate=20.0, pool=8, side=(512, 16384), seed=SEED_BASE + 5):
+    """Poisson arrivals at ``rate`` jobs/s. References come from a pool of ``pool``
+    square speckle images (side log-uniform in ``side``, u8 or u16 with p = 1/2,
+    1% noise); each job draws one with repeats, an odd subset size in [15, 61], a
+    step in 1..10, the affine or quadratic shape (p = 1/2), and a random affine
+    field about the centre with |u| <= 5 px and strains up to 1e-2 in magnitude;
+    one seed at the centre, search radius 8."""
+    rng = np.random.default_rng(seed)
+    refs = []
+    for i in range(pool):
+        s = int(round(float(np.exp(rng.uniform(np.log(side[0]), np.log(side[1]))))))
+        dtype = "u8" if rng.random() < 0.5 else "u16"
+        refs.append((s, dtype, 255.0 if dtype == "u8" else 65535.0, Speckle(seed=seed * 100 + i, **OPTICAL)))
+    t = 0.0
+    jobs = []
+    for j in range(n_jobs):
+        t += float(rng.exponential(1.0 / rate))
+        i = int(rng.integers(pool))
+        s, dtype, G, sp = refs[i]
+        S = 2 * int(rng.integers(7, 31)) + 1
+        step = int(rng.integers(1, 11))
+        shape = "affine" if rng.random() < 0.5 else "quadratic"
+        u0, v0 = (float(a) for a in rng.uniform(-3.5, 3.5, size=2))
+        exx, exy, eyx, eyy = (float(a) for a in rng.uniform(-1e-2, 1e-2, size=4))
+        fld = affine_field(s, s, u0=u0, v0=v0, exx=exx, exy=exy, eyx=eyx, eyy=eyy)
+        ref = ImageSpec(sp, gray_max=G, noise=0.01 * G, noise_tag=1)
+        dfm = ImageSpec(sp, field=fld, gray_max=G, noise=0.01 * G, noise_tag=100 + j)
+        w = Workload("serve_%d_ref%d_%d_%s" % (j, i, s, dtype), s, s, dtype, ref, dfm, S, step, shape,
+                     ((s // 2, s // 2),), 8)
+        jobs.append(ServingJob(j, t, i, w))
+    return jobs
 
 
 def scaled(w: Workload, **kw) -> Workload:
