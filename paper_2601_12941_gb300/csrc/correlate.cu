@@ -56,100 +56,103 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Solves A^T Z^T = R^T for two right-hand rows (6 x 6, partial pivoting), i.e. Z = R A^-1.
-__device__ void rows_times_inverse6(const double (&A)[6][6], double (&R)[2][6]) {
-  double M[6][6];
-  for (int i = 0; i < 6; ++i)
-    for (int j = 0; j < 6; ++j) M[i][j] = A[j][i];  // transpose
-  double B[6][2];
-  for (int i = 0; i < 6; ++i) {
-    B[i][0] = R[0][i];
-    B[i][1] = R[1][i];
+// p <- W(W^-1(.; dp); p) for the quadratic warp, through the second-order
+// monomial map m(W(x; p)) ~= A(p) m(x), m = [x^2, xy, y^2, x, y, 1] (terms above
+// second order dropped): the new x' and y' rows are Z = R A(dp)^-1 with R the x',
+// y' rows of A(p). Write A(dp) = [[I + E, e], [0, 1]] (E: 5 x 5, formed without
+// its identity part; e: the constant column) and R = [r, p0|p1]. Then
+// Z[:, 0:5] = r + delta with delta (I + E) = -r E, and Z[:, 5] = R[:, 5] - Z[:, 0:5] e.
+// Only the increments delta are solved for, so p keeps the full precision of C;
+// I + E is near the identity for any increment the iteration takes, so the
+// elimination runs without row exchanges, in registers.
+template <typename C>
+__device__ __forceinline__ void compose_quadratic(C* p, const C* dp) {
+  const C u = dp[0], v = dp[1], e2 = dp[2], b = dp[3], c = dp[4], e5 = dp[5];
+  const C a = C(1) + e2, d = C(1) + e5;
+  const C q6 = dp[6], q7 = dp[7], q8 = dp[8], q9 = dp[9], q10 = dp[10], q11 = dp[11];
+  C E[5][5];
+  // x'^2 row
+  E[0][0] = e2 * (C(2) + e2) + C(2) * u * q6;
+  E[0][1] = C(2) * a * b + C(2) * u * q7;
+  E[0][2] = b * b + C(2) * u * q8;
+  E[0][3] = C(2) * u * a;
+  E[0][4] = C(2) * u * b;
+  // x'y' row
+  E[1][0] = a * c + u * q9 + v * q6;
+  E[1][1] = e2 + e5 + e2 * e5 + b * c + u * q10 + v * q7;
+  E[1][2] = b * d + u * q11 + v * q8;
+  E[1][3] = u * c + v * a;
+  E[1][4] = u * d + v * b;
+  // y'^2 row
+  E[2][0] = c * c + C(2) * v * q9;
+  E[2][1] = C(2) * c * d + C(2) * v * q10;
+  E[2][2] = e5 * (C(2) + e5) + C(2) * v * q11;
+  E[2][3] = C(2) * v * c;
+  E[2][4] = C(2) * v * d;
+  // x', y' rows
+  E[3][0] = q6; E[3][1] = q7; E[3][2] = q8; E[3][3] = e2; E[3][4] = b;
+  E[4][0] = q9; E[4][1] = q10; E[4][2] = q11; E[4][3] = c; E[4][4] = e5;
+  const C ec[5] = {u * u, u * v, v * v, u, v};
+  // right-hand sides -r E, with r = [p6, p7, p8, 1 + p2, p3] and [p9, p10, p11, p4, 1 + p5]
+  C d0[5], d1[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    d0[j] = -(E[3][j] + (p[2] * E[3][j] + p[6] * E[0][j] + p[7] * E[1][j] + p[8] * E[2][j] + p[3] * E[4][j]));
+    d1[j] = -(E[4][j] + (p[5] * E[4][j] + p[9] * E[0][j] + p[10] * E[1][j] + p[11] * E[2][j] + p[4] * E[3][j]));
   }
-  for (int k = 0; k < 6; ++k) {
-    int piv = k;
-    for (int i = k + 1; i < 6; ++i)
-      if (fabs(M[i][k]) > fabs(M[piv][k])) piv = i;
-    if (piv != k) {
-      for (int j = 0; j < 6; ++j) {
-        double t = M[k][j];
-        M[k][j] = M[piv][j];
-        M[piv][j] = t;
-      }
-      for (int j = 0; j < 2; ++j) {
-        double t = B[k][j];
-        B[k][j] = B[piv][j];
-        B[piv][j] = t;
-      }
+  // delta (I + E) = rhs  <=>  (I + E)^T delta^T = rhs^T: elimination on T = (I + E)^T
+  C T[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) T[i][j] = (i == j ? C(1) : C(0)) + E[j][i];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const C inv = C(1) / T[k][k];
+#pragma unroll
+    for (int i = k + 1; i < 5; ++i) {
+      const C f = T[i][k] * inv;
+#pragma unroll
+      for (int j = k + 1; j < 5; ++j) T[i][j] -= f * T[k][j];
+      d0[i] -= f * d0[k];
+      d1[i] -= f * d1[k];
     }
-    for (int i = k + 1; i < 6; ++i) {
-      const double f = M[i][k] / M[k][k];
-      for (int j = k; j < 6; ++j) M[i][j] -= f * M[k][j];
-      B[i][0] -= f * B[k][0];
-      B[i][1] -= f * B[k][1];
-    }
+    T[k][k] = inv;
   }
-  for (int c = 0; c < 2; ++c)
-    for (int i = 5; i >= 0; --i) {
-      double s = B[i][c];
-      for (int j = i + 1; j < 6; ++j) s -= M[i][j] * R[c][j];
-      R[c][i] = s / M[i][i];
+#pragma unroll
+  for (int i = 4; i >= 0; --i) {
+    C s0 = d0[i], s1 = d1[i];
+#pragma unroll
+    for (int j = i + 1; j < 5; ++j) {
+      s0 -= T[i][j] * d0[j];
+      s1 -= T[i][j] * d1[j];
     }
-}
-
-// Monomial map of the quadratic warp: m(W(x; p)) ~= A(p) m(x) with
-// m = [x^2, xy, y^2, x, y, 1], terms above second order dropped.
-__device__ void quad_monomial_matrix(const double* p, double (&A)[6][6]) {
-  const double p0 = p[0], p1 = p[1], a = 1.0 + p[2], b = p[3], c = p[4], d = 1.0 + p[5];
-  const double q6 = p[6], q7 = p[7], q8 = p[8], q9 = p[9], q10 = p[10], q11 = p[11];
-  // x'^2
-  A[0][0] = a * a + 2.0 * p0 * q6;
-  A[0][1] = 2.0 * a * b + 2.0 * p0 * q7;
-  A[0][2] = b * b + 2.0 * p0 * q8;
-  A[0][3] = 2.0 * p0 * a;
-  A[0][4] = 2.0 * p0 * b;
-  A[0][5] = p0 * p0;
-  // x'y'
-  A[1][0] = a * c + p0 * q9 + p1 * q6;
-  A[1][1] = a * d + b * c + p0 * q10 + p1 * q7;
-  A[1][2] = b * d + p0 * q11 + p1 * q8;
-  A[1][3] = p0 * c + p1 * a;
-  A[1][4] = p0 * d + p1 * b;
-  A[1][5] = p0 * p1;
-  // y'^2
-  A[2][0] = c * c + 2.0 * p1 * q9;
-  A[2][1] = 2.0 * c * d + 2.0 * p1 * q10;
-  A[2][2] = d * d + 2.0 * p1 * q11;
-  A[2][3] = 2.0 * p1 * c;
-  A[2][4] = 2.0 * p1 * d;
-  A[2][5] = p1 * p1;
-  // x', y', 1
-  A[3][0] = q6; A[3][1] = q7; A[3][2] = q8; A[3][3] = a; A[3][4] = b; A[3][5] = p0;
-  A[4][0] = q9; A[4][1] = q10; A[4][2] = q11; A[4][3] = c; A[4][4] = d; A[4][5] = p1;
-  A[5][0] = 0.0; A[5][1] = 0.0; A[5][2] = 0.0; A[5][3] = 0.0; A[5][4] = 0.0; A[5][5] = 1.0;
-}
-
-// p <- W(W^-1(.; dp); p) for the quadratic warp: the x' and y' rows of
-// A(p) A(dp)^-1 (second-order monomial representation of the two warps).
-__device__ __noinline__ void compose_quadratic(double* p, const double* dp) {
-  double Ap[6][6], Ad[6][6];
-  quad_monomial_matrix(p, Ap);
-  quad_monomial_matrix(dp, Ad);
-  double R[2][6];
-  for (int j = 0; j < 6; ++j) {
-    R[0][j] = Ap[3][j];
-    R[1][j] = Ap[4][j];
+    d0[i] = s0 * T[i][i];
+    d1[i] = s1 * T[i][i];
   }
-  rows_times_inverse6(Ad, R);
-  p[6] = R[0][0]; p[7] = R[0][1]; p[8] = R[0][2]; p[2] = R[0][3] - 1.0; p[3] = R[0][4]; p[0] = R[0][5];
-  p[9] = R[1][0]; p[10] = R[1][1]; p[11] = R[1][2]; p[4] = R[1][3]; p[5] = R[1][4] - 1.0; p[1] = R[1][5];
+  const C n0 = p[0] - (ec[3] * (C(1) + p[2] + d0[3]) + ec[4] * (p[3] + d0[4]) + ec[0] * (p[6] + d0[0]) +
+                       ec[1] * (p[7] + d0[1]) + ec[2] * (p[8] + d0[2]));
+  const C n1 = p[1] - (ec[3] * (p[4] + d1[3]) + ec[4] * (C(1) + p[5] + d1[4]) + ec[0] * (p[9] + d1[0]) +
+                       ec[1] * (p[10] + d1[1]) + ec[2] * (p[11] + d1[2]));
+  p[0] = n0;
+  p[1] = n1;
+  p[2] += d0[3];
+  p[3] += d0[4];
+  p[4] += d1[3];
+  p[5] += d1[4];
+  p[6] += d0[0];
+  p[7] += d0[1];
+  p[8] += d0[2];
+  p[9] += d1[0];
+  p[10] += d1[1];
+  p[11] += d1[2];
 }
 
 // p <- W(W^-1(.; dp); p) in the working precision C. Rigid: p - dp. Affine, exact:
 // with A = I + [[p2, p3], [p4, p5]], F = [[dp2, dp3], [dp4, dp5]] and
 // E = (I + F)^-1 - I = -(I + F)^-1 F, the new linear part is A + A E and the new
 // translation t - (A + A E) dt; only the small increments A E and -(A + A E) dt
-// are formed, so p keeps the full precision of C. Quadratic: compose_quadratic.
+// are formed, so p keeps the full precision of C. Quadratic: compose_quadratic in C.
 template <typename C, int NP>
 __device__ void compose_inverse(C* p, const C* dp) {
   if (NP == 2) {
@@ -172,13 +175,7 @@ __device__ void compose_inverse(C* p, const C* dp) {
     p[4] += g10;
     p[5] += g11;
   } else {
-    double pd[kMaxParams], dd[kMaxParams];
-    for (int c = 0; c < 12; ++c) {
-      pd[c] = static_cast<double>(p[c]);
-      dd[c] = static_cast<double>(dp[c]);
-    }
-    compose_quadratic(pd, dd);
-    for (int c = 0; c < 12; ++c) p[c] = static_cast<C>(pd[c]);
+    compose_quadratic<C>(p, dp);
   }
 }
 
@@ -227,14 +224,28 @@ struct Window {
   int x0, y0, w, h;   // origin in the image, row pitch and rows in shared memory
 };
 
+// Solve state. FP64 path: the Hessian, its inverse and the vectors of the
+// refined FP64 solve. Mixed path: the inverse only, in FP32, stored by columns
+// (element (i, j) at j NP + i) so that lane i reads row i without bank conflicts.
+template <typename C, int NP>
+struct SolveState;
+template <int NP>
+struct SolveState<double, NP> {
+  double H[NP * NP];        // Gauss-Newton Hessian
+  double X[NP * NP];        // its inverse
+  double bvec[NP];          // right-hand side, then the residual
+  double dvec[NP];          // first solution
+};
+template <int NP>
+struct SolveState<float, NP> {
+  float X[NP * NP];         // H^-1 = D (D H D)^-1 D, column-major
+};
+
 // Per-block state of the point being correlated; C is the working precision
 // (float on the mixed path, double on the FP64 path).
 template <typename C, int NP>
 struct PointState {
-  double H[NP * NP];        // Gauss-Newton Hessian (FP64)
-  double X[NP * NP];        // its inverse as computed in C (FP64 copy)
-  double bvec[NP];          // right-hand side of the FP64 solve, then its residual
-  double dvec[NP];          // first FP64 solution
+  SolveState<C, NP> sv;
   C p[kMaxParams];          // current warp
   C dp[kMaxParams];         // last update
   C sdf[NP];                // sum SD (f - f_m)
@@ -281,6 +292,74 @@ __device__ double invert_spd_warp(const double* H, double* X, int lane) {
     for (int i = 0; i < N; ++i) X[i * N + (lane - N)] = static_cast<double>(col[i]);
   }
   return dmax > 0.0 ? static_cast<double>(pmin) / dmax : 0.0;
+}
+
+// Warp-parallel Gauss-Jordan inverse of the Jacobi-scaled SPD matrix D H D,
+// D = diag(H_ii^-1/2), in the precision V: lane j < N carries column j of D H D,
+// lane N + j column j of the identity; no row exchanges (SPD). H(i, j) comes from
+// hget. The unit diagonal removes the spread of the monomial scales (up to r^4
+// between the translation and quadratic columns), so FP32 suffices unless H itself
+// is ill-conditioned. Writes H^-1 = D (D H D)^-1 D column-major into X. Returns
+// the smallest scaled pivot; *ratio receives the smallest pivot of H itself (the
+// scaled pivot k times H_kk) over the largest diagonal entry (0 when a pivot is
+// not positive).
+template <typename V, int N, typename HGet>
+__device__ __forceinline__ float invert_scaled_warp(HGet hget, float* X, int lane, float* ratio) {
+  // lane i < N: d_i = H_ii^-1/2 (shared by shuffles)
+  const V hii = lane < N ? static_cast<V>(hget(lane, lane)) : V(0);
+  const V dl = hii > V(0) ? V(1) / sqrt(hii) : V(0);
+  V hmax = hii;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const V t = __shfl_xor_sync(0xffffffffu, hmax, o);
+    hmax = t > hmax ? t : hmax;
+  }
+  const bool mine = lane < 2 * N;
+  const int j = lane < N ? lane : (lane < 2 * N ? lane - N : 0);
+  const V dj = __shfl_sync(0xffffffffu, dl, j);
+  V col[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const V di = __shfl_sync(0xffffffffu, dl, i);
+    col[i] = !mine ? V(0) : (lane < N ? static_cast<V>(hget(i, j)) * di * dj : (i == j ? V(1) : V(0)));
+  }
+  V pmin = V(1e30), rmin = V(1e30);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const V piv = __shfl_sync(0xffffffffu, col[k], k);
+    const V dk = __shfl_sync(0xffffffffu, dl, k);
+    pmin = piv < pmin ? piv : pmin;
+    const V up = dk > V(0) ? piv / (dk * dk) : V(0);
+    rmin = up < rmin ? up : rmin;
+    if (!(piv > V(0))) {
+      *ratio = 0.0f;
+      return 0.0f;
+    }
+    col[k] *= V(1) / piv;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (i == k) continue;
+      const V f = __shfl_sync(0xffffffffu, col[i], k);
+      col[i] -= f * col[k];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const V di = __shfl_sync(0xffffffffu, dl, i);
+    if (mine && lane >= N) X[j * N + i] = static_cast<float>(col[i] * di * dj);
+  }
+  *ratio = hmax > V(0) ? static_cast<float>(rmin / hmax) : 0.0f;
+  return static_cast<float>(pmin);
+}
+
+// The FP64 fallback of invert_scaled_warp, out of line to keep its registers
+// away from the rest of the kernel; H is read from the FP32 moment sums.
+template <int N, int NMOM, int M2>
+__device__ __noinline__ void invert_scaled_fp64(const float* out, float* X, int lane, float* ratio) {
+  auto hget = [&](int ca, int cb) -> float {
+    return out[(sd_t(ca) + sd_t(cb)) * NMOM + mono(sd_i(ca) + sd_i(cb), sd_j(ca) + sd_j(cb), M2)];
+  };
+  invert_scaled_warp<double, N>(hget, X, lane, ratio);
 }
 
 // Coefficients under the warped subset: [x0, x1] x [y0, y1] holds the 4 x 4 support of
@@ -353,9 +432,11 @@ __device__ void plan_window(PointState<C, NP>& st, int xc, int yc, int r, int W,
 
 // Warp 0 after the reference reduction: mean and contrast of f, the Hessian and
 // its inverse. out: [H moments (3 NMOM), sum SD f', sum SD, sum f', sum f'^2].
-// The inverse is formed in C; in FP32 a pivot below 1e-5 of the largest diagonal
-// entry (too ill-conditioned for FP32) switches to the FP64 inverse. Sets st.ctl:
-// 0 ok, 3 flat, 4 singular (a pivot <= 1e-12 of the largest diagonal entry).
+// FP64 path: the Hessian in FP64 and its inverse by invert_spd_warp. Mixed path:
+// the Jacobi-scaled FP32 inverse; a scaled pivot below 1e-5 (H too
+// ill-conditioned for FP32) switches to the same scaled inverse in FP64. Sets
+// st.ctl: 0 ok, 3 flat, 4 singular (a pivot <= 1e-12 of the largest diagonal
+// entry of H).
 template <typename C, int NP, int NMOM, int M2>
 __device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int lane) {
   const C sf = out[3 * NMOM + 2 * NP];
@@ -366,14 +447,20 @@ __device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int
     if (lane == 0) st.ctl = 3;
     return;
   }
-  for (int e = lane; e < NP * NP; e += 32) {
-    const int ca = e / NP, cb = e % NP;
-    const int tt = sd_t(ca) + sd_t(cb);
-    st.H[e] = static_cast<double>(out[tt * NMOM + mono(sd_i(ca) + sd_i(cb), sd_j(ca) + sd_j(cb), M2)]);
+  auto hget = [&](int ca, int cb) -> C {
+    return out[(sd_t(ca) + sd_t(cb)) * NMOM + mono(sd_i(ca) + sd_i(cb), sd_j(ca) + sd_j(cb), M2)];
+  };
+  double ratio;
+  if constexpr (sizeof(C) == sizeof(double)) {
+    for (int e = lane; e < NP * NP; e += 32) st.sv.H[e] = static_cast<double>(hget(e / NP, e % NP));
+    __syncwarp();
+    ratio = invert_spd_warp<C, NP>(st.sv.H, st.sv.X, lane);
+  } else {
+    float rf;
+    if (invert_scaled_warp<float, NP>(hget, st.sv.X, lane, &rf) < 1e-5f)
+      invert_scaled_fp64<NP, NMOM, M2>(out, st.sv.X, lane, &rf);
+    ratio = rf;
   }
-  __syncwarp();
-  double ratio = invert_spd_warp<C, NP>(st.H, st.X, lane);
-  if (sizeof(C) < sizeof(double) && ratio < 1e-5) ratio = invert_spd_warp<double, NP>(st.H, st.X, lane);
   if (lane < NP) {
     st.sds[lane] = out[3 * NMOM + NP + lane];
     st.sdf[lane] = out[3 * NMOM + lane] - mu * out[3 * NMOM + NP + lane];   // sum SD (f' - mu)
@@ -387,11 +474,12 @@ __device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int
 }
 
 // Warp 0 after an iteration's reduction. out: [sum g', sum g'^2, sum SD g', bad].
-// b = sum SD (f - f_m) - (df/dg) sum SD (g - g_m), one component per lane. The
-// solve H dp = -b is done in FP64: dp0 = -X b, then one refinement step
-// dp = dp0 - X (b + H dp0) with X the inverse formed in C. Lane 0 composes
-// p <- p o dp^-1. Returns (on every lane) 0 continue, 1 converged, 2 flat,
-// 5 out of bounds.
+// b = sum SD (f - f_m) - (df/dg) sum SD (g - g_m), one component per lane.
+// FP64 path: dp0 = -X b in FP64, then one refinement step dp = dp0 - X (b + H dp0).
+// Mixed path: dp = -H^-1 b in FP32, b shared by shuffles (the precision of the
+// solve sets the rate of convergence, not the root, which b alone fixes). Lane 0
+// composes p <- p o dp^-1. Returns (on every lane) 0 continue, 1 converged,
+// 2 flat, 5 out of bounds.
 template <typename C, int NP>
 __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C r, C thr2, int lane) {
   if (out[2 + NP] > C(0.5)) return 5;
@@ -401,31 +489,41 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
   const C gm = fmax(fabs(nu + st.f0), C(1));
   if (dg2 <= C(1e-12) * static_cast<C>(N) * gm * gm) return 2;
   const C ratio = st.delta_f * rsqrt(dg2);
-  double bc = 0.0;
-  if (lane < NP) bc = static_cast<double>(st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]));
-  if (lane < NP) st.bvec[lane] = bc;
-  __syncwarp();
-  double d0 = 0.0;
-  if (lane < NP) {
+  C d;
+  if constexpr (sizeof(C) == sizeof(double)) {
+    double bc = 0.0;
+    if (lane < NP) bc = static_cast<double>(st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]));
+    if (lane < NP) st.sv.bvec[lane] = bc;
+    __syncwarp();
+    double d0 = 0.0;
+    if (lane < NP) {
 #pragma unroll
-    for (int m = 0; m < NP; ++m) d0 -= st.X[lane * NP + m] * st.bvec[m];
-    st.dvec[lane] = d0;
-  }
-  __syncwarp();
-  double res = bc;
-  if (lane < NP) {
+      for (int m = 0; m < NP; ++m) d0 -= st.sv.X[lane * NP + m] * st.sv.bvec[m];
+      st.sv.dvec[lane] = d0;
+    }
+    __syncwarp();
+    double res = bc;
+    if (lane < NP) {
 #pragma unroll
-    for (int m = 0; m < NP; ++m) res += st.H[lane * NP + m] * st.dvec[m];
-  }
-  __syncwarp();
-  if (lane < NP) st.bvec[lane] = res;
-  __syncwarp();
-  double dpc = d0;
-  if (lane < NP) {
+      for (int m = 0; m < NP; ++m) res += st.sv.H[lane * NP + m] * st.sv.dvec[m];
+    }
+    __syncwarp();
+    if (lane < NP) st.sv.bvec[lane] = res;
+    __syncwarp();
+    double dpc = d0;
+    if (lane < NP) {
 #pragma unroll
-    for (int m = 0; m < NP; ++m) dpc -= st.X[lane * NP + m] * st.bvec[m];
+      for (int m = 0; m < NP; ++m) dpc -= st.sv.X[lane * NP + m] * st.sv.bvec[m];
+    }
+    d = static_cast<C>(dpc);
+  } else {
+    const C bc = lane < NP ? st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]) : C(0);
+    const int row = lane < NP ? lane : 0;
+    C acc = C(0);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) acc -= st.sv.X[m * NP + row] * __shfl_sync(0xffffffffu, bc, m);
+    d = lane < NP ? acc : C(0);
   }
-  const C d = static_cast<C>(dpc);
   if (lane < NP) st.dp[lane] = d;
   // ||dp||^2 with weights 1, r^2, r^4 on the rigid, affine and quadratic terms
   const C wgt = lane < 2 ? C(1) : (lane < 6 ? r * r : r * r * r * r);
