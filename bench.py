@@ -244,7 +244,7 @@ def run_ours(args):
                                   % (w.width, w.height, w.subset_size, w.subset_step, len(seeds),
                                      w.search_radius),
                       "points": int(res["n_points"]), "accepted": accepted, "attempted": attempted,
-                      "waves": int(res["n_waves"]), "precision": "mixed (u8 gray, f32 spline and sums, f64 solve and ZNCC)",
+                      "waves": int(res["n_waves"]), "precision": "mixed (u8 gray; f32 spline, sums, Jacobi-scaled solve and ZNCC)",
                       "controls": "max_iter 40, threshold 0.01, zncc_min 0.70",
                       "l2": "no flush: each step reads two 1.07 GB gray planes and writes two 4.3 GB coefficient planes, above the 129 MB L2",
                       "parallelism": "replicas x%d" % world},

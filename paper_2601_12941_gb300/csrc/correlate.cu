@@ -56,6 +56,48 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// barrier id among the first `count` threads of the block (id 0 is __syncthreads)
+__device__ __forceinline__ void named_barrier_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Warp sums of K values per thread (K a power of two, <= 32) in K - 1 + 5 - log2 K
+// shuffles: each step sends half of the remaining values to the partner lane and
+// keeps the other half, so lane l ends with the warp sum of v[l >> (5 - log2 K)].
+template <typename T, int K>
+__device__ __forceinline__ T warp_transpose_sum(T (&v)[K], int lane) {
+  int o = 16;
+#pragma unroll
+  for (int h = K / 2; h >= 1; h >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = upper ? v[i] : v[i + h];
+      const T keep = upper ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  T s = v[0];
+#pragma unroll
+  for (; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+__host__ __device__ constexpr int pow2ceil(int n) {
+  int k = 1;
+  while (k < n) k <<= 1;
+  return k;
+}
+
+template <int K>
+struct Log2 {
+  static constexpr int kValue = K <= 1 ? 0 : 1 + Log2<K / 2>::kValue;
+};
+template <>
+struct Log2<1> {
+  static constexpr int kValue = 0;
+};
+
 // p <- W(W^-1(.; dp); p) for the quadratic warp, through the second-order
 // monomial map m(W(x; p)) ~= A(p) m(x), m = [x^2, xy, y^2, x, y, 1] (terms above
 // second order dropped): the new x' and y' rows are Z = R A(dp)^-1 with R the x',
@@ -729,10 +771,14 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
 #pragma unroll
   for (int i = 1; i <= M2; ++i) dxp[i] = dxp[i - 1] * dxv;
 
-  // warp partial of entry idx of a reduction vector
-  auto part = [&](int idx, T v) {
-    v = warp_sum(v);
-    if (lane == 0) s_part[warp][idx] = v;
+  // warp partials of entries [base, base + count) of a reduction vector from the
+  // values v[0..K) of every thread (entries count..K-1 are padding)
+  auto parts = [&](auto& v, int base, int count) {
+    constexpr int K = sizeof(v) / sizeof(v[0]);
+    constexpr int SH = 5 - Log2<K>::kValue;
+    const T sum = warp_transpose_sum<T, K>(v, lane);
+    const int e = lane >> SH;
+    if ((lane & ((1 << SH) - 1)) == 0 && e < count) s_part[warp][base + e] = sum;
   };
   // warp 0: cross-warp sums into s_out[0..nv)
   auto gather = [&](int nv) {
@@ -910,18 +956,32 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
         }
       }
 #pragma unroll
-      for (int tt = 0; tt < 3; ++tt)
+      for (int tt = 0; tt < 3; ++tt) {
+        T v[pow2ceil(NMOM)];
+#pragma unroll
+        for (int e = NMOM; e < pow2ceil(NMOM); ++e) v[e] = T(0);
 #pragma unroll
         for (int j = 0; j <= M2; ++j)
 #pragma unroll
-          for (int i = 0; i + j <= M2; ++i) part(tt * NMOM + mono(i, j, M2), dxp[i] * A[tt][j]);
-#pragma unroll
-      for (int c = 0; c < NP; ++c) {
-        part(3 * NMOM + c, dxp[sd_i(c)] * Bf[sd_t(c)][sd_j(c)]);
-        part(3 * NMOM + NP + c, dxp[sd_i(c)] * Bs[sd_t(c)][sd_j(c)]);
+          for (int i = 0; i + j <= M2; ++i) v[mono(i, j, M2)] = dxp[i] * A[tt][j];
+        parts(v, tt * NMOM, NMOM);
       }
-      part(3 * NMOM + 2 * NP, sf);
-      part(3 * NMOM + 2 * NP + 1, sff);
+      {
+        T v[pow2ceil(NP)], w[pow2ceil(NP)];
+#pragma unroll
+        for (int c = NP; c < pow2ceil(NP); ++c) v[c] = w[c] = T(0);
+#pragma unroll
+        for (int c = 0; c < NP; ++c) {
+          v[c] = dxp[sd_i(c)] * Bf[sd_t(c)][sd_j(c)];
+          w[c] = dxp[sd_i(c)] * Bs[sd_t(c)][sd_j(c)];
+        }
+        parts(v, 3 * NMOM, NP);
+        parts(w, 3 * NMOM + NP, NP);
+      }
+      {
+        T v[2] = {sf, sff};
+        parts(v, 3 * NMOM + 2 * NP, 2);
+      }
     }
     __syncthreads();
     if (warp == 0) {
@@ -1002,16 +1062,18 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
                                            acc, bad);
       }
       if (!final_pass) {
-        part(0, acc[0]);
-        part(1, acc[1]);
+        T v[pow2ceil(NV_IT)];
+        v[0] = acc[0];
+        v[1] = acc[1];
 #pragma unroll
-        for (int c = 0; c < NP; ++c) part(2 + c, dxp[sd_i(c)] * acc[2 + sd_t(c) * (D + 1) + sd_j(c)]);
-        part(2 + NP, bad);
+        for (int c = 0; c < NP; ++c) v[2 + c] = dxp[sd_i(c)] * acc[2 + sd_t(c) * (D + 1) + sd_j(c)];
+        v[2 + NP] = bad;
+#pragma unroll
+        for (int e = NV_IT; e < pow2ceil(NV_IT); ++e) v[e] = T(0);
+        parts(v, 0, NV_IT);
       } else {
-        part(0, acc[0]);
-        part(1, acc[1]);
-        part(2, acc[2]);
-        part(3, bad);
+        T v[4] = {acc[0], acc[1], acc[2], bad};
+        parts(v, 0, NV_FIN);
       }
       __syncthreads();
       if (warp == 0) {
@@ -1034,17 +1096,17 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
             }
           }
         } else if (lane == 0) {
-          // FP64 normalisation of the final correlation coefficient
-          const double sg = s_out[0], sgg = s_out[1], sfg = s_out[2];
-          const double nu = sg / N;
-          const double dg = sqrt(fmax(sgg - sg * nu, 0.0));
+          // normalisation of the final correlation coefficient in C (its sums are in C)
+          const C sg = s_out[0], sgg = s_out[1], sfg = s_out[2];
+          const C nu = sg / static_cast<C>(N);
+          const C dg = sqrt(fmax(sgg - sg * nu, C(0)));
           if (s_out[3] > C(0.5)) {
             st.status = DIC_PT_OUT_OF_BOUNDS;
-          } else if (is_flat<double>(dg, nu + static_cast<double>(st.f0), N)) {
+          } else if (is_flat<C>(dg, nu + st.f0, N)) {
             st.status = DIC_PT_FLAT;
           } else {
             // sum (f - f_m)(g - g_m) = sum f' g' - mu sum g'
-            st.zncc = (sfg - static_cast<double>(st.mu) * sg) / (static_cast<double>(st.delta_f) * dg);
+            st.zncc = static_cast<double>((sfg - st.mu * sg) / (st.delta_f * dg));
             if (!st.converged)
               st.status = DIC_PT_MAX_ITER;
             else if (st.zncc < a.zncc_min)
@@ -1064,20 +1126,30 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
       }
     }
 
-    // ---- 5. results and claims (warp 0)
+    // ---- 5. results and claims (warp 1, while warp 0 sets up the next point; the
+    //         named barrier of warps 0 and 1 orders warp 1's reads of st before
+    //         warp 0 rewrites it)
     if (warp == 0) {
+      named_barrier_sync(1, 64);
+    } else if (warp == 1) {
       const int status = st.status;
-      if (lane < NP) a.pts.p[static_cast<int64_t>(q) * NP + lane] = static_cast<double>(st.p[lane]);
-      if (lane == 0) {
-        a.pts.u[q] = static_cast<double>(st.p[0]);
-        a.pts.v[q] = static_cast<double>(st.p[1]);
-        a.pts.zncc[q] = static_cast<float>(st.zncc);
+      const double pv = lane < NP ? static_cast<double>(st.p[lane]) : 0.0;
+      const float z = static_cast<float>(st.zncc);
+      const int iters = st.iters, conv = st.converged;
+      named_barrier_sync(1, 64);
+      if (lane < NP) a.pts.p[static_cast<int64_t>(q) * NP + lane] = pv;
+      if (lane == 0) a.pts.u[q] = pv;
+      if (lane == 1) a.pts.v[q] = pv;
+      if (lane == 2) {
+        a.pts.zncc[q] = z;
         a.pts.accept[q] = status == DIC_PT_OK
                               ? (static_cast<int64_t>(a.k) << 32) |
-                                    static_cast<int64_t>(static_cast<uint32_t>(__float_as_int(static_cast<float>(st.zncc))))
+                                    static_cast<int64_t>(static_cast<uint32_t>(__float_as_int(z)))
                               : -1;
-        a.pts.iters[q] = st.iters;
-        a.pts.converged[q] = static_cast<uint8_t>(st.converged);
+      }
+      if (lane == 3) {
+        a.pts.iters[q] = iters;
+        a.pts.converged[q] = static_cast<uint8_t>(conv);
         a.pts.status[q] = static_cast<uint8_t>(status);
       }
       if (status == DIC_PT_OK && lane < 4) {
