@@ -40,6 +40,12 @@ FLOP_ITER = {2: 64, 6: 84, 12: 108}
 FLOP_FINAL = 72
 
 
+# DRAM bytes (read + write) per point of the wave kernel in its current form, from one
+# full ncu capture of two mid-run waves of 2,560 points each on the 6144^2 version of the
+# same workload (32.33 MB per launch); traffic grows with the points a launch processes.
+WAVE_DRAM_BYTES_PER_POINT = 12_629
+
+
 def fp32_peak_tflops():
     """152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz maximum SM clock."""
     return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -191,6 +197,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
 
+    wave_launches = []
+
     def timed_steps(c, steps, warmup):
         for _ in range(warmup):
             c.set_reference(ref)
@@ -200,6 +208,7 @@ def run_ours(args):
         lat = []
         kern = 0.0
         launches = 0
+        wave_launches.clear()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
@@ -215,7 +224,8 @@ def run_ours(args):
             lat.append(a.elapsed_time(b))
             tm = c.timing()
             kern += tm["icgn_kernel_ms"]
-            launches += tm["n_wave_launches"] + 6   # 2 prefilter, reset, 2 seed, finalize
+            launches += tm["n_wave_launches"] + 7   # 2 prefilter, reset, 2 seed search, commit, finalize
+            wave_launches.append(tm["n_wave_launches"])
         ev1.record(stream)
         barrier()
         total_ms = ev0.elapsed_time(ev1)
@@ -252,7 +262,10 @@ def run_ours(args):
            "gpu_launches": launches,
            "roofline": {"bound": "alu", "kernel": "wave_kernel (fused reference precompute, IC-GN, ZNCC, claims)",
                         "achieved": achieved, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
-                        "frac": achieved / fp32_peak_tflops(), "traffic": None,
+                        "frac": achieved / fp32_peak_tflops(),
+                        "traffic": WAVE_DRAM_BYTES_PER_POINT * attempted / (sum(wave_launches) / len(wave_launches)),
+                        "traffic_note": "bytes per launch: 12.6 KB per point (ncu, 6144^2 case) x attempted "
+                                        "points per wave launch; algorithmic bytes are not the bound (ALU)",
                         "peak_note": "FP32 peak from 152 SMs x 128 lanes x 2 x 2070 MHz (no measured FP32 peak)",
                         "kernel_ms_per_step": kern_avg, "share_of_step": kern_avg / (total_ms / args.steps),
                         "algorithmic_gflop_per_step": flops / 1e9},
