@@ -585,14 +585,15 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
 // a column usually step one coefficient row down with the same ix, so the four
 // rows of the support stay in registers (rotated by the 4-way unrolled loop) and
 // only the new row is loaded; anything else reloads all four.
-// FINAL = false: acc = [sum g', sum g'^2, sum fx g' dy^j (j <= D), sum fy g' dy^j]
-// FINAL = true:  acc = [sum g', sum g'^2, sum f' g']
-template <typename T, int D, bool FINAL>
+// fin = false: acc = [sum g', sum g'^2, sum fx g' dy^j (j <= D), sum fy g' dy^j]
+// fin = true:  acc = [sum g', sum g'^2, sum f' g'] (the final pass; one copy of the
+// unrolled loop serves both, fin being the same for the whole block)
+template <typename T, int D>
 __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld, T ax, T bx, T cxq,
                                               T ay, T by, T cyq, T xlo, T xhi, T ylo, T yhi, T f0,
                                               int row0, int row1, int r, int S, int col,
                                               const unsigned char* gtile, int gpitch, int gdtype,
-                                              const T* s_fx, const T* s_fy, T* acc, T& bad) {
+                                              const T* s_fx, const T* s_fy, bool fin, T* acc, T& bad) {
   T c0[4], c1[4], c2[4], c3[4];
   int pix_ix = -0x40000000, pix_iy = -0x40000000;
   auto step = [&](T (&A)[4], T (&B)[4], T (&Cc)[4], T (&Dn)[4], int row) {
@@ -629,7 +630,7 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
     const T gp = (wy0 * r0 + wy1 * r1 + wy2 * r2 + wy3 * r3) * (T(1) / T(36)) - f0;
     acc[0] += gp;
     acc[1] += gp * gp;
-    if (FINAL) {
+    if (fin) {
       acc[2] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
     } else {
       const int pix = row * S + col;
@@ -652,14 +653,15 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
 }
 
 // The rare path (window too large for shared memory): every sample reads its
-// 4 x 4 support from the global plane; a plain loop, light on registers.
-template <typename T, int D, bool FINAL>
-__device__ __forceinline__ void sample_column_global(const T* __restrict__ base, int64_t ld, T ax,
+// 4 x 4 support from the global plane; a plain loop, light on registers, kept out
+// of line so that it does not sit in the instruction stream of the common path.
+template <typename T, int D>
+__device__ __noinline__ void sample_column_global(const T* __restrict__ base, int64_t ld, T ax,
                                                      T bx, T cxq, T ay, T by, T cyq, T xlo, T xhi,
                                                      T ylo, T yhi, T f0, int row0, int row1, int r,
                                                      int S, int col, const unsigned char* gtile,
                                                      int gpitch, int gdtype, const T* s_fx,
-                                                     const T* s_fy, T* acc, T& bad) {
+                                                     const T* s_fy, bool fin, T* acc, T& bad) {
   for (int row = row0; row < row1; ++row) {
     const T dyv = static_cast<T>(row - r);
     const T xl = ax + dyv * (bx + cxq * dyv);
@@ -683,7 +685,7 @@ __device__ __forceinline__ void sample_column_global(const T* __restrict__ base,
     const T gp = g * (T(1) / T(36)) - f0;
     acc[0] += gp;
     acc[1] += gp * gp;
-    if (FINAL) {
+    if (fin) {
       acc[2] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
     } else {
       const int pix = row * S + col;
@@ -1044,22 +1046,12 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
       T bad = T(0);
       if (stage != 2) {
         const T* base = s_win + (yc - 1 - w.y0) * w.w + (xc - 1 - w.x0);
-        if (!final_pass)
-          sample_column<T, D, false>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0,
-                                     row1, r, S, col, gtile, gpitch, gdt, s_fx, s_fy, acc, bad);
-        else
-          sample_column<T, D, true>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0,
-                                    row1, r, S, col, gtile, gpitch, gdt, s_fx, s_fy, acc, bad);
+        sample_column<T, D>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r, S, col,
+                            gtile, gpitch, gdt, s_fx, s_fy, final_pass, acc, bad);
       } else {
         const T* base = a.c_def + static_cast<int64_t>(yc - 1) * a.ldc + (xc - 1);
-        if (!final_pass)
-          sample_column_global<T, D, false>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi,
-                                            f0, row0, row1, r, S, col, gtile, gpitch, gdt, s_fx, s_fy,
-                                            acc, bad);
-        else
-          sample_column_global<T, D, true>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi,
-                                           f0, row0, row1, r, S, col, gtile, gpitch, gdt, s_fx, s_fy,
-                                           acc, bad);
+        sample_column_global<T, D>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r,
+                                   S, col, gtile, gpitch, gdt, s_fx, s_fy, final_pass, acc, bad);
       }
       if (!final_pass) {
         T v[pow2ceil(NV_IT)];
