@@ -297,6 +297,7 @@ struct PointState {
   C f0;
   double zncc;
   int q, item, ctl, iters, status, converged, stage;
+  int inside;               // every sample of the next pass lies inside the sampling bounds
   Window win, next;
 };
 
@@ -406,11 +407,13 @@ __device__ __noinline__ void invert_scaled_fp64(const float* out, float* X, int 
 
 // Coefficients under the warped subset: [x0, x1] x [y0, y1] holds the 4 x 4 support of
 // every sample, from a bound on the warped offsets (0.05 px slack covers the
-// evaluation of the positions), clamped to the image. False for a non-finite or
-// absurd warp, or when nothing of the support lies in the image.
+// evaluation of the positions), clamped to the image. *inside: every sample position
+// lies in the sampling bounds 1 <= x < W - 2, 1 <= y < H - 2 (then the per-sample
+// test can be skipped). False for a non-finite or absurd warp, or when nothing of
+// the support lies in the image.
 template <typename C, int NP>
 __device__ bool needed_range(const C* p, int xc, int yc, int r, int W, int H, int* x0, int* x1, int* y0,
-                             int* y1) {
+                             int* y1, int* inside) {
   float ex, ey;
   const float rf = static_cast<float>(r);
   const float q0 = static_cast<float>(p[0]), q1 = static_cast<float>(p[1]);
@@ -429,6 +432,8 @@ __device__ bool needed_range(const C* p, int xc, int yc, int r, int W, int H, in
   ex += 0.05f;
   ey += 0.05f;
   if (!(fabsf(q0) < 1e6f && fabsf(q1) < 1e6f && ex < 1e6f && ey < 1e6f)) return false;
+  *inside = static_cast<float>(xc) + q0 - ex >= 1.0f && static_cast<float>(xc) + q0 + ex < static_cast<float>(W - 2) &&
+            static_cast<float>(yc) + q1 - ey >= 1.0f && static_cast<float>(yc) + q1 + ey < static_cast<float>(H - 2);
   *x0 = max(xc + static_cast<int>(floorf(q0 - ex)) - 1, 0);
   *x1 = min(xc + static_cast<int>(floorf(q0 + ex)) + 2, W - 1);
   *y0 = max(yc + static_cast<int>(floorf(q1 - ey)) - 1, 0);
@@ -444,7 +449,8 @@ template <typename C, int NP>
 __device__ void plan_window(PointState<C, NP>& st, int xc, int yc, int r, int W, int H,
                             const WaveTiles& t, int xalign) {
   int x0, x1, y0, y1;
-  if (!needed_range<C, NP>(st.p, xc, yc, r, W, H, &x0, &x1, &y0, &y1)) {
+  st.inside = 0;
+  if (!needed_range<C, NP>(st.p, xc, yc, r, W, H, &x0, &x1, &y0, &y1, &st.inside)) {
     st.stage = 2;
     return;
   }
@@ -593,14 +599,15 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
                                               T ay, T by, T cyq, T xlo, T xhi, T ylo, T yhi, T f0,
                                               int row0, int row1, int r, int S, int col,
                                               const unsigned char* gtile, int gpitch, int gdtype,
-                                              const T* s_fx, const T* s_fy, bool fin, T* acc, T& bad) {
+                                              const T* s_fx, const T* s_fy, bool fin, bool inside, T* acc,
+                                              T& bad) {
   T c0[4], c1[4], c2[4], c3[4];
   int pix_ix = -0x40000000, pix_iy = -0x40000000;
   auto step = [&](T (&A)[4], T (&B)[4], T (&Cc)[4], T (&Dn)[4], int row) {
     const T dyv = static_cast<T>(row - r);
     const T xl = ax + dyv * (bx + cxq * dyv);
     const T yl = ay + dyv * (by + cyq * dyv);
-    if (!(xl >= xlo && xl < xhi && yl >= ylo && yl < yhi)) {
+    if (!inside && !(xl >= xlo && xl < xhi && yl >= ylo && yl < yhi)) {
       bad += T(1);
       pix_ix = -0x40000000;
       return;
@@ -922,15 +929,32 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
       for (int j = 0; j <= M2; ++j) A[0][j] = A[1][j] = A[2][j] = T(0);
 #pragma unroll
       for (int j = 0; j <= D; ++j) Bf[0][j] = Bf[1][j] = Bs[0][j] = Bs[1][j] = T(0);
+      // the column walk keeps the three coefficient rows around the pixel in
+      // registers: each row loads only the row below
+      T m0 = T(0), m1 = T(0), m2 = T(0), z0 = T(0), z2 = T(0);
+      if (row0 < row1) {
+        const T* cm = wref + row0 * tl.bxc + col;   // row above, column left
+        m0 = cm[0];
+        m1 = cm[1];
+        m2 = cm[2];
+        z0 = cm[tl.bxc];
+        z2 = cm[tl.bxc + 2];
+      }
+      T z1 = row0 < row1 ? wref[(row0 + 1) * tl.bxc + col + 1] : T(0);
       for (int row = row0; row < row1; ++row) {
         const int pix = row * S + col;
         // exact derivative of the reference spline at the pixel:
         // (-1/2, 0, 1/2) along one axis times (1, 4, 1)/6 along the other
-        const T* cm = wref + row * tl.bxc + col;     // row above, column left
-        const T* c0 = cm + tl.bxc;
-        const T* cp = c0 + tl.bxc;
-        const T fx = ((cm[2] - cm[0]) + T(4) * (c0[2] - c0[0]) + (cp[2] - cp[0])) * (T(1) / T(12));
-        const T fy = ((cp[0] - cm[0]) + T(4) * (cp[1] - cm[1]) + (cp[2] - cm[2])) * (T(1) / T(12));
+        const T* cp = wref + (row + 2) * tl.bxc + col;
+        const T p0 = cp[0], p1 = cp[1], p2 = cp[2];
+        const T fx = ((m2 - m0) + T(4) * (z2 - z0) + (p2 - p0)) * (T(1) / T(12));
+        const T fy = ((p0 - m0) + T(4) * (p1 - m1) + (p2 - m2)) * (T(1) / T(12));
+        m0 = z0;
+        m1 = z1;
+        m2 = z2;
+        z0 = p0;
+        z1 = p1;
+        z2 = p2;
         s_fx[pix] = fx;
         s_fy[pix] = fy;
         const T fp = tile_gray<T>(gtile, gpitch, gdt, col, row) - f0;
@@ -1047,7 +1071,7 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
       if (stage != 2) {
         const T* base = s_win + (yc - 1 - w.y0) * w.w + (xc - 1 - w.x0);
         sample_column<T, D>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r, S, col,
-                            gtile, gpitch, gdt, s_fx, s_fy, final_pass, acc, bad);
+                            gtile, gpitch, gdt, s_fx, s_fy, final_pass, st.inside != 0, acc, bad);
       } else {
         const T* base = a.c_def + static_cast<int64_t>(yc - 1) * a.ldc + (xc - 1);
         sample_column_global<T, D>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r,
