@@ -328,19 +328,6 @@ PointArrays point_arrays(dic_handle* h) {
   return pa;
 }
 
-void choose_bands(int S, int* bands, int* band_h) {
-  for (int hgt = 1; hgt <= S; ++hgt) {
-    const int b = (S + hgt - 1) / hgt;
-    if (S * b <= kWaveThreads) {
-      *bands = b;
-      *band_h = hgt;
-      return;
-    }
-  }
-  *bands = 1;
-  *band_h = S;
-}
-
 template <typename T>
 int run_waves(dic_handle* h, cudaStream_t s) {
   WaveArgs<T> a{};
@@ -355,7 +342,8 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   a.step = h->step;
   a.nx = h->nx;
   a.ny = h->ny;
-  choose_bands(h->S, &a.bands, &a.band_h);
+  a.threads = wave_threads(h->S);
+  wave_bands(h->S, a.threads, &a.bands, &a.band_h);
   a.tiles = wave_tiles<T>(h->S, h->ref.dtype);
   {
     const CUtensorMapDataType ct = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -378,7 +366,7 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   int sms = 0;
   DIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "device query");
   const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
-  const int per_sm = wave_blocks_per_sm<T>(h->nparams, smem);
+  const int per_sm = wave_blocks_per_sm<T>(h->nparams, a.threads, smem);
   const int grid = sms * per_sm;
 
   const bool prof = h->prm.profile != 0;

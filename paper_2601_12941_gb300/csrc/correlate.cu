@@ -709,15 +709,19 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
 }
 
 // resident blocks per SM the register budget is sized for
-template <typename T>
+template <typename T, int NT>
 struct WaveOccupancy;
 template <>
-struct WaveOccupancy<float> { static constexpr int kBlocks = 7; };
+struct WaveOccupancy<float, 128> { static constexpr int kBlocks = 7; };
 template <>
-struct WaveOccupancy<double> { static constexpr int kBlocks = 4; };
+struct WaveOccupancy<float, 64> { static constexpr int kBlocks = 14; };
+template <>
+struct WaveOccupancy<double, 128> { static constexpr int kBlocks = 4; };
+template <>
+struct WaveOccupancy<double, 64> { static constexpr int kBlocks = 8; };
 
-template <typename T, int NP>
-__global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
+template <typename T, int NP, int NT>
+__global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
     wave_kernel(WaveArgs<T> a, const __grid_constant__ CUtensorMap tm_cref,
                 const __grid_constant__ CUtensorMap tm_cdef, const __grid_constant__ CUtensorMap tm_gray) {
   using C = T;  // working precision of the per-point control arithmetic
@@ -729,6 +733,7 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
   constexpr int NV_FIN = 4;                      // sum g', sum g'^2, sum f' g', bad samples
   constexpr int NACC = 2 + 2 * (D + 1);
   constexpr int XALIGN = 16 / static_cast<int>(sizeof(T));   // TMA x alignment of the coefficient planes
+  constexpr int NW = NT / 32;                                 // warps per block
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const WaveTiles& tl = a.tiles;
@@ -740,7 +745,7 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
   const int gdt = a.ref_gray.dtype;
   const int gpitch = tl.bxg * tl.gray_es;
 
-  __shared__ T s_part[kWaveWarps][NV_PRE];
+  __shared__ T s_part[NW][NV_PRE];
   __shared__ C s_out[NV_PRE];
   __shared__ PointState<C, NP> st;
   __shared__ __align__(8) uint64_t s_bar;
@@ -794,7 +799,7 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
     for (int i = lane; i < nv; i += 32) {
       C sacc = C(0);
 #pragma unroll
-      for (int w = 0; w < kWaveWarps; ++w) sacc += s_part[w][i];
+      for (int w = 0; w < NW; ++w) sacc += s_part[w][i];
       s_out[i] = sacc;
     }
     __syncwarp();
@@ -881,7 +886,7 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
         if (tl.gray_tma) tma_load_2d(s_gray, &tm_gray, gxa, yc - r, &s_bar);
       }
       if (!tl.coef_tma) {
-        for (int row = warp; row < S + 2; row += kWaveWarps) {
+        for (int row = warp; row < S + 2; row += NW) {
           const int gy = mirror_near(ry0 + row, a.H);
           const T* src = a.c_ref + static_cast<int64_t>(gy) * a.ldc;
           T* dst = s_win + row * tl.bxc + (rx0 - rxa);
@@ -890,7 +895,7 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
       }
       if (!tl.gray_tma) {
         const int es = tl.gray_es;
-        for (int row = warp; row < S; row += kWaveWarps) {
+        for (int row = warp; row < S; row += NW) {
           const unsigned char* src = static_cast<const unsigned char*>(a.ref_gray.data) +
                                      static_cast<int64_t>(yc - r + row) * a.ref_gray.stride +
                                      static_cast<int64_t>(gxa) * es;
@@ -906,12 +911,12 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
       // mirror the coefficient rows and columns that fall outside the image
       if (tl.coef_tma && (rx0 < 0 || ry0 < 0 || rx0 + S + 2 > a.W || ry0 + S + 2 > a.H)) {
         T* w0 = s_win + (rx0 - rxa);
-        for (int e = tid; e < S + 2; e += kWaveThreads) {
+        for (int e = tid; e < S + 2; e += NT) {
           if (rx0 < 0) w0[e * tl.bxc + 0] = w0[e * tl.bxc + 2];
           if (rx0 + S + 2 > a.W) w0[e * tl.bxc + S + 1] = w0[e * tl.bxc + S - 1];
         }
         __syncthreads();
-        for (int e = tid; e < S + 2; e += kWaveThreads) {
+        for (int e = tid; e < S + 2; e += NT) {
           if (ry0 < 0) w0[e] = w0[2 * tl.bxc + e];
           if (ry0 + S + 2 > a.H) w0[(S + 1) * tl.bxc + e] = w0[(S - 1) * tl.bxc + e];
         }
@@ -1040,7 +1045,7 @@ __global__ void __launch_bounds__(kWaveThreads, WaveOccupancy<T>::kBlocks)
         }
         if (!tma_wait()) return;
       } else if (stage == 3) {
-        for (int row = warp; row < w.h; row += kWaveWarps) {
+        for (int row = warp; row < w.h; row += NW) {
           const T* src = a.c_def + static_cast<int64_t>(w.y0 + row) * a.ldc + w.x0;
           T* dst = s_win + row * w.w;
           for (int c = lane; c < w.w; c += 32) dst[c] = src[c];
@@ -1270,38 +1275,50 @@ __global__ void finalize_points_kernel(PointArrays pa, int nparams, int nan_reje
 // Raises the kernel's dynamic shared-memory limit to the device's opt-in limit
 // less its static shared memory, once per instantiation (thread-safe); the
 // largest tile set (S = 61, FP64 coefficients, 8-byte gray) stays below it.
-template <typename T, int NP>
+template <typename T, int NP, int NT>
 cudaError_t configure_wave_smem() {
   static const cudaError_t result = []() {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa{};
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, wave_kernel<T, NP>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, wave_kernel<T, NP, NT>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(wave_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(wave_kernel<T, NP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin - static_cast<int>(fa.sharedSizeBytes));
     return e;
   }();
   return result;
 }
 
-template <typename T, int NP>
-cudaError_t launch_wave_np(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
+template <typename T, int NP, int NT>
+cudaError_t launch_wave_nt(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
   const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
-  const cudaError_t configured = configure_wave_smem<T, NP>();
+  const cudaError_t configured = configure_wave_smem<T, NP, NT>();
   if (configured != cudaSuccess) return configured;
-  wave_kernel<T, NP><<<grid, kWaveThreads, smem, s>>>(a, maps[0], maps[1], maps[2]);
+  wave_kernel<T, NP, NT><<<grid, NT, smem, s>>>(a, maps[0], maps[1], maps[2]);
   return cudaGetLastError();
 }
 
 template <typename T, int NP>
-int blocks_per_sm_np(size_t smem) {
-  if (configure_wave_smem<T, NP>() != cudaSuccess) return 1;
+cudaError_t launch_wave_np(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
+  return a.threads == kWaveThreadsSmall ? launch_wave_nt<T, NP, kWaveThreadsSmall>(a, maps, grid, s)
+                                        : launch_wave_nt<T, NP, kWaveThreads>(a, maps, grid, s);
+}
+
+template <typename T, int NP, int NT>
+int blocks_per_sm_nt(size_t smem) {
+  if (configure_wave_smem<T, NP, NT>() != cudaSuccess) return 1;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<T, NP>, kWaveThreads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<T, NP, NT>, NT, smem) != cudaSuccess)
     return 1;
   return nb > 0 ? nb : 1;
+}
+
+template <typename T, int NP>
+int blocks_per_sm_np(int threads, size_t smem) {
+  return threads == kWaveThreadsSmall ? blocks_per_sm_nt<T, NP, kWaveThreadsSmall>(smem)
+                                      : blocks_per_sm_nt<T, NP, kWaveThreads>(smem);
 }
 
 }  // namespace
@@ -1341,14 +1358,14 @@ cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensor
 }
 
 template <typename T>
-int wave_blocks_per_sm(int nparams, size_t smem) {
+int wave_blocks_per_sm(int nparams, int threads, size_t smem) {
   switch (nparams) {
     case 2:
-      return blocks_per_sm_np<T, 2>(smem);
+      return blocks_per_sm_np<T, 2>(threads, smem);
     case 6:
-      return blocks_per_sm_np<T, 6>(smem);
+      return blocks_per_sm_np<T, 6>(threads, smem);
     default:
-      return blocks_per_sm_np<T, 12>(smem);
+      return blocks_per_sm_np<T, 12>(threads, smem);
   }
 }
 
@@ -1395,7 +1412,7 @@ template cudaError_t launch_wave<float>(const WaveArgs<float>&, const WaveTiles&
                                         cudaStream_t);
 template cudaError_t launch_wave<double>(const WaveArgs<double>&, const WaveTiles&, const CUtensorMap*, int, int,
                                          cudaStream_t);
-template int wave_blocks_per_sm<float>(int, size_t);
-template int wave_blocks_per_sm<double>(int, size_t);
+template int wave_blocks_per_sm<float>(int, int, size_t);
+template int wave_blocks_per_sm<double>(int, int, size_t);
 
 }  // namespace dic

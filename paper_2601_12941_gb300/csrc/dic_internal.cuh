@@ -11,8 +11,8 @@
 namespace dic {
 
 constexpr int kThreads = 256;        // threads per block of the image kernels
-constexpr int kWaveThreads = 128;    // threads per block of the subset (wave) kernel
-constexpr int kWaveWarps = kWaveThreads / 32;
+constexpr int kWaveThreads = 128;    // threads per block of the subset (wave) kernel, S > 31
+constexpr int kWaveThreadsSmall = 64;  // the same for S <= 31
 constexpr int kMaxSubset = 61;       // largest odd subset side supported
 constexpr int kMaxParams = 12;
 
@@ -181,8 +181,9 @@ struct WaveArgs {
   int64_t ldc;
   // subset grid
   int S, r, step, nx, ny;
+  int threads;               // block size (wave_threads(S))
   int bands, band_h;         // thread t < S*bands: column t % S, rows band_h*(t/S) ...
-                             // (S * bands <= kWaveThreads)
+                             // (S * bands <= threads)
   WaveTiles tiles;
   // per-point state
   PointArrays pts;
@@ -199,6 +200,27 @@ struct WaveArgs {
   double zncc_min;
 };
 
+// Block size of the wave kernel for subset side S: two warps up to S = 31, four
+// above. A point's serial steps run on warp 0 while the block's other warps wait,
+// so smaller blocks for small subsets (whose shared memory allows twice as many
+// resident points) keep more warps busy.
+inline int wave_threads(int S) { return S <= 31 ? kWaveThreadsSmall : kWaveThreads; }
+
+// Thread t < S * bands owns column t % S and rows [band_h (t / S), band_h (t / S + 1))
+// of the subset: the fewest rows per band with S * bands <= threads.
+inline void wave_bands(int S, int threads, int* bands, int* band_h) {
+  for (int hgt = 1; hgt <= S; ++hgt) {
+    const int b = (S + hgt - 1) / hgt;
+    if (S * b <= threads) {
+      *bands = b;
+      *band_h = hgt;
+      return;
+    }
+  }
+  *bands = 1;
+  *band_h = S;
+}
+
 template <typename T>
 WaveTiles wave_tiles(int S, int gray_dtype);
 
@@ -207,6 +229,6 @@ cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensor
                         int grid, cudaStream_t s);
 
 template <typename T>
-int wave_blocks_per_sm(int nparams, size_t smem);
+int wave_blocks_per_sm(int nparams, int threads, size_t smem);
 
 }  // namespace dic

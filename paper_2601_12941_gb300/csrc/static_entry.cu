@@ -264,14 +264,8 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   a.step = subset_step;
   a.nx = nx;
   a.ny = ny;
-  for (int hgt = 1; hgt <= subset_size; ++hgt) {
-    const int b = (subset_size + hgt - 1) / hgt;
-    if (subset_size * b <= kWaveThreads) {
-      a.bands = b;
-      a.band_h = hgt;
-      break;
-    }
-  }
+  a.threads = wave_threads(subset_size);
+  wave_bands(subset_size, a.threads, &a.bands, &a.band_h);
   a.tiles = wave_tiles<float>(subset_size, ref->dtype);
   CUtensorMap maps[3];
   const bool m0 = encode_plane_static(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, c_ref, W, H, ldc * 4,
@@ -292,7 +286,7 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   int dev = 0, sms = 0;
   SCUDA(cudaGetDevice(&dev), "cudaGetDevice");
   SCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
-  const int grid = sms * wave_blocks_per_sm<float>(nparams, static_cast<size_t>(a.tiles.smem_bytes));
+  const int grid = sms * wave_blocks_per_sm<float>(nparams, a.threads, static_cast<size_t>(a.tiles.smem_bytes));
   int32_t hc[kNumCounters];
   int64_t k = 0;
   const int64_t max_waves = npts + 2;
