@@ -584,6 +584,80 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
   return n2 < thr2 ? 1 : 0;
 }
 
+// Two values that go through the same arithmetic (an x quantity with its y
+// counterpart): on the mixed path one packed FP32x2 instruction per operation,
+// rounded exactly like the two scalar operations; on the FP64 path two scalar ones.
+template <typename T>
+struct alignas(2 * sizeof(T)) Pair {
+  T x, y;
+};
+template <typename T>
+__device__ __forceinline__ Pair<T> pair(T a, T b) {
+  return Pair<T>{a, b};
+}
+template <typename T>
+__device__ __forceinline__ Pair<T> pfma(Pair<T> a, Pair<T> b, Pair<T> c) {   // a b + c
+  return Pair<T>{fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)};
+}
+template <typename T>
+__device__ __forceinline__ Pair<T> pmul(Pair<T> a, Pair<T> b) {
+  return Pair<T>{a.x * b.x, a.y * b.y};
+}
+template <typename T>
+__device__ __forceinline__ Pair<T> padd(Pair<T> a, Pair<T> b) {
+  return Pair<T>{a.x + b.x, a.y + b.y};
+}
+template <typename T>
+__device__ __forceinline__ Pair<T> psub(Pair<T> a, Pair<T> b) {
+  return Pair<T>{a.x - b.x, a.y - b.y};
+}
+__device__ __forceinline__ unsigned long long pair_bits(Pair<float> a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ Pair<float> bits_pair(unsigned long long r) {
+  Pair<float> a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+template <>
+__device__ __forceinline__ Pair<float> pfma<float>(Pair<float> a, Pair<float> b, Pair<float> c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pair_bits(a)), "l"(pair_bits(b)), "l"(pair_bits(c)));
+  return bits_pair(d);
+}
+template <>
+__device__ __forceinline__ Pair<float> pmul<float>(Pair<float> a, Pair<float> b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pair_bits(a)), "l"(pair_bits(b)));
+  return bits_pair(d);
+}
+template <>
+__device__ __forceinline__ Pair<float> padd<float>(Pair<float> a, Pair<float> b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pair_bits(a)), "l"(pair_bits(b)));
+  return bits_pair(d);
+}
+template <>
+__device__ __forceinline__ Pair<float> psub<float>(Pair<float> a, Pair<float> b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pair_bits(a)), "l"(pair_bits(b)));
+  return bits_pair(d);
+}
+
+// bspline_weights6 of two offsets at once (x in .x, y in .y), the same arithmetic
+template <typename T>
+__device__ __forceinline__ void bspline_weights6_pair(Pair<T> t, Pair<T>& w0, Pair<T>& w1, Pair<T>& w2,
+                                                      Pair<T>& w3) {
+  const Pair<T> s = psub(pair(T(1), T(1)), t);
+  const Pair<T> t2 = pmul(t, t), s2 = pmul(s, s);
+  w3 = pmul(t2, t);
+  w0 = pmul(s2, s);
+  w1 = pfma(t2, pfma(pair(T(3), T(3)), t, pair(T(-6), T(-6))), pair(T(4), T(4)));
+  w2 = pfma(s2, pfma(pair(T(3), T(3)), s, pair(T(-6), T(-6))), pair(T(4), T(4)));
+}
+
 // Sums over one thread's column of subset pixels at the warp given by
 // (ax, bx, cxq; ay, by, cyq): x = ax + dy (bx + cxq dy), y = ay + dy (by + cyq dy)
 // relative to the centre. The support of a sample at (ix + tx, iy + ty) starts at
@@ -599,14 +673,18 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
                                               T ay, T by, T cyq, T xlo, T xhi, T ylo, T yhi, T f0,
                                               int row0, int row1, int r, int S, int col,
                                               const unsigned char* gtile, int gpitch, int gdtype,
-                                              const T* s_fx, const T* s_fy, bool fin, bool inside, T* acc,
-                                              T& bad) {
+                                              const Pair<T>* s_fg, bool fin, bool inside, T* acc, T& bad) {
   T c0[4], c1[4], c2[4], c3[4];
+  Pair<T> sd[D + 1];   // sum fx g' dy^j in .x, sum fy g' dy^j in .y
+#pragma unroll
+  for (int j = 0; j <= D; ++j) sd[j] = pair(T(0), T(0));
+  const Pair<T> a2 = pair(ax, ay), b2 = pair(bx, by), cq2 = pair(cxq, cyq);
   int pix_ix = -0x40000000, pix_iy = -0x40000000;
   auto step = [&](T (&A)[4], T (&B)[4], T (&Cc)[4], T (&Dn)[4], int row) {
     const T dyv = static_cast<T>(row - r);
-    const T xl = ax + dyv * (bx + cxq * dyv);
-    const T yl = ay + dyv * (by + cyq * dyv);
+    const Pair<T> dy2 = pair(dyv, dyv);
+    const Pair<T> xy = D >= 2 ? pfma(dy2, pfma(cq2, dy2, b2), a2) : pfma(dy2, b2, a2);
+    const T xl = xy.x, yl = xy.y;
     if (!inside && !(xl >= xlo && xl < xhi && yl >= ylo && yl < yhi)) {
       bad += T(1);
       pix_ix = -0x40000000;
@@ -627,9 +705,10 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
     for (int k = 0; k < 4; ++k) Dn[k] = b[3 * ld + k];
     pix_ix = ix;
     pix_iy = iy;
-    T wx0, wx1, wx2, wx3, wy0, wy1, wy2, wy3;
-    bspline_weights6<T>(xl - xf, wx0, wx1, wx2, wx3);
-    bspline_weights6<T>(yl - yf, wy0, wy1, wy2, wy3);
+    Pair<T> w0, w1, w2, w3;
+    bspline_weights6_pair<T>(psub(xy, pair(xf, yf)), w0, w1, w2, w3);
+    const T wx0 = w0.x, wx1 = w1.x, wx2 = w2.x, wx3 = w3.x;
+    const T wy0 = w0.y, wy1 = w1.y, wy2 = w2.y, wy3 = w3.y;
     const T r0 = wx0 * A[0] + wx1 * A[1] + wx2 * A[2] + wx3 * A[3];
     const T r1 = wx0 * B[0] + wx1 * B[1] + wx2 * B[2] + wx3 * B[3];
     const T r2 = wx0 * Cc[0] + wx1 * Cc[1] + wx2 * Cc[2] + wx3 * Cc[3];
@@ -640,14 +719,13 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
     if (fin) {
       acc[2] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
     } else {
-      const int pix = row * S + col;
-      const T gxv = gp * s_fx[pix], gyv = gp * s_fy[pix];
-      T dyp = T(1);
+      const Pair<T> g2 = pmul(pair(gp, gp), s_fg[row * S + col]);   // (fx g', fy g')
+      sd[0] = padd(sd[0], g2);
+      Pair<T> dyp = dy2;
 #pragma unroll
-      for (int j = 0; j <= D; ++j) {
-        acc[2 + j] += gxv * dyp;
-        acc[2 + D + 1 + j] += gyv * dyp;
-        dyp *= dyv;
+      for (int j = 1; j <= D; ++j) {
+        sd[j] = pfma(g2, dyp, sd[j]);
+        if (j < D) dyp = pmul(dyp, dy2);
       }
     }
   };
@@ -656,6 +734,13 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
     if (row + 1 < row1) step(c1, c2, c3, c0, row + 1);
     if (row + 2 < row1) step(c2, c3, c0, c1, row + 2);
     if (row + 3 < row1) step(c3, c0, c1, c2, row + 3);
+  }
+  if (!fin) {
+#pragma unroll
+    for (int j = 0; j <= D; ++j) {
+      acc[2 + j] += sd[j].x;
+      acc[2 + D + 1 + j] += sd[j].y;
+    }
   }
 }
 
@@ -667,8 +752,8 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
                                                      T bx, T cxq, T ay, T by, T cyq, T xlo, T xhi,
                                                      T ylo, T yhi, T f0, int row0, int row1, int r,
                                                      int S, int col, const unsigned char* gtile,
-                                                     int gpitch, int gdtype, const T* s_fx,
-                                                     const T* s_fy, bool fin, T* acc, T& bad) {
+                                                     int gpitch, int gdtype, const Pair<T>* s_fg, bool fin,
+                                                     T* acc, T& bad) {
   for (int row = row0; row < row1; ++row) {
     const T dyv = static_cast<T>(row - r);
     const T xl = ax + dyv * (bx + cxq * dyv);
@@ -695,8 +780,8 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
     if (fin) {
       acc[2] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
     } else {
-      const int pix = row * S + col;
-      const T gxv = gp * s_fx[pix], gyv = gp * s_fy[pix];
+      const Pair<T> fg = s_fg[row * S + col];
+      const T gxv = gp * fg.x, gyv = gp * fg.y;
       T dyp = T(1);
 #pragma unroll
       for (int j = 0; j <= D; ++j) {
@@ -738,8 +823,8 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const WaveTiles& tl = a.tiles;
   const int S = a.S, r = a.r, N = S * S;
-  T* s_fx = reinterpret_cast<T*>(smem_raw + tl.off_fx);
-  T* s_fy = reinterpret_cast<T*>(smem_raw + tl.off_fy);
+  // reference gradients (fx, fy) of the subset pixels, interleaved
+  Pair<T>* s_fg = reinterpret_cast<Pair<T>*>(smem_raw + tl.off_fx);
   T* s_win = reinterpret_cast<T*>(smem_raw + tl.off_win);
   unsigned char* s_gray = smem_raw + tl.off_gray;
   const int gdt = a.ref_gray.dtype;
@@ -960,8 +1045,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
         z0 = p0;
         z1 = p1;
         z2 = p2;
-        s_fx[pix] = fx;
-        s_fy[pix] = fy;
+        s_fg[pix] = pair(fx, fy);
         const T fp = tile_gray<T>(gtile, gpitch, gdt, col, row) - f0;
         sf += fp;
         sff += fp * fp;
@@ -1076,11 +1160,11 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
       if (stage != 2) {
         const T* base = s_win + (yc - 1 - w.y0) * w.w + (xc - 1 - w.x0);
         sample_column<T, D>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r, S, col,
-                            gtile, gpitch, gdt, s_fx, s_fy, final_pass, st.inside != 0, acc, bad);
+                            gtile, gpitch, gdt, s_fg, final_pass, st.inside != 0, acc, bad);
       } else {
         const T* base = a.c_def + static_cast<int64_t>(yc - 1) * a.ldc + (xc - 1);
         sample_column_global<T, D>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r,
-                                   S, col, gtile, gpitch, gdt, s_fx, s_fy, final_pass, acc, bad);
+                                   S, col, gtile, gpitch, gdt, s_fg, final_pass, acc, bad);
       }
       if (!final_pass) {
         T v[pow2ceil(NV_IT)];
@@ -1335,9 +1419,10 @@ WaveTiles wave_tiles(int S, int gray_dtype) {
   t.bxg = ((S + galign - 1 + galign - 1) / galign) * galign;
   const int SS = ((S * S + 31) / 32) * 32;
   auto al = [](int x) { return (x + 127) & ~127; };
+  // reference gradients: (fx, fy) pairs of T per subset pixel
   t.off_fx = 0;
-  t.off_fy = al(t.off_fx + SS * static_cast<int>(sizeof(T)));
-  t.off_win = al(t.off_fy + SS * static_cast<int>(sizeof(T)));
+  t.off_fy = 0;
+  t.off_win = al(2 * SS * static_cast<int>(sizeof(T)));
   t.off_gray = al(t.off_win + t.bxc * t.byc * static_cast<int>(sizeof(T)));
   t.smem_bytes = al(t.off_gray + t.bxg * S * t.gray_es);
   return t;
