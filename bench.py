@@ -40,10 +40,9 @@ FLOP_ITER = {2: 64, 6: 84, 12: 108}
 FLOP_FINAL = 72
 
 
-# DRAM bytes (read + write) per point of the wave kernel in its current form, from one
-# full ncu capture of two mid-run waves of 2,560 points each on the 6144^2 version of the
-# same workload (32.33 MB per launch); traffic grows with the points a launch processes.
-WAVE_DRAM_BYTES_PER_POINT = 12_629
+# DRAM bytes (read + write) per point of the wave kernel as last captured by ncu, or
+# None when the kernel has changed since (the roofline then reports no traffic)
+WAVE_DRAM_BYTES_PER_POINT = None
 
 
 def fp32_peak_tflops():
@@ -263,8 +262,9 @@ def run_ours(args):
            "roofline": {"bound": "alu", "kernel": "wave_kernel (fused reference precompute, IC-GN, ZNCC, claims)",
                         "achieved": achieved, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
                         "frac": achieved / fp32_peak_tflops(),
-                        "traffic": WAVE_DRAM_BYTES_PER_POINT * attempted / (sum(wave_launches) / len(wave_launches)),
-                        "traffic_note": "bytes per launch: 12.6 KB per point (ncu, 6144^2 case) x attempted "
+                        "traffic": (WAVE_DRAM_BYTES_PER_POINT * attempted / (sum(wave_launches) / len(wave_launches))
+                                    if WAVE_DRAM_BYTES_PER_POINT else None),
+                        "traffic_note": "bytes per launch: DRAM bytes per point (ncu, 6144^2 case) x attempted "
                                         "points per wave launch; algorithmic bytes are not the bound (ALU)",
                         "peak_note": "FP32 peak from 152 SMs x 128 lanes x 2 x 2070 MHz (no measured FP32 peak)",
                         "kernel_ms_per_step": kern_avg, "share_of_step": kern_avg / (total_ms / args.steps),
