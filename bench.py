@@ -282,6 +282,8 @@ def run_ours(args):
                              "speedup_of_mixed": value / v64 if v64 else None}
         c64.close()
 
+    if not args.no_strain:
+        out["strain"] = strain_leg(c, w, stream)
     if not args.no_e2e:
         out["e2e"] = e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_ranks)
     c.close()
@@ -299,6 +301,52 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (generated file), else the
+    recipe's fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def strain_leg(c, w, stream, window=9, basis="biquadratic", measure="green_lagrange", reps=20):
+    """Sec. 2.3 strain of the step's displacement field (10.7 M points): one kernel
+    over the grid, HBM-bound. Algorithmic bytes per point: u, v (FP64) and status
+    read once, seven FP32 components and the valid flag written: 46 B."""
+    import torch
+
+    from paper_2601_12941_gb300 import binding as B
+
+    r = c.results(on_device=True)
+    n = int(r["n_points"])
+    outs = B.strain_outputs(n)
+    args = (r["u"], r["v"], r["status"], r["nx"], r["ny"], w.subset_step, window, basis, measure, outs,
+            stream.cuda_stream)
+    for _ in range(3):
+        B.dic_strain_field(*args)
+    ms = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.dic_strain_field(*args)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.median(ms))
+    bytes_per_point = 2 * 8 + 1 + 7 * 4 + 1
+    gbs = bytes_per_point * n / (t / 1e3) / 1e9
+    peak, note = hbm_peak_gbs()
+    valid = int(outs["valid"].sum().item())
+    return {"window": window, "basis": basis, "measure": measure,
+            "vsg_px": (window - 1) * w.subset_step + w.subset_size, "points": n, "valid": valid,
+            "ms": t, "points_per_s": n / (t / 1e3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_note": note, "algorithmic_bytes_per_point": bytes_per_point}}
 
 
 def e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_ranks):
@@ -521,6 +569,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-strain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-jobs", type=int, default=40,
                     help="jobs in the serving stream (0: skip the serving leg)")

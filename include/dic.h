@@ -198,6 +198,54 @@ int dic_get_coefficients(const dic_handle* h, int32_t which, const void** plane,
 /* Stage timings of the last dic_correlate; zeros unless params.profile = 1. */
 int dic_get_timing(const dic_handle* h, dic_timing* out);
 
+/* ---- strain (Sec. 2.3) -----------------------------------------------------
+ *
+ * At every grid point: the displacement gradient of a least-squares fit
+ * u(x, y) = P(x, y) c over the window x window grid points centred on it (Eq. 8-9),
+ * the deformation gradient F = I + grad u (Eq. 6) and one strain measure. The
+ * virtual strain gauge is (window - 1) subset_step + subset_size pixels (Eq. 7).
+ * Readings where the paper is silent: the window is centred on its point and
+ * grad u is the slope of the fit there; only accepted points (status 0) inside the
+ * grid enter a window and the centre must be accepted; the fit needs at least as
+ * many points as basis terms and a well-posed design (the unit-diagonal normal
+ * matrix in grid units keeps every elimination pivot above 1e-5), otherwise the
+ * point has no strain (NaN, valid 0). The bases are taken as printed (no xy term).
+ * FP32 arithmetic on displacements taken relative to the window's centre. */
+typedef enum { DIC_STRAIN_BILINEAR = 0, DIC_STRAIN_BIQUADRATIC = 1 } dic_strain_basis;
+
+/* Sec. 2.3: Green-Lagrange (F^T F - I)/2; Hencky ln sqrt(F^T F); Euler-Almansi
+ * (I - (F F^T)^-1)/2; Biot right sqrt(F^T F) - I; Biot left sqrt(F F^T) - I. */
+typedef enum {
+  DIC_GREEN_LAGRANGE = 0,
+  DIC_HENCKY = 1,
+  DIC_EULER_ALMANSI = 2,
+  DIC_BIOT_RIGHT = 3,
+  DIC_BIOT_LEFT = 4
+} dic_strain_measure;
+
+/* Device arrays of nx * ny elements in grid order, owned by the caller: the
+ * displacement gradient (du/dx, du/dy, dv/dx, dv/dy), the strain tensor
+ * components (exx, eyy and the tensor shear exy), and 1 where the point has them. */
+typedef struct {
+  float* dudx;
+  float* dudy;
+  float* dvdx;
+  float* dvdy;
+  float* exx;
+  float* eyy;
+  float* exy;
+  uint8_t* valid;
+} dic_strain_outputs;
+
+/* Strain of a displacement field on the subset grid: u, v and status are device
+ * arrays of nx * ny elements in grid order (as dic_get_results gives them on the
+ * device), subset_step the grid step in pixels, window odd in [3, 31]. Launches one
+ * kernel on cuda_stream and returns; allocates nothing. Errors: DIC_EINVAL (a NULL
+ * pointer, an empty grid, step < 1, a bad window, basis or measure), DIC_ECUDA. */
+int dic_strain_field(const double* u, const double* v, const uint8_t* status, int32_t nx, int32_t ny,
+                     int32_t subset_step, int32_t window, int32_t basis, int32_t measure,
+                     const dic_strain_outputs* out, void* cuda_stream);
+
 /* ---- serving support (the paper has no counterpart) ----------------------
  *
  * A server that keeps one handle per reference image answers later jobs on the

@@ -20,6 +20,12 @@ DIC_FP64, DIC_MIXED = 0, 1
 (PT_OK, PT_NOT_IN_ROI, PT_NOT_REACHED, PT_OUT_OF_BOUNDS, PT_MAX_ITER, PT_LOW_ZNCC, PT_SINGULAR,
  PT_FLAT) = range(8)
 SHAPES = {"rigid": DIC_RIGID, "affine": DIC_AFFINE, "quadratic": DIC_QUADRATIC}
+DIC_STRAIN_BILINEAR, DIC_STRAIN_BIQUADRATIC = 0, 1
+DIC_GREEN_LAGRANGE, DIC_HENCKY, DIC_EULER_ALMANSI, DIC_BIOT_RIGHT, DIC_BIOT_LEFT = range(5)
+STRAIN_BASES = {"bilinear": DIC_STRAIN_BILINEAR, "biquadratic": DIC_STRAIN_BIQUADRATIC}
+STRAIN_MEASURES = {"green_lagrange": DIC_GREEN_LAGRANGE, "hencky": DIC_HENCKY,
+                   "euler_almansi": DIC_EULER_ALMANSI, "biot_right": DIC_BIOT_RIGHT, "biot_left": DIC_BIOT_LEFT}
+STRAIN_FIELDS = ("dudx", "dudy", "dvdx", "dvdy", "exx", "eyy", "exy", "valid")
 N_PARAMS = {DIC_RIGID: 2, DIC_AFFINE: 6, DIC_QUADRATIC: 12}
 
 # every function declared in include/dic.h
@@ -27,7 +33,8 @@ EXPORTS = ("dic_default_params", "dic_create", "dic_set_params", "dic_get_params
            "dic_set_reference", "dic_set_deformed", "dic_correlate", "dic_get_results",
            "dic_get_coefficients", "dic_get_timing", "dic_destroy", "dic_last_error",
            "dic_correlate_static", "dic_correlate_sequence", "dic_set_subsets",
-           "dic_estimate_device_bytes", "dic_estimate_regrid_bytes", "dic_get_device_bytes")
+           "dic_estimate_device_bytes", "dic_estimate_regrid_bytes", "dic_get_device_bytes",
+           "dic_strain_field")
 
 
 class DicImage(ctypes.Structure):
@@ -65,6 +72,10 @@ class DicStaticOutputs(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("p", ctypes.c_void_p),
                 ("zncc", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("converged", ctypes.c_void_p),
                 ("status", ctypes.c_void_p), ("wave", ctypes.c_void_p), ("n_accepted", ctypes.c_void_p)]
+
+
+class DicStrainOutputs(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in STRAIN_FIELDS]
 
 
 class DicError(RuntimeError):
@@ -127,6 +138,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dic_estimate_regrid_bytes.argtypes = [vp, P(DicImage), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int32, P(DicParams), ctypes.c_int32, P(ctypes.c_int64)]
     lib.dic_estimate_regrid_bytes.restype = ctypes.c_int
+    lib.dic_strain_field.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int32, P(DicStrainOutputs), vp]
+    lib.dic_strain_field.restype = ctypes.c_int
     lib.dic_get_device_bytes.argtypes = [vp, P(ctypes.c_int64)]
     lib.dic_get_device_bytes.restype = ctypes.c_int
     _lib = lib
@@ -353,6 +367,26 @@ def dic_correlate_static(ref, deformed, subset_size, subset_step, shape_fn, prm:
     return acc.value
 
 
+def dic_strain_field(u, v, status, nx, ny, subset_step, window, basis, measure, out: dict, stream_ptr: int = 0):
+    """Sec. 2.3 strain on device arrays: u, v (float64), status (uint8) CUDA tensors of
+    nx * ny points; out maps STRAIN_FIELDS to CUDA tensors (float32, valid uint8)."""
+    basis = STRAIN_BASES[basis] if isinstance(basis, str) else basis
+    measure = STRAIN_MEASURES[measure] if isinstance(measure, str) else measure
+    o = DicStrainOutputs(*[out[k].data_ptr() for k in STRAIN_FIELDS])
+    _check(load().dic_strain_field(ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                   ctypes.c_void_p(status.data_ptr()), nx, ny, subset_step, window, basis, measure,
+                                   ctypes.byref(o), ctypes.c_void_p(stream_ptr)))
+
+
+def strain_outputs(n: int, device="cuda") -> dict:
+    """Output tensors for dic_strain_field over n points."""
+    import torch
+
+    out = {k: torch.empty(n, dtype=torch.float32, device=device) for k in STRAIN_FIELDS[:-1]}
+    out["valid"] = torch.empty(n, dtype=torch.uint8, device=device)
+    return out
+
+
 def params(**kw) -> DicParams:
     """Default parameters with the given fields replaced (precision may be a string)."""
     p = dic_default_params()
@@ -369,6 +403,7 @@ class Correlation:
     def __init__(self, ref, deformed, roi=None, subset_size=21, subset_step=5, shape="affine",
                  **param_kw):
         self.shape = SHAPES[shape] if isinstance(shape, str) else shape
+        self.step = subset_step
         self.h, self._keep = dic_create(ref, deformed, roi, subset_size, subset_step, self.shape)
         if param_kw:
             dic_set_params(self.h, params(**param_kw))
@@ -392,6 +427,7 @@ class Correlation:
         shape = SHAPES[shape] if isinstance(shape, str) else shape
         dic_set_subsets(self.h, roi, subset_size, subset_step, shape)
         self.shape = shape
+        self.step = subset_step
 
     def device_bytes(self) -> int:
         return dic_get_device_bytes(self.h)
@@ -410,6 +446,14 @@ class Correlation:
 
     def timing(self):
         return dic_get_timing(self.h)
+
+    def strain(self, window=9, basis="biquadratic", measure="green_lagrange", stream_ptr: int = 0) -> dict:
+        """Sec. 2.3 strain of the last correlation: CUDA tensors per STRAIN_FIELDS."""
+        r = self.results(on_device=True)
+        out = strain_outputs(r["n_points"])
+        dic_strain_field(r["u"], r["v"], r["status"], r["nx"], r["ny"], self.step, window, basis, measure, out,
+                         stream_ptr)
+        return out
 
     def close(self):
         if self.h is not None:

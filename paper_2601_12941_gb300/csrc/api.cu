@@ -979,6 +979,60 @@ int dic_get_timing(const dic_handle* h, dic_timing* out) {
   return DIC_OK;
 }
 
+int dic_strain_field(const double* u, const double* v, const uint8_t* status, int32_t nx, int32_t ny,
+                     int32_t subset_step, int32_t window, int32_t basis, int32_t measure,
+                     const dic_strain_outputs* out, void* cuda_stream) {
+  g_last_error.clear();
+  if (!u || !v || !status || !out) return fail(DIC_EINVAL, "NULL argument");
+  if (!out->dudx || !out->dudy || !out->dvdx || !out->dvdy || !out->exx || !out->eyy || !out->exy || !out->valid)
+    return fail(DIC_EINVAL, "an output array is NULL");
+  if (nx < 1 || ny < 1) return fail(DIC_EINVAL, "grid %dx%d is empty", nx, ny);
+  if (subset_step < 1) return fail(DIC_EINVAL, "subset_step %d must be >= 1", subset_step);
+  if (window < 3 || window > 31 || window % 2 == 0)
+    return fail(DIC_EINVAL, "window %d must be odd and in [3, 31]", window);
+  if (basis != DIC_STRAIN_BILINEAR && basis != DIC_STRAIN_BIQUADRATIC)
+    return fail(DIC_EINVAL, "unknown strain basis %d", basis);
+  if (measure < DIC_GREEN_LAGRANGE || measure > DIC_BIOT_LEFT)
+    return fail(DIC_EINVAL, "unknown strain measure %d", measure);
+  StrainArgs a{};
+  a.u = u;
+  a.v = v;
+  a.status = status;
+  a.nx = nx;
+  a.ny = ny;
+  a.step = subset_step;
+  a.window = window;
+  a.basis = basis;
+  a.measure = measure;
+  // full-window slope weights: the odd-in-x terms {x} (bilinear) or {x, x y^2}
+  // (biquadratic) are orthogonal to the rest on the symmetric window
+  const int h = (window - 1) / 2;
+  double s2 = 0.0, s4 = 0.0;
+  for (int i = -h; i <= h; ++i) {
+    s2 += static_cast<double>(i) * i;
+    s4 += static_cast<double>(i) * i * i * i;
+  }
+  const double n = window;
+  if (basis == DIC_STRAIN_BILINEAR) {
+    a.wa = static_cast<float>(1.0 / (n * s2));
+    a.wb = 0.0f;
+  } else {
+    const double den = n * s4 - s2 * s2;
+    a.wa = static_cast<float>(s4 / (s2 * den));
+    a.wb = static_cast<float>(-1.0 / den);
+  }
+  a.dudx = out->dudx;
+  a.dudy = out->dudy;
+  a.dvdx = out->dvdx;
+  a.dvdy = out->dvdy;
+  a.exx = out->exx;
+  a.eyy = out->eyy;
+  a.exy = out->exy;
+  a.valid = out->valid;
+  DIC_CUDA(launch_strain(a, static_cast<cudaStream_t>(cuda_stream)), "strain launch");
+  return DIC_OK;
+}
+
 void dic_destroy(dic_handle* h) { release(h); }
 
 }  // extern "C"

@@ -224,6 +224,19 @@ inline void wave_bands(int S, int threads, int* bands, int* band_h) {
 template <typename T>
 WaveTiles wave_tiles(int S, int gray_dtype);
 
+// ---------------------------------------------------------------- strain
+struct StrainArgs {
+  const double* u;
+  const double* v;
+  const uint8_t* status;
+  int nx, ny, step, window, basis, measure;
+  float wa, wb;   // full-window slope weights in grid units: x slope = sum i (wa + wb j^2) u_ij
+  float *dudx, *dudy, *dvdx, *dvdy, *exx, *eyy, *exy;
+  uint8_t* valid;
+};
+
+cudaError_t launch_strain(const StrainArgs& a, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensorMap* maps, int nparams,
                         int grid, cudaStream_t s);

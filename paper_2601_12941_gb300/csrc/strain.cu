@@ -1,0 +1,301 @@
+// Strain post-processing (Sec. 2.3): at every grid point the displacement gradient
+// of a least-squares fit u = P c over the N x N window of grid points centred on it
+// (Eq. 8-9; P = [1, x, y] or [1, x, y, x^2, y^2, x^2 y, x y^2, x^2 y^2]), the
+// deformation gradient F = I + grad u (Eq. 6) and one of the five strain measures.
+//
+// Only accepted points (status 0) inside the grid enter a window, and the centre
+// must be accepted. A full window (every point present) is the common case: there
+// the odd-in-x basis terms {x, x y^2} are orthogonal to the others, so the fitted
+// x slope is sum_ij i (a + b j^2) u_ij / s in grid units (i, j) with two constants
+// a, b of the window, and the y slope sum_ij j (a + b i^2) u_ij / s, applied
+// separably from shared-memory tiles. A window with missing points is fitted
+// from its normal equations (grid units, unit-diagonal scaling, elimination
+// without exchanges); a scaled pivot at or below 1e-5 leaves the point without
+// strain (NaN). Arithmetic in FP32 on displacements taken relative to the centre.
+#include <math.h>
+
+#include "dic_internal.cuh"
+
+namespace dic {
+namespace {
+
+constexpr float kMinScaledPivot = 1e-5f;
+
+__device__ __forceinline__ int basis_terms(int basis) { return basis == DIC_STRAIN_BILINEAR ? 3 : 8; }
+
+// P(x, y) for the basis (Eq. 9, as printed)
+__device__ __forceinline__ void basis_row(int basis, float x, float y, float* P) {
+  P[0] = 1.0f;
+  P[1] = x;
+  P[2] = y;
+  if (basis != DIC_STRAIN_BILINEAR) {
+    P[3] = x * x;
+    P[4] = y * y;
+    P[5] = x * x * y;
+    P[6] = x * y * y;
+    P[7] = x * x * y * y;
+  }
+}
+
+// General least squares over the valid points of the window (out of line: windows with
+// missing points are the rare case): returns false when the
+// design is not well posed; else the x and y slopes (grid units) of u and v.
+__device__ __noinline__ bool fit_window(const StrainArgs& a, int ic, int jc, double uc, double vc, float* g) {
+  const int K = basis_terms(a.basis);
+  const int h = (a.window - 1) / 2;
+  float M[8][8], ru[8], rv[8];
+  for (int r = 0; r < K; ++r) {
+    ru[r] = rv[r] = 0.0f;
+    for (int c = 0; c < K; ++c) M[r][c] = 0.0f;
+  }
+  int count = 0;
+  for (int dj = -h; dj <= h; ++dj) {
+    const int j = jc + dj;
+    if (j < 0 || j >= a.ny) continue;
+    for (int di = -h; di <= h; ++di) {
+      const int i = ic + di;
+      if (i < 0 || i >= a.nx) continue;
+      const int64_t q = static_cast<int64_t>(j) * a.nx + i;
+      if (a.status[q] != 0) continue;
+      float P[8];
+      basis_row(a.basis, static_cast<float>(di), static_cast<float>(dj), P);
+      const float du = static_cast<float>(a.u[q] - uc), dv = static_cast<float>(a.v[q] - vc);
+      for (int r = 0; r < K; ++r) {
+        ru[r] += P[r] * du;
+        rv[r] += P[r] * dv;
+        for (int c = r; c < K; ++c) M[r][c] += P[r] * P[c];
+      }
+      ++count;
+    }
+  }
+  if (count < K) return false;
+  // unit-diagonal scaling, then elimination without exchanges
+  float d[8];
+  for (int r = 0; r < K; ++r) {
+    if (!(M[r][r] > 0.0f)) return false;
+    d[r] = rsqrtf(M[r][r]);
+  }
+  for (int r = 0; r < K; ++r) {
+    for (int c = r; c < K; ++c) M[r][c] *= d[r] * d[c];
+    for (int c = 0; c < r; ++c) M[r][c] = M[c][r];
+    ru[r] *= d[r];
+    rv[r] *= d[r];
+  }
+  for (int k = 0; k < K; ++k) {
+    const float piv = M[k][k];
+    if (!(piv > kMinScaledPivot)) return false;
+    const float inv = 1.0f / piv;
+    for (int r = k + 1; r < K; ++r) {
+      const float f = M[r][k] * inv;
+      for (int c = k + 1; c < K; ++c) M[r][c] -= f * M[k][c];
+      ru[r] -= f * ru[k];
+      rv[r] -= f * rv[k];
+    }
+  }
+  for (int r = K - 1; r >= 0; --r) {
+    float su = ru[r], sv = rv[r];
+    for (int c = r + 1; c < K; ++c) {
+      su -= M[r][c] * ru[c];
+      sv -= M[r][c] * rv[c];
+    }
+    ru[r] = su / M[r][r];
+    rv[r] = sv / M[r][r];
+  }
+  // undo the scaling: coefficient r is d[r] z[r]
+  g[0] = d[1] * ru[1];
+  g[1] = d[2] * ru[2];
+  g[2] = d[1] * rv[1];
+  g[3] = d[2] * rv[2];
+  return true;
+}
+
+// eigenvalues mu1 >= mu2 of the symmetric [[d11, d12], [d12, d22]]
+__device__ __forceinline__ void sym_eig(float d11, float d12, float d22, float* mu1, float* mu2) {
+  const float m = 0.5f * (d11 + d22);
+  const float q = sqrtf(0.25f * (d11 - d22) * (d11 - d22) + d12 * d12);
+  *mu1 = m + q;
+  *mu2 = m - q;
+}
+
+// f(I + D) = m I + g (D - tr(D)/2 I) for a symmetric D with eigenvalues mu1, mu2,
+// where m is the mean of f at 1 + mu_k and g their divided difference
+__device__ __forceinline__ void spectral(float d11, float d12, float d22, float m, float g, float* e) {
+  const float t = 0.5f * (d11 + d22);
+  e[0] = m + g * (d11 - t);
+  e[1] = m + g * (d22 - t);
+  e[2] = g * d12;
+}
+
+// Sec. 2.3: strain (exx, eyy, exy) from H = grad u, formed from the small parts of
+// F^T F = I + D or F F^T = I + D' so that no 1 is subtracted from a near-1 value.
+__device__ void strain_from_gradient(int measure, float h11, float h12, float h21, float h22, float* e) {
+  const bool left = measure == DIC_EULER_ALMANSI || measure == DIC_BIOT_LEFT;
+  // D = H + H^T + H^T H (right) or D' = H + H^T + H H^T (left)
+  const float d11 = left ? 2.0f * h11 + h11 * h11 + h12 * h12 : 2.0f * h11 + h11 * h11 + h21 * h21;
+  const float d22 = left ? 2.0f * h22 + h21 * h21 + h22 * h22 : 2.0f * h22 + h12 * h12 + h22 * h22;
+  const float d12 = left ? h12 + h21 + h11 * h21 + h12 * h22 : h12 + h21 + h11 * h12 + h21 * h22;
+  if (measure == DIC_GREEN_LAGRANGE) {            // (F^T F - I) / 2
+    e[0] = 0.5f * d11;
+    e[1] = 0.5f * d22;
+    e[2] = 0.5f * d12;
+    return;
+  }
+  if (measure == DIC_EULER_ALMANSI) {             // (I - (F F^T)^-1) / 2 = (D' + det D' I) / (2 det(I + D'))
+    const float det = d11 * d22 - d12 * d12;
+    const float s = 0.5f / (1.0f + d11 + d22 + det);
+    e[0] = (d11 + det) * s;
+    e[1] = (d22 + det) * s;
+    e[2] = d12 * s;
+    return;
+  }
+  float mu1, mu2;
+  sym_eig(d11, d12, d22, &mu1, &mu2);
+  if (measure == DIC_HENCKY) {                    // ln sqrt(C): f(lambda) = ln(lambda) / 2
+    const float m = 0.25f * (log1pf(mu1) + log1pf(mu2));
+    const float z = (mu1 - mu2) / (1.0f + mu2);
+    const float l = z < 1e-3f ? 1.0f - z * (0.5f - z * (1.0f / 3.0f)) : log1pf(z) / z;
+    spectral(d11, d12, d22, m, 0.5f * l / (1.0f + mu2), e);
+    return;
+  }
+  // Biot, right or left: sqrt(I + D) - I: f(lambda) = sqrt(lambda) - 1
+  const float r1 = sqrtf(1.0f + mu1), r2 = sqrtf(1.0f + mu2);
+  const float m = 0.5f * (mu1 / (1.0f + r1) + mu2 / (1.0f + r2));
+  spectral(d11, d12, d22, m, 1.0f / (r1 + r2), e);
+}
+
+constexpr int kTileX = 32, kTileY = 8;   // grid points per block (one per thread)
+
+// Block of kTileX x kTileY grid points. The block stages the displacements of its
+// points and of a halo of h = (window - 1) / 2 points as FP32 offsets from one
+// accepted point of the tile (points outside the grid or not accepted become NaN),
+// then applies the full-window slope filter separably: along each staged row the
+// sums sum_i i d, sum_i d and sum_i i^2 d over the window's columns, then down each
+// point's column the x slope sum_j (a + b j^2) (sum_i i d)_j and the y slope
+// sum_j j (a (sum_i d)_j + b (sum_i i^2 d)_j). A NaN anywhere in a window reaches
+// its sums (even through a zero weight), which sends the point to the general fit.
+__global__ void __launch_bounds__(kTileX * kTileY, 4) strain_kernel(StrainArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const int h = (a.window - 1) / 2, N = a.window;
+  const int SX = kTileX + 2 * h, SY = kTileY + 2 * h;
+  float* su = sm;                 // [SY][SX] staged offsets of u
+  float* sv = su + SY * SX;       // ... of v
+  float* fx = sv + SY * SX;       // [2][SY][kTileX] row sums: sum i d   (u, v)
+  float* f0 = fx + 2 * SY * kTileX;   // sum d
+  float* f2 = f0 + 2 * SY * kTileX;   // sum i^2 d
+  __shared__ double s_ref[2];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+  if (tid == 0) {
+    // reference: the first accepted point of the tile (offsets stay small)
+    double ur = 0.0, vr = 0.0;
+    for (int k = 0; k < kTileX * kTileY; ++k) {
+      const int i = x0 + k % kTileX, j = y0 + k / kTileX;
+      if (i >= a.nx || j >= a.ny) continue;
+      const int64_t q = static_cast<int64_t>(j) * a.nx + i;
+      if (a.status[q] == 0) {
+        ur = a.u[q];
+        vr = a.v[q];
+        break;
+      }
+    }
+    s_ref[0] = ur;
+    s_ref[1] = vr;
+  }
+  __syncthreads();
+  const double ur = s_ref[0], vr = s_ref[1];
+  const float nan_ = __int_as_float(0x7fc00000);
+  for (int e = tid; e < SY * SX; e += blockDim.x) {
+    const int i = x0 - h + e % SX, j = y0 - h + e / SX;
+    float du = nan_, dv = nan_;
+    if (i >= 0 && i < a.nx && j >= 0 && j < a.ny) {
+      // the three loads are issued together; status then selects
+      const int64_t q = static_cast<int64_t>(j) * a.nx + i;
+      const uint8_t st = a.status[q];
+      const double uq = a.u[q], vq = a.v[q];
+      if (st == 0) {
+        du = static_cast<float>(uq - ur);
+        dv = static_cast<float>(vq - vr);
+      }
+    }
+    su[e] = du;
+    sv[e] = dv;
+  }
+  __syncthreads();
+  for (int e = tid; e < 2 * SY * kTileX; e += blockDim.x) {
+    const int comp = e / (SY * kTileX), rc = e % (SY * kTileX);
+    const int row = rc / kTileX, c = rc % kTileX;
+    const float* src = (comp == 0 ? su : sv) + row * SX + c;   // window columns c .. c + 2h
+    float sx = 0.0f, s0 = 0.0f, s2 = 0.0f;
+    for (int k = 0; k < N; ++k) {
+      const float di = static_cast<float>(k - h), d = src[k];
+      sx += di * d;
+      s0 += d;
+      s2 += di * di * d;
+    }
+    fx[e] = sx;
+    f0[e] = s0;
+    f2[e] = s2;
+  }
+  __syncthreads();
+  const int tx = tid % kTileX, ty = tid / kTileX;
+  const int ic = x0 + tx, jc = y0 + ty;
+  if (ic >= a.nx || jc >= a.ny) return;
+  const int64_t q = static_cast<int64_t>(jc) * a.nx + ic;
+  float g[4];
+  bool ok = a.status[q] == 0;
+  if (ok) {
+    float sux = 0.0f, suy = 0.0f, svx = 0.0f, svy = 0.0f;
+    const int o = ty * kTileX + tx, ov = SY * kTileX;
+    for (int k = 0; k < N; ++k) {
+      const float dj = static_cast<float>(k - h);
+      const float wxj = a.wa + a.wb * dj * dj;
+      const int r = o + k * kTileX;
+      sux += wxj * fx[r];
+      svx += wxj * fx[ov + r];
+      suy += dj * (a.wa * f0[r] + a.wb * f2[r]);
+      svy += dj * (a.wa * f0[ov + r] + a.wb * f2[ov + r]);
+    }
+    if (isfinite(sux) && isfinite(suy) && isfinite(svx) && isfinite(svy)) {
+      g[0] = sux;
+      g[1] = suy;
+      g[2] = svx;
+      g[3] = svy;
+    } else {
+      ok = fit_window(a, ic, jc, a.u[q], a.v[q], g);
+    }
+  }
+  if (ok) {
+    const float inv_s = 1.0f / static_cast<float>(a.step);   // grid units -> pixels
+    const float h11 = g[0] * inv_s, h12 = g[1] * inv_s, h21 = g[2] * inv_s, h22 = g[3] * inv_s;
+    float e[3];
+    strain_from_gradient(a.measure, h11, h12, h21, h22, e);
+    a.dudx[q] = h11;
+    a.dudy[q] = h12;
+    a.dvdx[q] = h21;
+    a.dvdy[q] = h22;
+    a.exx[q] = e[0];
+    a.eyy[q] = e[1];
+    a.exy[q] = e[2];
+  } else {
+    a.dudx[q] = a.dudy[q] = a.dvdx[q] = a.dvdy[q] = nan_;
+    a.exx[q] = a.eyy[q] = a.exy[q] = nan_;
+  }
+  a.valid[q] = ok ? 1 : 0;
+}
+
+}  // namespace
+
+cudaError_t launch_strain(const StrainArgs& a, cudaStream_t s) {
+  const int h = (a.window - 1) / 2;
+  const int SX = kTileX + 2 * h, SY = kTileY + 2 * h;
+  const size_t smem = sizeof(float) * (2 * static_cast<size_t>(SY) * SX + 6 * static_cast<size_t>(SY) * kTileX);
+  // the largest window (31) needs about 48 KB; the limit is raised once (thread-safe)
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(strain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  if (configured != cudaSuccess) return configured;
+  dim3 grid((a.nx + kTileX - 1) / kTileX, (a.ny + kTileY - 1) / kTileY);
+  strain_kernel<<<grid, kTileX * kTileY, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dic

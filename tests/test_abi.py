@@ -69,6 +69,29 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
     p = B.dic_default_params()
     assert lib.dic_set_params(None, ctypes.byref(p)) == B.DIC_EINVAL
     assert lib.dic_correlate(None, None, 0, None) == B.DIC_EINVAL
+    # strain: arguments are checked before anything is launched (the pointers below
+    # are never dereferenced)
+    fake = ctypes.c_void_p(16)
+    out = B.DicStrainOutputs(*([16] * len(B.STRAIN_FIELDS)))
+    assert lib.dic_strain_field(None, fake, fake, 10, 10, 5, 9, 1, 0, ctypes.byref(out), None) == B.DIC_EINVAL
+    assert lib.dic_strain_field(fake, fake, fake, 10, 10, 5, 8, 1, 0, ctypes.byref(out), None) == B.DIC_EINVAL
+    assert b"odd" in lib.dic_last_error()
+    assert lib.dic_strain_field(fake, fake, fake, 10, 10, 5, 33, 1, 0, ctypes.byref(out), None) == B.DIC_EINVAL
+    assert lib.dic_strain_field(fake, fake, fake, 10, 10, 0, 9, 1, 0, ctypes.byref(out), None) == B.DIC_EINVAL
+    assert lib.dic_strain_field(fake, fake, fake, 0, 10, 5, 9, 1, 0, ctypes.byref(out), None) == B.DIC_EINVAL
+    assert lib.dic_strain_field(fake, fake, fake, 10, 10, 5, 9, 2, 0, ctypes.byref(out), None) == B.DIC_EINVAL
+    assert lib.dic_strain_field(fake, fake, fake, 10, 10, 5, 9, 1, 5, ctypes.byref(out), None) == B.DIC_EINVAL
+    out.exy = None
+    assert lib.dic_strain_field(fake, fake, fake, 10, 10, 5, 9, 1, 0, ctypes.byref(out), None) == B.DIC_EINVAL
+    # estimates and re-grids on NULL
+    assert lib.dic_set_subsets(None, None, 21, 5, 1) == B.DIC_EINVAL
+    assert lib.dic_get_device_bytes(None, None) == B.DIC_EINVAL
+    nb = ctypes.c_int64(0)
+    assert lib.dic_estimate_device_bytes(ctypes.byref(ri), ctypes.byref(ri), 0, 20, 5, 1, ctypes.byref(p), 1,
+                                         ctypes.byref(nb)) == B.DIC_EINVAL
+    assert lib.dic_estimate_device_bytes(ctypes.byref(ri), ctypes.byref(ri), 0, 21, 5, 1, ctypes.byref(p), 1,
+                                         ctypes.byref(nb)) == B.DIC_OK
+    assert nb.value > 2 * 64 * 64 * 4      # at least the two FP32 coefficient planes
 
 
 def test_loading_fails_loudly_without_the_library(tmp_path):
