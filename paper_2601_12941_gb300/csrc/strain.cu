@@ -182,27 +182,37 @@ __global__ void __launch_bounds__(kTileX * kTileY, 4) strain_kernel(StrainArgs a
   float* fx = sv + SY * SX;       // [2][SY][kTileX] row sums: sum i d   (u, v)
   float* f0 = fx + 2 * SY * kTileX;   // sum d
   float* f2 = f0 + 2 * SY * kTileX;   // sum i^2 d
-  __shared__ double s_ref[2];
+  __shared__ float s_ref[2];
+  __shared__ int s_first;
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
-  if (tid == 0) {
-    // reference: the first accepted point of the tile (offsets stay small)
-    double ur = 0.0, vr = 0.0;
-    for (int k = 0; k < kTileX * kTileY; ++k) {
-      const int i = x0 + k % kTileX, j = y0 + k / kTileX;
-      if (i >= a.nx || j >= a.ny) continue;
-      const int64_t q = static_cast<int64_t>(j) * a.nx + i;
-      if (a.status[q] == 0) {
-        ur = a.u[q];
-        vr = a.v[q];
-        break;
-      }
-    }
-    s_ref[0] = ur;
-    s_ref[1] = vr;
+  const int tx = tid % kTileX, ty = tid / kTileX;
+  const int ic = x0 + tx, jc = y0 + ty;
+  const bool inside = ic < a.nx && jc < a.ny;
+  const int64_t q = static_cast<int64_t>(jc) * a.nx + ic;
+  // the thread's own point; the tile's first accepted point is the reference of the
+  // staged offsets (which keeps them small)
+  uint8_t st_c = 1;
+  double uc = 0.0, vc = 0.0;
+  if (inside) {
+    st_c = a.status[q];
+    uc = a.u[q];
+    vc = a.v[q];
   }
+  if (tid == 0) s_first = kTileX * kTileY;
   __syncthreads();
-  const double ur = s_ref[0], vr = s_ref[1];
+  if (inside && st_c == 0) atomicMin(&s_first, tid);
+  __syncthreads();
+  if (tid == s_first) {
+    s_ref[0] = static_cast<float>(uc);
+    s_ref[1] = static_cast<float>(vc);
+  }
+  if (s_first == kTileX * kTileY && tid == 0) s_ref[0] = s_ref[1] = 0.0f;
+  __syncthreads();
+  // offsets are formed in FP32 after one conversion per value (FP64 arithmetic runs at a
+  // small fraction of the FP32 rate here); exact when the displacements are FP32 values,
+  // as the mixed path produces them
+  const float ur = s_ref[0], vr = s_ref[1];
   const float nan_ = __int_as_float(0x7fc00000);
   for (int e = tid; e < SY * SX; e += blockDim.x) {
     const int i = x0 - h + e % SX, j = y0 - h + e / SX;
@@ -213,8 +223,8 @@ __global__ void __launch_bounds__(kTileX * kTileY, 4) strain_kernel(StrainArgs a
       const uint8_t st = a.status[q];
       const double uq = a.u[q], vq = a.v[q];
       if (st == 0) {
-        du = static_cast<float>(uq - ur);
-        dv = static_cast<float>(vq - vr);
+        du = static_cast<float>(uq) - ur;
+        dv = static_cast<float>(vq) - vr;
       }
     }
     su[e] = du;
@@ -237,12 +247,9 @@ __global__ void __launch_bounds__(kTileX * kTileY, 4) strain_kernel(StrainArgs a
     f2[e] = s2;
   }
   __syncthreads();
-  const int tx = tid % kTileX, ty = tid / kTileX;
-  const int ic = x0 + tx, jc = y0 + ty;
-  if (ic >= a.nx || jc >= a.ny) return;
-  const int64_t q = static_cast<int64_t>(jc) * a.nx + ic;
+  if (!inside) return;
   float g[4];
-  bool ok = a.status[q] == 0;
+  bool ok = st_c == 0;
   if (ok) {
     float sux = 0.0f, suy = 0.0f, svx = 0.0f, svy = 0.0f;
     const int o = ty * kTileX + tx, ov = SY * kTileX;
@@ -261,7 +268,7 @@ __global__ void __launch_bounds__(kTileX * kTileY, 4) strain_kernel(StrainArgs a
       g[2] = svx;
       g[3] = svy;
     } else {
-      ok = fit_window(a, ic, jc, a.u[q], a.v[q], g);
+      ok = fit_window(a, ic, jc, uc, vc, g);
     }
   }
   if (ok) {
