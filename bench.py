@@ -40,9 +40,10 @@ FLOP_ITER = {2: 64, 6: 84, 12: 108}
 FLOP_FINAL = 72
 
 
-# DRAM bytes (read + write) per point of the wave kernel as last captured by ncu
-# (profiles/wave_kernel_sem_6144_u8_full.md: 31.37 MB for a wave of 2,560 points), or
-# None when the kernel has changed since (the roofline then reports no traffic)
+# DRAM bytes (read + write) per point of the wave kernel as last captured by ncu (a
+# full capture of two mid-run waves of 2,560 points on the 6144^2 version of the
+# workload: 31.37 MB per launch), or None when the kernel has changed since (the
+# roofline then reports no traffic)
 WAVE_DRAM_BYTES_PER_POINT = 12_255
 
 
