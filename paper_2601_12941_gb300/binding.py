@@ -284,11 +284,12 @@ def dic_correlate_sequence(h, stream_ptr: int = 0):
     _check(load().dic_correlate_sequence(h, ctypes.c_void_p(stream_ptr)))
 
 
-def _host_array(ptr, count, dtype):
+def _host_array(ptr, count, dtype, copy=True):
     if count == 0:
         return np.zeros(0, dtype)
     buf = (ctypes.c_char * (count * np.dtype(dtype).itemsize)).from_address(ptr)
-    return np.frombuffer(buf, dtype=dtype, count=count).copy()
+    a = np.frombuffer(buf, dtype=dtype, count=count)
+    return a.copy() if copy else a
 
 
 class _DeviceArray:
@@ -297,9 +298,11 @@ class _DeviceArray:
                                              version=3, strides=None)
 
 
-def dic_get_results(h, on_device: bool = False) -> dict:
-    """Per-point arrays in grid order: numpy copies (host) or zero-copy CUDA tensors
-    viewing the handle's buffers (device; valid until the next correlate/destroy)."""
+def dic_get_results(h, on_device: bool = False, copy: bool = True) -> dict:
+    """Per-point arrays in grid order: numpy arrays (host) or zero-copy CUDA tensors
+    viewing the handle's buffers (device; valid until the next correlate/destroy).
+    Host arrays are copies, or with copy=False views of the handle's pinned host
+    buffers (valid until the next dic_get_results, correlate or destroy)."""
     r = DicResults()
     _check(load().dic_get_results(h, ctypes.byref(r), 1 if on_device else 0))
     n, npar = r.n_points, r.n_params
@@ -317,7 +320,7 @@ def dic_get_results(h, on_device: bool = False) -> dict:
                                         device="cuda")
     else:
         for name, dt, shape in spec:
-            out[name] = _host_array(getattr(r, name), int(np.prod(shape)), dt).reshape(shape)
+            out[name] = _host_array(getattr(r, name), int(np.prod(shape)), dt, copy).reshape(shape)
     return out
 
 
@@ -441,8 +444,8 @@ class Correlation:
         dic_correlate_sequence(self.h, stream_ptr)
         return self
 
-    def results(self, on_device=False):
-        return dic_get_results(self.h, on_device)
+    def results(self, on_device=False, copy=True):
+        return dic_get_results(self.h, on_device, copy)
 
     def timing(self):
         return dic_get_timing(self.h)
