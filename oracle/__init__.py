@@ -6,7 +6,7 @@ share no code: see ``dic_oracle`` for what is computed and which passage of the
 paper each step follows.
 """
 from .dic_oracle import *  # noqa: F401,F403
-from .dic_oracle import (AFFINE, DEFAULT_PARAMS, N_PARAMS, QUADRATIC, RIGID, Plane,  # noqa: F401
+from .dic_oracle import (AFFINE, DEFAULT_PARAMS, N_PARAMS, NSSD, QUADRATIC, RIGID, SSD, ZNSSD, Plane,  # noqa: F401
                          ReferenceSubset, bspline_coefficients, correlate, correlate_sequence, grid, icgn,
                          interpolate, seed_search)
 from . import strain_oracle  # noqa: F401

@@ -60,6 +60,14 @@ Readings taken where the paper is silent (all of them, in one place):
   R11 Sequences (one reference, many deformed images, Sec. 2.1): frame k starts
       every point accepted in frame k-1 from its frame k-1 warp, all in wave 0;
       the remaining points are reached by propagation as in R10.
+  R12 Cost functions (Eq. 2-4): ZNSSD (the default), NSSD and SSD. The IC-GN
+      step solves H dp = -b with b = sum SD_i e_i and
+        ZNSSD  e_i = fbar_i - (df / dg) gbar_i,   df = ||fbar||, dg = ||gbar||,
+        NSSD   e_i = f_i - (||f|| / ||g||) g_i,
+        SSD    e_i = f_i - g_i,
+      the Gauss-Newton step of each cost in the inverse-compositional form (H =
+      sum SD_i^T SD_i for all three). Whatever the cost, the reported coefficient
+      and the acceptance test stay the ZNCC at the final p (R8).
 """
 from __future__ import annotations
 
@@ -73,8 +81,9 @@ N_PARAMS = {RIGID: 2, AFFINE: 6, QUADRATIC: 12}
 OK, NOT_IN_ROI, NOT_REACHED, OUT_OF_BOUNDS, MAX_ITER, LOW_ZNCC, SINGULAR_H, FLAT_SUBSET = range(8)
 
 # Sec. 4: 40 iterations, convergence threshold 0.01, precision 0.70 (reading R8)
+ZNSSD, NSSD, SSD = "znssd", "nssd", "ssd"
 DEFAULT_PARAMS = dict(max_iter=40, conv_threshold=0.01, zncc_min=0.70, search_radius=8,
-                      nan_unconverged=False)
+                      nan_unconverged=False, cost=ZNSSD)
 
 
 # --------------------------------------------------------------------------- R1
@@ -386,6 +395,8 @@ class ReferenceSubset:
         xi = xc + self.dx.astype(np.int64)
         yi = yc + self.dy.astype(np.int64)
         f = ref.gray_at(xi, yi).astype(np.float64)
+        self.f = f
+        self.norm_f = math.sqrt(np.sum(f * f))
         self.f_m = f.mean()
         self.fbar = f - self.f_m
         self.delta_f = math.sqrt(np.sum(self.fbar ** 2))
@@ -394,6 +405,17 @@ class ReferenceSubset:
         self.SD = steepest_descent_images(fx, fy, self.dx, self.dy, n)
         self.H = self.SD.T @ self.SD
         self.LU, self.piv, self.singular = lu_partial_pivot(self.H)
+
+
+def residual(rs: ReferenceSubset, g, gbar, delta_g, cost):
+    """e_i of reading R12 for the cost (Eq. 2-4)."""
+    if cost == ZNSSD:
+        return rs.fbar - (rs.delta_f / delta_g) * gbar
+    if cost == NSSD:
+        return rs.f - (rs.norm_f / math.sqrt(np.sum(g * g))) * g
+    if cost == SSD:
+        return rs.f - g
+    raise ValueError("unknown cost %r" % cost)
 
 
 def icgn(ref: Plane, dfm: Plane, xc, yc, subset_size, shape, p_init, params=None, ref_subset=None):
@@ -425,7 +447,7 @@ def icgn(ref: Plane, dfm: Plane, xc, yc, subset_size, shape, p_init, params=None
         if _flat(delta_g, g_m, g.size):
             ratio_status = FLAT_SUBSET
             break
-        e = rs.fbar - (rs.delta_f / delta_g) * gbar
+        e = residual(rs, g, gbar, delta_g, prm["cost"])
         b = rs.SD.T @ e
         dp = -lu_solve(rs.LU, rs.piv, b)
         p = compose_inverse(p, dp, rs.dx, rs.dy)

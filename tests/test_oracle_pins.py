@@ -421,6 +421,69 @@ def test_tiny_subsets_agree_with_brute_force_minimisation(shape, S):
     assert sol.fun <= cost(p) + 1e-9
 
 
+# ------------------------------------------------------------------ cost functions (Eq. 2-4)
+def test_costs_have_exactly_the_invariances_of_eq2_to_eq4():
+    """An integer shift of the pattern under an intensity change g = a f + c: ZNSSD
+    (Eq. 4) recovers it for any a, c; NSSD (Eq. 3) for c = 0 only; SSD (Eq. 2) only
+    without a change. A cost that subtracts a mean it should not, or omits a
+    normalisation, fails one of these."""
+    big, _ = _speckle_pair(110, 110, synth.IDENTITY, dtype="f64")
+    ref = big[5:105, 5:105]
+    shifted = big[5 + 2:105 + 2, 5 - 3:105 - 3]      # pattern moved by (+3, -2)
+    refp = O.Plane(ref)
+    want = np.array([3.0, -2.0, 0, 0, 0, 0])
+    prm = dict(conv_threshold=1e-10, max_iter=100)
+
+    def err(cost, a, c):
+        res = O.icgn(refp, O.Plane(a * shifted + c), 50, 50, 21, O.AFFINE, [3.2, -1.8], dict(prm, cost=cost))
+        assert res["status"] in (O.OK, O.LOW_ZNCC), (cost, a, c, res["status"])
+        return np.abs(res["p"] - want).max()
+
+    for cost in (O.ZNSSD, O.NSSD, O.SSD):
+        assert err(cost, 1.0, 0.0) < 1e-9, cost
+    assert err(O.ZNSSD, 1.7, 25.0) < 1e-9
+    assert err(O.NSSD, 1.7, 0.0) < 1e-9
+    assert err(O.NSSD, 1.0, 25.0) > 1e-4
+    assert err(O.SSD, 1.7, 0.0) > 1e-4
+
+
+def _stationarity(img_ref, img_def, xc, yc, S, p, cost):
+    """min over dp of || e + J dp || with e the residual of the cost and J, f, g from scipy alone."""
+    n = len(p)
+    r = S // 2
+    dy, dx = np.mgrid[-r:r + 1, -r:r + 1]
+    dx = dx.ravel().astype(float)
+    dy = dy.ravel().astype(float)
+    f = img_ref[yc + dy.astype(int), xc + dx.astype(int)]
+    h = 1e-6
+    J = np.empty((S * S, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = h
+        xp, yp = O.warp(e, dx, dy)
+        xm, ym = O.warp(-e, dx, dy)
+        J[:, j] = (ndimage.map_coordinates(img_ref, [yc + yp, xc + xp], order=3, mode="mirror")
+                   - ndimage.map_coordinates(img_ref, [yc + ym, xc + xm], order=3,
+                                             mode="mirror")) / (2 * h)
+    wx, wy = O.warp(p, dx, dy)
+    g = ndimage.map_coordinates(img_def, [yc + wy, xc + wx], order=3, mode="mirror")
+    if cost == O.NSSD:
+        e = f - math.sqrt(np.sum(f ** 2) / np.sum(g ** 2)) * g
+    else:
+        e = f - g
+    return np.linalg.lstsq(J, -e, rcond=None)[0]
+
+
+@pytest.mark.parametrize("cost", [O.NSSD, O.SSD])
+def test_nssd_and_ssd_roots_are_stationary_points_computed_independently(cost):
+    fld = synth.affine_field(64, 64, u0=0.4, v0=-0.3, exx=4e-3, exy=-2e-3, eyx=1e-3, eyy=3e-3)
+    ref, dfm = _speckle_pair(64, 64, fld, seed=3)
+    res = O.icgn(O.Plane(ref), O.Plane(dfm), 31, 33, 11, O.AFFINE, [0, 0],
+                 dict(conv_threshold=1e-12, max_iter=200, cost=cost))
+    assert res["status"] == O.OK
+    assert np.abs(_stationarity(ref, dfm, 31, 33, 11, res["p"], cost)).max() < 1e-6
+
+
 def test_flat_and_singular_subsets():
     flat = np.full((40, 40), 100.0)
     res = O.icgn(O.Plane(flat), O.Plane(flat), 20, 20, 11, O.AFFINE, [0, 0])
