@@ -58,6 +58,12 @@ typedef enum { DIC_U8 = 0, DIC_U16 = 1, DIC_BF16 = 2, DIC_F32 = 3, DIC_F64 = 4 }
  * with (dx, dy) the pixel offset from the subset centre (x_c, y_c). */
 typedef enum { DIC_RIGID = 0, DIC_AFFINE = 1, DIC_QUADRATIC = 2 } dic_shape;
 
+/* Cost minimised per subset: ZNSSD (Eq. 4, the paper's default), NSSD (Eq. 3) or
+ * SSD (Eq. 2). Each enters the IC-GN step through its residual: b = sum SD_i e_i with
+ * e_i = fbar_i - (||fbar|| / ||gbar||) gbar_i, f_i - (||f|| / ||g||) g_i or f_i - g_i.
+ * The reported coefficient and the acceptance test remain the ZNCC at the final p. */
+typedef enum { DIC_COST_ZNSSD = 0, DIC_COST_NSSD = 1, DIC_COST_SSD = 2 } dic_cost;
+
 /* Sec. 2.2: interpolating cubic B-spline, mirror boundary. */
 typedef enum { DIC_BSPLINE3 = 0 } dic_interp;
 
@@ -95,7 +101,7 @@ typedef struct {
   int32_t precision;         /* dic_precision (default DIC_MIXED)                   */
   int32_t nan_unconverged;   /* Sec. 4: 1 sets u, v, p of rejected points to NaN    */
   int32_t profile;           /* 1: record CUDA-event stage timings (dic_get_timing) */
-  int32_t reserved;
+  int32_t cost;              /* dic_cost (default DIC_COST_ZNSSD)                    */
 } dic_params;
 /* ||dp|| = sqrt(dp0^2 + dp1^2 + r^2 (dp2^2+..+dp5^2) + r^4 (dp6^2+..+dp11^2)),
  * r = (subset_size - 1) / 2; a subset has converged once ||dp|| < conv_threshold. */

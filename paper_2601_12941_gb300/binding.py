@@ -17,6 +17,8 @@ DIC_U8, DIC_U16, DIC_BF16, DIC_F32, DIC_F64 = range(5)
 DIC_RIGID, DIC_AFFINE, DIC_QUADRATIC = range(3)
 DIC_BSPLINE3 = 0
 DIC_FP64, DIC_MIXED = 0, 1
+DIC_COST_ZNSSD, DIC_COST_NSSD, DIC_COST_SSD = 0, 1, 2
+COSTS = {"znssd": DIC_COST_ZNSSD, "nssd": DIC_COST_NSSD, "ssd": DIC_COST_SSD}
 (PT_OK, PT_NOT_IN_ROI, PT_NOT_REACHED, PT_OUT_OF_BOUNDS, PT_MAX_ITER, PT_LOW_ZNCC, PT_SINGULAR,
  PT_FLAT) = range(8)
 SHAPES = {"rigid": DIC_RIGID, "affine": DIC_AFFINE, "quadratic": DIC_QUADRATIC}
@@ -47,7 +49,7 @@ class DicParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("search_radius", ctypes.c_int32),
                 ("conv_threshold", ctypes.c_double), ("zncc_min", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("nan_unconverged", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("cost", ctypes.c_int32)]
 
 
 class DicResults(ctypes.Structure):
@@ -390,14 +392,23 @@ def strain_outputs(n: int, device="cuda") -> dict:
     return out
 
 
-def params(**kw) -> DicParams:
-    """Default parameters with the given fields replaced (precision may be a string)."""
-    p = dic_default_params()
+def _apply(p: DicParams, kw: dict) -> DicParams:
+    fields = {name for name, _ in DicParams._fields_}
     for k, v in kw.items():
+        if k not in fields:
+            raise TypeError("unknown parameter %r" % k)
         if k == "precision" and isinstance(v, str):
-            v = DIC_FP64 if v == "fp64" else DIC_MIXED
+            v = {"fp64": DIC_FP64, "mixed": DIC_MIXED}[v]
+        if k == "cost" and isinstance(v, str):
+            v = COSTS[v]
         setattr(p, k, v)
     return p
+
+
+def params(**kw) -> DicParams:
+    """Default parameters with the given fields replaced (precision and cost may be
+    strings: "fp64"/"mixed", "znssd"/"nssd"/"ssd")."""
+    return _apply(dic_default_params(), kw)
 
 
 class Correlation:
@@ -412,12 +423,7 @@ class Correlation:
             dic_set_params(self.h, params(**param_kw))
 
     def set_params(self, **kw):
-        p = dic_get_params(self.h)
-        for k, v in kw.items():
-            if k == "precision" and isinstance(v, str):
-                v = DIC_FP64 if v == "fp64" else DIC_MIXED
-            setattr(p, k, v)
-        dic_set_params(self.h, p)
+        dic_set_params(self.h, _apply(dic_get_params(self.h), kw))
 
     def set_reference(self, ref):
         self._keep = (dic_set_reference(self.h, ref), self._keep[1])

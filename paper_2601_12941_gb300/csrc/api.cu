@@ -360,6 +360,7 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   a.counters = h->counters;
   a.wave_sizes = h->wave_sizes;
   a.max_iter = h->prm.max_iter;
+  a.cost = h->prm.cost;
   a.conv_threshold = h->prm.conv_threshold;
   a.zncc_min = h->prm.zncc_min;
 
@@ -603,6 +604,8 @@ int validate_params(const dic_params* p) {
     return fail(DIC_EINVAL, "search_radius %d out of range", p->search_radius);
   if (p->precision != DIC_FP64 && p->precision != DIC_MIXED)
     return fail(DIC_EINVAL, "unknown precision %d", p->precision);
+  if (p->cost != DIC_COST_ZNSSD && p->cost != DIC_COST_NSSD && p->cost != DIC_COST_SSD)
+    return fail(DIC_EINVAL, "unknown cost %d", p->cost);
   return DIC_OK;
 }
 
@@ -681,7 +684,7 @@ dic_params dic_default_params(void) {
   p.precision = DIC_MIXED;
   p.nan_unconverged = 0;
   p.profile = 0;
-  p.reserved = 0;
+  p.cost = DIC_COST_ZNSSD;
   return p;
 }
 

@@ -294,6 +294,7 @@ struct PointState {
   C sds[NP];                // sum SD
   C mu;                     // mean of f' = f - f0 (f0: reference gray level at the centre)
   C delta_f;                // ||f - f_m||
+  C sf, sff;                // sum f', sum f'^2 (the NSSD norm ||f||)
   C f0;
   double zncc;
   int q, item, ctl, iters, status, converged, stage;
@@ -486,7 +487,7 @@ __device__ void plan_window(PointState<C, NP>& st, int xc, int yc, int r, int W,
 // st.ctl: 0 ok, 3 flat, 4 singular (a pivot <= 1e-12 of the largest diagonal
 // entry of H).
 template <typename C, int NP, int NMOM, int M2>
-__device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int lane) {
+__device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int lane, int cost) {
   const C sf = out[3 * NMOM + 2 * NP];
   const C sff = out[3 * NMOM + 2 * NP + 1];
   const C mu = sf / static_cast<C>(N);
@@ -511,25 +512,33 @@ __device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int
   }
   if (lane < NP) {
     st.sds[lane] = out[3 * NMOM + NP + lane];
-    st.sdf[lane] = out[3 * NMOM + lane] - mu * out[3 * NMOM + NP + lane];   // sum SD (f' - mu)
+    // ZNSSD: sum SD (f' - mu) = sum SD fbar; NSSD and SSD: sum SD f'
+    st.sdf[lane] = out[3 * NMOM + lane] - (cost == DIC_COST_ZNSSD ? mu : C(0)) * out[3 * NMOM + NP + lane];
   }
   if (lane == 0) {
     st.mu = mu;
     st.delta_f = df;
+    st.sf = sf;
+    st.sff = sff;
     st.ctl = ratio > 1e-12 ? 0 : 4;
   }
   __syncwarp();
 }
 
 // Warp 0 after an iteration's reduction. out: [sum g', sum g'^2, sum SD g', bad].
-// b = sum SD (f - f_m) - (df/dg) sum SD (g - g_m), one component per lane.
+// b = sum SD e, one component per lane (f' = f - f0, g' = g - f0 with f0 the
+// reference gray level at the centre, so that the large common level cancels):
+//   ZNSSD  b = sum SD (f - f_m) - (df/dg) sum SD (g - g_m),
+//   NSSD   b = sum SD f' - r sum SD g' + f0 (1 - r) sum SD, r = ||f|| / ||g||,
+//   SSD    b = sum SD f' - sum SD g'.
 // FP64 path: dp0 = -X b in FP64, then one refinement step dp = dp0 - X (b + H dp0).
 // Mixed path: dp = -H^-1 b in FP32, b shared by shuffles (the precision of the
 // solve sets the rate of convergence, not the root, which b alone fixes). Lane 0
 // composes p <- p o dp^-1. Returns (on every lane) 0 continue, 1 converged,
 // 2 flat, 5 out of bounds.
 template <typename C, int NP>
-__device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C r, C thr2, int lane) {
+__device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C r, C thr2, int lane,
+                                   int cost) {
   if (out[2 + NP] > C(0.5)) return 5;
   const C nu = out[0] * (C(1) / static_cast<C>(N));  // mean of g' = g - f0
   const C dg2 = fmax(out[1] - out[0] * nu, C(0));
@@ -537,10 +546,24 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
   const C gm = fmax(fabs(nu + st.f0), C(1));
   if (dg2 <= C(1e-12) * static_cast<C>(N) * gm * gm) return 2;
   const C ratio = st.delta_f * rsqrt(dg2);
+  // coefficients of b = sdf - kg sum SD g' + kc sum SD
+  C kg = ratio, kc = ratio * nu;
+  if (cost == DIC_COST_SSD) {
+    kg = C(1);
+    kc = C(0);
+  } else if (cost == DIC_COST_NSSD) {
+    const C f0 = st.f0, n = static_cast<C>(N);
+    const C nf2 = st.sff + C(2) * f0 * st.sf + n * f0 * f0;   // ||f||^2
+    const C ng2 = out[1] + C(2) * f0 * out[0] + n * f0 * f0;  // ||g||^2
+    const C nf = sqrt(nf2), ng = sqrt(ng2);
+    kg = nf / ng;
+    // 1 - r from the difference of the squared norms (the N f0^2 terms cancel)
+    kc = f0 * ((out[1] - st.sff) + C(2) * f0 * (out[0] - st.sf)) / (ng * (ng + nf));
+  }
   C d;
   if constexpr (sizeof(C) == sizeof(double)) {
     double bc = 0.0;
-    if (lane < NP) bc = static_cast<double>(st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]));
+    if (lane < NP) bc = static_cast<double>(st.sdf[lane] - kg * out[2 + lane] + kc * st.sds[lane]);
     if (lane < NP) st.sv.bvec[lane] = bc;
     __syncwarp();
     double d0 = 0.0;
@@ -565,7 +588,7 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
     }
     d = static_cast<C>(dpc);
   } else {
-    const C bc = lane < NP ? st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]) : C(0);
+    const C bc = lane < NP ? st.sdf[lane] - kg * out[2 + lane] + kc * st.sds[lane] : C(0);
     const int row = lane < NP ? lane : 0;
     C acc = C(0);
 #pragma unroll
@@ -1101,7 +1124,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
     __syncthreads();
     if (warp == 0) {
       gather(NV_PRE);
-      finish_reference<C, NP, NMOM, M2>(st, s_out, N, lane);
+      finish_reference<C, NP, NMOM, M2>(st, s_out, N, lane, a.cost);
       if (lane == 0) {
         if (st.ctl == 0)
           plan_window<C, NP>(st, xc, yc, r, a.W, a.H, tl, XALIGN);
@@ -1185,7 +1208,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
         gather(final_pass ? NV_FIN : NV_IT);
         if (lane == 0 && (st.stage == 1 || st.stage == 3)) st.win = st.next;
         if (!final_pass) {
-          const int ctl = gauss_newton_update<C, NP>(st, s_out, N, static_cast<C>(r), thr2, lane);
+          const int ctl = gauss_newton_update<C, NP>(st, s_out, N, static_cast<C>(r), thr2, lane, a.cost);
           if (lane == 0) {
             if (ctl == 5) {
               st.status = DIC_PT_OUT_OF_BOUNDS;

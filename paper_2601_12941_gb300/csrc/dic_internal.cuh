@@ -196,6 +196,7 @@ struct WaveArgs {
   int k;                     // wave index
   // controls
   int max_iter;
+  int cost;                  // dic_cost
   double conv_threshold;
   double zncc_min;
 };

@@ -281,6 +281,7 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   a.counters = counters;
   a.wave_sizes = wave_sizes;
   a.max_iter = params->max_iter;
+  a.cost = params->cost;
   a.conv_threshold = params->conv_threshold;
   a.zncc_min = params->zncc_min;
   int dev = 0, sms = 0;
