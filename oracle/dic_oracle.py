@@ -68,6 +68,13 @@ Readings taken where the paper is silent (all of them, in one place):
       the Gauss-Newton step of each cost in the inverse-compositional form (H =
       sum SD_i^T SD_i for all three). Whatever the cost, the reported coefficient
       and the acceptance test stay the ZNCC at the final p (R8).
+  R13 Levenberg-Marquardt (Sec. 2.2 names the method and leaves its details to the
+      literature; optimizer "lm"): every iteration samples the trial warp p_k and
+      evaluates the cost C_k (Eq. 2-4) there. The trial is kept when it is the first
+      or C_k < C_best (then lambda /= 10 and p_best, b_best become p_k, b(p_k)),
+      otherwise lambda *= 10. The step solves (H + lambda diag(H)) dp = -b_best and
+      the next trial is p_best o dp^-1; lambda starts at 1e-3; the point has
+      converged when ||dp||_s (R7) is below the threshold; iters counts the trials.
 """
 from __future__ import annotations
 
@@ -82,8 +89,10 @@ OK, NOT_IN_ROI, NOT_REACHED, OUT_OF_BOUNDS, MAX_ITER, LOW_ZNCC, SINGULAR_H, FLAT
 
 # Sec. 4: 40 iterations, convergence threshold 0.01, precision 0.70 (reading R8)
 ZNSSD, NSSD, SSD = "znssd", "nssd", "ssd"
+GAUSS_NEWTON, LEVENBERG_MARQUARDT = "gn", "lm"
+LM_LAMBDA0, LM_FACTOR = 1e-3, 10.0
 DEFAULT_PARAMS = dict(max_iter=40, conv_threshold=0.01, zncc_min=0.70, search_radius=8,
-                      nan_unconverged=False, cost=ZNSSD)
+                      nan_unconverged=False, cost=ZNSSD, optimizer=GAUSS_NEWTON)
 
 
 # --------------------------------------------------------------------------- R1
@@ -418,6 +427,18 @@ def residual(rs: ReferenceSubset, g, gbar, delta_g, cost):
     raise ValueError("unknown cost %r" % cost)
 
 
+def cost_value(rs: ReferenceSubset, g, cost):
+    """Eq. 2 (SSD), Eq. 3 (NSSD) or Eq. 4 (ZNSSD) of the samples g."""
+    if cost == ZNSSD:
+        gbar = g - g.mean()
+        return znssd(rs.fbar, gbar)
+    if cost == NSSD:
+        return float(np.sum((rs.f / rs.norm_f - g / math.sqrt(np.sum(g * g))) ** 2))
+    if cost == SSD:
+        return float(np.sum((rs.f - g) ** 2))
+    raise ValueError("unknown cost %r" % cost)
+
+
 def icgn(ref: Plane, dfm: Plane, xc, yc, subset_size, shape, p_init, params=None, ref_subset=None):
     """IC-GN for one subset from p_init; returns p, zncc, iters, converged, status."""
     prm = dict(DEFAULT_PARAMS)
@@ -435,6 +456,8 @@ def icgn(ref: Plane, dfm: Plane, xc, yc, subset_size, shape, p_init, params=None
         out["status"] = SINGULAR_H
         return out
     ratio_status = None
+    lm = prm["optimizer"] == LEVENBERG_MARQUARDT
+    lam, c_best, p_best, b_best = LM_LAMBDA0, None, None, None
     for _ in range(int(prm["max_iter"])):
         wx, wy = warp(p, rs.dx, rs.dy)
         g, valid = interpolate(dfm, xc + wx, yc + wy)
@@ -449,8 +472,20 @@ def icgn(ref: Plane, dfm: Plane, xc, yc, subset_size, shape, p_init, params=None
             break
         e = residual(rs, g, gbar, delta_g, prm["cost"])
         b = rs.SD.T @ e
-        dp = -lu_solve(rs.LU, rs.piv, b)
-        p = compose_inverse(p, dp, rs.dx, rs.dy)
+        if lm:
+            c = cost_value(rs, g, prm["cost"])
+            if c_best is None or c < c_best:
+                c_best, p_best, b_best = c, p.copy(), b
+                lam /= LM_FACTOR
+            else:
+                lam *= LM_FACTOR
+            Hd = rs.H + lam * np.diag(np.diag(rs.H))
+            LU, piv, _ = lu_partial_pivot(Hd)
+            dp = -lu_solve(LU, piv, b_best)
+            p = compose_inverse(p_best, dp, rs.dx, rs.dy)
+        else:
+            dp = -lu_solve(rs.LU, rs.piv, b)
+            p = compose_inverse(p, dp, rs.dx, rs.dy)
         out["iters"] += 1
         if update_norm(dp, rs.r) < prm["conv_threshold"]:
             out["converged"] = True

@@ -484,6 +484,39 @@ def test_nssd_and_ssd_roots_are_stationary_points_computed_independently(cost):
     assert np.abs(_stationarity(ref, dfm, 31, 33, 11, res["p"], cost)).max() < 1e-6
 
 
+# ------------------------------------------------------------------ Levenberg-Marquardt (Sec. 2.2)
+def test_levenberg_marquardt_reaches_the_gauss_newton_root(monkeypatch):
+    fld = synth.affine_field(64, 64, u0=0.4, v0=-0.3, exx=4e-3, exy=-2e-3, eyx=1e-3, eyy=3e-3)
+    ref, dfm = _speckle_pair(64, 64, fld, seed=3)
+    refp, defp = O.Plane(ref), O.Plane(dfm)
+    prm = dict(conv_threshold=1e-12, max_iter=200)
+    gn = O.icgn(refp, defp, 31, 33, 11, O.AFFINE, [0, 0], prm)
+    lm = O.icgn(refp, defp, 31, 33, 11, O.AFFINE, [0, 0], dict(prm, optimizer=O.LEVENBERG_MARQUARDT))
+    assert gn["status"] == lm["status"] == O.OK
+    assert np.abs(gn["p"] - lm["p"]).max() < 1e-9
+    # the LM root is a stationary point of Eq. 4 by an independent computation
+    assert np.abs(_independent_stationarity(ref, dfm, 31, 33, 11, lm["p"])).max() < 1e-6
+    # without damping (lambda0 = 0, factor 1) and with every trial improving, LM is
+    # Gauss-Newton step for step
+    monkeypatch.setattr(O, "LM_LAMBDA0", 0.0)
+    monkeypatch.setattr(O, "LM_FACTOR", 1.0)
+    prm2 = dict(conv_threshold=1e-3, max_iter=3)
+    a = O.icgn(refp, defp, 31, 33, 11, O.AFFINE, [0.3, -0.2], prm2)
+    b = O.icgn(refp, defp, 31, 33, 11, O.AFFINE, [0.3, -0.2], dict(prm2, optimizer=O.LEVENBERG_MARQUARDT))
+    assert np.abs(a["p"] - b["p"]).max() < 1e-12 and a["iters"] == b["iters"]
+
+
+def test_levenberg_marquardt_recovers_from_a_poor_start():
+    fld = synth.affine_field(96, 96, u0=1.3, v0=0.6, exx=2e-3)
+    ref, dfm = _speckle_pair(96, 96, fld)
+    refp, defp = O.Plane(ref), O.Plane(dfm)
+    prm = dict(conv_threshold=1e-10, max_iter=100, optimizer=O.LEVENBERG_MARQUARDT)
+    near = O.icgn(refp, defp, 48, 48, 21, O.AFFINE, [1.3, 0.6], prm)
+    far = O.icgn(refp, defp, 48, 48, 21, O.AFFINE, [2.4, -0.3], prm)
+    assert near["status"] == far["status"] == O.OK
+    assert np.abs(near["p"] - far["p"]).max() < 1e-8
+
+
 def test_flat_and_singular_subsets():
     flat = np.full((40, 40), 100.0)
     res = O.icgn(O.Plane(flat), O.Plane(flat), 20, 20, 11, O.AFFINE, [0, 0])
