@@ -64,6 +64,13 @@ typedef enum { DIC_RIGID = 0, DIC_AFFINE = 1, DIC_QUADRATIC = 2 } dic_shape;
  * The reported coefficient and the acceptance test remain the ZNCC at the final p. */
 typedef enum { DIC_COST_ZNSSD = 0, DIC_COST_NSSD = 1, DIC_COST_SSD = 2 } dic_cost;
 
+/* Per-subset optimiser (Sec. 2.2 names Levenberg-Marquardt and leaves the details to
+ * the literature): undamped inverse-compositional Gauss-Newton (default), or
+ * Levenberg-Marquardt with Marquardt's diagonal damping H + lambda diag(H), lambda from
+ * 1e-3, divided by 10 when a trial lowers the cost and multiplied by 10 when it does
+ * not (the step is then retaken from the best warp so far). Both reach the same root. */
+typedef enum { DIC_OPT_GAUSS_NEWTON = 0, DIC_OPT_LEVENBERG_MARQUARDT = 1 } dic_optimizer;
+
 /* Sec. 2.2: interpolating cubic B-spline, mirror boundary. */
 typedef enum { DIC_BSPLINE3 = 0 } dic_interp;
 
@@ -102,6 +109,8 @@ typedef struct {
   int32_t nan_unconverged;   /* Sec. 4: 1 sets u, v, p of rejected points to NaN    */
   int32_t profile;           /* 1: record CUDA-event stage timings (dic_get_timing) */
   int32_t cost;              /* dic_cost (default DIC_COST_ZNSSD)                    */
+  int32_t optimizer;         /* dic_optimizer (default DIC_OPT_GAUSS_NEWTON)         */
+  int32_t reserved;          /* 0                                                    */
 } dic_params;
 /* ||dp|| = sqrt(dp0^2 + dp1^2 + r^2 (dp2^2+..+dp5^2) + r^4 (dp6^2+..+dp11^2)),
  * r = (subset_size - 1) / 2; a subset has converged once ||dp|| < conv_threshold. */

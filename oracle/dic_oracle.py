@@ -70,11 +70,17 @@ Readings taken where the paper is silent (all of them, in one place):
       and the acceptance test stay the ZNCC at the final p (R8).
   R13 Levenberg-Marquardt (Sec. 2.2 names the method and leaves its details to the
       literature; optimizer "lm"): every iteration samples the trial warp p_k and
-      evaluates the cost C_k (Eq. 2-4) there. The trial is kept when it is the first
-      or C_k < C_best (then lambda /= 10 and p_best, b_best become p_k, b(p_k)),
-      otherwise lambda *= 10. The step solves (H + lambda diag(H)) dp = -b_best and
-      the next trial is p_best o dp^-1; lambda starts at 1e-3; the point has
-      converged when ||dp||_s (R7) is below the threshold; iters counts the trials.
+      evaluates the cost C_k (Eq. 2-4) and the undamped Gauss-Newton step
+      s_k = ||-H^-1 b(p_k)||_s (R7) there. The trial is kept when it is the first,
+      lowers the cost (C_k < C_best) or shortens that step (s_k < s_best): the
+      inverse-compositional root and the minimum of the cost differ at second order,
+      so near convergence the cost alone can refuse every step towards the root.
+      Keeping divides lambda by 10 (p_best, b_best, C_best, s_best become the
+      trial's), refusing multiplies it by 10; lambda starts at 1e-3. The point has
+      converged when s_best is below the threshold; the undamped step is then
+      applied (p_best o dp^-1), so the stopping rule, and the root, are those of
+      Gauss-Newton. Otherwise the damped step solves (H + lambda diag(H)) dp =
+      -b_best and the next trial is p_best o dp^-1. iters counts the trials.
 """
 from __future__ import annotations
 
@@ -457,7 +463,7 @@ def icgn(ref: Plane, dfm: Plane, xc, yc, subset_size, shape, p_init, params=None
         return out
     ratio_status = None
     lm = prm["optimizer"] == LEVENBERG_MARQUARDT
-    lam, c_best, p_best, b_best = LM_LAMBDA0, None, None, None
+    lam, c_best, s_best, p_best, b_best = LM_LAMBDA0, None, None, None, None
     for _ in range(int(prm["max_iter"])):
         wx, wy = warp(p, rs.dx, rs.dy)
         g, valid = interpolate(dfm, xc + wx, yc + wy)
@@ -474,14 +480,20 @@ def icgn(ref: Plane, dfm: Plane, xc, yc, subset_size, shape, p_init, params=None
         b = rs.SD.T @ e
         if lm:
             c = cost_value(rs, g, prm["cost"])
-            if c_best is None or c < c_best:
-                c_best, p_best, b_best = c, p.copy(), b
+            s_k = update_norm(-lu_solve(rs.LU, rs.piv, b), rs.r)
+            if c_best is None or c < c_best or s_k < s_best:
+                c_best, s_best, p_best, b_best = c, s_k, p.copy(), b
                 lam /= LM_FACTOR
             else:
                 lam *= LM_FACTOR
-            Hd = rs.H + lam * np.diag(np.diag(rs.H))
-            LU, piv, _ = lu_partial_pivot(Hd)
-            dp = -lu_solve(LU, piv, b_best)
+            dp = -lu_solve(rs.LU, rs.piv, b_best)         # undamped: the convergence test
+            if update_norm(dp, rs.r) >= prm["conv_threshold"]:
+                Hd = rs.H + lam * np.diag(np.diag(rs.H))
+                LU, piv, _ = lu_partial_pivot(Hd)
+                dp = -lu_solve(LU, piv, b_best)
+                p = compose_inverse(p_best, dp, rs.dx, rs.dy)
+                out["iters"] += 1
+                continue
             p = compose_inverse(p_best, dp, rs.dx, rs.dy)
         else:
             dp = -lu_solve(rs.LU, rs.piv, b)

@@ -19,6 +19,8 @@ DIC_BSPLINE3 = 0
 DIC_FP64, DIC_MIXED = 0, 1
 DIC_COST_ZNSSD, DIC_COST_NSSD, DIC_COST_SSD = 0, 1, 2
 COSTS = {"znssd": DIC_COST_ZNSSD, "nssd": DIC_COST_NSSD, "ssd": DIC_COST_SSD}
+DIC_OPT_GAUSS_NEWTON, DIC_OPT_LEVENBERG_MARQUARDT = 0, 1
+OPTIMIZERS = {"gn": DIC_OPT_GAUSS_NEWTON, "lm": DIC_OPT_LEVENBERG_MARQUARDT}
 (PT_OK, PT_NOT_IN_ROI, PT_NOT_REACHED, PT_OUT_OF_BOUNDS, PT_MAX_ITER, PT_LOW_ZNCC, PT_SINGULAR,
  PT_FLAT) = range(8)
 SHAPES = {"rigid": DIC_RIGID, "affine": DIC_AFFINE, "quadratic": DIC_QUADRATIC}
@@ -49,7 +51,8 @@ class DicParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("search_radius", ctypes.c_int32),
                 ("conv_threshold", ctypes.c_double), ("zncc_min", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("nan_unconverged", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("cost", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("cost", ctypes.c_int32),
+                ("optimizer", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class DicResults(ctypes.Structure):
@@ -401,13 +404,15 @@ def _apply(p: DicParams, kw: dict) -> DicParams:
             v = {"fp64": DIC_FP64, "mixed": DIC_MIXED}[v]
         if k == "cost" and isinstance(v, str):
             v = COSTS[v]
+        if k == "optimizer" and isinstance(v, str):
+            v = OPTIMIZERS[v]
         setattr(p, k, v)
     return p
 
 
 def params(**kw) -> DicParams:
-    """Default parameters with the given fields replaced (precision and cost may be
-    strings: "fp64"/"mixed", "znssd"/"nssd"/"ssd")."""
+    """Default parameters with the given fields replaced (precision, cost and optimizer
+    may be strings: "fp64"/"mixed", "znssd"/"nssd"/"ssd", "gn"/"lm")."""
     return _apply(dic_default_params(), kw)
 
 

@@ -361,13 +361,14 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   a.wave_sizes = h->wave_sizes;
   a.max_iter = h->prm.max_iter;
   a.cost = h->prm.cost;
+  a.lm = h->prm.optimizer == DIC_OPT_LEVENBERG_MARQUARDT;
   a.conv_threshold = h->prm.conv_threshold;
   a.zncc_min = h->prm.zncc_min;
 
   int sms = 0;
   DIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "device query");
   const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
-  const int per_sm = wave_blocks_per_sm<T>(h->nparams, a.threads, smem);
+  const int per_sm = wave_blocks_per_sm<T>(h->nparams, a.threads, a.lm, smem);
   const int grid = sms * per_sm;
 
   const bool prof = h->prm.profile != 0;
@@ -606,6 +607,8 @@ int validate_params(const dic_params* p) {
     return fail(DIC_EINVAL, "unknown precision %d", p->precision);
   if (p->cost != DIC_COST_ZNSSD && p->cost != DIC_COST_NSSD && p->cost != DIC_COST_SSD)
     return fail(DIC_EINVAL, "unknown cost %d", p->cost);
+  if (p->optimizer != DIC_OPT_GAUSS_NEWTON && p->optimizer != DIC_OPT_LEVENBERG_MARQUARDT)
+    return fail(DIC_EINVAL, "unknown optimizer %d", p->optimizer);
   return DIC_OK;
 }
 
@@ -685,6 +688,8 @@ dic_params dic_default_params(void) {
   p.nan_unconverged = 0;
   p.profile = 0;
   p.cost = DIC_COST_ZNSSD;
+  p.optimizer = DIC_OPT_GAUSS_NEWTON;
+  p.reserved = 0;
   return p;
 }
 

@@ -607,6 +607,122 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
   return n2 < thr2 ? 1 : 0;
 }
 
+// Levenberg-Marquardt state of a point (Sec. 2.2): the undamped Hessian, the best
+// trial so far (its warp, right-hand side and cost) and the damping; empty for
+// Gauss-Newton.
+constexpr float kLmLambda0 = 1e-3f, kLmFactor = 10.0f;
+template <typename C, int NP, bool LM>
+struct LmState {};
+template <typename C, int NP>
+struct LmState<C, NP, true> {
+  C H[NP * NP];
+  C b_best[NP];
+  C p_best[kMaxParams];
+  C lam, c_best;
+  int has_best;
+};
+
+// The out-of-line FP64 inverse of a scaled matrix read through hget (the FP32 one
+// met a tiny pivot).
+template <int N, typename HGet>
+__device__ __noinline__ void invert_scaled_fp64_from(HGet hget, float* X, int lane, float* ratio) {
+  invert_scaled_warp<double, N>(hget, X, lane, ratio);
+}
+
+// Warp 0 after an iteration's reduction, Levenberg-Marquardt: out = [sum g', sum g'^2,
+// sum SD g', bad, sum f' g']. The trial's cost (Eq. 2-4, from the sums) decides: a
+// first or lower cost keeps the trial (its warp, b and cost become the best, lambda
+// / 10), otherwise lambda x 10; then the step solves (H + lambda diag H) dp = -b_best
+// (the scaled inverse is formed again) and the next trial is p_best o dp^-1. Returns
+// like gauss_newton_update.
+template <typename C, int NP>
+__device__ int lm_update(PointState<C, NP>& st, LmState<C, NP, true>& lm, const C* out, int N, C r, C thr2,
+                         int lane, int cost) {
+  if (out[2 + NP] > C(0.5)) return 5;
+  const C n = static_cast<C>(N);
+  const C nu = out[0] * (C(1) / n);
+  const C dg2 = fmax(out[1] - out[0] * nu, C(0));
+  const C gm = fmax(fabs(nu + st.f0), C(1));
+  if (dg2 <= C(1e-12) * n * gm * gm) return 2;
+  const C sfg = out[3 + NP];
+  const C f0 = st.f0;
+  C kg, kc, cval;
+  if (cost == DIC_COST_SSD) {
+    kg = C(1);
+    kc = C(0);
+    cval = st.sff - C(2) * sfg + out[1];                        // sum (f' - g')^2
+  } else if (cost == DIC_COST_NSSD) {
+    const C nf2 = st.sff + C(2) * f0 * st.sf + n * f0 * f0;
+    const C ng2 = out[1] + C(2) * f0 * out[0] + n * f0 * f0;
+    const C nf = sqrt(nf2), ng = sqrt(ng2);
+    kg = nf / ng;
+    kc = f0 * ((out[1] - st.sff) + C(2) * f0 * (out[0] - st.sf)) / (ng * (ng + nf));
+    const C sfgf = sfg + f0 * (out[0] + st.sf) + n * f0 * f0;    // sum f g
+    cval = C(2) - C(2) * sfgf / (nf * ng);
+  } else {
+    const C dg = sqrt(dg2);
+    kg = st.delta_f / dg;
+    kc = kg * nu;
+    cval = C(2) - C(2) * (sfg - st.mu * out[0]) / (st.delta_f * dg);   // sum fbar gbar = sum f'g' - mu sum g'
+  }
+  const C bk = lane < NP ? st.sdf[lane] - kg * out[2 + lane] + kc * st.sds[lane] : C(0);
+  const bool keep = !lm.has_best || cval < lm.c_best;   // the same on every lane
+  if (keep) {
+    if (lane < NP) lm.b_best[lane] = bk;
+    if (lane < kMaxParams) lm.p_best[lane] = st.p[lane];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    if (keep) {
+      lm.c_best = cval;
+      lm.has_best = 1;
+      lm.lam = lm.lam / C(kLmFactor);
+    } else {
+      lm.lam = lm.lam * C(kLmFactor);
+    }
+  }
+  __syncwarp();
+  const C lam = lm.lam;
+  C d;
+  if constexpr (sizeof(C) == sizeof(double)) {
+    for (int e = lane; e < NP * NP; e += 32)
+      st.sv.H[e] = lm.H[e] * ((e / NP == e % NP) ? C(1) + lam : C(1));
+    __syncwarp();
+    invert_spd_warp<C, NP>(st.sv.H, st.sv.X, lane);
+    __syncwarp();
+    C acc = C(0);
+    if (lane < NP) {
+#pragma unroll
+      for (int m = 0; m < NP; ++m) acc -= st.sv.X[lane * NP + m] * lm.b_best[m];
+    }
+    d = lane < NP ? acc : C(0);
+  } else {
+    auto hget = [&](int i, int j) -> float { return lm.H[i * NP + j] * (i == j ? 1.0f + lam : 1.0f); };
+    float rf;
+    if (invert_scaled_warp<float, NP>(hget, st.sv.X, lane, &rf) < 1e-5f)
+      invert_scaled_fp64_from<NP>(hget, st.sv.X, lane, &rf);
+    __syncwarp();
+    const C bb = lane < NP ? lm.b_best[lane] : C(0);
+    const int row = lane < NP ? lane : 0;
+    C acc = C(0);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) acc -= st.sv.X[m * NP + row] * __shfl_sync(0xffffffffu, bb, m);
+    d = lane < NP ? acc : C(0);
+  }
+  if (lane < NP) st.dp[lane] = d;
+  const C wgt = lane < 2 ? C(1) : (lane < 6 ? r * r : r * r * r * r);
+  C n2 = lane < NP ? wgt * d * d : C(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  __syncwarp();
+  if (lane == 0) {
+    for (int c = 0; c < NP; ++c) st.p[c] = lm.p_best[c];
+    compose_inverse<C, NP>(st.p, st.dp);
+  }
+  __syncwarp();
+  return n2 < thr2 ? 1 : 0;
+}
+
 // Two values that go through the same arithmetic (an x quantity with its y
 // counterpart): on the mixed path one packed FP32x2 instruction per operation,
 // rounded exactly like the two scalar operations; on the FP64 path two scalar ones.
@@ -689,9 +805,10 @@ __device__ __forceinline__ void bspline_weights6_pair(Pair<T> t, Pair<T>& w0, Pa
 // rows of the support stay in registers (rotated by the 4-way unrolled loop) and
 // only the new row is loaded; anything else reloads all four.
 // fin = false: acc = [sum g', sum g'^2, sum fx g' dy^j (j <= D), sum fy g' dy^j]
+//              (FG: then sum f' g', which the Levenberg-Marquardt cost needs)
 // fin = true:  acc = [sum g', sum g'^2, sum f' g'] (the final pass; one copy of the
 // unrolled loop serves both, fin being the same for the whole block)
-template <typename T, int D>
+template <typename T, int D, bool FG>
 __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld, T ax, T bx, T cxq,
                                               T ay, T by, T cyq, T xlo, T xhi, T ylo, T yhi, T f0,
                                               int row0, int row1, int r, int S, int col,
@@ -743,6 +860,7 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
       acc[2] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
     } else {
       const Pair<T> g2 = pmul(pair(gp, gp), s_fg[row * S + col]);   // (fx g', fy g')
+      if (FG) acc[2 + 2 * (D + 1)] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
       sd[0] = padd(sd[0], g2);
       Pair<T> dyp = dy2;
 #pragma unroll
@@ -770,7 +888,7 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
 // The rare path (window too large for shared memory): every sample reads its
 // 4 x 4 support from the global plane; a plain loop, light on registers, kept out
 // of line so that it does not sit in the instruction stream of the common path.
-template <typename T, int D>
+template <typename T, int D, bool FG>
 __device__ __noinline__ void sample_column_global(const T* __restrict__ base, int64_t ld, T ax,
                                                      T bx, T cxq, T ay, T by, T cyq, T xlo, T xhi,
                                                      T ylo, T yhi, T f0, int row0, int row1, int r,
@@ -805,6 +923,7 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
     } else {
       const Pair<T> fg = s_fg[row * S + col];
       const T gxv = gp * fg.x, gyv = gp * fg.y;
+      if (FG) acc[2 + 2 * (D + 1)] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
       T dyp = T(1);
 #pragma unroll
       for (int j = 0; j <= D; ++j) {
@@ -828,7 +947,7 @@ struct WaveOccupancy<double, 128> { static constexpr int kBlocks = 4; };
 template <>
 struct WaveOccupancy<double, 64> { static constexpr int kBlocks = 8; };
 
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, bool LM>
 __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
     wave_kernel(WaveArgs<T> a, const __grid_constant__ CUtensorMap tm_cref,
                 const __grid_constant__ CUtensorMap tm_cdef, const __grid_constant__ CUtensorMap tm_gray) {
@@ -837,9 +956,9 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
   constexpr int M2 = 2 * D;
   constexpr int NMOM = (M2 + 1) * (M2 + 2) / 2;
   constexpr int NV_PRE = 3 * NMOM + 2 * NP + 2;  // H moments, sum SD f', sum SD, sum f', sum f'^2
-  constexpr int NV_IT = 3 + NP;                  // sum g', sum g'^2, sum SD g', bad samples
+  constexpr int NV_IT = 3 + NP + (LM ? 1 : 0);   // sum g', sum g'^2, sum SD g', bad samples (LM: sum f'g')
   constexpr int NV_FIN = 4;                      // sum g', sum g'^2, sum f' g', bad samples
-  constexpr int NACC = 2 + 2 * (D + 1);
+  constexpr int NACC = 2 + 2 * (D + 1) + (LM ? 1 : 0);
   constexpr int XALIGN = 16 / static_cast<int>(sizeof(T));   // TMA x alignment of the coefficient planes
   constexpr int NW = NT / 32;                                 // warps per block
 
@@ -856,6 +975,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
   __shared__ T s_part[NW][NV_PRE];
   __shared__ C s_out[NV_PRE];
   __shared__ PointState<C, NP> st;
+  __shared__ LmState<C, NP, LM> lms;
   __shared__ __align__(8) uint64_t s_bar;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1125,6 +1245,17 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
     if (warp == 0) {
       gather(NV_PRE);
       finish_reference<C, NP, NMOM, M2>(st, s_out, N, lane, a.cost);
+      if constexpr (LM) {
+        // the undamped Hessian, kept for the damped inverses of every iteration
+        for (int e = lane; e < NP * NP; e += 32) {
+          const int ca = e / NP, cb = e % NP;
+          lms.H[e] = s_out[(sd_t(ca) + sd_t(cb)) * NMOM + mono(sd_i(ca) + sd_i(cb), sd_j(ca) + sd_j(cb), M2)];
+        }
+        if (lane == 0) {
+          lms.lam = C(kLmLambda0);
+          lms.has_best = 0;
+        }
+      }
       if (lane == 0) {
         if (st.ctl == 0)
           plan_window<C, NP>(st, xc, yc, r, a.W, a.H, tl, XALIGN);
@@ -1182,12 +1313,12 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
       T bad = T(0);
       if (stage != 2) {
         const T* base = s_win + (yc - 1 - w.y0) * w.w + (xc - 1 - w.x0);
-        sample_column<T, D>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r, S, col,
-                            gtile, gpitch, gdt, s_fg, final_pass, st.inside != 0, acc, bad);
+        sample_column<T, D, LM>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r, S,
+                                col, gtile, gpitch, gdt, s_fg, final_pass, st.inside != 0, acc, bad);
       } else {
         const T* base = a.c_def + static_cast<int64_t>(yc - 1) * a.ldc + (xc - 1);
-        sample_column_global<T, D>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r,
-                                   S, col, gtile, gpitch, gdt, s_fg, final_pass, acc, bad);
+        sample_column_global<T, D, LM>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1,
+                                       r, S, col, gtile, gpitch, gdt, s_fg, final_pass, acc, bad);
       }
       if (!final_pass) {
         T v[pow2ceil(NV_IT)];
@@ -1196,6 +1327,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
 #pragma unroll
         for (int c = 0; c < NP; ++c) v[2 + c] = dxp[sd_i(c)] * acc[2 + sd_t(c) * (D + 1) + sd_j(c)];
         v[2 + NP] = bad;
+        if constexpr (LM) v[3 + NP] = acc[2 + 2 * (D + 1)];
 #pragma unroll
         for (int e = NV_IT; e < pow2ceil(NV_IT); ++e) v[e] = T(0);
         parts(v, 0, NV_IT);
@@ -1208,7 +1340,11 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
         gather(final_pass ? NV_FIN : NV_IT);
         if (lane == 0 && (st.stage == 1 || st.stage == 3)) st.win = st.next;
         if (!final_pass) {
-          const int ctl = gauss_newton_update<C, NP>(st, s_out, N, static_cast<C>(r), thr2, lane, a.cost);
+          int ctl;
+          if constexpr (LM)
+            ctl = lm_update<C, NP>(st, lms, s_out, N, static_cast<C>(r), thr2, lane, a.cost);
+          else
+            ctl = gauss_newton_update<C, NP>(st, s_out, N, static_cast<C>(r), thr2, lane, a.cost);
           if (lane == 0) {
             if (ctl == 5) {
               st.status = DIC_PT_OUT_OF_BOUNDS;
@@ -1382,50 +1518,56 @@ __global__ void finalize_points_kernel(PointArrays pa, int nparams, int nan_reje
 // Raises the kernel's dynamic shared-memory limit to the device's opt-in limit
 // less its static shared memory, once per instantiation (thread-safe); the
 // largest tile set (S = 61, FP64 coefficients, 8-byte gray) stays below it.
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, bool LM>
 cudaError_t configure_wave_smem() {
   static const cudaError_t result = []() {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa{};
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, wave_kernel<T, NP, NT>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, wave_kernel<T, NP, NT, LM>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(wave_kernel<T, NP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(wave_kernel<T, NP, NT, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin - static_cast<int>(fa.sharedSizeBytes));
     return e;
   }();
   return result;
 }
 
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, bool LM>
 cudaError_t launch_wave_nt(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
   const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
-  const cudaError_t configured = configure_wave_smem<T, NP, NT>();
+  const cudaError_t configured = configure_wave_smem<T, NP, NT, LM>();
   if (configured != cudaSuccess) return configured;
-  wave_kernel<T, NP, NT><<<grid, NT, smem, s>>>(a, maps[0], maps[1], maps[2]);
+  wave_kernel<T, NP, NT, LM><<<grid, NT, smem, s>>>(a, maps[0], maps[1], maps[2]);
   return cudaGetLastError();
 }
 
 template <typename T, int NP>
 cudaError_t launch_wave_np(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
-  return a.threads == kWaveThreadsSmall ? launch_wave_nt<T, NP, kWaveThreadsSmall>(a, maps, grid, s)
-                                        : launch_wave_nt<T, NP, kWaveThreads>(a, maps, grid, s);
+  if (a.lm)
+    return a.threads == kWaveThreadsSmall ? launch_wave_nt<T, NP, kWaveThreadsSmall, true>(a, maps, grid, s)
+                                          : launch_wave_nt<T, NP, kWaveThreads, true>(a, maps, grid, s);
+  return a.threads == kWaveThreadsSmall ? launch_wave_nt<T, NP, kWaveThreadsSmall, false>(a, maps, grid, s)
+                                        : launch_wave_nt<T, NP, kWaveThreads, false>(a, maps, grid, s);
 }
 
-template <typename T, int NP, int NT>
+template <typename T, int NP, int NT, bool LM>
 int blocks_per_sm_nt(size_t smem) {
-  if (configure_wave_smem<T, NP, NT>() != cudaSuccess) return 1;
+  if (configure_wave_smem<T, NP, NT, LM>() != cudaSuccess) return 1;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<T, NP, NT>, NT, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<T, NP, NT, LM>, NT, smem) != cudaSuccess)
     return 1;
   return nb > 0 ? nb : 1;
 }
 
 template <typename T, int NP>
-int blocks_per_sm_np(int threads, size_t smem) {
-  return threads == kWaveThreadsSmall ? blocks_per_sm_nt<T, NP, kWaveThreadsSmall>(smem)
-                                      : blocks_per_sm_nt<T, NP, kWaveThreads>(smem);
+int blocks_per_sm_np(int threads, bool lm, size_t smem) {
+  if (lm)
+    return threads == kWaveThreadsSmall ? blocks_per_sm_nt<T, NP, kWaveThreadsSmall, true>(smem)
+                                        : blocks_per_sm_nt<T, NP, kWaveThreads, true>(smem);
+  return threads == kWaveThreadsSmall ? blocks_per_sm_nt<T, NP, kWaveThreadsSmall, false>(smem)
+                                      : blocks_per_sm_nt<T, NP, kWaveThreads, false>(smem);
 }
 
 }  // namespace
@@ -1466,14 +1608,14 @@ cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensor
 }
 
 template <typename T>
-int wave_blocks_per_sm(int nparams, int threads, size_t smem) {
+int wave_blocks_per_sm(int nparams, int threads, int lm, size_t smem) {
   switch (nparams) {
     case 2:
-      return blocks_per_sm_np<T, 2>(threads, smem);
+      return blocks_per_sm_np<T, 2>(threads, lm != 0, smem);
     case 6:
-      return blocks_per_sm_np<T, 6>(threads, smem);
+      return blocks_per_sm_np<T, 6>(threads, lm != 0, smem);
     default:
-      return blocks_per_sm_np<T, 12>(threads, smem);
+      return blocks_per_sm_np<T, 12>(threads, lm != 0, smem);
   }
 }
 
@@ -1520,7 +1662,7 @@ template cudaError_t launch_wave<float>(const WaveArgs<float>&, const WaveTiles&
                                         cudaStream_t);
 template cudaError_t launch_wave<double>(const WaveArgs<double>&, const WaveTiles&, const CUtensorMap*, int, int,
                                          cudaStream_t);
-template int wave_blocks_per_sm<float>(int, int, size_t);
-template int wave_blocks_per_sm<double>(int, int, size_t);
+template int wave_blocks_per_sm<float>(int, int, int, size_t);
+template int wave_blocks_per_sm<double>(int, int, int, size_t);
 
 }  // namespace dic

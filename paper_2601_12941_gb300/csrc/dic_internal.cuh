@@ -197,6 +197,7 @@ struct WaveArgs {
   // controls
   int max_iter;
   int cost;                  // dic_cost
+  int lm;                    // 1: Levenberg-Marquardt (dic_optimizer)
   double conv_threshold;
   double zncc_min;
 };
@@ -243,6 +244,6 @@ cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensor
                         int grid, cudaStream_t s);
 
 template <typename T>
-int wave_blocks_per_sm(int nparams, int threads, size_t smem);
+int wave_blocks_per_sm(int nparams, int threads, int lm, size_t smem);
 
 }  // namespace dic

@@ -47,6 +47,8 @@ def test_default_params_are_the_papers(lib):
     p = binding.dic_default_params()
     assert (p.max_iter, p.conv_threshold, p.zncc_min) == (40, 0.01, 0.70)
     assert p.precision == binding.DIC_MIXED and p.nan_unconverged == 0
+    # ZNSSD (Eq. 4) is the paper's default cost; undamped Gauss-Newton the default optimiser
+    assert p.cost == binding.DIC_COST_ZNSSD and p.optimizer == binding.DIC_OPT_GAUSS_NEWTON
 
 
 def test_invalid_arguments_fail_before_any_device_work(lib):

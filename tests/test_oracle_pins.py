@@ -506,6 +506,19 @@ def test_levenberg_marquardt_reaches_the_gauss_newton_root(monkeypatch):
     assert np.abs(a["p"] - b["p"]).max() < 1e-12 and a["iters"] == b["iters"]
 
 
+def test_levenberg_marquardt_matches_gauss_newton_on_every_point_of_a_correlation():
+    # the convergence test is Gauss-Newton's, so every accepted point lands on the same root
+    fld = synth.affine_field(120, 110, u0=1.2, v0=-0.7, exx=1.5e-3, exy=4e-4, eyx=4e-4, eyy=-8e-4)
+    ref, dfm = _speckle_pair(120, 110, fld, seed=9, noise=1.0)
+    prm = dict(conv_threshold=1e-8, max_iter=100, search_radius=4)
+    gn = oracle.correlate(ref, dfm, None, 17, 6, O.AFFINE, [(60, 55)], prm)
+    lm = oracle.correlate(ref, dfm, None, 17, 6, O.AFFINE, [(60, 55)], dict(prm, optimizer=O.LEVENBERG_MARQUARDT))
+    both = (gn["status"] == O.OK) & (lm["status"] == O.OK)
+    assert both.sum() > 0.85 * len(gn["status"])    # the rest leave the image near its edges, in both
+    assert np.array_equal(gn["status"] == O.OK, lm["status"] == O.OK)
+    assert np.abs(gn["p"][both] - lm["p"][both]).max() < 1e-7
+
+
 def test_levenberg_marquardt_recovers_from_a_poor_start():
     fld = synth.affine_field(96, 96, u0=1.3, v0=0.6, exx=2e-3)
     ref, dfm = _speckle_pair(96, 96, fld)
