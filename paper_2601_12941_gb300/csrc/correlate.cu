@@ -607,8 +607,9 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
   return n2 < thr2 ? 1 : 0;
 }
 
-// Levenberg-Marquardt state of a point (Sec. 2.2): the undamped Hessian, the best
-// trial so far (its warp, right-hand side and cost) and the damping; empty for
+// Levenberg-Marquardt state of a point (Sec. 2.2): the undamped Hessian and its
+// inverse (the layout of the solve state's inverse), the best trial so far (its warp,
+// right-hand side, cost and squared undamped step) and the damping; empty for
 // Gauss-Newton.
 constexpr float kLmLambda0 = 1e-3f, kLmFactor = 10.0f;
 template <typename C, int NP, bool LM>
@@ -616,11 +617,36 @@ struct LmState {};
 template <typename C, int NP>
 struct LmState<C, NP, true> {
   C H[NP * NP];
+  C X0[NP * NP];
   C b_best[NP];
   C p_best[kMaxParams];
-  C lam, c_best;
+  C lam, c_best, s2_best;
   int has_best;
 };
+
+// -X0 b (the undamped step) on lanes < NP; X0 column-major on the mixed path (shared
+// through b by shuffles), row-major on the FP64 path
+template <typename C, int NP>
+__device__ __forceinline__ C undamped_step(const C* X0, C b, int lane) {
+  const int row = lane < NP ? lane : 0;
+  C acc = C(0);
+#pragma unroll
+  for (int m = 0; m < NP; ++m) {
+    const C bm = __shfl_sync(0xffffffffu, b, m);
+    acc -= (sizeof(C) == sizeof(double) ? X0[row * NP + m] : X0[m * NP + row]) * bm;
+  }
+  return lane < NP ? acc : C(0);
+}
+
+// squared ||d||_s of reading R7 over the warp (every lane gets it)
+template <typename C>
+__device__ __forceinline__ C step_norm2(C d, C r, int lane, int NP) {
+  const C wgt = lane < 2 ? C(1) : (lane < 6 ? r * r : r * r * r * r);
+  C n2 = lane < NP ? wgt * d * d : C(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+  return n2;
+}
 
 // The out-of-line FP64 inverse of a scaled matrix read through hget (the FP32 one
 // met a tiny pivot).
@@ -630,11 +656,14 @@ __device__ __noinline__ void invert_scaled_fp64_from(HGet hget, float* X, int la
 }
 
 // Warp 0 after an iteration's reduction, Levenberg-Marquardt: out = [sum g', sum g'^2,
-// sum SD g', bad, sum f' g']. The trial's cost (Eq. 2-4, from the sums) decides: a
-// first or lower cost keeps the trial (its warp, b and cost become the best, lambda
-// / 10), otherwise lambda x 10; then the step solves (H + lambda diag H) dp = -b_best
-// (the scaled inverse is formed again) and the next trial is p_best o dp^-1. Returns
-// like gauss_newton_update.
+// sum SD g', bad, sum f' g']. At the trial: the cost (Eq. 2-4, from the sums) and the
+// undamped Gauss-Newton step -H^-1 b. The trial is kept when it is the first, lowers
+// the cost or shortens that step (the inverse-compositional root and the minimum of
+// the cost differ at second order); keeping divides lambda by 10, refusing multiplies
+// it by 10. Converged when the best trial's undamped step is below the threshold:
+// that step is applied. Otherwise the damped step solves (H + lambda diag H) dp =
+// -b_best (its inverse formed again). The next trial is p_best o dp^-1. Returns like
+// gauss_newton_update.
 template <typename C, int NP>
 __device__ int lm_update(PointState<C, NP>& st, LmState<C, NP, true>& lm, const C* out, int N, C r, C thr2,
                          int lane, int cost) {
@@ -666,7 +695,8 @@ __device__ int lm_update(PointState<C, NP>& st, LmState<C, NP, true>& lm, const 
     cval = C(2) - C(2) * (sfg - st.mu * out[0]) / (st.delta_f * dg);   // sum fbar gbar = sum f'g' - mu sum g'
   }
   const C bk = lane < NP ? st.sdf[lane] - kg * out[2 + lane] + kc * st.sds[lane] : C(0);
-  const bool keep = !lm.has_best || cval < lm.c_best;   // the same on every lane
+  const C s2 = step_norm2<C>(undamped_step<C, NP>(lm.X0, bk, lane), r, lane, NP);
+  const bool keep = !lm.has_best || cval < lm.c_best || s2 < lm.s2_best;   // the same on every lane
   if (keep) {
     if (lane < NP) lm.b_best[lane] = bk;
     if (lane < kMaxParams) lm.p_best[lane] = st.p[lane];
@@ -675,6 +705,7 @@ __device__ int lm_update(PointState<C, NP>& st, LmState<C, NP, true>& lm, const 
   if (lane == 0) {
     if (keep) {
       lm.c_best = cval;
+      lm.s2_best = s2;
       lm.has_best = 1;
       lm.lam = lm.lam / C(kLmFactor);
     } else {
@@ -682,45 +713,35 @@ __device__ int lm_update(PointState<C, NP>& st, LmState<C, NP, true>& lm, const 
     }
   }
   __syncwarp();
-  const C lam = lm.lam;
+  const bool converged = lm.s2_best < thr2;
+  const C bb = lane < NP ? lm.b_best[lane] : C(0);
   C d;
-  if constexpr (sizeof(C) == sizeof(double)) {
-    for (int e = lane; e < NP * NP; e += 32)
-      st.sv.H[e] = lm.H[e] * ((e / NP == e % NP) ? C(1) + lam : C(1));
-    __syncwarp();
-    invert_spd_warp<C, NP>(st.sv.H, st.sv.X, lane);
-    __syncwarp();
-    C acc = C(0);
-    if (lane < NP) {
-#pragma unroll
-      for (int m = 0; m < NP; ++m) acc -= st.sv.X[lane * NP + m] * lm.b_best[m];
-    }
-    d = lane < NP ? acc : C(0);
+  if (converged) {
+    d = undamped_step<C, NP>(lm.X0, bb, lane);
   } else {
-    auto hget = [&](int i, int j) -> float { return lm.H[i * NP + j] * (i == j ? 1.0f + lam : 1.0f); };
-    float rf;
-    if (invert_scaled_warp<float, NP>(hget, st.sv.X, lane, &rf) < 1e-5f)
-      invert_scaled_fp64_from<NP>(hget, st.sv.X, lane, &rf);
+    const C lam = lm.lam;
+    if constexpr (sizeof(C) == sizeof(double)) {
+      for (int e = lane; e < NP * NP; e += 32)
+        st.sv.H[e] = lm.H[e] * ((e / NP == e % NP) ? C(1) + lam : C(1));
+      __syncwarp();
+      invert_spd_warp<C, NP>(st.sv.H, st.sv.X, lane);
+    } else {
+      auto hget = [&](int i, int j) -> float { return lm.H[i * NP + j] * (i == j ? 1.0f + lam : 1.0f); };
+      float rf;
+      if (invert_scaled_warp<float, NP>(hget, st.sv.X, lane, &rf) < 1e-5f)
+        invert_scaled_fp64_from<NP>(hget, st.sv.X, lane, &rf);
+    }
     __syncwarp();
-    const C bb = lane < NP ? lm.b_best[lane] : C(0);
-    const int row = lane < NP ? lane : 0;
-    C acc = C(0);
-#pragma unroll
-    for (int m = 0; m < NP; ++m) acc -= st.sv.X[m * NP + row] * __shfl_sync(0xffffffffu, bb, m);
-    d = lane < NP ? acc : C(0);
+    d = undamped_step<C, NP>(st.sv.X, bb, lane);   // the same product with the damped inverse
   }
   if (lane < NP) st.dp[lane] = d;
-  const C wgt = lane < 2 ? C(1) : (lane < 6 ? r * r : r * r * r * r);
-  C n2 = lane < NP ? wgt * d * d : C(0);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
   __syncwarp();
   if (lane == 0) {
     for (int c = 0; c < NP; ++c) st.p[c] = lm.p_best[c];
     compose_inverse<C, NP>(st.p, st.dp);
   }
   __syncwarp();
-  return n2 < thr2 ? 1 : 0;
+  return converged ? 1 : 0;
 }
 
 // Two values that go through the same arithmetic (an x quantity with its y
@@ -1251,6 +1272,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
           const int ca = e / NP, cb = e % NP;
           lms.H[e] = s_out[(sd_t(ca) + sd_t(cb)) * NMOM + mono(sd_i(ca) + sd_i(cb), sd_j(ca) + sd_j(cb), M2)];
         }
+        for (int e = lane; e < NP * NP; e += 32) lms.X0[e] = st.sv.X[e];
         if (lane == 0) {
           lms.lam = C(kLmLambda0);
           lms.has_best = 0;
