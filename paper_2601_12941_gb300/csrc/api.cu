@@ -368,7 +368,7 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   int sms = 0;
   DIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "device query");
   const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
-  const int per_sm = wave_blocks_per_sm<T>(h->nparams, a.threads, a.lm, smem);
+  const int per_sm = wave_blocks_per_sm<T>(h->nparams, a.threads, a.lm, a.cost, smem);
   const int grid = sms * per_sm;
 
   const bool prof = h->prm.profile != 0;

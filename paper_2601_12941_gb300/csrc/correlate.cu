@@ -486,7 +486,7 @@ __device__ void plan_window(PointState<C, NP>& st, int xc, int yc, int r, int W,
 // ill-conditioned for FP32) switches to the same scaled inverse in FP64. Sets
 // st.ctl: 0 ok, 3 flat, 4 singular (a pivot <= 1e-12 of the largest diagonal
 // entry of H).
-template <typename C, int NP, int NMOM, int M2>
+template <typename C, int NP, int NMOM, int M2, bool ANYCOST>
 __device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int lane, int cost) {
   const C sf = out[3 * NMOM + 2 * NP];
   const C sff = out[3 * NMOM + 2 * NP + 1];
@@ -513,13 +513,15 @@ __device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int
   if (lane < NP) {
     st.sds[lane] = out[3 * NMOM + NP + lane];
     // ZNSSD: sum SD (f' - mu) = sum SD fbar; NSSD and SSD: sum SD f'
-    st.sdf[lane] = out[3 * NMOM + lane] - (cost == DIC_COST_ZNSSD ? mu : C(0)) * out[3 * NMOM + NP + lane];
+    st.sdf[lane] = out[3 * NMOM + lane] - ((!ANYCOST || cost == DIC_COST_ZNSSD) ? mu : C(0)) * out[3 * NMOM + NP + lane];
   }
   if (lane == 0) {
     st.mu = mu;
     st.delta_f = df;
-    st.sf = sf;
-    st.sff = sff;
+    if (ANYCOST) {
+      st.sf = sf;
+      st.sff = sff;
+    }
     st.ctl = ratio > 1e-12 ? 0 : 4;
   }
   __syncwarp();
@@ -536,7 +538,7 @@ __device__ void finish_reference(PointState<C, NP>& st, const C* out, int N, int
 // solve sets the rate of convergence, not the root, which b alone fixes). Lane 0
 // composes p <- p o dp^-1. Returns (on every lane) 0 continue, 1 converged,
 // 2 flat, 5 out of bounds.
-template <typename C, int NP>
+template <typename C, int NP, bool ANYCOST>
 __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C r, C thr2, int lane,
                                    int cost) {
   if (out[2 + NP] > C(0.5)) return 5;
@@ -548,7 +550,8 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
   const C ratio = st.delta_f * rsqrt(dg2);
   // coefficients of b = sdf - kg sum SD g' + kc sum SD
   C kg = ratio, kc = ratio * nu;
-  if (cost == DIC_COST_SSD) {
+  if (!ANYCOST) {
+  } else if (cost == DIC_COST_SSD) {
     kg = C(1);
     kc = C(0);
   } else if (cost == DIC_COST_NSSD) {
@@ -563,7 +566,9 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
   C d;
   if constexpr (sizeof(C) == sizeof(double)) {
     double bc = 0.0;
-    if (lane < NP) bc = static_cast<double>(st.sdf[lane] - kg * out[2 + lane] + kc * st.sds[lane]);
+    if (lane < NP)
+      bc = static_cast<double>(ANYCOST ? st.sdf[lane] - kg * out[2 + lane] + kc * st.sds[lane]
+                                       : st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]));
     if (lane < NP) st.sv.bvec[lane] = bc;
     __syncwarp();
     double d0 = 0.0;
@@ -588,7 +593,9 @@ __device__ int gauss_newton_update(PointState<C, NP>& st, const C* out, int N, C
     }
     d = static_cast<C>(dpc);
   } else {
-    const C bc = lane < NP ? st.sdf[lane] - kg * out[2 + lane] + kc * st.sds[lane] : C(0);
+    const C bc = lane >= NP ? C(0)
+                 : ANYCOST ? st.sdf[lane] - kg * out[2 + lane] + kc * st.sds[lane]
+                           : st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]);
     const int row = lane < NP ? lane : 0;
     C acc = C(0);
 #pragma unroll
@@ -968,11 +975,15 @@ struct WaveOccupancy<double, 128> { static constexpr int kBlocks = 4; };
 template <>
 struct WaveOccupancy<double, 64> { static constexpr int kBlocks = 8; };
 
-template <typename T, int NP, int NT, bool LM>
+// MODE 0: Gauss-Newton, ZNSSD only (the default, leanest); 1: Gauss-Newton, any cost;
+// 2: Levenberg-Marquardt, any cost
+template <typename T, int NP, int NT, int MODE>
 __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
     wave_kernel(WaveArgs<T> a, const __grid_constant__ CUtensorMap tm_cref,
                 const __grid_constant__ CUtensorMap tm_cdef, const __grid_constant__ CUtensorMap tm_gray) {
   using C = T;  // working precision of the per-point control arithmetic
+  constexpr bool LM = MODE == 2;
+  constexpr bool ANYCOST = MODE != 0;
   constexpr int D = Shape<NP>::D;
   constexpr int M2 = 2 * D;
   constexpr int NMOM = (M2 + 1) * (M2 + 2) / 2;
@@ -1265,7 +1276,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
     __syncthreads();
     if (warp == 0) {
       gather(NV_PRE);
-      finish_reference<C, NP, NMOM, M2>(st, s_out, N, lane, a.cost);
+      finish_reference<C, NP, NMOM, M2, ANYCOST>(st, s_out, N, lane, a.cost);
       if constexpr (LM) {
         // the undamped Hessian, kept for the damped inverses of every iteration
         for (int e = lane; e < NP * NP; e += 32) {
@@ -1366,7 +1377,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
           if constexpr (LM)
             ctl = lm_update<C, NP>(st, lms, s_out, N, static_cast<C>(r), thr2, lane, a.cost);
           else
-            ctl = gauss_newton_update<C, NP>(st, s_out, N, static_cast<C>(r), thr2, lane, a.cost);
+            ctl = gauss_newton_update<C, NP, ANYCOST>(st, s_out, N, static_cast<C>(r), thr2, lane, a.cost);
           if (lane == 0) {
             if (ctl == 5) {
               st.status = DIC_PT_OUT_OF_BOUNDS;
@@ -1540,56 +1551,81 @@ __global__ void finalize_points_kernel(PointArrays pa, int nparams, int nan_reje
 // Raises the kernel's dynamic shared-memory limit to the device's opt-in limit
 // less its static shared memory, once per instantiation (thread-safe); the
 // largest tile set (S = 61, FP64 coefficients, 8-byte gray) stays below it.
-template <typename T, int NP, int NT, bool LM>
+template <typename T, int NP, int NT, int MODE>
 cudaError_t configure_wave_smem() {
   static const cudaError_t result = []() {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa{};
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, wave_kernel<T, NP, NT, LM>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, wave_kernel<T, NP, NT, MODE>);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(wave_kernel<T, NP, NT, LM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(wave_kernel<T, NP, NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                optin - static_cast<int>(fa.sharedSizeBytes));
     return e;
   }();
   return result;
 }
 
-template <typename T, int NP, int NT, bool LM>
+template <typename T, int NP, int NT, int MODE>
 cudaError_t launch_wave_nt(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
   const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
-  const cudaError_t configured = configure_wave_smem<T, NP, NT, LM>();
+  const cudaError_t configured = configure_wave_smem<T, NP, NT, MODE>();
   if (configured != cudaSuccess) return configured;
-  wave_kernel<T, NP, NT, LM><<<grid, NT, smem, s>>>(a, maps[0], maps[1], maps[2]);
+  wave_kernel<T, NP, NT, MODE><<<grid, NT, smem, s>>>(a, maps[0], maps[1], maps[2]);
   return cudaGetLastError();
+}
+
+// kernel variant of the optimiser and cost: 0 Gauss-Newton with ZNSSD, 1 Gauss-Newton
+// with another cost, 2 Levenberg-Marquardt
+template <typename T>
+int wave_mode(const WaveArgs<T>& a) {
+  return a.lm ? 2 : (a.cost == DIC_COST_ZNSSD ? 0 : 1);
+}
+
+template <typename T, int NP, int MODE>
+cudaError_t launch_wave_mode(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
+  return a.threads == kWaveThreadsSmall ? launch_wave_nt<T, NP, kWaveThreadsSmall, MODE>(a, maps, grid, s)
+                                        : launch_wave_nt<T, NP, kWaveThreads, MODE>(a, maps, grid, s);
 }
 
 template <typename T, int NP>
 cudaError_t launch_wave_np(const WaveArgs<T>& a, const CUtensorMap* maps, int grid, cudaStream_t s) {
-  if (a.lm)
-    return a.threads == kWaveThreadsSmall ? launch_wave_nt<T, NP, kWaveThreadsSmall, true>(a, maps, grid, s)
-                                          : launch_wave_nt<T, NP, kWaveThreads, true>(a, maps, grid, s);
-  return a.threads == kWaveThreadsSmall ? launch_wave_nt<T, NP, kWaveThreadsSmall, false>(a, maps, grid, s)
-                                        : launch_wave_nt<T, NP, kWaveThreads, false>(a, maps, grid, s);
+  switch (wave_mode(a)) {
+    case 0:
+      return launch_wave_mode<T, NP, 0>(a, maps, grid, s);
+    case 1:
+      return launch_wave_mode<T, NP, 1>(a, maps, grid, s);
+    default:
+      return launch_wave_mode<T, NP, 2>(a, maps, grid, s);
+  }
 }
 
-template <typename T, int NP, int NT, bool LM>
+template <typename T, int NP, int NT, int MODE>
 int blocks_per_sm_nt(size_t smem) {
-  if (configure_wave_smem<T, NP, NT, LM>() != cudaSuccess) return 1;
+  if (configure_wave_smem<T, NP, NT, MODE>() != cudaSuccess) return 1;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<T, NP, NT, LM>, NT, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, wave_kernel<T, NP, NT, MODE>, NT, smem) != cudaSuccess)
     return 1;
   return nb > 0 ? nb : 1;
 }
 
+template <typename T, int NP, int MODE>
+int blocks_per_sm_mode(int threads, size_t smem) {
+  return threads == kWaveThreadsSmall ? blocks_per_sm_nt<T, NP, kWaveThreadsSmall, MODE>(smem)
+                                      : blocks_per_sm_nt<T, NP, kWaveThreads, MODE>(smem);
+}
+
 template <typename T, int NP>
-int blocks_per_sm_np(int threads, bool lm, size_t smem) {
-  if (lm)
-    return threads == kWaveThreadsSmall ? blocks_per_sm_nt<T, NP, kWaveThreadsSmall, true>(smem)
-                                        : blocks_per_sm_nt<T, NP, kWaveThreads, true>(smem);
-  return threads == kWaveThreadsSmall ? blocks_per_sm_nt<T, NP, kWaveThreadsSmall, false>(smem)
-                                      : blocks_per_sm_nt<T, NP, kWaveThreads, false>(smem);
+int blocks_per_sm_np(int threads, int mode, size_t smem) {
+  switch (mode) {
+    case 0:
+      return blocks_per_sm_mode<T, NP, 0>(threads, smem);
+    case 1:
+      return blocks_per_sm_mode<T, NP, 1>(threads, smem);
+    default:
+      return blocks_per_sm_mode<T, NP, 2>(threads, smem);
+  }
 }
 
 }  // namespace
@@ -1630,14 +1666,15 @@ cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensor
 }
 
 template <typename T>
-int wave_blocks_per_sm(int nparams, int threads, int lm, size_t smem) {
+int wave_blocks_per_sm(int nparams, int threads, int lm, int cost, size_t smem) {
+  const int mode = lm ? 2 : (cost == DIC_COST_ZNSSD ? 0 : 1);
   switch (nparams) {
     case 2:
-      return blocks_per_sm_np<T, 2>(threads, lm != 0, smem);
+      return blocks_per_sm_np<T, 2>(threads, mode, smem);
     case 6:
-      return blocks_per_sm_np<T, 6>(threads, lm != 0, smem);
+      return blocks_per_sm_np<T, 6>(threads, mode, smem);
     default:
-      return blocks_per_sm_np<T, 12>(threads, lm != 0, smem);
+      return blocks_per_sm_np<T, 12>(threads, mode, smem);
   }
 }
 
@@ -1684,7 +1721,7 @@ template cudaError_t launch_wave<float>(const WaveArgs<float>&, const WaveTiles&
                                         cudaStream_t);
 template cudaError_t launch_wave<double>(const WaveArgs<double>&, const WaveTiles&, const CUtensorMap*, int, int,
                                          cudaStream_t);
-template int wave_blocks_per_sm<float>(int, int, int, size_t);
-template int wave_blocks_per_sm<double>(int, int, int, size_t);
+template int wave_blocks_per_sm<float>(int, int, int, int, size_t);
+template int wave_blocks_per_sm<double>(int, int, int, int, size_t);
 
 }  // namespace dic

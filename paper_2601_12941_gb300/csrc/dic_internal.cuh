@@ -244,6 +244,6 @@ cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensor
                         int grid, cudaStream_t s);
 
 template <typename T>
-int wave_blocks_per_sm(int nparams, int threads, int lm, size_t smem);
+int wave_blocks_per_sm(int nparams, int threads, int lm, int cost, size_t smem);
 
 }  // namespace dic

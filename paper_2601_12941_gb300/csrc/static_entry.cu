@@ -288,7 +288,7 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   int dev = 0, sms = 0;
   SCUDA(cudaGetDevice(&dev), "cudaGetDevice");
   SCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
-  const int grid = sms * wave_blocks_per_sm<float>(nparams, a.threads, a.lm, static_cast<size_t>(a.tiles.smem_bytes));
+  const int grid = sms * wave_blocks_per_sm<float>(nparams, a.threads, a.lm, a.cost, static_cast<size_t>(a.tiles.smem_bytes));
   int32_t hc[kNumCounters];
   int64_t k = 0;
   const int64_t max_waves = npts + 2;
