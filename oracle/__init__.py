@@ -6,8 +6,8 @@ share no code: see ``dic_oracle`` for what is computed and which passage of the
 paper each step follows.
 """
 from .dic_oracle import *  # noqa: F401,F403
-from .dic_oracle import (AFFINE, DEFAULT_PARAMS, GAUSS_NEWTON, LEVENBERG_MARQUARDT, N_PARAMS, NSSD,  # noqa: F401
+from .dic_oracle import (AFFINE, BICUBIC, BSPLINE3, DEFAULT_PARAMS, GAUSS_NEWTON, LEVENBERG_MARQUARDT, N_PARAMS, NSSD,  # noqa: F401
                          QUADRATIC, RIGID, SSD, ZNSSD, Plane,
                          ReferenceSubset, bspline_coefficients, correlate, correlate_sequence, grid, icgn,
-                         interpolate, seed_search)
+                         interpolate, keys, seed_search)
 from . import strain_oracle  # noqa: F401

@@ -1,7 +1,7 @@
 """FP64 CPU oracle for local-subset 2D DIC: ZNSSD cost, rigid / affine / quadratic
-shape functions, cubic B-spline interpolation, inverse-compositional Gauss-Newton
-(IC-GN) per subset, integer ZNCC seed search and reliability-guided propagation
-in deterministic waves.
+shape functions, cubic B-spline (or Keys bicubic) interpolation,
+inverse-compositional Gauss-Newton (IC-GN) per subset, integer ZNCC seed search
+and reliability-guided propagation in deterministic waves.
 
 TEST INFRASTRUCTURE. This module is the plain, slow, obviously correct reference
 that the CUDA library is checked against. Only the tests, the smoke check and the
@@ -81,6 +81,15 @@ Readings taken where the paper is silent (all of them, in one place):
       applied (p_best o dp^-1), so the stopping rule, and the root, are those of
       Gauss-Newton. Otherwise the damped step solves (H + lambda diag(H)) dp =
       -b_best and the next trial is p_best o dp^-1. iters counts the trials.
+  R14 Bicubic interpolation (interp "bicubic"; Sec. 2.2 names the bicubic B-spline
+      as the default, the library's create call takes the interpolant as an
+      argument): Keys' cubic convolution kernel with a = -1/2,
+        K(s) = (a+2)|s|^3 - (a+3)|s|^2 + 1         on |s| <= 1,
+        K(s) = a|s|^3 - 5a|s|^2 + 8a|s| - 4a       on 1 < |s| < 2,  0 beyond,
+      applied to the gray levels themselves (no prefilter: K interpolates), with the
+      same support {-1, 0, 1, 2}, sampling bounds (R2) and mirror boundary (R1) as
+      the spline. grad f at a pixel is the derivative of that interpolant there,
+      which is the central difference (f[k+1] - f[k-1]) / 2.
 """
 from __future__ import annotations
 
@@ -97,8 +106,10 @@ OK, NOT_IN_ROI, NOT_REACHED, OUT_OF_BOUNDS, MAX_ITER, LOW_ZNCC, SINGULAR_H, FLAT
 ZNSSD, NSSD, SSD = "znssd", "nssd", "ssd"
 GAUSS_NEWTON, LEVENBERG_MARQUARDT = "gn", "lm"
 LM_LAMBDA0, LM_FACTOR = 1e-3, 10.0
+BSPLINE3, BICUBIC = "bspline3", "bicubic"
+KEYS_A = -0.5
 DEFAULT_PARAMS = dict(max_iter=40, conv_threshold=0.01, zncc_min=0.70, search_radius=8,
-                      nan_unconverged=False, cost=ZNSSD, optimizer=GAUSS_NEWTON)
+                      nan_unconverged=False, cost=ZNSSD, optimizer=GAUSS_NEWTON, interp=BSPLINE3)
 
 
 # --------------------------------------------------------------------------- R1
@@ -151,15 +162,40 @@ def beta3_prime(s):
     return np.sign(s) * d
 
 
-class Plane:
-    """Gray levels and spline coefficients of an image, or of a crop of it whose
-    top-left pixel is (x0, y0) in a width x height image. A crop's coefficients
-    carry the mirror boundary at its own edges; where a crop edge is not an image
-    edge, points must stay far from it (the influence decays as 0.268^distance)."""
+def keys(s, a=KEYS_A):
+    """Keys' cubic convolution kernel (reading R14)."""
+    s = np.abs(np.asarray(s, dtype=np.float64))
+    return np.where(s <= 1.0, (a + 2.0) * s ** 3 - (a + 3.0) * s * s + 1.0,
+                    np.where(s < 2.0, a * s ** 3 - 5.0 * a * s * s + 8.0 * a * s - 4.0 * a, 0.0))
 
-    def __init__(self, gray, x0=0, y0=0, width=None, height=None):
+
+def keys_prime(s, a=KEYS_A):
+    """Derivative of keys."""
+    s = np.asarray(s, dtype=np.float64)
+    m = np.abs(s)
+    d = np.where(m <= 1.0, 3.0 * (a + 2.0) * m * m - 2.0 * (a + 3.0) * m,
+                 np.where(m < 2.0, 3.0 * a * m * m - 10.0 * a * m + 8.0 * a, 0.0))
+    return np.sign(s) * d
+
+
+_KERNELS = {BSPLINE3: (beta3, beta3_prime), BICUBIC: (keys, keys_prime)}
+
+
+class Plane:
+    """Gray levels and interpolation coefficients of an image, or of a crop of it
+    whose top-left pixel is (x0, y0) in a width x height image. Spline coefficients
+    (R1) carry the mirror boundary at a crop's own edges; where a crop edge is not an
+    image edge, points must stay far from it (the influence decays as
+    0.268^distance). The bicubic interpolant (R14) uses the gray levels as its
+    coefficients."""
+
+    def __init__(self, gray, x0=0, y0=0, width=None, height=None, interp=BSPLINE3):
         self.gray = np.asarray(gray)
-        self.c = bspline_coefficients(self.gray)
+        if interp not in _KERNELS:
+            raise ValueError("unknown interpolant %r" % (interp,))
+        self.interp = interp
+        self.kernel, self.kernel_prime = _KERNELS[interp]
+        self.c = bspline_coefficients(self.gray) if interp == BSPLINE3 else self.gray.astype(np.float64)
         self.x0, self.y0 = int(x0), int(y0)
         self.h, self.w = self.gray.shape
         self.W = int(width) if width is not None else self.w
@@ -174,8 +210,9 @@ class CropMiss(RuntimeError):
 
 
 def interpolate(plane: Plane, x, y):
-    """Spline value at (x, y) (image coordinates) and the validity mask of reading R2.
-    value = sum over l, k in {-1, 0, 1, 2} of c[j+l, i+k] beta3(tx-k) beta3(ty-l)."""
+    """Interpolated value at (x, y) (image coordinates) and the validity mask of
+    reading R2. value = sum over l, k in {-1, 0, 1, 2} of c[j+l, i+k] K(tx-k) K(ty-l),
+    K = beta3 on spline coefficients (R1) or Keys' kernel on gray levels (R14)."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     valid = (x >= 1.0) & (x < plane.W - 2) & (y >= 1.0) & (y < plane.H - 2)
@@ -192,17 +229,18 @@ def interpolate(plane: Plane, x, y):
     li = np.clip(li, 1, plane.w - 3)
     lj = np.clip(lj, 1, plane.h - 3)
     out = np.zeros_like(x)
+    K = plane.kernel
     for l in range(-1, 3):
-        wy = beta3(ty - l)
+        wy = K(ty - l)
         for k in range(-1, 3):
-            out += plane.c[lj + l, li + k] * beta3(tx - k) * wy
+            out += plane.c[lj + l, li + k] * K(tx - k) * wy
     return out, valid
 
 
 def gradient_at_pixels(plane: Plane, xs, ys):
-    """Exact derivatives of the spline at integer pixels (reading R4):
-    fx = sum_{l,k} c[y+l, x+k] beta3'(-k) beta3(-l), fy likewise; coefficients
-    beyond the image border are mirrored (c[-1] = c[1], c[N] = c[N-2])."""
+    """Exact derivatives of the interpolant at integer pixels (readings R4, R14):
+    fx = sum_{l,k} c[y+l, x+k] K'(-k) K(-l), fy likewise; coefficients beyond the
+    image border are mirrored (c[-1] = c[1], c[N] = c[N-2])."""
     xs = np.asarray(xs, dtype=np.int64)
     ys = np.asarray(ys, dtype=np.int64)
 
@@ -219,8 +257,8 @@ def gradient_at_pixels(plane: Plane, xs, ys):
             if gx.min() < 0 or gy.min() < 0 or gx.max() >= plane.w or gy.max() >= plane.h:
                 raise CropMiss("gradient stencil outside the crop")
             cv = plane.c[gy, gx]
-            fx += cv * beta3_prime(-k) * beta3(-l)
-            fy += cv * beta3(-k) * beta3_prime(-l)
+            fx += cv * plane.kernel_prime(-k) * plane.kernel(-l)
+            fy += cv * plane.kernel(-k) * plane.kernel_prime(-l)
     return fx, fy
 
 
@@ -612,8 +650,8 @@ def _propagate(ref, deformed, roi, subset_size, subset_step, shape, params, prog
     nx, ny = len(xs), len(ys)
     npts = nx * ny
     inroi = roi_points(roi, W, H, subset_size, subset_step).ravel()
-    refp = Plane(ref)
-    defp = Plane(deformed)
+    refp = Plane(ref, interp=prm["interp"])
+    defp = Plane(deformed, interp=prm["interp"])
     P = np.zeros((npts, n))
     zncc = np.full(npts, np.nan)
     iters = np.zeros(npts, np.int32)
