@@ -9,7 +9,8 @@
  * map", unconverged points optionally NaN).
  *
  * Method (all of it runs in this library's CUDA kernels):
- *   - cubic B-spline interpolation of gray levels at sub-pixel positions (Sec. 2.2);
+ *   - cubic B-spline interpolation of gray levels at sub-pixel positions (Sec. 2.2),
+ *     or Keys' bicubic convolution (dic_interp);
  *   - the ZNSSD cost (Eq. 4) minimised per subset over the rigid, affine or
  *     quadratic shape function (Eq. 5) by inverse-compositional Gauss-Newton;
  *   - reliability-guided propagation to the four nearest neighbours (Sec. 2.4,
@@ -71,8 +72,15 @@ typedef enum { DIC_COST_ZNSSD = 0, DIC_COST_NSSD = 1, DIC_COST_SSD = 2 } dic_cos
  * not (the step is then retaken from the best warp so far). Both reach the same root. */
 typedef enum { DIC_OPT_GAUSS_NEWTON = 0, DIC_OPT_LEVENBERG_MARQUARDT = 1 } dic_optimizer;
 
-/* Sec. 2.2: interpolating cubic B-spline, mirror boundary. */
-typedef enum { DIC_BSPLINE3 = 0 } dic_interp;
+/* Interpolant of the gray levels at sub-pixel positions.
+ *   DIC_BSPLINE3: interpolating cubic B-spline, whole-sample mirror boundary
+ *                 (Sec. 2.2, the default); the coefficient planes come from a
+ *                 prefilter of each image.
+ *   DIC_BICUBIC:  Keys' bicubic convolution, kernel parameter a = -1/2, on the gray
+ *                 levels themselves (no prefilter), same 4 x 4 support, sampling
+ *                 bounds and mirror boundary; the reference gradient is the
+ *                 central difference (f[k+1] - f[k-1]) / 2. */
+typedef enum { DIC_BSPLINE3 = 0, DIC_BICUBIC = 1 } dic_interp;
 
 /* DIC_MIXED: gray levels kept in their input type, spline coefficients, samples
  * and sums in FP32, Hessian solve, parameter update and final ZNCC in FP64.
@@ -159,7 +167,7 @@ dic_params dic_default_params(void);
  *                  nonzero = inside; a point is used iff its whole S x S subset is.
  *   subset_size  : odd, 3 <= S <= 61 and S <= min(width, height).
  *   subset_step  : >= 1.
- *   shape_fn     : dic_shape. interp: DIC_BSPLINE3.
+ *   shape_fn     : dic_shape. interp: dic_interp (DIC_BSPLINE3 or DIC_BICUBIC).
  * Allocates every device buffer the correlation needs; host images are copied,
  * device images borrowed. No kernel runs until dic_correlate.
  * Errors: DIC_EINVAL, DIC_ENOMEM, DIC_ECUDA. On error *out is NULL. */
@@ -203,7 +211,8 @@ int dic_correlate_sequence(dic_handle* h, void* cuda_stream);
  * after dic_set_subsets. */
 int dic_get_results(dic_handle* h, dic_results* out, int32_t on_device);
 
-/* Device pointer to the spline coefficients of the reference (which = 0) or the
+/* Device pointer to the interpolation coefficients (spline coefficients, or the
+ * gray levels as T under DIC_BICUBIC) of the reference (which = 0) or the
  * deformed image (which = 1) as computed by the last dic_correlate: height rows of
  * *ld elements, each element *elem_bytes wide (4: FP32 under DIC_MIXED, 8: FP64).
  * Owned by the handle; for inspection and tests. DIC_ESTATE before any correlate. */
@@ -317,7 +326,8 @@ int dic_get_device_bytes(const dic_handle* h, int64_t* bytes);
  * Limits (larger problems return DIC_EINVAL and a message saying which):
  *   H * (W rounded up to 32) <= DIC_STATIC_MAX_PIXELS, grid points <=
  *   DIC_STATIC_MAX_POINTS, n_seeds <= DIC_STATIC_MAX_SEEDS, search_radius <=
- *   DIC_STATIC_MAX_RADIUS; precision must be DIC_MIXED; no ROI (every grid point).
+ *   DIC_STATIC_MAX_RADIUS; precision must be DIC_MIXED; no ROI (every grid point);
+ *   the interpolant is the cubic B-spline.
  * Shared state: all calls in the process use the same array and it keeps the
  * last call's contents (every call clears what must start from zero). Calls that
  * overlap on the GPU (other streams or host threads) race on it: serialise them.

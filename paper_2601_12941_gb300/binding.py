@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(HERE, "libdic.so")
 DIC_OK, DIC_EINVAL, DIC_ENOMEM, DIC_ECUDA, DIC_ETIMEOUT, DIC_ENOSEED, DIC_ESTATE = 0, -1, -2, -3, -4, -5, -6
 DIC_U8, DIC_U16, DIC_BF16, DIC_F32, DIC_F64 = range(5)
 DIC_RIGID, DIC_AFFINE, DIC_QUADRATIC = range(3)
-DIC_BSPLINE3 = 0
+DIC_BSPLINE3, DIC_BICUBIC = 0, 1
+INTERPS = {"bspline3": DIC_BSPLINE3, "bicubic": DIC_BICUBIC}
 DIC_FP64, DIC_MIXED = 0, 1
 DIC_COST_ZNSSD, DIC_COST_NSSD, DIC_COST_SSD = 0, 1, 2
 COSTS = {"znssd": DIC_COST_ZNSSD, "nssd": DIC_COST_NSSD, "ssd": DIC_COST_SSD}
@@ -420,10 +421,11 @@ class Correlation:
     """One reference/deformed pair on one handle (convenience over the calls above)."""
 
     def __init__(self, ref, deformed, roi=None, subset_size=21, subset_step=5, shape="affine",
-                 **param_kw):
+                 interp="bspline3", **param_kw):
         self.shape = SHAPES[shape] if isinstance(shape, str) else shape
         self.step = subset_step
-        self.h, self._keep = dic_create(ref, deformed, roi, subset_size, subset_step, self.shape)
+        interp = INTERPS[interp] if isinstance(interp, str) else interp
+        self.h, self._keep = dic_create(ref, deformed, roi, subset_size, subset_step, self.shape, interp)
         if param_kw:
             dic_set_params(self.h, params(**param_kw))
 

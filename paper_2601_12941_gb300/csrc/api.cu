@@ -81,6 +81,7 @@ void dev_free(void* p) {
 
 struct dic_handle {
   int W = 0, H = 0, S = 0, step = 0, r = 0, shape = 0, nparams = 0, nx = 0, ny = 0;
+  int interp = DIC_BSPLINE3;  // dic_interp of both coefficient planes
   int64_t npts = 0;
   dic_params prm{};
   int device = 0;
@@ -307,7 +308,11 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 template <typename T>
 int prefilter(dic_handle* h, const GrayPlane& src, void* dst, cudaStream_t s) {
   PrefilterArgs<T> a{src, h->W, h->H, static_cast<T*>(dst), h->ldc};
-  DIC_CUDA(launch_prefilter<T>(a, s), "prefilter launch");
+  if (h->interp == DIC_BICUBIC) {
+    DIC_CUDA(launch_gray_plane<T>(a, s), "gray plane launch");
+  } else {
+    DIC_CUDA(launch_prefilter<T>(a, s), "prefilter launch");
+  }
   return DIC_OK;
 }
 
@@ -362,13 +367,14 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   a.max_iter = h->prm.max_iter;
   a.cost = h->prm.cost;
   a.lm = h->prm.optimizer == DIC_OPT_LEVENBERG_MARQUARDT;
+  a.interp = h->interp;
   a.conv_threshold = h->prm.conv_threshold;
   a.zncc_min = h->prm.zncc_min;
 
   int sms = 0;
   DIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "device query");
   const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
-  const int per_sm = wave_blocks_per_sm<T>(h->nparams, a.threads, a.lm, a.cost, smem);
+  const int per_sm = wave_blocks_per_sm<T>(h->nparams, a.threads, wave_mode(a.lm, a.cost, a.interp), smem);
   const int grid = sms * per_sm;
 
   const bool prof = h->prm.profile != 0;
@@ -707,13 +713,14 @@ int dic_create(const dic_image* ref, const dic_image* def, const dic_image* roi,
     return fail(DIC_EINVAL, "reference %dx%d and deformed %dx%d differ in size", ref->width, ref->height,
                 def->width, def->height);
   if ((rc = check_subsets(ref->width, ref->height, roi, subset_size, subset_step, shape_fn))) return rc;
-  if (interp != DIC_BSPLINE3) return fail(DIC_EINVAL, "unknown interpolation %d", interp);
+  if (interp != DIC_BSPLINE3 && interp != DIC_BICUBIC) return fail(DIC_EINVAL, "unknown interpolation %d", interp);
   dic_handle* h = new (std::nothrow) dic_handle();
   if (!h) return fail(DIC_ENOMEM, "handle allocation");
   cudaGetDevice(&h->device);
   h->W = ref->width;
   h->H = ref->height;
   h->prm = dic_default_params();
+  h->interp = interp;
   if ((rc = bind_image(h, ref, &h->ref, &h->ref_owned, &h->ref_dtype)) ||
       (rc = bind_image(h, def, &h->def, &h->def_owned, &h->def_dtype)) ||
       (rc = configure_subsets(h, roi, subset_size, subset_step, shape_fn))) {

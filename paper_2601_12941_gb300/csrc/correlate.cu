@@ -3,12 +3,13 @@
 // Per point (Sec. 2.2, Eq. 4, Eq. 5; Sec. 2.4 for the propagation):
 //   1. starting warp: the seed's integer offset (wave 0), else the warp of the
 //      accepted 4-neighbour with the highest ZNCC, re-expanded about this centre;
-//   2. reference subset: f, f - f_m and the exact spline gradient of the
-//      reference at the S x S pixels, and the Gauss-Newton Hessian
+//   2. reference subset: f, f - f_m and the exact gradient of the reference
+//      interpolant (cubic B-spline, or bicubic convolution) at the S x S pixels,
+//      and the Gauss-Newton Hessian
 //      H = sum SD^T SD of the steepest-descent images SD = grad f . dxi/dp,
 //      assembled from gradient moments and factorised (Cholesky) in FP64;
-//   3. inverse-compositional Gauss-Newton: sample the deformed spline at the
-//      warped pixels, reduce sum g, sum g^2 and sum SD g, solve
+//   3. inverse-compositional Gauss-Newton: sample the deformed interpolant at
+//      the warped pixels, reduce sum g, sum g^2 and sum SD g, solve
 //      dp = -H^-1 sum SD (f - f_m - (df/dg)(g - g_m)) in FP64, update
 //      p <- p o dp^-1, stop when ||dp|| < threshold;
 //   4. ZNCC = sum (f - f_m)(g - g_m) / (df dg) at the final p; accept when
@@ -825,6 +826,32 @@ __device__ __forceinline__ void bspline_weights6_pair(Pair<T> t, Pair<T>& w0, Pa
   w2 = pfma(s2, pfma(pair(T(3), T(3)), s, pair(T(-6), T(-6))), pair(T(4), T(4)));
 }
 
+// Keys' cubic convolution weights (a = -1/2) of two offsets, times 2, in the layout
+// of bspline_weights6_pair: w0..w3 weigh the samples at -1, 0, 1, 2, so that the
+// interpolated value is the weighted sum over the 4 x 4 support divided by 4.
+//   2 K(1 + t) = -t s^2,  2 K(t) = t^2 (3t - 5) + 2,  2 K(s) = s^2 (3s - 5) + 2,
+//   2 K(1 + s) = -s t^2,  s = 1 - t
+template <typename T>
+__device__ __forceinline__ void keys_weights2_pair(Pair<T> t, Pair<T>& w0, Pair<T>& w1, Pair<T>& w2,
+                                                   Pair<T>& w3) {
+  const Pair<T> s = psub(pair(T(1), T(1)), t);
+  const Pair<T> t2 = pmul(t, t), s2 = pmul(s, s);
+  const Pair<T> m1 = pair(T(-1), T(-1));
+  w0 = pmul(pmul(s2, t), m1);
+  w3 = pmul(pmul(t2, s), m1);
+  w1 = pfma(t2, pfma(pair(T(3), T(3)), t, pair(T(-5), T(-5))), pair(T(2), T(2)));
+  w2 = pfma(s2, pfma(pair(T(3), T(3)), s, pair(T(-5), T(-5))), pair(T(2), T(2)));
+}
+template <typename T>
+__device__ __forceinline__ void keys_weights2(T t, T& w0, T& w1, T& w2, T& w3) {
+  const T s = T(1) - t;
+  const T t2 = t * t, s2 = s * s;
+  w0 = -(s2 * t);
+  w3 = -(t2 * s);
+  w1 = t2 * (T(3) * t - T(5)) + T(2);
+  w2 = s2 * (T(3) * s - T(5)) + T(2);
+}
+
 // Sums over one thread's column of subset pixels at the warp given by
 // (ax, bx, cxq; ay, by, cyq): x = ax + dy (bx + cxq dy), y = ay + dy (by + cyq dy)
 // relative to the centre. The support of a sample at (ix + tx, iy + ty) starts at
@@ -836,12 +863,15 @@ __device__ __forceinline__ void bspline_weights6_pair(Pair<T> t, Pair<T>& w0, Pa
 //              (FG: then sum f' g', which the Levenberg-Marquardt cost needs)
 // fin = true:  acc = [sum g', sum g'^2, sum f' g'] (the final pass; one copy of the
 // unrolled loop serves both, fin being the same for the whole block)
-template <typename T, int D, bool FG>
+// GEN: the interpolant is a runtime choice (keys: bicubic convolution on gray
+// levels; otherwise the B-spline), else the B-spline is compiled in.
+template <typename T, int D, bool FG, bool GEN>
 __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld, T ax, T bx, T cxq,
                                               T ay, T by, T cyq, T xlo, T xhi, T ylo, T yhi, T f0,
                                               int row0, int row1, int r, int S, int col,
                                               const unsigned char* gtile, int gpitch, int gdtype,
-                                              const Pair<T>* s_fg, bool fin, bool inside, T* acc, T& bad) {
+                                              const Pair<T>* s_fg, bool fin, bool inside, bool keys, T* acc,
+                                              T& bad) {
   T c0[4], c1[4], c2[4], c3[4];
   Pair<T> sd[D + 1];   // sum fx g' dy^j in .x, sum fy g' dy^j in .y
 #pragma unroll
@@ -874,14 +904,17 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
     pix_ix = ix;
     pix_iy = iy;
     Pair<T> w0, w1, w2, w3;
-    bspline_weights6_pair<T>(psub(xy, pair(xf, yf)), w0, w1, w2, w3);
+    if (GEN && keys)
+      keys_weights2_pair<T>(psub(xy, pair(xf, yf)), w0, w1, w2, w3);
+    else
+      bspline_weights6_pair<T>(psub(xy, pair(xf, yf)), w0, w1, w2, w3);
     const T wx0 = w0.x, wx1 = w1.x, wx2 = w2.x, wx3 = w3.x;
     const T wy0 = w0.y, wy1 = w1.y, wy2 = w2.y, wy3 = w3.y;
     const T r0 = wx0 * A[0] + wx1 * A[1] + wx2 * A[2] + wx3 * A[3];
     const T r1 = wx0 * B[0] + wx1 * B[1] + wx2 * B[2] + wx3 * B[3];
     const T r2 = wx0 * Cc[0] + wx1 * Cc[1] + wx2 * Cc[2] + wx3 * Cc[3];
     const T r3 = wx0 * Dn[0] + wx1 * Dn[1] + wx2 * Dn[2] + wx3 * Dn[3];
-    const T gp = (wy0 * r0 + wy1 * r1 + wy2 * r2 + wy3 * r3) * (T(1) / T(36)) - f0;
+    const T gp = (wy0 * r0 + wy1 * r1 + wy2 * r2 + wy3 * r3) * (GEN && keys ? T(0.25) : T(1) / T(36)) - f0;
     acc[0] += gp;
     acc[1] += gp * gp;
     if (fin) {
@@ -922,7 +955,7 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
                                                      T ylo, T yhi, T f0, int row0, int row1, int r,
                                                      int S, int col, const unsigned char* gtile,
                                                      int gpitch, int gdtype, const Pair<T>* s_fg, bool fin,
-                                                     T* acc, T& bad) {
+                                                     bool keys, T* acc, T& bad) {
   for (int row = row0; row < row1; ++row) {
     const T dyv = static_cast<T>(row - r);
     const T xl = ax + dyv * (bx + cxq * dyv);
@@ -934,8 +967,13 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
     const T xf = floor(xl), yf = floor(yl);
     const T* b = base + (static_cast<int64_t>(yf) * ld + static_cast<int64_t>(xf));
     T wx0, wx1, wx2, wx3, wy0, wy1, wy2, wy3;
-    bspline_weights6<T>(xl - xf, wx0, wx1, wx2, wx3);
-    bspline_weights6<T>(yl - yf, wy0, wy1, wy2, wy3);
+    if (keys) {
+      keys_weights2<T>(xl - xf, wx0, wx1, wx2, wx3);
+      keys_weights2<T>(yl - yf, wy0, wy1, wy2, wy3);
+    } else {
+      bspline_weights6<T>(xl - xf, wx0, wx1, wx2, wx3);
+      bspline_weights6<T>(yl - yf, wy0, wy1, wy2, wy3);
+    }
     T g = T(0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -943,7 +981,7 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
       const T wy = j == 0 ? wy0 : j == 1 ? wy1 : j == 2 ? wy2 : wy3;
       g += wy * (wx0 * rj[0] + wx1 * rj[1] + wx2 * rj[2] + wx3 * rj[3]);
     }
-    const T gp = g * (T(1) / T(36)) - f0;
+    const T gp = g * (keys ? T(0.25) : T(1) / T(36)) - f0;
     acc[0] += gp;
     acc[1] += gp * gp;
     if (fin) {
@@ -984,6 +1022,8 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
   using C = T;  // working precision of the per-point control arithmetic
   constexpr bool LM = MODE == 2;
   constexpr bool ANYCOST = MODE != 0;
+  constexpr bool GEN = MODE != 0;                    // the interpolant is a runtime choice
+  const bool keys = GEN && a.interp == DIC_BICUBIC;
   constexpr int D = Shape<NP>::D;
   constexpr int M2 = 2 * D;
   constexpr int NMOM = (M2 + 1) * (M2 + 2) / 2;
@@ -1212,8 +1252,15 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
         // (-1/2, 0, 1/2) along one axis times (1, 4, 1)/6 along the other
         const T* cp = wref + (row + 2) * tl.bxc + col;
         const T p0 = cp[0], p1 = cp[1], p2 = cp[2];
-        const T fx = ((m2 - m0) + T(4) * (z2 - z0) + (p2 - p0)) * (T(1) / T(12));
-        const T fy = ((p0 - m0) + T(4) * (p1 - m1) + (p2 - m2)) * (T(1) / T(12));
+        // (bicubic convolution: the central difference (f[k+1] - f[k-1]) / 2)
+        T fx, fy;
+        if (GEN && keys) {
+          fx = (z2 - z0) * T(0.5);
+          fy = (p1 - m1) * T(0.5);
+        } else {
+          fx = ((m2 - m0) + T(4) * (z2 - z0) + (p2 - p0)) * (T(1) / T(12));
+          fy = ((p0 - m0) + T(4) * (p1 - m1) + (p2 - m2)) * (T(1) / T(12));
+        }
         m0 = z0;
         m1 = z1;
         m2 = z2;
@@ -1346,12 +1393,12 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
       T bad = T(0);
       if (stage != 2) {
         const T* base = s_win + (yc - 1 - w.y0) * w.w + (xc - 1 - w.x0);
-        sample_column<T, D, LM>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r, S,
-                                col, gtile, gpitch, gdt, s_fg, final_pass, st.inside != 0, acc, bad);
+        sample_column<T, D, LM, GEN>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r,
+                                     S, col, gtile, gpitch, gdt, s_fg, final_pass, st.inside != 0, keys, acc, bad);
       } else {
         const T* base = a.c_def + static_cast<int64_t>(yc - 1) * a.ldc + (xc - 1);
         sample_column_global<T, D, LM>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1,
-                                       r, S, col, gtile, gpitch, gdt, s_fg, final_pass, acc, bad);
+                                       r, S, col, gtile, gpitch, gdt, s_fg, final_pass, GEN && keys, acc, bad);
       }
       if (!final_pass) {
         T v[pow2ceil(NV_IT)];
@@ -1580,7 +1627,7 @@ cudaError_t launch_wave_nt(const WaveArgs<T>& a, const CUtensorMap* maps, int gr
 // with another cost, 2 Levenberg-Marquardt
 template <typename T>
 int wave_mode(const WaveArgs<T>& a) {
-  return a.lm ? 2 : (a.cost == DIC_COST_ZNSSD ? 0 : 1);
+  return dic::wave_mode(a.lm, a.cost, a.interp);
 }
 
 template <typename T, int NP, int MODE>
@@ -1666,8 +1713,7 @@ cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensor
 }
 
 template <typename T>
-int wave_blocks_per_sm(int nparams, int threads, int lm, int cost, size_t smem) {
-  const int mode = lm ? 2 : (cost == DIC_COST_ZNSSD ? 0 : 1);
+int wave_blocks_per_sm(int nparams, int threads, int mode, size_t smem) {
   switch (nparams) {
     case 2:
       return blocks_per_sm_np<T, 2>(threads, mode, smem);
@@ -1721,7 +1767,7 @@ template cudaError_t launch_wave<float>(const WaveArgs<float>&, const WaveTiles&
                                         cudaStream_t);
 template cudaError_t launch_wave<double>(const WaveArgs<double>&, const WaveTiles&, const CUtensorMap*, int, int,
                                          cudaStream_t);
-template int wave_blocks_per_sm<float>(int, int, int, int, size_t);
-template int wave_blocks_per_sm<double>(int, int, int, int, size_t);
+template int wave_blocks_per_sm<float>(int, int, int, size_t);
+template int wave_blocks_per_sm<double>(int, int, int, size_t);
 
 }  // namespace dic

@@ -99,6 +99,10 @@ struct PrefilterArgs {
 // Interpolating cubic B-spline coefficients of a whole image (mirror boundary).
 template <typename T>
 cudaError_t launch_prefilter(const PrefilterArgs<T>& a, cudaStream_t s);
+// The gray levels themselves as the coefficient plane (the bicubic convolution
+// interpolant needs no prefilter).
+template <typename T>
+cudaError_t launch_gray_plane(const PrefilterArgs<T>& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- seeds
 struct SeedArgs {
@@ -198,6 +202,7 @@ struct WaveArgs {
   int max_iter;
   int cost;                  // dic_cost
   int lm;                    // 1: Levenberg-Marquardt (dic_optimizer)
+  int interp;                // dic_interp of the coefficient planes
   double conv_threshold;
   double zncc_min;
 };
@@ -244,6 +249,12 @@ cudaError_t launch_wave(const WaveArgs<T>& a, const WaveTiles& t, const CUtensor
                         int grid, cudaStream_t s);
 
 template <typename T>
-int wave_blocks_per_sm(int nparams, int threads, int lm, int cost, size_t smem);
+int wave_blocks_per_sm(int nparams, int threads, int mode, size_t smem);
+
+// Kernel variant: 0 Gauss-Newton with ZNSSD on the B-spline (the default, leanest
+// instantiation); 1 Gauss-Newton with any cost or interpolant; 2 Levenberg-Marquardt.
+inline int wave_mode(int lm, int cost, int interp) {
+  return lm ? 2 : (cost == DIC_COST_ZNSSD && interp == DIC_BSPLINE3 ? 0 : 1);
+}
 
 }  // namespace dic

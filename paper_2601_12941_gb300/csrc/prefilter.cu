@@ -1,4 +1,5 @@
-// Cubic B-spline prefilter (Sec. 2.2: "bicubic b-spline" interpolation set-up).
+// Cubic B-spline prefilter (Sec. 2.2: bicubic B-spline interpolation set-up), and
+// the plain gray-level plane of the bicubic convolution interpolant.
 //
 // The interpolating coefficients c of a line I satisfy (c[k-1] + 4 c[k] + c[k+1]) / 6
 // = I[k] with the whole-sample mirror boundary. On the mirror-extended line this is
@@ -115,7 +116,34 @@ __global__ void __launch_bounds__(kThreads) prefilter_kernel(PrefilterArgs<T> a,
   }
 }
 
+// Bicubic convolution (Keys, a = -1/2) interpolates the gray levels directly: the
+// coefficient plane is the image converted to T, row by row, coalesced.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) gray_plane_kernel(PrefilterArgs<T> a) {
+  const int64_t n = static_cast<int64_t>(a.W) * a.H;
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * kThreads) {
+    const int y = static_cast<int>(e / a.W), x = static_cast<int>(e % a.W);
+    a.coef[static_cast<int64_t>(y) * a.ldc + x] = load_gray<T>(a.src, x, y);
+  }
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_gray_plane(const PrefilterArgs<T>& a, cudaStream_t s) {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = (static_cast<int64_t>(a.W) * a.H + kThreads - 1) / kThreads;
+  const int64_t cap = static_cast<int64_t>(sms > 0 ? sms : 1) * 8;
+  const unsigned blocks = static_cast<unsigned>(need < cap ? (need > 0 ? need : 1) : cap);
+  gray_plane_kernel<T><<<blocks, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gray_plane<float>(const PrefilterArgs<float>&, cudaStream_t);
+template cudaError_t launch_gray_plane<double>(const PrefilterArgs<double>&, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_prefilter(const PrefilterArgs<T>& a, cudaStream_t s) {

@@ -283,12 +283,14 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   a.max_iter = params->max_iter;
   a.cost = params->cost;
   a.lm = params->optimizer == DIC_OPT_LEVENBERG_MARQUARDT;
+  a.interp = DIC_BSPLINE3;
   a.conv_threshold = params->conv_threshold;
   a.zncc_min = params->zncc_min;
   int dev = 0, sms = 0;
   SCUDA(cudaGetDevice(&dev), "cudaGetDevice");
   SCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
-  const int grid = sms * wave_blocks_per_sm<float>(nparams, a.threads, a.lm, a.cost, static_cast<size_t>(a.tiles.smem_bytes));
+  const int grid = sms * wave_blocks_per_sm<float>(nparams, a.threads, wave_mode(a.lm, a.cost, a.interp),
+                                                    static_cast<size_t>(a.tiles.smem_bytes));
   int32_t hc[kNumCounters];
   int64_t k = 0;
   const int64_t max_waves = npts + 2;

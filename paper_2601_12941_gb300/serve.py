@@ -46,6 +46,7 @@ class Job:
     subset_size: int = 21
     subset_step: int = 5
     shape: str = "affine"
+    interp: str = "bspline3"
     roi: Any = None
     params: dict = field(default_factory=dict)
     ref_key: Hashable = None
@@ -126,11 +127,13 @@ class LibdicEngine:
         if job.ref_key is None:
             return None
         h, w = job.ref.shape
+        # the resident reference plane depends on the interpolant and the precision
         return (job.ref_key, w, h, B.image_dtype_code(job.ref), self._on_device(job.ref),
-                self._params(job).precision)
+                self._params(job).precision, job.interp)
 
     def open(self, job):
-        h, keep = B.dic_create(job.ref, job.deformed, job.roi, job.subset_size, job.subset_step, self._shape(job))
+        h, keep = B.dic_create(job.ref, job.deformed, job.roi, job.subset_size, job.subset_step, self._shape(job),
+                               B.INTERPS[job.interp])
         # a borrowed reference must outlive the handle
         return {"h": h, "ref": keep[0] if self._on_device(job.ref) else None}
 

@@ -66,6 +66,9 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
     assert lib.dic_create(ctypes.byref(ri), ctypes.byref(small), None, 21, 5, 1, 0, ctypes.byref(h)) == B.DIC_EINVAL
     assert lib.dic_create(None, ctypes.byref(ri), None, 21, 5, 1, 0, ctypes.byref(h)) == B.DIC_EINVAL
     assert lib.dic_create(ctypes.byref(ri), ctypes.byref(ri), None, 63, 5, 1, 0, ctypes.byref(h)) == B.DIC_EINVAL
+    # unknown interpolant (DIC_BSPLINE3 = 0 and DIC_BICUBIC = 1 exist)
+    assert lib.dic_create(ctypes.byref(ri), ctypes.byref(ri), None, 21, 5, 1, 2, ctypes.byref(h)) == B.DIC_EINVAL
+    assert b"interpolation" in lib.dic_last_error()
     assert h.value is None
     # parameter validation on a NULL handle
     p = B.dic_default_params()
