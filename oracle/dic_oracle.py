@@ -90,6 +90,9 @@ Readings taken where the paper is silent (all of them, in one place):
       same support {-1, 0, 1, 2}, sampling bounds (R2) and mirror boundary (R1) as
       the spline. grad f at a pixel is the derivative of that interpolant there,
       which is the central difference (f[k+1] - f[k-1]) / 2.
+  R15 Seeds from the multi-window FFT initialiser (init "fft"; Sec. 2.2): the
+      seeds start from its estimate instead of the integer search of R9, as stated
+      in reading F8 of fft_oracle, which holds the initialiser's own readings.
 """
 from __future__ import annotations
 
@@ -109,7 +112,8 @@ LM_LAMBDA0, LM_FACTOR = 1e-3, 10.0
 BSPLINE3, BICUBIC = "bspline3", "bicubic"
 KEYS_A = -0.5
 DEFAULT_PARAMS = dict(max_iter=40, conv_threshold=0.01, zncc_min=0.70, search_radius=8,
-                      nan_unconverged=False, cost=ZNSSD, optimizer=GAUSS_NEWTON, interp=BSPLINE3)
+                      nan_unconverged=False, cost=ZNSSD, optimizer=GAUSS_NEWTON, interp=BSPLINE3,
+                      init="search", max_displacement=32, mad_tau=3.0, mad_eps=0.5)
 
 
 # --------------------------------------------------------------------------- R1
@@ -661,6 +665,14 @@ def _propagate(ref, deformed, roi, subset_size, subset_step, shape, params, prog
     px = np.tile(xs, ny)
     py = np.repeat(ys, nx)
 
+    fft_field = None
+    if seeds is not None and prm["init"] == "fft":
+        # reading F8 of the FFT initialiser's oracle: the seeds start from its estimate
+        from .fft_oracle import multiwindow, round_half_up
+        fft_field = multiwindow(ref, deformed, roi, subset_size, subset_step, int(prm["max_displacement"]),
+                                False, prm["mad_tau"], prm["mad_eps"])
+    elif prm["init"] not in ("search", "fft"):
+        raise ValueError("unknown init %r" % (prm["init"],))
     current = []
     if seeds is not None:
         for (sx, sy) in seeds:
@@ -678,7 +690,11 @@ def _propagate(ref, deformed, roi, subset_size, subset_step, shape, params, prog
     while current:
         for q in current:
             xc, yc = int(px[q]), int(py[q])
-            if k == 0 and seeds is not None:
+            if k == 0 and fft_field is not None:
+                p0 = np.zeros(n)
+                p0[0] = round_half_up(fft_field["u"][q])
+                p0[1] = round_half_up(fft_field["v"][q])
+            elif k == 0 and seeds is not None:
                 found = seed_search(ref, deformed, xc, yc, subset_size, int(prm["search_radius"]))
                 if found is None:
                     status[q] = OUT_OF_BOUNDS
