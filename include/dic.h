@@ -82,6 +82,14 @@ typedef enum { DIC_OPT_GAUSS_NEWTON = 0, DIC_OPT_LEVENBERG_MARQUARDT = 1 } dic_o
  *                 central difference (f[k+1] - f[k-1]) / 2. */
 typedef enum { DIC_BSPLINE3 = 0, DIC_BICUBIC = 1 } dic_interp;
 
+/* How the seeds of dic_correlate start (Sec. 2.2):
+ *   DIC_INIT_SEARCH: the integer ZNCC search over |du|, |dv| <= search_radius;
+ *   DIC_INIT_FFT:    the multi-window FFT initialiser (dic_fft_field, without the
+ *                    sub-pixel fit) runs first and every seed starts from its
+ *                    estimate at the seed's grid point, rounded to the nearest
+ *                    integer, halves up (the paper's default MULTIWINDOW_RG). */
+typedef enum { DIC_INIT_SEARCH = 0, DIC_INIT_FFT = 1 } dic_init;
+
 /* DIC_MIXED: gray levels kept in their input type, spline coefficients, samples
  * and sums in FP32, Hessian solve, parameter update and final ZNCC in FP64.
  * DIC_FP64: FP64 everywhere. */
@@ -118,7 +126,12 @@ typedef struct {
   int32_t profile;           /* 1: record CUDA-event stage timings (dic_get_timing) */
   int32_t cost;              /* dic_cost (default DIC_COST_ZNSSD)                    */
   int32_t optimizer;         /* dic_optimizer (default DIC_OPT_GAUSS_NEWTON)         */
+  int32_t init;              /* dic_init: how seeds start (default DIC_INIT_SEARCH)  */
+  int32_t max_displacement;  /* DIC_INIT_FFT: expected largest |u|, |v| in px,       */
+                             /* 0 <= D <= 4095 (default 32); see dic_fft_params      */
   int32_t reserved;          /* 0                                                    */
+  double mad_tau;            /* DIC_INIT_FFT: outlier cut (default 3; <= 0: off)     */
+  double mad_eps;            /* DIC_INIT_FFT: px added to the scaled MAD (0.5)       */
 } dic_params;
 /* ||dp|| = sqrt(dp0^2 + dp1^2 + r^2 (dp2^2+..+dp5^2) + r^4 (dp6^2+..+dp11^2)),
  * r = (subset_size - 1) / 2; a subset has converged once ||dp|| < conv_threshold. */
@@ -310,6 +323,76 @@ int dic_estimate_regrid_bytes(const dic_handle* h, const dic_image* def, int32_t
 
 /* Device bytes the handle holds now: the requested sizes of its live allocations. */
 int dic_get_device_bytes(const dic_handle* h, int64_t* bytes);
+
+/* ---- multi-window FFT initialiser (Sec. 2.2, Eq. 1; Sec. 4) ---------------- */
+/* Rigid displacement estimates by normalised FFT cross-correlation of square
+ * windows that halve from above the expected maximum displacement down to the
+ * subset size (window sizes: the powers of two above D, largest first, that exceed
+ * the subset size S and fit in the image, then S). A power-of-two level tiles the
+ * image (window (i, j) covers [iL, iL + L) x [jL, jL + L)); the last level's windows
+ * are the S x S subsets of the correlation grid. Each window's deformed window is
+ * moved by the previous level's estimate, interpolated bilinearly between the four
+ * nearest window centres and rounded (halves up), and clamped into the image.
+ * Eq. 1 is computed as the zero-normalised circular cross-correlation
+ *   R(s) = sum_x (f(x) - f_m)(g(x - s) - g_m) / (||f - f_m|| ||g - g_m||)
+ * through one packed complex 2-D transform per window; its largest value (ties to
+ * the lower row-major index (s_y, s_x)) gives the shift d = -s wrapped into
+ * [-floor(L/2), ceil(L/2) - 1], and the window's displacement is the deformed
+ * window's offset plus d. After every level each value whose u or v differs from
+ * the median over its 3 x 3 neighbourhood of windows (itself included) by more than
+ * tau (1.4826 MAD + eps) takes the neighbourhood medians. A window with a constant
+ * f or g gives d = 0 and peak 0. Sub-pixel (last level, optional): per axis the
+ * vertex of the Gaussian through the peak and its two circular neighbours, kept at
+ * 0 unless all three are positive. FP32 transforms, FP64 guesses and MAD tests. */
+typedef struct {
+  int32_t max_displacement;  /* D, px, 0 <= D <= 4095 (default 32)                   */
+  int32_t subpixel;          /* 1: Gaussian peak fit on the last level (default 1)   */
+  double mad_tau;            /* outlier cut (default 3); <= 0 switches it off        */
+  double mad_eps;            /* px added to the scaled MAD (default 0.5)             */
+} dic_fft_params;
+
+typedef struct {
+  int64_t n_points;          /* grid points, as in dic_results                       */
+  int32_t nx, ny;
+  int32_t n_levels;          /* window sizes used, coarse to fine; the last is S     */
+  int32_t window[16];
+  const float* u;            /* [n_points] last-level displacement, px (device)      */
+  const float* v;
+  const float* peak;         /* [n_points] R at the integer peak (Eq. 1)             */
+  const uint8_t* status;     /* [n_points] DIC_PT_OK, or DIC_PT_NOT_IN_ROI           */
+  const uint8_t* replaced;   /* [n_points] 1 where the MAD rule replaced the value   */
+} dic_fft_results;
+
+/* Sec. 2.2 defaults of this library: D = 32, sub-pixel fit on, tau = 3, eps = 0.5. */
+dic_fft_params dic_fft_default_params(void);
+
+/* Runs the whole initialiser (the paper's MULTIWINDOW method) on the handle's
+ * reference and deformed images over its subset grid and ROI. Allocates, on first
+ * use, a work buffer of up to 8 bytes per image pixel for windows above 64 px and
+ * per-window arrays (kept until dic_destroy). Errors: DIC_EINVAL (D outside
+ * [0, 4095], or no handle), DIC_ESTATE (no grid), DIC_ENOMEM, DIC_ECUDA. */
+int dic_fft_field(dic_handle* h, const dic_fft_params* fp, void* cuda_stream);
+
+/* Device arrays of the last dic_fft_field (or of the initialiser run by a
+ * dic_correlate with DIC_INIT_FFT), owned by the handle. DIC_ESTATE before any. */
+int dic_get_fft_results(const dic_handle* h, dic_fft_results* out);
+
+/* Eq. 1 over explicit windows of side `window` (odd 3..63, or a power of two
+ * 4..4096) on the handle's images: origins is a device array of n_windows
+ * (x0, y0, gx0, gy0) int32 quadruples, reference and deformed window origins (each
+ * window inside its image; x0 < 0 marks a window to skip, which gets 0s). Writes
+ * device arrays u, v (the deformed offset plus the shift, sub-pixel when subpixel
+ * = 1, which needs window <= 64) and peak. Errors: DIC_EINVAL, DIC_ENOMEM,
+ * DIC_ECUDA. */
+int dic_fftcc_windows(dic_handle* h, int32_t window, int64_t n_windows, const int32_t* origins,
+                      int32_t subpixel, float* u, float* v, float* peak, void* cuda_stream);
+
+/* The MAD rule above over an nx x ny field of device arrays u, v (valid: NULL, or
+ * nonzero for the values that take part and get tested); writes u_out, v_out and,
+ * when non-NULL, replaced. In-place calls (u_out == u) are not allowed. Errors:
+ * DIC_EINVAL. */
+int dic_mad_filter(const float* u, const float* v, const uint8_t* valid, int32_t nx, int32_t ny, double tau,
+                   double eps, float* u_out, float* v_out, uint8_t* replaced, void* cuda_stream);
 
 /* ---- allocation-free correlation (the paper has no counterpart) ----------
  *

@@ -28,8 +28,8 @@ Readings taken where the paper is silent (all of them, in one place):
      norms of the transforms of the mean-removed windows, so that R is the
      zero-normalised circular cross-correlation
         R(s) = IDFT( F conj(G) )(s) / (||f - f_m|| ||g - g_m||),
-     F and G the L x L DFTs with the zero-frequency term removed, the inverse
-     carrying 1/L^2 (by Parseval the denominator is ||F|| ||G|| / L^2). R is 1 at the
+     F and G the L x L DFTs of the mean-removed windows, the inverse carrying 1/L^2
+     (by Parseval the denominator is ||F|| ||G|| / L^2). R is 1 at the
      shift of a circularly shifted copy, and unchanged by gain and offset of either
      window; a flat window gives R = 0. (Dividing each frequency by its own |F| |G|,
      phase correlation, fails on smooth speckle inside hard-edged windows: the
@@ -85,15 +85,15 @@ def window_sizes(max_displacement: int, subset_size: int, width: int, height: in
 def fftcc(f: np.ndarray, g: np.ndarray) -> np.ndarray:
     """Eq. 1 as reading F4 takes it: the zero-normalised circular cross-correlation
     of two L x L windows, computed through their DFTs."""
-    f = np.asarray(f, dtype=np.float64)
-    g = np.asarray(g, dtype=np.float64)
-    F = np.fft.fft2(f)
-    G = np.fft.fft2(g)
-    F[0, 0] = 0.0                              # mean removal
-    G[0, 0] = 0.0
-    den = np.sqrt(np.sum(np.abs(F) ** 2)) * np.sqrt(np.sum(np.abs(G) ** 2)) / f.size
+    fb = np.asarray(f, dtype=np.float64)
+    gb = np.asarray(g, dtype=np.float64)
+    fb = fb - fb.mean()                        # exactly 0 where a window is constant
+    gb = gb - gb.mean()
+    den = math.sqrt(np.sum(fb * fb)) * math.sqrt(np.sum(gb * gb))
     if den == 0:
-        return np.zeros(f.shape)
+        return np.zeros(fb.shape)              # a flat window: R = 0
+    F = np.fft.fft2(fb)
+    G = np.fft.fft2(gb)
     return np.real(np.fft.ifft2(F * np.conj(G))) / den
 
 

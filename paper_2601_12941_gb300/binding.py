@@ -22,6 +22,8 @@ DIC_COST_ZNSSD, DIC_COST_NSSD, DIC_COST_SSD = 0, 1, 2
 COSTS = {"znssd": DIC_COST_ZNSSD, "nssd": DIC_COST_NSSD, "ssd": DIC_COST_SSD}
 DIC_OPT_GAUSS_NEWTON, DIC_OPT_LEVENBERG_MARQUARDT = 0, 1
 OPTIMIZERS = {"gn": DIC_OPT_GAUSS_NEWTON, "lm": DIC_OPT_LEVENBERG_MARQUARDT}
+DIC_INIT_SEARCH, DIC_INIT_FFT = 0, 1
+INITS = {"search": DIC_INIT_SEARCH, "fft": DIC_INIT_FFT}
 (PT_OK, PT_NOT_IN_ROI, PT_NOT_REACHED, PT_OUT_OF_BOUNDS, PT_MAX_ITER, PT_LOW_ZNCC, PT_SINGULAR,
  PT_FLAT) = range(8)
 SHAPES = {"rigid": DIC_RIGID, "affine": DIC_AFFINE, "quadratic": DIC_QUADRATIC}
@@ -39,7 +41,8 @@ EXPORTS = ("dic_default_params", "dic_create", "dic_set_params", "dic_get_params
            "dic_get_coefficients", "dic_get_timing", "dic_destroy", "dic_last_error",
            "dic_correlate_static", "dic_correlate_sequence", "dic_set_subsets",
            "dic_estimate_device_bytes", "dic_estimate_regrid_bytes", "dic_get_device_bytes",
-           "dic_strain_field")
+           "dic_strain_field", "dic_fft_default_params", "dic_fft_field", "dic_get_fft_results",
+           "dic_fftcc_windows", "dic_mad_filter")
 
 
 class DicImage(ctypes.Structure):
@@ -53,7 +56,21 @@ class DicParams(ctypes.Structure):
                 ("conv_threshold", ctypes.c_double), ("zncc_min", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("nan_unconverged", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("cost", ctypes.c_int32),
-                ("optimizer", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("optimizer", ctypes.c_int32), ("init", ctypes.c_int32),
+                ("max_displacement", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mad_tau", ctypes.c_double), ("mad_eps", ctypes.c_double)]
+
+
+class DicFftParams(ctypes.Structure):
+    _fields_ = [("max_displacement", ctypes.c_int32), ("subpixel", ctypes.c_int32),
+                ("mad_tau", ctypes.c_double), ("mad_eps", ctypes.c_double)]
+
+
+class DicFftResults(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("window", ctypes.c_int32 * 16),
+                ("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("peak", ctypes.c_void_p),
+                ("status", ctypes.c_void_p), ("replaced", ctypes.c_void_p)]
 
 
 class DicResults(ctypes.Structure):
@@ -148,6 +165,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.c_int32, ctypes.c_int32, P(DicStrainOutputs), vp]
     lib.dic_strain_field.restype = ctypes.c_int
     lib.dic_get_device_bytes.argtypes = [vp, P(ctypes.c_int64)]
+    lib.dic_fft_default_params.argtypes = []
+    lib.dic_fft_default_params.restype = DicFftParams
+    lib.dic_fft_field.argtypes = [vp, P(DicFftParams), vp]
+    lib.dic_fft_field.restype = ctypes.c_int
+    lib.dic_get_fft_results.argtypes = [vp, P(DicFftResults)]
+    lib.dic_get_fft_results.restype = ctypes.c_int
+    lib.dic_fftcc_windows.argtypes = [vp, ctypes.c_int32, ctypes.c_int64, vp, ctypes.c_int32, vp, vp, vp, vp]
+    lib.dic_fftcc_windows.restype = ctypes.c_int
+    lib.dic_mad_filter.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                   vp, vp, vp, vp]
+    lib.dic_mad_filter.restype = ctypes.c_int
     lib.dic_get_device_bytes.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -387,6 +415,56 @@ def dic_strain_field(u, v, status, nx, ny, subset_step, window, basis, measure, 
                                    ctypes.byref(o), ctypes.c_void_p(stream_ptr)))
 
 
+def dic_fft_default_params() -> DicFftParams:
+    return load().dic_fft_default_params()
+
+
+def fft_params(**kw) -> DicFftParams:
+    p = dic_fft_default_params()
+    for k, v in kw.items():
+        if k not in {name for name, _ in DicFftParams._fields_}:
+            raise TypeError("unknown FFT parameter %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def dic_fft_field(h, fp: DicFftParams, stream_ptr: int = 0):
+    """The multi-window FFT initialiser over the handle's grid (Sec. 2.2)."""
+    _check(load().dic_fft_field(h, ctypes.byref(fp), ctypes.c_void_p(stream_ptr)))
+
+
+def dic_get_fft_results(h) -> dict:
+    """Zero-copy CUDA tensors of the last initialiser run: u, v, peak (float32),
+    status, replaced (uint8); plus nx, ny and the window sizes of its levels."""
+    import torch
+
+    r = DicFftResults()
+    _check(load().dic_get_fft_results(h, ctypes.byref(r)))
+    n = r.n_points
+    out = dict(n_points=n, nx=r.nx, ny=r.ny, windows=[r.window[i] for i in range(r.n_levels)])
+    for name, dt in (("u", np.float32), ("v", np.float32), ("peak", np.float32), ("status", np.uint8),
+                     ("replaced", np.uint8)):
+        out[name] = torch.as_tensor(_DeviceArray(getattr(r, name), (n,), np.dtype(dt).str), device="cuda")
+    return out
+
+
+def dic_fftcc_windows(h, window: int, origins, subpixel: bool, u, v, peak, stream_ptr: int = 0):
+    """Eq. 1 over explicit windows: origins an int32 CUDA tensor [n, 4] of (x0, y0,
+    gx0, gy0); u, v, peak float32 CUDA tensors [n]."""
+    n = int(origins.shape[0])
+    _check(load().dic_fftcc_windows(h, window, n, ctypes.c_void_p(origins.data_ptr()), 1 if subpixel else 0,
+                                    ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                    ctypes.c_void_p(peak.data_ptr()), ctypes.c_void_p(stream_ptr)))
+
+
+def dic_mad_filter(u, v, valid, nx: int, ny: int, tau: float, eps: float, u_out, v_out, replaced=None,
+                   stream_ptr: int = 0):
+    """The initialiser's MAD rule on float32 CUDA tensors of nx * ny values."""
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    _check(load().dic_mad_filter(ptr(u), ptr(v), ptr(valid), nx, ny, tau, eps, ptr(u_out), ptr(v_out),
+                                 ptr(replaced), ctypes.c_void_p(stream_ptr)))
+
+
 def strain_outputs(n: int, device="cuda") -> dict:
     """Output tensors for dic_strain_field over n points."""
     import torch
@@ -407,6 +485,8 @@ def _apply(p: DicParams, kw: dict) -> DicParams:
             v = COSTS[v]
         if k == "optimizer" and isinstance(v, str):
             v = OPTIMIZERS[v]
+        if k == "init" and isinstance(v, str):
+            v = INITS[v]
         setattr(p, k, v)
     return p
 
@@ -462,6 +542,12 @@ class Correlation:
 
     def timing(self):
         return dic_get_timing(self.h)
+
+    def fft_field(self, max_displacement=32, subpixel=True, mad_tau=3.0, mad_eps=0.5, stream_ptr: int = 0) -> dict:
+        """The multi-window FFT initialiser alone (the paper's MULTIWINDOW method)."""
+        dic_fft_field(self.h, fft_params(max_displacement=max_displacement, subpixel=1 if subpixel else 0,
+                                         mad_tau=mad_tau, mad_eps=mad_eps), stream_ptr)
+        return dic_get_fft_results(self.h)
 
     def strain(self, window=9, basis="biquadratic", measure="green_lagrange", stream_ptr: int = 0) -> dict:
         """Sec. 2.3 strain of the last correlation: CUDA tensors per STRAIN_FIELDS."""

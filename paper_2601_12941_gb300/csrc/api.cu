@@ -146,6 +146,24 @@ struct dic_handle {
   std::vector<cudaEvent_t> events;       // stage boundaries
   std::vector<cudaEvent_t> wave_events;  // two per wave kernel when profiling
   cudaEvent_t batch_ev[2] = {nullptr, nullptr};
+  // multi-window FFT initialiser: twiddles (and the odd length they hold), window
+  // origins, per-level raw and filtered fields, large-window scratch, results
+  float2* fft_tw = nullptr;
+  int fft_tw_odd = -1;
+  int4* fft_org = nullptr;
+  float* fft_raw[3] = {nullptr, nullptr, nullptr};       // u, v, peak
+  float* fft_filt[4] = {nullptr, nullptr, nullptr, nullptr};  // ping-pong (u, v) x 2
+  float2* fft_work = nullptr;
+  double* fft_norms = nullptr;
+  unsigned long long* fft_keys = nullptr;
+  int32_t* fft_nonflat = nullptr;
+  float* fft_res[3] = {nullptr, nullptr, nullptr};       // u, v, peak per grid point
+  uint8_t* fft_status = nullptr;
+  uint8_t* fft_rep = nullptr;
+  int64_t fft_win_cap = 0, fft_mid_cap = 0, fft_large_cap = 0, fft_work_cap = 0, fft_res_cap = 0;
+  bool has_fft = false;
+  int fft_levels = 0;
+  int fft_window[kFftMaxLevels] = {};
 };
 
 namespace {
@@ -563,8 +581,10 @@ int configure_subsets(dic_handle* h, const dic_image* roi, int32_t subset_size, 
 // of halloc sizes. With cur given, the handle is re-gridded rather than created:
 // the reference copy is kept, and every array keeps its capacity unless it is too
 // small, the same rules as configure_subsets, replace_image and dic_correlate.
+int64_t fft_bytes_for(const dic_handle* cur, int W, int H, int S, int64_t npts, int D);
+
 int64_t footprint(const dic_handle* cur, const dic_image* ref, const dic_image* def, bool roi, int S, int step,
-                  int shape, int precision, int n_seeds, int R) {
+                  int shape, int precision, int n_seeds, int R, int fft_D) {
   const int64_t W = ref->width, H = ref->height;
   const int r = (S - 1) / 2;
   const int64_t n = ((W - 1 - 2 * r) / step + 1) * ((H - 1 - 2 * r) / step + 1);
@@ -583,7 +603,8 @@ int64_t footprint(const dic_handle* cur, const dic_image* ref, const dic_image* 
     if (!ref->on_device) b += static_cast<int64_t>(owned_pitch(ref)) * H;
     if (!def->on_device) b += static_cast<int64_t>(owned_pitch(def)) * H;
     b += plane_bytes + points_bytes(n) + 8 * n * np;
-    b += static_cast<int64_t>(n_seeds) * (8 + 4 + 4) + 8 * n_seeds * side * side;
+    b += static_cast<int64_t>(n_seeds) * (8 + 4 + 4) + (fft_D < 0 ? 8 * n_seeds * side * side : 0);
+    if (fft_D >= 0) b += fft_bytes_for(nullptr, static_cast<int>(W), static_cast<int>(H), S, n, fft_D);
     return b;
   }
   b += cur->ref_owned ? owned_bytes(cur, cur->ref_owned) : 0;
@@ -596,9 +617,14 @@ int64_t footprint(const dic_handle* cur, const dic_image* ref, const dic_image* 
   b += 8 * (n * np > cur->p_cap ? n * np : cur->p_cap);
   const int64_t sc = static_cast<int64_t>(n_seeds) > static_cast<int64_t>(cur->seed_cap)
                          ? n_seeds : static_cast<int64_t>(cur->seed_cap);
-  const int64_t scores = n_seeds * side * side > static_cast<int64_t>(cur->score_cap)
-                             ? n_seeds * side * side : static_cast<int64_t>(cur->score_cap);
+  const int64_t want_scores = fft_D < 0 ? n_seeds * side * side : 0;
+  const int64_t scores = want_scores > static_cast<int64_t>(cur->score_cap) ? want_scores
+                                                                           : static_cast<int64_t>(cur->score_cap);
   b += sc * (8 + 4 + 4) + 8 * scores;
+  if (fft_D >= 0)
+    b += fft_bytes_for(cur, static_cast<int>(W), static_cast<int>(H), S, n, fft_D);
+  else if (cur->fft_tw)
+    b += fft_bytes_for(cur, static_cast<int>(W), static_cast<int>(H), S, 0, -1);
   return b;
 }
 
@@ -615,6 +641,10 @@ int validate_params(const dic_params* p) {
     return fail(DIC_EINVAL, "unknown cost %d", p->cost);
   if (p->optimizer != DIC_OPT_GAUSS_NEWTON && p->optimizer != DIC_OPT_LEVENBERG_MARQUARDT)
     return fail(DIC_EINVAL, "unknown optimizer %d", p->optimizer);
+  if (p->init != DIC_INIT_SEARCH && p->init != DIC_INIT_FFT) return fail(DIC_EINVAL, "unknown init %d", p->init);
+  if (p->max_displacement < 0 || p->max_displacement >= kFftLargeMax)
+    return fail(DIC_EINVAL, "max_displacement %d outside [0, %d]", p->max_displacement, kFftLargeMax - 1);
+  if (!(p->mad_eps >= 0.0) || p->mad_tau != p->mad_tau) return fail(DIC_EINVAL, "mad_tau/mad_eps invalid");
   return DIC_OK;
 }
 
@@ -682,6 +712,203 @@ int finish_run(dic_handle* h, cudaStream_t s) {
 
 }  // namespace
 
+namespace {
+
+// Window sizes of the initialiser: the powers of two above D, largest first, that
+// exceed the subset size and fit in the image, then the subset size.
+std::vector<int> fft_sizes(int D, int S, int W, int H) {
+  int L = 1;
+  while (L <= D) L *= 2;
+  std::vector<int> out;
+  for (; L > S; L /= 2)
+    if (L <= W && L <= H) out.push_back(L);
+  out.push_back(S);
+  return out;
+}
+
+struct FftCaps {
+  int64_t win = 0, mid = 0, large = 0, work = 0, res = 0;
+};
+
+FftCaps fft_caps(int W, int H, int S, int64_t npts, int D) {
+  FftCaps c;
+  const std::vector<int> sizes = fft_sizes(D, S, W, H);
+  for (size_t i = 0; i + 1 < sizes.size(); ++i) {
+    const int64_t L = sizes[i];
+    const int64_t n = (W / L) * (H / L);
+    c.mid = n > c.mid ? n : c.mid;
+    if (L > kFftSmallMax) {
+      c.large = n > c.large ? n : c.large;
+      c.work = n * L * L > c.work ? n * L * L : c.work;
+    }
+  }
+  c.res = npts;
+  c.win = c.mid > npts ? c.mid : npts;
+  return c;
+}
+
+constexpr int64_t kFftTwiddleEntries = kFftTwiddlesPow2 + kFftSmallMax;
+
+// Device bytes of the initialiser's arrays once a run with caps has grown them
+// from cur's capacities (cur NULL: a fresh handle).
+int64_t fft_bytes(const FftCaps& c, const dic_handle* cur) {
+  auto mx = [](int64_t a, int64_t b) { return a > b ? a : b; };
+  const int64_t win = mx(c.win, cur ? cur->fft_win_cap : 0), mid = mx(c.mid, cur ? cur->fft_mid_cap : 0);
+  const int64_t large = mx(c.large, cur ? cur->fft_large_cap : 0), work = mx(c.work, cur ? cur->fft_work_cap : 0);
+  const int64_t res = mx(c.res, cur ? cur->fft_res_cap : 0);
+  int64_t b = 8 * kFftTwiddleEntries + 16 * win + 12 * win + 16 * mid + 14 * res;
+  if (large > 0) b += 8 * work + 16 * large + 8 * large + 8 * large;
+  return b;
+}
+
+int64_t fft_bytes_for(const dic_handle* cur, int W, int H, int S, int64_t npts, int D) {
+  return fft_bytes(D >= 0 ? fft_caps(W, H, S, npts, D) : FftCaps{}, cur);
+}
+
+template <typename P>
+int regrow(dic_handle* h, P** ptr, int64_t need, const char* what) {
+  hfree(h, *ptr);
+  return halloc(h, ptr, static_cast<size_t>(need), what);
+}
+
+int fft_prepare(dic_handle* h, const FftCaps& c) {
+  int rc;
+  if (!h->fft_tw && (rc = halloc(h, &h->fft_tw, static_cast<size_t>(kFftTwiddleEntries), "fft twiddles"))) return rc;
+  if (c.win > h->fft_win_cap) {
+    h->fft_win_cap = 0;
+    if ((rc = regrow(h, &h->fft_org, c.win, "fft origins"))) return rc;
+    for (int i = 0; i < 3; ++i)
+      if ((rc = regrow(h, &h->fft_raw[i], c.win, "fft level"))) return rc;
+    h->fft_win_cap = c.win;
+  }
+  if (c.mid > h->fft_mid_cap) {
+    h->fft_mid_cap = 0;
+    for (int i = 0; i < 4; ++i)
+      if ((rc = regrow(h, &h->fft_filt[i], c.mid, "fft level"))) return rc;
+    h->fft_mid_cap = c.mid;
+  }
+  if (c.large > h->fft_large_cap) {
+    h->fft_large_cap = 0;
+    if ((rc = regrow(h, &h->fft_norms, 2 * c.large, "fft norms")) ||
+        (rc = regrow(h, &h->fft_keys, c.large, "fft peaks")) ||
+        (rc = regrow(h, &h->fft_nonflat, 2 * c.large, "fft flags")))
+      return rc;
+    h->fft_large_cap = c.large;
+  }
+  if (c.work > h->fft_work_cap) {
+    h->fft_work_cap = 0;
+    if ((rc = regrow(h, &h->fft_work, c.work, "fft work"))) return rc;
+    h->fft_work_cap = c.work;
+  }
+  if (c.res > h->fft_res_cap) {
+    h->fft_res_cap = 0;
+    for (int i = 0; i < 3; ++i)
+      if ((rc = regrow(h, &h->fft_res[i], c.res, "fft results"))) return rc;
+    if ((rc = regrow(h, &h->fft_status, c.res, "fft results")) ||
+        (rc = regrow(h, &h->fft_rep, c.res, "fft results")))
+      return rc;
+    h->fft_res_cap = c.res;
+  }
+  return DIC_OK;
+}
+
+FftccArgs fftcc_args(dic_handle* h, int L, int64_t n, int subpixel, float* u, float* v, float* peak) {
+  FftccArgs a{};
+  a.ref = h->ref;
+  a.def = h->def;
+  a.W = h->W;
+  a.H = h->H;
+  a.L = L;
+  a.n = n;
+  a.org = h->fft_org;
+  a.tw_pow2 = h->fft_tw;
+  a.tw_odd = h->fft_tw + kFftTwiddlesPow2;
+  a.subpixel = subpixel;
+  a.u = u;
+  a.v = v;
+  a.peak = peak;
+  a.work = h->fft_work;
+  a.norms = h->fft_norms;
+  a.keys = h->fft_keys;
+  a.nonflat = h->fft_nonflat;
+  return a;
+}
+
+int fft_twiddles(dic_handle* h, int L_odd, cudaStream_t s) {
+  if (h->fft_tw_odd == L_odd) return DIC_OK;
+  DIC_CUDA(launch_twiddles(h->fft_tw, L_odd, s), "fft twiddles");
+  h->fft_tw_odd = L_odd;
+  return DIC_OK;
+}
+
+// The whole initialiser over the handle's grid: every level's origins, Eq. 1 and
+// the MAD rule; the last level's values land in fft_res, fft_rep and fft_status.
+int run_fft(dic_handle* h, int D, int subpixel, double tau, double eps, cudaStream_t s) {
+  const std::vector<int> sizes = fft_sizes(D, h->S, h->W, h->H);
+  if (static_cast<int>(sizes.size()) > kFftMaxLevels) return fail(DIC_EINVAL, "too many window levels");
+  int rc = fft_prepare(h, fft_caps(h->W, h->H, h->S, h->npts, D));
+  if (rc) return rc;
+  if ((rc = fft_twiddles(h, h->S, s))) return rc;
+  const float* pu = nullptr;
+  const float* pv = nullptr;
+  int pnx = 0, pny = 0, ping = 0;
+  double pc0 = 0.0, pstep = 1.0;
+  h->has_fft = false;
+  for (size_t li = 0; li < sizes.size(); ++li) {
+    const int L = sizes[li];
+    const bool last = li + 1 == sizes.size();
+    const int nx = last ? h->nx : h->W / L, ny = last ? h->ny : h->H / L;
+    const int64_t n = static_cast<int64_t>(nx) * ny;
+    FftLevelArgs la{};
+    la.W = h->W;
+    la.H = h->H;
+    la.L = L;
+    la.nx = nx;
+    la.ny = ny;
+    la.grid = last ? 1 : 0;
+    la.r = h->r;
+    la.step = h->step;
+    la.roi_ok = last ? h->roi_ok : nullptr;
+    la.pu = pu;
+    la.pv = pv;
+    la.pnx = pnx;
+    la.pny = pny;
+    la.pc0 = pc0;
+    la.pstep = pstep;
+    la.org = h->fft_org;
+    DIC_CUDA(launch_fftcc_origins(la, s), "fft origins");
+    float* peak_out = last ? h->fft_res[2] : h->fft_raw[2];
+    DIC_CUDA(launch_fftcc(fftcc_args(h, L, n, last ? subpixel : 0, h->fft_raw[0], h->fft_raw[1], peak_out), s),
+             "fft cross-correlation");
+    MadArgs ma{};
+    ma.u = h->fft_raw[0];
+    ma.v = h->fft_raw[1];
+    ma.valid = last ? h->roi_ok : nullptr;
+    ma.nx = nx;
+    ma.ny = ny;
+    ma.tau = tau;
+    ma.eps = eps;
+    ma.u_out = last ? h->fft_res[0] : h->fft_filt[2 * ping];
+    ma.v_out = last ? h->fft_res[1] : h->fft_filt[2 * ping + 1];
+    ma.replaced = last ? h->fft_rep : nullptr;
+    DIC_CUDA(launch_mad(ma, s), "fft outlier removal");
+    pu = ma.u_out;
+    pv = ma.v_out;
+    pnx = nx;
+    pny = ny;
+    pc0 = L / 2;
+    pstep = L;
+    ping ^= 1;
+  }
+  DIC_CUDA(launch_fft_status(h->roi_ok, h->fft_status, h->npts, s), "fft status");
+  h->fft_levels = static_cast<int>(sizes.size());
+  for (size_t i = 0; i < sizes.size(); ++i) h->fft_window[i] = sizes[i];
+  h->has_fft = true;
+  return DIC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 dic_params dic_default_params(void) {
@@ -695,8 +922,21 @@ dic_params dic_default_params(void) {
   p.profile = 0;
   p.cost = DIC_COST_ZNSSD;
   p.optimizer = DIC_OPT_GAUSS_NEWTON;
+  p.init = DIC_INIT_SEARCH;
+  p.max_displacement = 32;
   p.reserved = 0;
+  p.mad_tau = 3.0;
+  p.mad_eps = 0.5;
   return p;
+}
+
+dic_fft_params dic_fft_default_params(void) {
+  dic_fft_params f{};
+  f.max_displacement = 32;
+  f.subpixel = 1;
+  f.mad_tau = 3.0;
+  f.mad_eps = 0.5;
+  return f;
 }
 
 const char* dic_last_error(void) { return g_last_error.c_str(); }
@@ -748,7 +988,7 @@ int dic_estimate_device_bytes(const dic_image* ref, const dic_image* def, int32_
   int rc = check_estimate_args(ref, def, subset_size, subset_step, shape_fn, params, n_seeds);
   if (rc) return rc;
   *bytes = footprint(nullptr, ref, def, has_roi != 0, subset_size, subset_step, shape_fn, params->precision,
-                     n_seeds, params->search_radius);
+                     n_seeds, params->search_radius, params->init == DIC_INIT_FFT ? params->max_displacement : -1);
   return DIC_OK;
 }
 
@@ -765,7 +1005,7 @@ int dic_estimate_regrid_bytes(const dic_handle* h, const dic_image* def, int32_t
   int rc = check_estimate_args(&ref, def, subset_size, subset_step, shape_fn, params, n_seeds);
   if (rc) return rc;
   *bytes = footprint(h, &ref, def, has_roi != 0, subset_size, subset_step, shape_fn, params->precision, n_seeds,
-                     params->search_radius);
+                     params->search_radius, params->init == DIC_INIT_FFT ? params->max_displacement : -1);
   return DIC_OK;
 }
 
@@ -865,7 +1105,8 @@ int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void*
       return rc;
     h->seed_cap = n_seeds;
   }
-  if (n_seeds * side * side > h->score_cap) {
+  const bool fft_init = h->prm.init == DIC_INIT_FFT;
+  if (!fft_init && n_seeds * side * side > h->score_cap) {
     hfree(h, h->seed_scores);
     h->score_cap = 0;
     if ((rc = halloc(h, &h->seed_scores, n_seeds * side * side, "seed scores"))) return rc;
@@ -879,11 +1120,18 @@ int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void*
   DIC_CUDA(launch_reset_points(pa, h->nparams, h->roi_ok, s), "point reset");
   DIC_CUDA(cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * kNumCounters, s), "counter reset");
   if (prof) cudaEventRecord(h->events[2], s);
-  SeedArgs sa{h->ref, h->def, h->W, h->H, h->S, R, n_seeds, h->seed_xy, h->seed_scores};
-  DIC_CUDA(launch_seed_scores(sa, s), "seed search");
-  if (prof) cudaEventRecord(h->events[3], s);
   SeedCommitArgs ca{n_seeds, R, h->nparams, h->seed_q, h->seed_scores, h->seed_best, h->p, h->status,
-                    h->wave, h->front[0], h->counters, h->roi_ok};
+                    h->wave, h->front[0], h->counters, h->roi_ok, nullptr, nullptr};
+  if (fft_init) {
+    // the seeds start from the multi-window FFT estimate (no sub-pixel fit)
+    if ((rc = run_fft(h, h->prm.max_displacement, 0, h->prm.mad_tau, h->prm.mad_eps, s))) return rc;
+    ca.fft_u = h->fft_res[0];
+    ca.fft_v = h->fft_res[1];
+  } else {
+    SeedArgs sa{h->ref, h->def, h->W, h->H, h->S, R, n_seeds, h->seed_xy, h->seed_scores};
+    DIC_CUDA(launch_seed_scores(sa, s), "seed search");
+  }
+  if (prof) cudaEventRecord(h->events[3], s);
   DIC_CUDA(launch_seed_commit(ca, s), "seed commit");
 
   return finish_run(h, s);
@@ -1045,6 +1293,79 @@ int dic_strain_field(const double* u, const double* v, const uint8_t* status, in
   a.exy = out->exy;
   a.valid = out->valid;
   DIC_CUDA(launch_strain(a, static_cast<cudaStream_t>(cuda_stream)), "strain launch");
+  return DIC_OK;
+}
+
+int dic_fft_field(dic_handle* h, const dic_fft_params* fp, void* cuda_stream) {
+  if (!h || !fp) return fail(DIC_EINVAL, "NULL argument");
+  g_last_error.clear();
+  if (fp->max_displacement < 0 || fp->max_displacement >= kFftLargeMax)
+    return fail(DIC_EINVAL, "max_displacement %d outside [0, %d]", fp->max_displacement, kFftLargeMax - 1);
+  if (!(fp->mad_eps >= 0.0) || fp->mad_tau != fp->mad_tau) return fail(DIC_EINVAL, "mad_tau/mad_eps invalid");
+  if (!h->grid_ok) return fail(DIC_ESTATE, "the handle has no subset grid; call dic_set_subsets");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = s;
+  return run_fft(h, fp->max_displacement, fp->subpixel ? 1 : 0, fp->mad_tau, fp->mad_eps, s);
+}
+
+int dic_get_fft_results(const dic_handle* h, dic_fft_results* out) {
+  if (!h || !out) return fail(DIC_EINVAL, "NULL argument");
+  if (!h->has_fft) return fail(DIC_ESTATE, "no FFT initialiser run on this handle");
+  dic_fft_results r{};
+  r.n_points = h->npts;
+  r.nx = h->nx;
+  r.ny = h->ny;
+  r.n_levels = h->fft_levels;
+  for (int i = 0; i < h->fft_levels; ++i) r.window[i] = h->fft_window[i];
+  r.u = h->fft_res[0];
+  r.v = h->fft_res[1];
+  r.peak = h->fft_res[2];
+  r.status = h->fft_status;
+  r.replaced = h->fft_rep;
+  *out = r;
+  return DIC_OK;
+}
+
+int dic_fftcc_windows(dic_handle* h, int32_t window, int64_t n_windows, const int32_t* origins, int32_t subpixel,
+                      float* u, float* v, float* peak, void* cuda_stream) {
+  if (!h) return fail(DIC_EINVAL, "handle is NULL");
+  g_last_error.clear();
+  const bool pow2 = window >= 4 && (window & (window - 1)) == 0;
+  const bool odd = (window & 1) == 1 && window >= 3 && window < kFftSmallMax;
+  if (!(pow2 && window <= kFftLargeMax) && !odd)
+    return fail(DIC_EINVAL, "window %d: odd 3..%d or a power of two 4..%d", window, kFftSmallMax - 1, kFftLargeMax);
+  if (window > h->W || window > h->H) return fail(DIC_EINVAL, "window %d larger than the images", window);
+  if (subpixel && window > kFftSmallMax) return fail(DIC_EINVAL, "the sub-pixel fit needs window <= %d", kFftSmallMax);
+  if (n_windows < 0) return fail(DIC_EINVAL, "n_windows < 0");
+  if (n_windows == 0) return DIC_OK;
+  if (n_windows > (int64_t{1} << 31) - 1) return fail(DIC_EINVAL, "too many windows");
+  if (!origins || !u || !v || !peak) return fail(DIC_EINVAL, "NULL array");
+  if ((reinterpret_cast<uintptr_t>(origins) & 15) != 0) return fail(DIC_EINVAL, "origins must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  FftCaps c;
+  if (window > kFftSmallMax) {
+    c.large = n_windows;
+    c.work = n_windows * window * window;
+  }
+  int rc = fft_prepare(h, c);
+  if (rc) return rc;
+  if ((rc = fft_twiddles(h, odd ? window : (h->fft_tw_odd > 0 ? h->fft_tw_odd : 1), s))) return rc;
+  FftccArgs a = fftcc_args(h, window, n_windows, subpixel ? 1 : 0, u, v, peak);
+  a.org = reinterpret_cast<const int4*>(origins);
+  DIC_CUDA(launch_fftcc(a, s), "fft cross-correlation");
+  return DIC_OK;
+}
+
+int dic_mad_filter(const float* u, const float* v, const uint8_t* valid, int32_t nx, int32_t ny, double tau,
+                   double eps, float* u_out, float* v_out, uint8_t* replaced, void* cuda_stream) {
+  g_last_error.clear();
+  if (nx < 0 || ny < 0) return fail(DIC_EINVAL, "negative field size");
+  if (static_cast<int64_t>(nx) * ny == 0) return DIC_OK;
+  if (!u || !v || !u_out || !v_out) return fail(DIC_EINVAL, "NULL array");
+  if (u_out == u || v_out == v || u_out == v || v_out == u) return fail(DIC_EINVAL, "in-place filtering");
+  if (!(eps >= 0.0) || tau != tau) return fail(DIC_EINVAL, "tau/eps invalid");
+  MadArgs a{u, v, valid, nx, ny, tau, eps, u_out, v_out, replaced};
+  DIC_CUDA(launch_mad(a, static_cast<cudaStream_t>(cuda_stream)), "outlier removal");
   return DIC_OK;
 }
 

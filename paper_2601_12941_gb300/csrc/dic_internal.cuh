@@ -104,6 +104,58 @@ cudaError_t launch_prefilter(const PrefilterArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gray_plane(const PrefilterArgs<T>& a, cudaStream_t s);
 
+// ---------------------------------------------------------------- FFT initialiser
+constexpr int kFftSmallMax = 64;           // windows up to this side: one block each
+constexpr int kFftLargeMax = 4096;
+constexpr int kFftTwiddlesPow2 = 4095;     // nested table: exp(-2 pi i k / (2 ns)) at ns - 1 + k
+constexpr int kFftMaxLevels = 16;
+
+struct FftccArgs {
+  GrayPlane ref, def;
+  int W, H, L;
+  int64_t n;                   // windows
+  const int4* org;             // [n] (x0, y0, gx0, gy0); x0 < 0: skipped
+  const float2* tw_pow2;       // kFftTwiddlesPow2 entries
+  const float2* tw_odd;        // exp(-2 pi i t / L), t < L (odd L)
+  int subpixel;                // Gaussian peak fit (L <= kFftSmallMax)
+  float* u;                    // [n] outputs
+  float* v;
+  float* peak;
+  float2* work;                // L > kFftSmallMax: [n][L][L] scratch
+  double* norms;               // [n][2]
+  unsigned long long* keys;    // [n]
+  int32_t* nonflat;            // [n][2]
+};
+
+struct FftLevelArgs {
+  int W, H, L;                 // image and window side
+  int nx, ny;                  // windows of the level
+  int grid;                    // 1: the subsets of the correlation grid; 0: tiles of side L
+  int r, step;                 // grid geometry (grid = 1)
+  const uint8_t* roi_ok;       // grid = 1: NULL or per grid point
+  const float* pu;             // previous level's filtered field, NULL on the first level
+  const float* pv;
+  int pnx, pny;
+  double pc0, pstep;           // its window centres: pc0 + i pstep
+  int4* org;                   // [nx * ny] out
+};
+
+struct MadArgs {
+  const float* u;
+  const float* v;
+  const uint8_t* valid;        // NULL: every value
+  int nx, ny;
+  double tau, eps;
+  float* u_out;
+  float* v_out;
+  uint8_t* replaced;           // NULL or [nx * ny]
+};
+
+cudaError_t launch_twiddles(float2* tw, int L_odd, cudaStream_t s);
+cudaError_t launch_fftcc_origins(const FftLevelArgs& a, cudaStream_t s);
+cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s);
+cudaError_t launch_mad(const MadArgs& a, cudaStream_t s);
+
 // ---------------------------------------------------------------- seeds
 struct SeedArgs {
   GrayPlane ref, def;
@@ -126,8 +178,11 @@ struct SeedCommitArgs {
   int32_t* frontier0;        // wave-0 list
   int32_t* counters;
   const uint8_t* roi_ok;     // NULL: all points in the ROI
+  const float* fft_u;        // non-NULL: seeds start from these estimates (rounded,
+  const float* fft_v;        //   halves up) instead of the search scores
 };
 cudaError_t launch_seed_commit(const SeedCommitArgs& a, cudaStream_t s);
+cudaError_t launch_fft_status(const uint8_t* roi_ok, uint8_t* status, int64_t n, cudaStream_t s);
 
 // ---------------------------------------------------------------- points
 struct PointArrays {

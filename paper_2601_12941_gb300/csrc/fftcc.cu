@@ -1,0 +1,689 @@
+// Multi-window FFT cross-correlation (Sec. 2.2, Eq. 1): rigid displacement
+// estimates of square windows, coarse to fine, with the median-absolute-deviation
+// outlier removal of Sec. 4 after every level and an optional Gaussian peak fit.
+//
+// Per window (side L, reference origin (x0, y0), deformed origin (gx0, gy0)):
+//   z = (f - f_m) + i (g - g_m) packs both real windows into one complex one, so a
+//   single 2-D transform Z gives F(k) = (Z(k) + conj Z(-k)) / 2 and
+//   G(k) = (Z(k) - conj Z(-k)) / 2i. The cross power of Eq. 1's numerator is then
+//       F conj(G)(k) = Im(Z(k) Z(-k)) / 2 + i (|Z(k)|^2 - |Z(-k)|^2) / 4,
+//   whose inverse transform is the circular cross-correlation; divided by
+//   ||f - f_m|| ||g - g_m|| it is the zero-normalised correlation R (Eq. 1 with the
+//   norms of the transforms in the denominator). The peak of R sits at minus the
+//   shift of the deformed window's content.
+//
+// Two paths:
+//   * L <= 64 (the subset-sized last level, and the 32 / 64 levels): one block per
+//     window, the whole window in shared memory; radix-2 Stockham FFTs along rows
+//     and columns for powers of two, a direct DFT for the odd subset size.
+//   * 128 <= L <= 4096: the window in a global work buffer; row FFTs, an in-place
+//     tile transpose, paired-row FFTs that form the cross power and transform it
+//     back, a transpose back and the inverse row FFTs with a per-window arg-max
+//     (packed 64-bit keys: the larger R, ties to the lower row-major index).
+#include <math.h>
+#include <stdint.h>
+
+#include "dic_internal.cuh"
+
+namespace dic {
+namespace {
+
+constexpr int kSmallThreads = 256;
+constexpr int kLineThreads = 512;
+constexpr int kLineElems = 4096;       // complex elements per block of the line kernels
+constexpr int kTransposeTile = 32;
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// The cross power F conj(G) at k from the packed spectrum values Z(k) and Z(-k).
+__device__ __forceinline__ float2 cross_power(float2 zk, float2 zm) {
+  const float im_prod = zk.x * zm.y + zk.y * zm.x;                  // Im(Z(k) Z(-k))
+  const float d = (zk.x * zk.x + zk.y * zk.y) - (zm.x * zm.x + zm.y * zm.y);
+  return make_float2(0.5f * im_prod, 0.25f * d);
+}
+
+// Orderable key of (value, index): the larger value wins, ties to the lower index.
+__device__ __forceinline__ unsigned long long peak_key(float v, int idx) {
+  uint32_t u = __float_as_uint(v);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return (static_cast<unsigned long long>(u) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(idx));
+}
+__device__ __forceinline__ float key_value(unsigned long long k) {
+  uint32_t u = static_cast<uint32_t>(k >> 32);
+  u = (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+  return __uint_as_float(u);
+}
+__device__ __forceinline__ int key_index(unsigned long long k) {
+  return static_cast<int>(0xFFFFFFFFu - static_cast<uint32_t>(k & 0xFFFFFFFFu));
+}
+
+// A window takes part when both its reference and deformed squares lie inside the
+// images (x0 < 0 marks a window to skip); anything else is skipped, never read.
+__device__ __forceinline__ bool window_ok(int4 o, int L, int W, int H) {
+  return o.x >= 0 && o.y >= 0 && o.z >= 0 && o.w >= 0 && o.x <= W - L && o.y <= H - L && o.z <= W - L &&
+         o.w <= H - L;
+}
+
+// d = wrap(-k): the shift of the deformed window's content from the peak index k.
+__device__ __forceinline__ int shift_of_peak(int k, int L) {
+  const int h = L / 2;
+  int m = (-k + h) % L;
+  if (m < 0) m += L;
+  return m - h;
+}
+
+// Vertex offset of the Gaussian through three samples (0 unless all are positive
+// and the middle one is a strict maximum of the fitted parabola of logarithms).
+__device__ __forceinline__ float gauss3(float rm, float r0, float rp) {
+  if (!(rm > 0.f && r0 > 0.f && rp > 0.f)) return 0.f;
+  const float lm = logf(rm), l0 = logf(r0), lp = logf(rp);
+  const float den = 2.f * (lm - 2.f * l0 + lp);
+  if (!(den < 0.f)) return 0.f;
+  return (lm - lp) / den;
+}
+
+// Radix-2 Stockham passes over `lines` lines of length L (a power of two): element
+// i of line l at p[l * ls + i * es]; ping-pong between p and q, the result in the
+// returned buffer. tw[ns - 1 + k] = exp(-2 pi i k / (2 ns)), k < ns.
+__device__ float2* fft_lines(float2* p, float2* q, int L, int lines, int ls, int es, const float2* __restrict__ tw,
+                             bool inv) {
+  const int half = L >> 1;
+  const int total = lines * half;
+  const int lg = __ffs(half) - 1;                         // log2(half)
+  for (int ns = 1; ns < L; ns <<= 1) {
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int l = t >> lg, j = t & (half - 1);
+      const float2* in = p + l * ls;
+      float2* out = q + l * ls;
+      const int k = j & (ns - 1);
+      float2 w = tw[ns - 1 + k];
+      if (inv) w.y = -w.y;
+      const float2 a0 = in[j * es];
+      const float2 b = cmul(in[(j + half) * es], w);
+      const int d = ((j - k) << 1) + k;
+      out[d * es] = cadd(a0, b);
+      out[(d + ns) * es] = csub(a0, b);
+    }
+    __syncthreads();
+    float2* t = p;
+    p = q;
+    q = t;
+  }
+  return p;
+}
+
+// Direct DFT of `lines` lines of odd length L from p into q (same layout);
+// twl[t] = exp(-2 pi i t / L).
+__device__ void dft_lines(const float2* p, float2* q, int L, int lines, int ls, int es, const float2* twl,
+                          bool inv) {
+  const int total = lines * L;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int l = t / L, k = t - l * L;
+    const float2* in = p + l * ls;
+    float ax = 0.f, ay = 0.f;
+    int idx = 0;
+    for (int x = 0; x < L; ++x) {
+      const float2 v = in[x * es];
+      const float2 w = twl[idx];
+      const float wy = inv ? -w.y : w.y;
+      ax = fmaf(v.x, w.x, fmaf(-v.y, wy, ax));
+      ay = fmaf(v.x, wy, fmaf(v.y, w.x, ay));
+      idx += k;
+      if (idx >= L) idx -= L;
+    }
+    q[l * ls + k * es] = make_float2(ax, ay);
+  }
+  __syncthreads();
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Sums of two values over the block (all threads get them).
+__device__ void block_sum2(double& a, double& b, double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) {
+    scratch[2 * wid] = a;
+    scratch[2 * wid + 1] = b;
+  }
+  __syncthreads();
+  a = 0.0;
+  b = 0.0;
+  for (int w = 0; w < nw; ++w) {
+    a += scratch[2 * w];
+    b += scratch[2 * w + 1];
+  }
+}
+
+__device__ unsigned long long block_max_key(unsigned long long v, unsigned long long* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max_key(v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  v = 0ull;
+  for (int w = 0; w < nw; ++w) v = scratch[w] > v ? scratch[w] : v;
+  return v;
+}
+
+// ---------------------------------------------------------------- small windows
+template <bool POW2>
+__global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = a.L, N = L * L;
+  float2* A = reinterpret_cast<float2*>(smem_raw);
+  float2* B = A + N;
+  float2* tws = B + N;                                   // L - 1 (power of two) or L (odd) twiddles
+  __shared__ double s_red[2 * (kSmallThreads / 32)];
+  __shared__ unsigned long long s_key[kSmallThreads / 32];
+  const int tid = threadIdx.x;
+  // the nested power-of-two table: stage ns <= L/2 reads tw_pow2[ns - 1 + k], k < ns,
+  // so the block keeps entries 0 .. L - 2
+  const int ntw = POW2 ? L - 1 : L;
+  for (int e = tid; e < ntw; e += kSmallThreads) tws[e] = POW2 ? a.tw_pow2[e] : a.tw_odd[e];
+  __syncthreads();
+
+  for (int64_t w = blockIdx.x; w < a.n; w += gridDim.x) {
+    const int4 o = a.org[w];
+    if (!window_ok(o, L, a.W, a.H)) {                    // skipped (outside the ROI)
+      if (tid == 0) {
+        a.u[w] = 0.f;
+        a.v[w] = 0.f;
+        a.peak[w] = 0.f;
+      }
+      continue;
+    }
+    double sf = 0.0, sg = 0.0;
+    for (int e = tid; e < N; e += kSmallThreads) {
+      const int y = e / L, x = e - y * L;
+      const float f = load_gray<float>(a.ref, o.x + x, o.y + y);
+      const float g = load_gray<float>(a.def, o.z + x, o.w + y);
+      A[e] = make_float2(f, g);
+      sf += f;
+      sg += g;
+    }
+    block_sum2(sf, sg, s_red);
+    const float mf = static_cast<float>(sf / N), mg = static_cast<float>(sg / N);
+    double qf = 0.0, qg = 0.0;
+    for (int e = tid; e < N; e += kSmallThreads) {
+      float2 v = A[e];
+      v.x -= mf;
+      v.y -= mg;
+      A[e] = v;
+      qf += static_cast<double>(v.x) * v.x;
+      qg += static_cast<double>(v.y) * v.y;
+    }
+    block_sum2(qf, qg, s_red);                           // (its barriers also order the writes above)
+    float2* X;
+    float2* Y;
+    if (POW2) {
+      X = fft_lines(A, B, L, L, L, 1, tws, false);       // rows
+      Y = X == A ? B : A;
+      X = fft_lines(X, Y, L, L, 1, L, tws, false);       // columns
+    } else {
+      dft_lines(A, B, L, L, L, 1, tws, false);
+      dft_lines(B, A, L, L, 1, L, tws, false);
+      X = A;
+    }
+    Y = X == A ? B : A;
+    for (int e = tid; e < N; e += kSmallThreads) {
+      const int ky = e / L, kx = e - ky * L;
+      const int m = (ky == 0 ? 0 : L - ky) * L + (kx == 0 ? 0 : L - kx);
+      Y[e] = e == 0 ? make_float2(0.f, 0.f) : cross_power(X[e], X[m]);
+    }
+    __syncthreads();
+    float2* R;
+    if (POW2) {
+      R = fft_lines(Y, X, L, L, L, 1, tws, true);
+      float2* S2 = R == A ? B : A;
+      R = fft_lines(R, S2, L, L, 1, L, tws, true);
+    } else {
+      dft_lines(Y, X, L, L, L, 1, tws, true);
+      dft_lines(X, Y, L, L, 1, L, tws, true);
+      R = Y;
+    }
+    unsigned long long best = 0ull;
+    for (int e = tid; e < N; e += kSmallThreads) {
+      const unsigned long long k = peak_key(R[e].x, e);
+      best = k > best ? k : best;
+    }
+    best = block_max_key(best, s_key);
+    if (tid == 0) {
+      const bool flat = !(qf > 0.0) || !(qg > 0.0);
+      const int e = flat ? 0 : key_index(best);
+      const int ky = e / L, kx = e - ky * L;
+      float dx = static_cast<float>(shift_of_peak(kx, L)), dy = static_cast<float>(shift_of_peak(ky, L));
+      if (a.subpixel && !flat) {
+        const int xm = kx == 0 ? L - 1 : kx - 1, xp = kx == L - 1 ? 0 : kx + 1;
+        const int ym = ky == 0 ? L - 1 : ky - 1, yp = ky == L - 1 ? 0 : ky + 1;
+        const float r0 = R[e].x;
+        dx -= gauss3(R[ky * L + xm].x, r0, R[ky * L + xp].x);
+        dy -= gauss3(R[ym * L + kx].x, r0, R[yp * L + kx].x);
+      }
+      a.u[w] = static_cast<float>(o.z - o.x) + dx;
+      a.v[w] = static_cast<float>(o.w - o.y) + dy;
+      a.peak[w] = flat ? 0.f : static_cast<float>(static_cast<double>(R[e].x) /
+                                                  (static_cast<double>(N) * sqrt(qf * qg)));
+    }
+    __syncthreads();                                     // the next window reuses the buffers
+  }
+}
+
+// ---------------------------------------------------------------- large windows
+// Rows of the packed windows, transformed along x: work[w][y][kx]. Also marks the
+// windows whose f or g is not constant (an exactly flat window correlates to 0).
+__global__ void __launch_bounds__(kLineThreads) fftcc_rows_fwd_kernel(FftccArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = a.L;
+  const int rows = kLineElems / L;                       // L >= 128: 1 .. 32 rows per block
+  float2* P = reinterpret_cast<float2*>(smem_raw);
+  float2* Q = P + kLineElems;
+  const int64_t w = blockIdx.y;
+  const int4 o = a.org[w];
+  if (!window_ok(o, L, a.W, a.H)) return;                // uniform: the whole block
+  const int y0 = blockIdx.x * rows;
+  const float f00 = load_gray<float>(a.ref, o.x, o.y);
+  const float g00 = load_gray<float>(a.def, o.z, o.w);
+  bool vf = false, vg = false;
+  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) {
+    const int r = e / L, x = e - r * L;
+    const float f = load_gray<float>(a.ref, o.x + x, o.y + y0 + r);
+    const float g = load_gray<float>(a.def, o.z + x, o.w + y0 + r);
+    vf |= f != f00;
+    vg |= g != g00;
+    P[e] = make_float2(f, g);
+  }
+  if (__syncthreads_or(vf) && threadIdx.x == 0) atomicOr(&a.nonflat[2 * w], 1);
+  if (__syncthreads_or(vg) && threadIdx.x == 0) atomicOr(&a.nonflat[2 * w + 1], 1);
+  const float2* R = fft_lines(P, Q, L, rows, L, 1, a.tw_pow2, false);
+  float2* dst = a.work + w * static_cast<int64_t>(L) * L + static_cast<int64_t>(y0) * L;
+  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) dst[e] = R[e];
+}
+
+// In-place transpose of every L x L window: the block of tile (ti, tj), ti <= tj,
+// swaps it with its mirror tile (tj, ti).
+__global__ void __launch_bounds__(kTransposeTile * 8) fftcc_transpose_kernel(FftccArgs a) {
+  __shared__ float2 t0[kTransposeTile][kTransposeTile + 1];
+  __shared__ float2 t1[kTransposeTile][kTransposeTile + 1];
+  const int L = a.L, T = L / kTransposeTile;
+  const int ti = blockIdx.x % T, tj = blockIdx.x / T;
+  if (ti > tj) return;
+  const int64_t w = blockIdx.y;
+  if (!window_ok(a.org[w], L, a.W, a.H)) return;
+  float2* base = a.work + w * static_cast<int64_t>(L) * L;
+  const int tx = threadIdx.x & (kTransposeTile - 1), ty = threadIdx.x / kTransposeTile;   // 32 x 8
+  for (int r = ty; r < kTransposeTile; r += 8) {
+    t0[r][tx] = base[static_cast<int64_t>(ti * kTransposeTile + r) * L + tj * kTransposeTile + tx];
+    t1[r][tx] = base[static_cast<int64_t>(tj * kTransposeTile + r) * L + ti * kTransposeTile + tx];
+  }
+  __syncthreads();
+  for (int r = ty; r < kTransposeTile; r += 8) {
+    base[static_cast<int64_t>(tj * kTransposeTile + r) * L + ti * kTransposeTile + tx] = t0[tx][r];
+    base[static_cast<int64_t>(ti * kTransposeTile + r) * L + tj * kTransposeTile + tx] = t1[tx][r];
+  }
+}
+
+// After the transpose, row kx holds Z1(y, kx) along y. A unit is the row pair
+// (u, L - u) (rows 0 and L/2 pair with themselves): FFT both along y, form the cross
+// power of each frequency with its mirror, accumulate the norms of F and G (zero
+// frequency excluded), transform back along y, write both rows back.
+__global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = a.L;
+  const int units = kLineElems / L;                      // each unit holds 2 lines: 2 * units * L <= 8192
+  const int lines = 2 * units;
+  float2* P = reinterpret_cast<float2*>(smem_raw);
+  float2* Q = P + 2 * kLineElems;
+  __shared__ double s_red[2 * (kLineThreads / 32)];
+  const int64_t w = blockIdx.y;
+  if (!window_ok(a.org[w], L, a.W, a.H)) return;
+  const int u0 = blockIdx.x * units;
+  const int nunits = L / 2 + 1;
+  float2* base = a.work + w * static_cast<int64_t>(L) * L;
+  for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
+    const int line = e / L, y = e - line * L;
+    const int u = u0 + (line >> 1);
+    float2 v = make_float2(0.f, 0.f);
+    if (u < nunits) {
+      const int row = (line & 1) ? (L - u) & (L - 1) : u;
+      v = base[static_cast<int64_t>(row) * L + y];
+    }
+    P[e] = v;
+  }
+  __syncthreads();
+  float2* X = fft_lines(P, Q, L, lines, L, 1, a.tw_pow2, false);
+  float2* Y = X == P ? Q : P;
+  double nf = 0.0, ng = 0.0;
+  for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
+    const int line = e / L, ky = e - line * L;
+    const int u = u0 + (line >> 1);
+    const int mline = line ^ 1;                          // the mirror row's line
+    const int mky = ky == 0 ? 0 : L - ky;
+    const float2 zk = X[e], zm = X[mline * L + mky];
+    const bool dc = u == 0 && ky == 0;
+    Y[e] = dc ? make_float2(0.f, 0.f) : cross_power(zk, zm);
+    // each frequency once: line 0 of the unit, and line 1 only when its row differs
+    const bool count = u < nunits && !dc && ((line & 1) == 0 || (u != 0 && 2 * u != L));
+    if (count) {
+      const float fx = 0.5f * (zk.x + zm.x), fy = 0.5f * (zk.y - zm.y);   // F(k)
+      const float gx = 0.5f * (zk.y + zm.y), gy = 0.5f * (zm.x - zk.x);   // G(k)
+      nf += static_cast<double>(fx) * fx + static_cast<double>(fy) * fy;
+      ng += static_cast<double>(gx) * gx + static_cast<double>(gy) * gy;
+    }
+  }
+  block_sum2(nf, ng, s_red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&a.norms[2 * w], nf);
+    atomicAdd(&a.norms[2 * w + 1], ng);
+  }
+  float2* R = fft_lines(Y, X, L, lines, L, 1, a.tw_pow2, true);
+  for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
+    const int line = e / L, y = e - line * L;
+    const int u = u0 + (line >> 1);
+    if (u >= nunits) continue;
+    if ((line & 1) && (u == 0 || 2 * u == L)) continue;   // a self-paired row is written once
+    const int row = (line & 1) ? (L - u) & (L - 1) : u;
+    base[static_cast<int64_t>(row) * L + y] = R[e];
+  }
+}
+
+// Inverse transform of the rows along kx and the per-window arg-max of R.
+__global__ void __launch_bounds__(kLineThreads) fftcc_rows_inv_kernel(FftccArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = a.L;
+  const int rows = kLineElems / L;
+  float2* P = reinterpret_cast<float2*>(smem_raw);
+  float2* Q = P + kLineElems;
+  __shared__ unsigned long long s_key[kLineThreads / 32];
+  const int64_t w = blockIdx.y;
+  if (!window_ok(a.org[w], L, a.W, a.H)) return;
+  const int y0 = blockIdx.x * rows;
+  const float2* src = a.work + w * static_cast<int64_t>(L) * L + static_cast<int64_t>(y0) * L;
+  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) P[e] = src[e];
+  __syncthreads();
+  const float2* R = fft_lines(P, Q, L, rows, L, 1, a.tw_pow2, true);
+  unsigned long long best = 0ull;
+  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) {
+    const unsigned long long k = peak_key(R[e].x, y0 * L + e);
+    best = k > best ? k : best;
+  }
+  best = block_max_key(best, s_key);
+  if (threadIdx.x == 0) atomicMax(&a.keys[w], best);
+}
+
+__global__ void fftcc_finish_kernel(FftccArgs a) {
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w >= a.n) return;
+  const int4 o = a.org[w];
+  const int L = a.L;
+  if (!window_ok(o, L, a.W, a.H)) {
+    a.u[w] = 0.f;
+    a.v[w] = 0.f;
+    a.peak[w] = 0.f;
+    return;
+  }
+  const bool flat = !a.nonflat[2 * w] || !a.nonflat[2 * w + 1];
+  const unsigned long long key = a.keys[w];
+  const int e = flat ? 0 : key_index(key);
+  const int ky = e / L, kx = e - ky * L;
+  a.u[w] = static_cast<float>(o.z - o.x + shift_of_peak(kx, L));
+  a.v[w] = static_cast<float>(o.w - o.y + shift_of_peak(ky, L));
+  const double den = sqrt(a.norms[2 * w] * a.norms[2 * w + 1]);
+  a.peak[w] = flat || !(den > 0.0) ? 0.f : static_cast<float>(static_cast<double>(key_value(key)) / den);
+}
+
+// ---------------------------------------------------------------- level set-up
+// Reference and deformed origins of every window of a level (readings of the
+// initialiser: tiles of side L, or the subsets of the correlation grid, each moved
+// by the previous level's field interpolated bilinearly and rounded, clamped into
+// the image). The arithmetic is FP64 without contraction, as in the definition.
+__global__ void fftcc_origins_kernel(FftLevelArgs a) {
+  const int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (w >= static_cast<int64_t>(a.nx) * a.ny) return;
+  const int i = static_cast<int>(w % a.nx), j = static_cast<int>(w / a.nx);
+  if (a.roi_ok && !a.roi_ok[w]) {
+    a.org[w] = make_int4(-1, -1, -1, -1);
+    return;
+  }
+  int x0, y0, cx, cy;
+  if (a.grid) {
+    cx = a.r + i * a.step;
+    cy = a.r + j * a.step;
+    x0 = cx - a.r;
+    y0 = cy - a.r;
+  } else {
+    x0 = i * a.L;
+    y0 = j * a.L;
+    cx = x0 + a.L / 2;
+    cy = y0 + a.L / 2;
+  }
+  int gu = 0, gv = 0;
+  if (a.pu) {
+    const double c0 = a.pc0, st = a.pstep;
+    double tx = __ddiv_rn(__dsub_rn(static_cast<double>(cx), c0), st);
+    double ty = __ddiv_rn(__dsub_rn(static_cast<double>(cy), c0), st);
+    tx = fmin(fmax(tx, 0.0), static_cast<double>(a.pnx - 1));
+    ty = fmin(fmax(ty, 0.0), static_cast<double>(a.pny - 1));
+    int i0 = static_cast<int>(floor(tx)), j0 = static_cast<int>(floor(ty));
+    i0 = min(i0, max(a.pnx - 2, 0));
+    j0 = min(j0, max(a.pny - 2, 0));
+    const int i1 = min(i0 + 1, a.pnx - 1), j1 = min(j0 + 1, a.pny - 1);
+    const double fx = __dsub_rn(tx, static_cast<double>(i0)), fy = __dsub_rn(ty, static_cast<double>(j0));
+    auto lerp2 = [&](const float* F) {
+      const double f00 = F[static_cast<int64_t>(j0) * a.pnx + i0], f01 = F[static_cast<int64_t>(j0) * a.pnx + i1];
+      const double f10 = F[static_cast<int64_t>(j1) * a.pnx + i0], f11 = F[static_cast<int64_t>(j1) * a.pnx + i1];
+      const double top = __dadd_rn(__dmul_rn(__dsub_rn(1.0, fx), f00), __dmul_rn(fx, f01));
+      const double bot = __dadd_rn(__dmul_rn(__dsub_rn(1.0, fx), f10), __dmul_rn(fx, f11));
+      return __dadd_rn(__dmul_rn(__dsub_rn(1.0, fy), top), __dmul_rn(fy, bot));
+    };
+    gu = static_cast<int>(floor(__dadd_rn(lerp2(a.pu), 0.5)));
+    gv = static_cast<int>(floor(__dadd_rn(lerp2(a.pv), 0.5)));
+  }
+  const int gx0 = min(max(x0 + gu, 0), a.W - a.L);
+  const int gy0 = min(max(y0 + gv, 0), a.H - a.L);
+  a.org[w] = make_int4(x0, y0, gx0, gy0);
+}
+
+// ---------------------------------------------------------------- MAD removal
+__device__ double median_sorted(const double* s, int n) {
+  return (n & 1) ? s[n / 2] : __ddiv_rn(__dadd_rn(s[n / 2 - 1], s[n / 2]), 2.0);
+}
+__device__ void sort_small(double* s, int n) {
+  for (int i = 1; i < n; ++i) {
+    const double v = s[i];
+    int j = i - 1;
+    while (j >= 0 && s[j] > v) {
+      s[j + 1] = s[j];
+      --j;
+    }
+    s[j + 1] = v;
+  }
+}
+
+__global__ void mad_kernel(MadArgs a) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= static_cast<int64_t>(a.nx) * a.ny) return;
+  const int i = static_cast<int>(q % a.nx), j = static_cast<int>(q / a.nx);
+  const double uq = a.u[q], vq = a.v[q];
+  uint8_t rep = 0;
+  double ou = uq, ov = vq;
+  const bool valid = a.valid ? a.valid[q] != 0 : true;
+  if (valid && a.tau > 0.0) {
+    double su[9], sv[9];
+    int n = 0;
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int jj = j + dj;
+      if (jj < 0 || jj >= a.ny) continue;
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = i + di;
+        if (ii < 0 || ii >= a.nx) continue;
+        const int64_t r = static_cast<int64_t>(jj) * a.nx + ii;
+        if (a.valid && !a.valid[r]) continue;
+        su[n] = a.u[r];
+        sv[n] = a.v[r];
+        ++n;
+      }
+    }
+    sort_small(su, n);
+    sort_small(sv, n);
+    const double mu = median_sorted(su, n), mv = median_sorted(sv, n);
+    double du[9], dv[9];
+    for (int k = 0; k < n; ++k) {
+      du[k] = fabs(__dsub_rn(su[k], mu));
+      dv[k] = fabs(__dsub_rn(sv[k], mv));
+    }
+    sort_small(du, n);
+    sort_small(dv, n);
+    const double madu = median_sorted(du, n), madv = median_sorted(dv, n);
+    const double lim_u = __dmul_rn(a.tau, __dadd_rn(__dmul_rn(1.4826, madu), a.eps));
+    const double lim_v = __dmul_rn(a.tau, __dadd_rn(__dmul_rn(1.4826, madv), a.eps));
+    if (fabs(__dsub_rn(uq, mu)) > lim_u || fabs(__dsub_rn(vq, mv)) > lim_v) {
+      ou = mu;
+      ov = mv;
+      rep = 1;
+    }
+  }
+  a.u_out[q] = static_cast<float>(ou);
+  a.v_out[q] = static_cast<float>(ov);
+  if (a.replaced) a.replaced[q] = rep;
+}
+
+// ---------------------------------------------------------------- twiddles
+// tw[ns - 1 + k] = exp(-2 pi i k / (2 ns)) for ns = 1, 2, .., 2048 (4095 entries),
+// then exp(-2 pi i t / L) for t < L (the odd table), from FP64 sincospi.
+__global__ void twiddle_kernel(float2* tw, int L_odd) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < kFftTwiddlesPow2) {
+    const int ns = 1 << (31 - __clz(e + 1));              // the largest power of two <= e + 1
+    const int k = e + 1 - ns;
+    double s, c;
+    sincospi(-static_cast<double>(k) / ns, &s, &c);
+    tw[e] = make_float2(static_cast<float>(c), static_cast<float>(s));
+  } else if (e < kFftTwiddlesPow2 + L_odd) {
+    const int t = e - kFftTwiddlesPow2;
+    double s, c;
+    sincospi(-2.0 * t / L_odd, &s, &c);
+    tw[e] = make_float2(static_cast<float>(c), static_cast<float>(s));
+  }
+}
+
+__global__ void fft_status_kernel(const uint8_t* roi_ok, uint8_t* status, int64_t n) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q < n) status[q] = (!roi_ok || roi_ok[q]) ? DIC_PT_OK : DIC_PT_NOT_IN_ROI;
+}
+
+size_t small_smem(int L, bool pow2) {
+  return sizeof(float2) * (2 * static_cast<size_t>(L) * L + (pow2 ? L - 1 : L));
+}
+
+int blocks_for(int64_t n, int per_sm) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t cap = static_cast<int64_t>(sms) * per_sm;
+  return static_cast<int>(n < cap ? (n > 0 ? n : 1) : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_twiddles(float2* tw, int L_odd, cudaStream_t s) {
+  const int n = kFftTwiddlesPow2 + L_odd;
+  twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, L_odd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fftcc_origins(const FftLevelArgs& a, cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(a.nx) * a.ny;
+  if (n == 0) return cudaSuccess;
+  fftcc_origins_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft_status(const uint8_t* roi_ok, uint8_t* status, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  fft_status_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(roi_ok, status, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mad(const MadArgs& a, cudaStream_t s) {
+  const int64_t n = static_cast<int64_t>(a.nx) * a.ny;
+  if (n == 0) return cudaSuccess;
+  mad_kernel<<<static_cast<unsigned>((n + 127) / 128), 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  const int L = a.L;
+  const bool pow2 = (L & (L - 1)) == 0;
+  if (L <= kFftSmallMax) {
+    const size_t smem = small_smem(L, pow2);
+    if (pow2) {
+      static const cudaError_t ok = cudaFuncSetAttribute(fftcc_small_kernel<true>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         static_cast<int>(small_smem(kFftSmallMax, true)));
+      if (ok != cudaSuccess) return ok;
+      const int per_sm = static_cast<int>(200 * 1024 / smem) < 8 ? static_cast<int>(200 * 1024 / smem) : 8;
+      fftcc_small_kernel<true><<<blocks_for(a.n, per_sm > 0 ? per_sm : 1), kSmallThreads, smem, s>>>(a);
+    } else {
+      static const cudaError_t ok = cudaFuncSetAttribute(fftcc_small_kernel<false>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         static_cast<int>(small_smem(kFftSmallMax, false)));
+      if (ok != cudaSuccess) return ok;
+      const int per_sm = static_cast<int>(200 * 1024 / smem) < 8 ? static_cast<int>(200 * 1024 / smem) : 8;
+      fftcc_small_kernel<false><<<blocks_for(a.n, per_sm > 0 ? per_sm : 1), kSmallThreads, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
+  // large windows: a power of two in [128, 4096] (checked by the caller)
+  static const cudaError_t ok1 = cudaFuncSetAttribute(fftcc_rows_fwd_kernel,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      static_cast<int>(2 * kLineElems * sizeof(float2)));
+  static const cudaError_t ok2 = cudaFuncSetAttribute(fftcc_pairs_kernel,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      static_cast<int>(4 * kLineElems * sizeof(float2)));
+  static const cudaError_t ok3 = cudaFuncSetAttribute(fftcc_rows_inv_kernel,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      static_cast<int>(2 * kLineElems * sizeof(float2)));
+  if (ok1 != cudaSuccess) return ok1;
+  if (ok2 != cudaSuccess) return ok2;
+  if (ok3 != cudaSuccess) return ok3;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(a.nonflat, 0, sizeof(int32_t) * 2 * a.n, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.norms, 0, sizeof(double) * 2 * a.n, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(a.keys, 0, sizeof(unsigned long long) * a.n, s)) != cudaSuccess) return e;
+  const unsigned nw = static_cast<unsigned>(a.n);
+  const int rows = kLineElems / L;
+  const size_t line_smem = 2 * kLineElems * sizeof(float2);
+  fftcc_rows_fwd_kernel<<<dim3(L / rows, nw), kLineThreads, line_smem, s>>>(a);
+  const int T = L / kTransposeTile;
+  fftcc_transpose_kernel<<<dim3(T * T, nw), kTransposeTile * 8, 0, s>>>(a);
+  const int units = kLineElems / L;
+  const int nunits = L / 2 + 1;
+  fftcc_pairs_kernel<<<dim3((nunits + units - 1) / units, nw), kLineThreads, 2 * line_smem, s>>>(a);
+  fftcc_transpose_kernel<<<dim3(T * T, nw), kTransposeTile * 8, 0, s>>>(a);
+  fftcc_rows_inv_kernel<<<dim3(L / rows, nw), kLineThreads, line_smem, s>>>(a);
+  fftcc_finish_kernel<<<(nw + 255) / 256, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dic

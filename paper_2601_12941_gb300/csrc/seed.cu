@@ -163,12 +163,19 @@ __global__ void seed_commit_kernel(SeedCommitArgs a) {
     if (a.roi_ok && !a.roi_ok[q]) continue;
     if (a.wave[q] >= 0) continue;
     a.wave[q] = 0;
+    double* p = a.p + static_cast<int64_t>(q) * a.nparams;
+    if (a.fft_u) {
+      for (int c = 0; c < a.nparams; ++c) p[c] = 0.0;
+      p[0] = floor(static_cast<double>(a.fft_u[q]) + 0.5);
+      p[1] = floor(static_cast<double>(a.fft_v[q]) + 0.5);
+      a.frontier0[count++] = q;
+      continue;
+    }
     const int best = a.best[s];
     if (best < 0) {
       a.status[q] = best == -2 ? DIC_PT_FLAT : DIC_PT_OUT_OF_BOUNDS;
       continue;
     }
-    double* p = a.p + static_cast<int64_t>(q) * a.nparams;
     for (int c = 0; c < a.nparams; ++c) p[c] = 0.0;
     p[0] = static_cast<double>(best % side - a.R);
     p[1] = static_cast<double>(best / side - a.R);
@@ -194,7 +201,7 @@ cudaError_t launch_seed_scores(const SeedArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_seed_commit(const SeedCommitArgs& a, cudaStream_t s) {
-  seed_best_kernel<<<a.n_seeds, 256, 0, s>>>(a);
+  if (!a.fft_u) seed_best_kernel<<<a.n_seeds, 256, 0, s>>>(a);
   seed_commit_kernel<<<1, 32, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -162,6 +162,7 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   if (shape_fn != DIC_RIGID && shape_fn != DIC_AFFINE && shape_fn != DIC_QUADRATIC)
     return sfail(DIC_EINVAL, "unknown shape function %d", shape_fn);
   if (params->precision != DIC_MIXED) return sfail(DIC_EINVAL, "only DIC_MIXED is available here");
+  if (params->init != DIC_INIT_SEARCH) return sfail(DIC_EINVAL, "only DIC_INIT_SEARCH is available here");
   if (params->max_iter < 1 || !(params->conv_threshold > 0.0) || !(params->zncc_min >= -1.0) ||
       !(params->zncc_min <= 1.0))
     return sfail(DIC_EINVAL, "invalid parameters");
@@ -247,7 +248,7 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   SCUDA(launch_seed_scores(SeedArgs{gref, gdef, W, H, subset_size, R, n_seeds, seed_xy, scores}, s),
         "seed search");
   SCUDA(launch_seed_commit(SeedCommitArgs{n_seeds, R, nparams, seed_q, scores, seed_best, out->p, out->status,
-                                          out->wave, front0, counters, nullptr},
+                                          out->wave, front0, counters, nullptr, nullptr, nullptr},
                            s),
         "seed commit");
 

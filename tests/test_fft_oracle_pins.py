@@ -65,6 +65,10 @@ def test_eq1_is_invariant_to_gain_and_offset_and_zero_on_flat_windows():
     g = RNG.uniform(0, 255, (16, 16))
     assert np.abs(F.fftcc(3.0 * f + 40.0, 0.5 * g - 7.0) - F.fftcc(f, g)).max() < 1e-12
     assert not F.fftcc(np.full((16, 16), 9.0), g).any()
+    # exactly zero for any size and either window (no transform noise gets through)
+    h = RNG.uniform(0, 255, (31, 31))
+    assert not F.fftcc(np.full((31, 31), 9.0), h).any() and not F.fftcc(h, np.full((31, 31), 0.3)).any()
+    assert F.peak(F.fftcc(h, np.full((31, 31), 0.3)))[:2] == (0.0, 0.0)
 
 
 @pytest.mark.parametrize("L,d", [(32, (5, -7)), (32, (-16, 15)), (64, (0, 0)), (21, (10, -10)), (21, (-3, 4))])
