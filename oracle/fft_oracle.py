@@ -31,7 +31,7 @@ Readings taken where the paper is silent (all of them, in one place):
      F and G the L x L DFTs of the mean-removed windows, the inverse carrying 1/L^2
      (by Parseval the denominator is ||F|| ||G|| / L^2). R is 1 at the
      shift of a circularly shifted copy, and unchanged by gain and offset of either
-     window; a flat window gives R = 0. (Dividing each frequency by its own |F| |G|,
+     window; a flat window (all its values equal) gives R = 0. (Dividing each frequency by its own |F| |G|,
      phase correlation, fails on smooth speckle inside hard-edged windows: the
      frequencies without speckle content carry the windows' edge leakage, which
      aligns at zero shift. Nor would its delta-like peak suit the Gaussian peak
@@ -87,11 +87,11 @@ def fftcc(f: np.ndarray, g: np.ndarray) -> np.ndarray:
     of two L x L windows, computed through their DFTs."""
     fb = np.asarray(f, dtype=np.float64)
     gb = np.asarray(g, dtype=np.float64)
-    fb = fb - fb.mean()                        # exactly 0 where a window is constant
+    if (fb == fb.flat[0]).all() or (gb == gb.flat[0]).all():
+        return np.zeros(fb.shape)              # a flat (constant) window: R = 0
+    fb = fb - fb.mean()
     gb = gb - gb.mean()
     den = math.sqrt(np.sum(fb * fb)) * math.sqrt(np.sum(gb * gb))
-    if den == 0:
-        return np.zeros(fb.shape)              # a flat window: R = 0
     F = np.fft.fft2(fb)
     G = np.fft.fft2(gb)
     return np.real(np.fft.ifft2(F * np.conj(G))) / den

@@ -213,6 +213,8 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       continue;
     }
     double sf = 0.0, sg = 0.0;
+    const float f00 = load_gray<float>(a.ref, o.x, o.y), g00 = load_gray<float>(a.def, o.z, o.w);
+    bool vf = false, vg = false;                         // a value differs from the first
     for (int e = tid; e < N; e += kSmallThreads) {
       const int y = e / L, x = e - y * L;
       const float f = load_gray<float>(a.ref, o.x + x, o.y + y);
@@ -220,7 +222,12 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       A[e] = make_float2(f, g);
       sf += f;
       sg += g;
+      vf |= f != f00;
+      vg |= g != g00;
     }
+    const int any_f = __syncthreads_or(vf);
+    const int any_g = __syncthreads_or(vg);
+    const bool flat = !any_f || !any_g;
     block_sum2(sf, sg, s_red);
     const float mf = static_cast<float>(sf / N), mg = static_cast<float>(sg / N);
     double qf = 0.0, qg = 0.0;
@@ -268,7 +275,6 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
     }
     best = block_max_key(best, s_key);
     if (tid == 0) {
-      const bool flat = !(qf > 0.0) || !(qg > 0.0);
       const int e = flat ? 0 : key_index(best);
       const int ky = e / L, kx = e - ky * L;
       float dx = static_cast<float>(shift_of_peak(kx, L)), dy = static_cast<float>(shift_of_peak(ky, L));
