@@ -303,10 +303,10 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_rows_fwd_kernel(FftccArgs 
   const int rows = kLineElems / L;                       // L >= 128: 1 .. 32 rows per block
   float2* P = reinterpret_cast<float2*>(smem_raw);
   float2* Q = P + kLineElems;
-  const int64_t w = blockIdx.y;
+  const int64_t w = blockIdx.x;
   const int4 o = a.org[w];
   if (!window_ok(o, L, a.W, a.H)) return;                // uniform: the whole block
-  const int y0 = blockIdx.x * rows;
+  const int y0 = blockIdx.y * rows;
   const float f00 = load_gray<float>(a.ref, o.x, o.y);
   const float g00 = load_gray<float>(a.def, o.z, o.w);
   bool vf = false, vg = false;
@@ -331,9 +331,9 @@ __global__ void __launch_bounds__(kTransposeTile * 8) fftcc_transpose_kernel(Fft
   __shared__ float2 t0[kTransposeTile][kTransposeTile + 1];
   __shared__ float2 t1[kTransposeTile][kTransposeTile + 1];
   const int L = a.L, T = L / kTransposeTile;
-  const int ti = blockIdx.x % T, tj = blockIdx.x / T;
+  const int ti = blockIdx.y % T, tj = blockIdx.y / T;
   if (ti > tj) return;
-  const int64_t w = blockIdx.y;
+  const int64_t w = blockIdx.x;
   if (!window_ok(a.org[w], L, a.W, a.H)) return;
   float2* base = a.work + w * static_cast<int64_t>(L) * L;
   const int tx = threadIdx.x & (kTransposeTile - 1), ty = threadIdx.x / kTransposeTile;   // 32 x 8
@@ -360,9 +360,9 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
   float2* P = reinterpret_cast<float2*>(smem_raw);
   float2* Q = P + 2 * kLineElems;
   __shared__ double s_red[2 * (kLineThreads / 32)];
-  const int64_t w = blockIdx.y;
+  const int64_t w = blockIdx.x;
   if (!window_ok(a.org[w], L, a.W, a.H)) return;
-  const int u0 = blockIdx.x * units;
+  const int u0 = blockIdx.y * units;
   const int nunits = L / 2 + 1;
   float2* base = a.work + w * static_cast<int64_t>(L) * L;
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
@@ -420,9 +420,9 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_rows_inv_kernel(FftccArgs 
   float2* P = reinterpret_cast<float2*>(smem_raw);
   float2* Q = P + kLineElems;
   __shared__ unsigned long long s_key[kLineThreads / 32];
-  const int64_t w = blockIdx.y;
+  const int64_t w = blockIdx.x;
   if (!window_ok(a.org[w], L, a.W, a.H)) return;
-  const int y0 = blockIdx.x * rows;
+  const int y0 = blockIdx.y * rows;
   const float2* src = a.work + w * static_cast<int64_t>(L) * L + static_cast<int64_t>(y0) * L;
   for (int e = threadIdx.x; e < rows * L; e += kLineThreads) P[e] = src[e];
   __syncthreads();
@@ -680,14 +680,14 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
   const unsigned nw = static_cast<unsigned>(a.n);
   const int rows = kLineElems / L;
   const size_t line_smem = 2 * kLineElems * sizeof(float2);
-  fftcc_rows_fwd_kernel<<<dim3(L / rows, nw), kLineThreads, line_smem, s>>>(a);
+  fftcc_rows_fwd_kernel<<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
   const int T = L / kTransposeTile;
-  fftcc_transpose_kernel<<<dim3(T * T, nw), kTransposeTile * 8, 0, s>>>(a);
+  fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
   const int units = kLineElems / L;
   const int nunits = L / 2 + 1;
-  fftcc_pairs_kernel<<<dim3((nunits + units - 1) / units, nw), kLineThreads, 2 * line_smem, s>>>(a);
-  fftcc_transpose_kernel<<<dim3(T * T, nw), kTransposeTile * 8, 0, s>>>(a);
-  fftcc_rows_inv_kernel<<<dim3(L / rows, nw), kLineThreads, line_smem, s>>>(a);
+  fftcc_pairs_kernel<<<dim3(nw, (nunits + units - 1) / units), kLineThreads, 2 * line_smem, s>>>(a);
+  fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
+  fftcc_rows_inv_kernel<<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
   fftcc_finish_kernel<<<(nw + 255) / 256, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
