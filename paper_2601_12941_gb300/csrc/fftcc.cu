@@ -86,15 +86,64 @@ __device__ __forceinline__ float gauss3(float rm, float r0, float rp) {
   return (lm - lp) / den;
 }
 
-// Radix-2 Stockham passes over `lines` lines of length L (a power of two): element
-// i of line l at p[l * ls + i * es]; ping-pong between p and q, the result in the
-// returned buffer. tw[ns - 1 + k] = exp(-2 pi i k / (2 ns)), k < ns.
+// exp(-2 pi i m / M) (conjugated for the inverse), 0 <= m < M, M a power of two
+// >= 2, from the nested table tw[ns - 1 + k] = exp(-2 pi i k / (2 ns)), k < ns.
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int m, int M, bool inv) {
+  const int h = M >> 1;
+  float2 w = m < h ? tw[h - 1 + m] : tw[m - 1];          // m >= h: the entry of m - h, negated
+  if (m >= h) {
+    w.x = -w.x;
+    w.y = -w.y;
+  }
+  if (inv) w.y = -w.y;
+  return w;
+}
+
+// Stockham passes (radix 4, then one radix-2 pass when log2 L is odd) over `lines`
+// lines of length L (a power of two): element i of line l at p[l * ls + i * es];
+// ping-pong between p and q, the result in the returned buffer. A pass of radix R
+// after sub-transforms of size ns takes butterfly j's inputs at j + r L / R,
+// twiddles them by exp(-2 pi i r (j mod ns) / (R ns)) and writes output r at
+// (j - j mod ns) R + j mod ns + r ns.
 __device__ float2* fft_lines(float2* p, float2* q, int L, int lines, int ls, int es, const float2* __restrict__ tw,
                              bool inv) {
-  const int half = L >> 1;
-  const int total = lines * half;
-  const int lg = __ffs(half) - 1;                         // log2(half)
-  for (int ns = 1; ns < L; ns <<= 1) {
+  int ns = 1;
+  const int quarter = L >> 2;
+  if (quarter > 0) {
+    const int lgq = __ffs(quarter) - 1;
+    const int total = lines * quarter;
+    for (; ns * 4 <= L; ns <<= 2) {
+      for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int l = t >> lgq, j = t & (quarter - 1);
+        const float2* in = p + l * ls;
+        float2* out = q + l * ls;
+        const int k = j & (ns - 1);
+        float2 v0 = in[j * es], v1 = in[(j + quarter) * es], v2 = in[(j + 2 * quarter) * es],
+               v3 = in[(j + 3 * quarter) * es];
+        if (ns > 1) {
+          const int M = ns << 2;
+          v1 = cmul(v1, twiddle(tw, k, M, inv));
+          v2 = cmul(v2, twiddle(tw, 2 * k, M, inv));
+          v3 = cmul(v3, twiddle(tw, 3 * k, M, inv));
+        }
+        const float2 a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = csub(v1, v3);
+        const float2 rot = inv ? make_float2(-a3.y, a3.x) : make_float2(a3.y, -a3.x);   // +-i a3
+        const int d = ((j - k) << 2) + k;
+        out[d * es] = cadd(a0, a2);
+        out[(d + ns) * es] = cadd(a1, rot);
+        out[(d + 2 * ns) * es] = csub(a0, a2);
+        out[(d + 3 * ns) * es] = csub(a1, rot);
+      }
+      __syncthreads();
+      float2* t = p;
+      p = q;
+      q = t;
+    }
+  }
+  if (ns < L) {                                           // one radix-2 pass, ns = L / 2
+    const int half = L >> 1;
+    const int lg = __ffs(half) - 1;
+    const int total = lines * half;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const int l = t >> lg, j = t & (half - 1);
       const float2* in = p + l * ls;
@@ -116,26 +165,56 @@ __device__ float2* fft_lines(float2* p, float2* q, int L, int lines, int ls, int
   return p;
 }
 
-// Direct DFT of `lines` lines of odd length L from p into q (same layout);
-// twl[t] = exp(-2 pi i t / L).
-__device__ void dft_lines(const float2* p, float2* q, int L, int lines, int ls, int es, const float2* twl,
-                          bool inv) {
-  const int total = lines * L;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int l = t / L, k = t - l * L;
-    const float2* in = p + l * ls;
-    float ax = 0.f, ay = 0.f;
-    int idx = 0;
+// acc += p q (complex)
+__device__ __forceinline__ void cmac(float2& acc, float2 p, float2 q) {
+  acc.x = fmaf(p.x, q.x, fmaf(-p.y, q.y, acc.x));
+  acc.y = fmaf(p.x, q.y, fmaf(p.y, q.x, acc.y));
+}
+
+// One pass of the 2-D DFT of odd side L as a complex matrix product with the DFT
+// matrix Wm[x][k] = exp(-2 pi i x k / L) (symmetric): along rows OUT = IN Wm, along
+// columns OUT = Wm IN; INV uses conj(Wm). Each thread accumulates a 2 x 2 tile of
+// OUT over the L terms (4 complex loads for 4 complex multiply-adds).
+template <bool ROWS, bool INV>
+__device__ void dft_matmul(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ Wm,
+                           int L) {
+  const int nt = (L + 1) >> 1;
+  for (int t = threadIdx.x; t < nt * nt; t += blockDim.x) {
+    const int r0 = (t / nt) * 2, c0 = (t - (t / nt) * nt) * 2;
+    const int r1 = min(r0 + 1, L - 1), c1 = min(c0 + 1, L - 1);
+    float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
     for (int x = 0; x < L; ++x) {
-      const float2 v = in[x * es];
-      const float2 w = twl[idx];
-      const float wy = inv ? -w.y : w.y;
-      ax = fmaf(v.x, w.x, fmaf(-v.y, wy, ax));
-      ay = fmaf(v.x, wy, fmaf(v.y, w.x, ay));
-      idx += k;
-      if (idx >= L) idx -= L;
+      float2 p0, p1, q0, q1;
+      if (ROWS) {
+        p0 = in[r0 * L + x];
+        p1 = in[r1 * L + x];
+        q0 = Wm[x * L + c0];
+        q1 = Wm[x * L + c1];
+        if (INV) {
+          q0.y = -q0.y;
+          q1.y = -q1.y;
+        }
+      } else {
+        p0 = Wm[r0 * L + x];
+        p1 = Wm[r1 * L + x];
+        q0 = in[x * L + c0];
+        q1 = in[x * L + c1];
+        if (INV) {
+          p0.y = -p0.y;
+          p1.y = -p1.y;
+        }
+      }
+      cmac(a00, p0, q0);
+      cmac(a01, p0, q1);
+      cmac(a10, p1, q0);
+      cmac(a11, p1, q1);
     }
-    q[l * ls + k * es] = make_float2(ax, ay);
+    out[r0 * L + c0] = a00;
+    if (c0 + 1 < L) out[r0 * L + c0 + 1] = a01;
+    if (r0 + 1 < L) {
+      out[(r0 + 1) * L + c0] = a10;
+      if (c0 + 1 < L) out[(r0 + 1) * L + c0 + 1] = a11;
+    }
   }
   __syncthreads();
 }
@@ -192,14 +271,20 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
   const int L = a.L, N = L * L;
   float2* A = reinterpret_cast<float2*>(smem_raw);
   float2* B = A + N;
-  float2* tws = B + N;                                   // L - 1 (power of two) or L (odd) twiddles
+  float2* tws = B + N;                                   // L - 1 twiddles (power of two) or the L x L DFT matrix
   __shared__ double s_red[2 * (kSmallThreads / 32)];
   __shared__ unsigned long long s_key[kSmallThreads / 32];
   const int tid = threadIdx.x;
   // the nested power-of-two table: stage ns <= L/2 reads tw_pow2[ns - 1 + k], k < ns,
   // so the block keeps entries 0 .. L - 2
-  const int ntw = POW2 ? L - 1 : L;
-  for (int e = tid; e < ntw; e += kSmallThreads) tws[e] = POW2 ? a.tw_pow2[e] : a.tw_odd[e];
+  if (POW2) {
+    for (int e = tid; e < L - 1; e += kSmallThreads) tws[e] = a.tw_pow2[e];
+  } else {
+    for (int e = tid; e < N; e += kSmallThreads) {
+      const int x = e / L, k = e - x * L;
+      tws[e] = a.tw_odd[(x * k) % L];
+    }
+  }
   __syncthreads();
 
   for (int64_t w = blockIdx.x; w < a.n; w += gridDim.x) {
@@ -247,8 +332,8 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       Y = X == A ? B : A;
       X = fft_lines(X, Y, L, L, 1, L, tws, false);       // columns
     } else {
-      dft_lines(A, B, L, L, L, 1, tws, false);
-      dft_lines(B, A, L, L, 1, L, tws, false);
+      dft_matmul<true, false>(A, B, tws, L);
+      dft_matmul<false, false>(B, A, tws, L);
       X = A;
     }
     Y = X == A ? B : A;
@@ -264,8 +349,8 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       float2* S2 = R == A ? B : A;
       R = fft_lines(R, S2, L, L, 1, L, tws, true);
     } else {
-      dft_lines(Y, X, L, L, L, 1, tws, true);
-      dft_lines(X, Y, L, L, 1, L, tws, true);
+      dft_matmul<true, true>(Y, X, tws, L);
+      dft_matmul<false, true>(X, Y, tws, L);
       R = Y;
     }
     unsigned long long best = 0ull;
@@ -355,10 +440,10 @@ __global__ void __launch_bounds__(kTransposeTile * 8) fftcc_transpose_kernel(Fft
 __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.L;
-  const int units = kLineElems / L;                      // each unit holds 2 lines: 2 * units * L <= 8192
+  const int units = L <= kLineElems / 2 ? kLineElems / 2 / L : 1;   // 2 lines each: 4096 elements (8192 at L = 4096)
   const int lines = 2 * units;
   float2* P = reinterpret_cast<float2*>(smem_raw);
-  float2* Q = P + 2 * kLineElems;
+  float2* Q = P + lines * L;
   __shared__ double s_red[2 * (kLineThreads / 32)];
   const int64_t w = blockIdx.x;
   if (!window_ok(a.org[w], L, a.W, a.H)) return;
@@ -598,7 +683,7 @@ __global__ void fft_status_kernel(const uint8_t* roi_ok, uint8_t* status, int64_
 }
 
 size_t small_smem(int L, bool pow2) {
-  return sizeof(float2) * (2 * static_cast<size_t>(L) * L + (pow2 ? L - 1 : L));
+  return sizeof(float2) * (2 * static_cast<size_t>(L) * L + (pow2 ? L - 1 : static_cast<size_t>(L) * L));
 }
 
 int blocks_for(int64_t n, int per_sm) {
@@ -683,9 +768,10 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
   fftcc_rows_fwd_kernel<<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
   const int T = L / kTransposeTile;
   fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
-  const int units = kLineElems / L;
+  const int units = L <= kLineElems / 2 ? kLineElems / 2 / L : 1;
   const int nunits = L / 2 + 1;
-  fftcc_pairs_kernel<<<dim3(nw, (nunits + units - 1) / units), kLineThreads, 2 * line_smem, s>>>(a);
+  const size_t pair_smem = 2 * sizeof(float2) * 2 * units * L;
+  fftcc_pairs_kernel<<<dim3(nw, (nunits + units - 1) / units), kLineThreads, pair_smem, s>>>(a);
   fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
   fftcc_rows_inv_kernel<<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
   fftcc_finish_kernel<<<(nw + 255) / 256, 256, 0, s>>>(a);
