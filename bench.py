@@ -287,7 +287,7 @@ def run_ours(args):
     if not args.no_strain:
         out["strain"] = strain_leg(c, w, stream)
     if not args.no_fft:
-        out["fft_init"] = fft_leg(ref, dfm, stream)
+        out["fft_init"] = fft_leg(ref, dfm, stream, reps=args.fft_reps, kernel_reps=args.fft_kernel_reps)
     if not args.no_e2e:
         out["e2e"] = e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_ranks)
     c.close()
@@ -353,20 +353,24 @@ def strain_leg(c, w, stream, window=9, basis="biquadratic", measure="green_lagra
                          "peak_note": note, "algorithmic_bytes_per_point": bytes_per_point}}
 
 
-def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=1000, reps=3):
+def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel_reps=3):
     """Multi-window FFT initialiser (Sec. 2.2, Eq. 1; MAD) on the 1 Gpx pair with the
     SEM study's settings (Sec. 4): subset 31, step 15, maximum displacement 2000 px
     (windows 2048 .. 32, then 31), a 1000 px border outside the ROI, Gaussian
     sub-pixel fit. The last level (one 31 x 31 window per grid point, direct DFT) is
-    the dominant kernel: algorithmic FLOPs per window 32 S^3 (forward and inverse
-    2-D DFT, 4 S^3 complex multiply-adds); it is timed alone through
-    dic_fftcc_windows on the same number of windows."""
+    the dominant kernel: algorithmic FLOPs per window 22 S^3 + 2 S^2 (the forward 2-D
+    DFT, 2 S^3 complex multiply-adds of 8 FLOPs; the inverse of the Hermitian cross
+    power, (S+1)/2 rows of S^2 complex multiply-adds and a real column pass of
+    S^2 (S-1)/2 two-FMA terms); it is timed alone through dic_fftcc_windows on the
+    same number of windows."""
     import torch
 
     import paper_2601_12941_gb300 as P
     from paper_2601_12941_gb300 import binding as B
 
     H, W = ref.shape
+    if border is None:
+        border = int(round(1000 * W / 32768))             # the SEM study's 1000 px at 32768 px
     roi = torch.zeros((H, W), dtype=torch.uint8, device="cuda")
     roi[border:H - border, border:W - border] = 1
     c = P.Correlation(ref, dfm, roi, S, step, "affine")
@@ -393,9 +397,10 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=1000, reps=3):
     org = org.contiguous()
     n = org.shape[0]
     u, v, pk = (torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3))
-    B.dic_fftcc_windows(c.h, S, org, True, u, v, pk, stream.cuda_stream)
+    if kernel_reps > 0:
+        B.dic_fftcc_windows(c.h, S, org, True, u, v, pk, stream.cuda_stream)
     kms = []
-    for _ in range(reps):
+    for _ in range(kernel_reps):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -403,8 +408,8 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=1000, reps=3):
         b.record(stream)
         b.synchronize()
         kms.append(a.elapsed_time(b))
-    k = float(np.median(kms))
-    flops = 32.0 * S ** 3 * n
+    k = float(np.median(kms)) if kms else float("nan")
+    flops = (22.0 * S ** 3 + 2.0 * S ** 2) * n
     achieved = flops / (k / 1e3) / 1e12
     levels = g["windows"]
     launches = 1 + 3 * len(levels) + 5 * sum(1 for L in levels if L > 64)   # origins, fftcc (6 when > 64 px), MAD; status
@@ -417,7 +422,7 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=1000, reps=3):
             "last_level_ms": k, "last_level_share": k / t,
             "roofline": {"bound": "alu", "kernel": "fftcc_small_kernel<odd> (direct DFT, one window per block)",
                          "achieved": achieved, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak_tflops(), "algorithmic_flops_per_window": 32 * S ** 3,
+                         "frac": achieved / fp32_peak_tflops(), "algorithmic_flops_per_window": 22 * S ** 3 + 2 * S ** 2,
                          "peak_note": "FP32 peak from 152 SMs x 128 lanes x 2 x 2070 MHz"}}
 
 
@@ -632,6 +637,23 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_fft_only(args):
+    """The FFT initialiser leg alone on the synthetic pair of --size (profiling)."""
+    import torch
+
+    import synth
+    from synth import workloads as wl
+
+    w = wl.gigapixel_u8(args.size)
+    ref = torch.empty((w.height, w.width), dtype=torch.uint8, device="cuda")
+    dfm = torch.empty_like(ref)
+    synth.render_gpu(w.ref, ref)
+    synth.render_gpu(w.deformed, dfm)
+    torch.cuda.synchronize()
+    out = fft_leg(ref, dfm, torch.cuda.Stream(), reps=args.fft_reps, kernel_reps=args.fft_kernel_reps)
+    print(json.dumps({"fft_init": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -644,6 +666,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-strain", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
+    ap.add_argument("--fft-only", action="store_true",
+                    help="run only the FFT initialiser leg on the pair of --size (profiling)")
+    ap.add_argument("--fft-reps", type=int, default=3, help="timed fields of the FFT leg (after one warm-up)")
+    ap.add_argument("--fft-kernel-reps", type=int, default=3,
+                    help="timed runs of the last level alone (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-jobs", type=int, default=40,
                     help="jobs in the serving stream (0: skip the serving leg)")
@@ -654,6 +681,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.fft_only:
+        run_fft_only(args)
     else:
         run_ours(args)
 

@@ -177,9 +177,9 @@ __device__ __forceinline__ void cmac(float2& acc, float2 p, float2 q) {
 // OUT over the L terms (4 complex loads for 4 complex multiply-adds).
 template <bool ROWS, bool INV>
 __device__ void dft_matmul(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ Wm,
-                           int L) {
-  const int nt = (L + 1) >> 1;
-  for (int t = threadIdx.x; t < nt * nt; t += blockDim.x) {
+                           int L, int rows_out) {
+  const int nt = (L + 1) >> 1, ntr = (rows_out + 1) >> 1;
+  for (int t = threadIdx.x; t < ntr * nt; t += blockDim.x) {
     const int r0 = (t / nt) * 2, c0 = (t - (t / nt) * nt) * 2;
     const int r1 = min(r0 + 1, L - 1), c1 = min(c0 + 1, L - 1);
     float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
@@ -211,9 +211,39 @@ __device__ void dft_matmul(const float2* __restrict__ in, float2* __restrict__ o
     }
     out[r0 * L + c0] = a00;
     if (c0 + 1 < L) out[r0 * L + c0 + 1] = a01;
-    if (r0 + 1 < L) {
+    if (r0 + 1 < rows_out) {
       out[(r0 + 1) * L + c0] = a10;
       if (c0 + 1 < L) out[(r0 + 1) * L + c0 + 1] = a11;
+    }
+  }
+  __syncthreads();
+}
+
+// The last inverse pass for a Hermitian spectrum: T holds the inverse row transforms
+// of rows ky = 0 .. (L-1)/2 only (the others are their conjugates, T[-ky] = conj T[ky]),
+// and R[y][x] = Re T[0][x] + 2 sum_{ky >= 1} Re(T[ky][x] exp(2 pi i ky y / L)), the real
+// part only (R is real). 2 x 2 tiles of R; R is written as the .x of out.
+__device__ void dft_inverse_columns_real(const float2* __restrict__ T, float2* __restrict__ out,
+                                         const float2* __restrict__ Wm, int L) {
+  const int nt = (L + 1) >> 1, kh = (L + 1) >> 1;
+  for (int t = threadIdx.x; t < nt * nt; t += blockDim.x) {
+    const int r0 = (t / nt) * 2, c0 = (t - (t / nt) * nt) * 2;
+    const int r1 = min(r0 + 1, L - 1), c1 = min(c0 + 1, L - 1);
+    float a00 = 0.5f * T[c0].x, a01 = 0.5f * T[c1].x, a10 = a00, a11 = a01;   // the ky = 0 term, halved
+    for (int ky = 1; ky < kh; ++ky) {
+      const float2 p0 = Wm[r0 * L + ky], p1 = Wm[r1 * L + ky];                 // exp(-2 pi i ky y / L)
+      const float2 q0 = T[ky * L + c0], q1 = T[ky * L + c1];
+      // Re(q conj(p)) = q.x p.x + q.y p.y
+      a00 = fmaf(q0.x, p0.x, fmaf(q0.y, p0.y, a00));
+      a01 = fmaf(q1.x, p0.x, fmaf(q1.y, p0.y, a01));
+      a10 = fmaf(q0.x, p1.x, fmaf(q0.y, p1.y, a10));
+      a11 = fmaf(q1.x, p1.x, fmaf(q1.y, p1.y, a11));
+    }
+    out[r0 * L + c0].x = 2.f * a00;
+    if (c0 + 1 < L) out[r0 * L + c0 + 1].x = 2.f * a01;
+    if (r0 + 1 < L) {
+      out[(r0 + 1) * L + c0].x = 2.f * a10;
+      if (c0 + 1 < L) out[(r0 + 1) * L + c0 + 1].x = 2.f * a11;
     }
   }
   __syncthreads();
@@ -297,7 +327,9 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       }
       continue;
     }
-    double sf = 0.0, sg = 0.0;
+    // per-thread partial sums in FP32 (a few values each), the block reduction in FP64:
+    // FP64 arithmetic per element would bind the kernel on this GPU's FP64 pipe
+    float pf = 0.f, pg = 0.f;
     const float f00 = load_gray<float>(a.ref, o.x, o.y), g00 = load_gray<float>(a.def, o.z, o.w);
     bool vf = false, vg = false;                         // a value differs from the first
     for (int e = tid; e < N; e += kSmallThreads) {
@@ -305,25 +337,27 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       const float f = load_gray<float>(a.ref, o.x + x, o.y + y);
       const float g = load_gray<float>(a.def, o.z + x, o.w + y);
       A[e] = make_float2(f, g);
-      sf += f;
-      sg += g;
+      pf += f;
+      pg += g;
       vf |= f != f00;
       vg |= g != g00;
     }
+    double sf = pf, sg = pg;
     const int any_f = __syncthreads_or(vf);
     const int any_g = __syncthreads_or(vg);
     const bool flat = !any_f || !any_g;
     block_sum2(sf, sg, s_red);
     const float mf = static_cast<float>(sf / N), mg = static_cast<float>(sg / N);
-    double qf = 0.0, qg = 0.0;
+    float pqf = 0.f, pqg = 0.f;
     for (int e = tid; e < N; e += kSmallThreads) {
       float2 v = A[e];
       v.x -= mf;
       v.y -= mg;
       A[e] = v;
-      qf += static_cast<double>(v.x) * v.x;
-      qg += static_cast<double>(v.y) * v.y;
+      pqf = fmaf(v.x, v.x, pqf);
+      pqg = fmaf(v.y, v.y, pqg);
     }
+    double qf = pqf, qg = pqg;
     block_sum2(qf, qg, s_red);                           // (its barriers also order the writes above)
     float2* X;
     float2* Y;
@@ -332,8 +366,8 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       Y = X == A ? B : A;
       X = fft_lines(X, Y, L, L, 1, L, tws, false);       // columns
     } else {
-      dft_matmul<true, false>(A, B, tws, L);
-      dft_matmul<false, false>(B, A, tws, L);
+      dft_matmul<true, false>(A, B, tws, L, L);
+      dft_matmul<false, false>(B, A, tws, L, L);
       X = A;
     }
     Y = X == A ? B : A;
@@ -349,8 +383,8 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       float2* S2 = R == A ? B : A;
       R = fft_lines(R, S2, L, L, 1, L, tws, true);
     } else {
-      dft_matmul<true, true>(Y, X, tws, L);
-      dft_matmul<false, true>(X, Y, tws, L);
+      dft_matmul<true, true>(Y, X, tws, L, (L + 1) / 2);   // rows ky <= (L-1)/2 of the Hermitian half
+      dft_inverse_columns_real(X, Y, tws, L);
       R = Y;
     }
     unsigned long long best = 0ull;
@@ -463,7 +497,7 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
   __syncthreads();
   float2* X = fft_lines(P, Q, L, lines, L, 1, a.tw_pow2, false);
   float2* Y = X == P ? Q : P;
-  double nf = 0.0, ng = 0.0;
+  float pnf = 0.f, png = 0.f;                             // FP32 per thread, FP64 across the block
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
     const int line = e / L, ky = e - line * L;
     const int u = u0 + (line >> 1);
@@ -477,10 +511,11 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
     if (count) {
       const float fx = 0.5f * (zk.x + zm.x), fy = 0.5f * (zk.y - zm.y);   // F(k)
       const float gx = 0.5f * (zk.y + zm.y), gy = 0.5f * (zm.x - zk.x);   // G(k)
-      nf += static_cast<double>(fx) * fx + static_cast<double>(fy) * fy;
-      ng += static_cast<double>(gx) * gx + static_cast<double>(gy) * gy;
+      pnf = fmaf(fx, fx, fmaf(fy, fy, pnf));
+      png = fmaf(gx, gx, fmaf(gy, gy, png));
     }
   }
+  double nf = pnf, ng = png;
   block_sum2(nf, ng, s_red);
   if (threadIdx.x == 0) {
     atomicAdd(&a.norms[2 * w], nf);
