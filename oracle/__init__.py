@@ -10,4 +10,4 @@ from .dic_oracle import (AFFINE, BICUBIC, BSPLINE3, DEFAULT_PARAMS, GAUSS_NEWTON
                          QUADRATIC, RIGID, SSD, ZNSSD, Plane,
                          ReferenceSubset, bspline_coefficients, correlate, correlate_sequence, grid, icgn,
                          interpolate, keys, seed_search)
-from . import fft_oracle, strain_oracle  # noqa: F401
+from . import fft_oracle, incremental_oracle, strain_oracle  # noqa: F401
