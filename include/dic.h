@@ -394,6 +394,47 @@ int dic_fftcc_windows(dic_handle* h, int32_t window, int64_t n_windows, const in
 int dic_mad_filter(const float* u, const float* v, const uint8_t* valid, int32_t nx, int32_t ny, double tau,
                    double eps, float* u_out, float* v_out, uint8_t* replaced, void* cuda_stream);
 
+/* ---- incremental reference updating (planned in Sec. 6) --------------------- */
+/* For sequences with large strains, after Pan et al. 2012: the reference image
+ * evolves through the sequence. Every grid point of the first reference carries its
+ * warp from the first frame; a frame correlated against the current reference gives
+ * the point's total warp: x_r = X + (u_a, v_a) is its current position, the grid
+ * point q nearest to x_r (per axis, ties to the lower index) must be accepted in the
+ * frame, q's warp re-expanded at x_r - x_q gives (d, A_i), and
+ *     (u, v) = (u_a, v_a) + d,     I + A = (I + A_i)(I + A_a)
+ * with A = [[p2, p3], [p4, p5]] of Eq. 5 (A = 0 for the rigid shape function). The
+ * first reference is the one of the last dic_correlate (or dic_set_reference, or
+ * dic_set_subsets); until the first update the totals are the frame's own warps. */
+typedef struct {
+  int64_t n_points;          /* grid points, as in dic_results                       */
+  int32_t nx, ny;
+  int32_t n_params;
+  int32_t n_updates;         /* reference updates since the first reference          */
+  const double* u;           /* [n_points] total displacement, px (device)           */
+  const double* v;
+  const double* p;           /* [n_points][n_params] total warp; p2..p5 composed     */
+  const uint8_t* status;     /* [n_points] DIC_PT_OK, DIC_PT_NOT_REACHED (no total   */
+                             /* this frame, or lost at an earlier update), or        */
+                             /* DIC_PT_NOT_IN_ROI                                    */
+} dic_total_results;
+
+/* Makes the handle's current deformed image the reference for the following frames:
+ * the totals of the last correlation become the accumulated warps (points without
+ * one drop out for good), the deformed image and its coefficients become the
+ * reference's (a borrowed device image must stay valid while it is the reference),
+ * and the next dic_correlate_sequence starts every in-ROI point from the identity
+ * warp in wave 0 (dic_get_results shows that start until then). Rigid and affine
+ * shape functions only: two quadratic warps of Eq. 5 do not compose into one.
+ * Errors: DIC_EINVAL (no handle, quadratic), DIC_ESTATE (no correlation yet),
+ * DIC_ENOMEM, DIC_ECUDA. */
+int dic_update_reference(dic_handle* h, void* cuda_stream);
+
+/* Computes, on cuda_stream, the total warps of the last correlated frame from the
+ * first reference; device arrays owned by the handle, valid until its next
+ * correlation, update or destroy. Errors: DIC_EINVAL, DIC_ESTATE, DIC_ENOMEM,
+ * DIC_ECUDA. */
+int dic_get_total_results(dic_handle* h, dic_total_results* out, void* cuda_stream);
+
 /* ---- allocation-free correlation (the paper has no counterpart) ----------
  *
  * For callers that must not allocate device memory when they correlate: code

@@ -42,7 +42,7 @@ EXPORTS = ("dic_default_params", "dic_create", "dic_set_params", "dic_get_params
            "dic_correlate_static", "dic_correlate_sequence", "dic_set_subsets",
            "dic_estimate_device_bytes", "dic_estimate_regrid_bytes", "dic_get_device_bytes",
            "dic_strain_field", "dic_fft_default_params", "dic_fft_field", "dic_get_fft_results",
-           "dic_fftcc_windows", "dic_mad_filter")
+           "dic_fftcc_windows", "dic_mad_filter", "dic_update_reference", "dic_get_total_results")
 
 
 class DicImage(ctypes.Structure):
@@ -59,6 +59,13 @@ class DicParams(ctypes.Structure):
                 ("optimizer", ctypes.c_int32), ("init", ctypes.c_int32),
                 ("max_displacement", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("mad_tau", ctypes.c_double), ("mad_eps", ctypes.c_double)]
+
+
+class DicTotalResults(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("n_params", ctypes.c_int32), ("n_updates", ctypes.c_int32),
+                ("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("p", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
 
 
 class DicFftParams(ctypes.Structure):
@@ -165,6 +172,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.c_int32, ctypes.c_int32, P(DicStrainOutputs), vp]
     lib.dic_strain_field.restype = ctypes.c_int
     lib.dic_get_device_bytes.argtypes = [vp, P(ctypes.c_int64)]
+    lib.dic_update_reference.argtypes = [vp, vp]
+    lib.dic_update_reference.restype = ctypes.c_int
+    lib.dic_get_total_results.argtypes = [vp, P(DicTotalResults), vp]
+    lib.dic_get_total_results.restype = ctypes.c_int
     lib.dic_fft_default_params.argtypes = []
     lib.dic_fft_default_params.restype = DicFftParams
     lib.dic_fft_field.argtypes = [vp, P(DicFftParams), vp]
@@ -415,6 +426,27 @@ def dic_strain_field(u, v, status, nx, ny, subset_step, window, basis, measure, 
                                    ctypes.byref(o), ctypes.c_void_p(stream_ptr)))
 
 
+def dic_update_reference(h, stream_ptr: int = 0):
+    """The current deformed image becomes the reference (incremental updating)."""
+    _check(load().dic_update_reference(h, ctypes.c_void_p(stream_ptr)))
+
+
+def dic_get_total_results(h, on_device: bool = False, stream_ptr: int = 0) -> dict:
+    """Total warps from the first reference to the last frame: u, v, p, status (CUDA
+    tensors viewing the handle's arrays, or numpy copies)."""
+    import torch
+
+    r = DicTotalResults()
+    _check(load().dic_get_total_results(h, ctypes.byref(r), ctypes.c_void_p(stream_ptr)))
+    n, npar = r.n_points, r.n_params
+    out = dict(n_points=n, nx=r.nx, ny=r.ny, n_params=npar, n_updates=r.n_updates)
+    for name, dt, shape in (("u", np.float64, (n,)), ("v", np.float64, (n,)), ("p", np.float64, (n, npar)),
+                            ("status", np.uint8, (n,))):
+        t = torch.as_tensor(_DeviceArray(getattr(r, name), shape, np.dtype(dt).str), device="cuda")
+        out[name] = t if on_device else t.cpu().numpy()
+    return out
+
+
 def dic_fft_default_params() -> DicFftParams:
     return load().dic_fft_default_params()
 
@@ -542,6 +574,15 @@ class Correlation:
 
     def timing(self):
         return dic_get_timing(self.h)
+
+    def update_reference(self, stream_ptr: int = 0):
+        """Incremental updating: the current deformed image becomes the reference."""
+        dic_update_reference(self.h, stream_ptr)
+        return self
+
+    def totals(self, on_device=False, stream_ptr: int = 0) -> dict:
+        """Total warps from the first reference to the last correlated frame."""
+        return dic_get_total_results(self.h, on_device, stream_ptr)
 
     def fft_field(self, max_displacement=32, subpixel=True, mad_tau=3.0, mad_eps=0.5, stream_ptr: int = 0) -> dict:
         """The multi-window FFT initialiser alone (the paper's MULTIWINDOW method)."""

@@ -164,6 +164,19 @@ struct dic_handle {
   bool has_fft = false;
   int fft_levels = 0;
   int fft_window[kFftMaxLevels] = {};
+  // incremental reference updating: accumulated warps from the first reference, and
+  // the total warps of the last frame
+  double* acc_u = nullptr;
+  double* acc_v = nullptr;
+  double* acc_A = nullptr;
+  uint8_t* acc_ok = nullptr;
+  double* tot_u = nullptr;
+  double* tot_v = nullptr;
+  double* tot_p = nullptr;
+  uint8_t* tot_status = nullptr;
+  int64_t inc_cap = 0, tot_p_cap = 0;
+  bool acc_identity = true;
+  int n_updates = 0;
 };
 
 namespace {
@@ -547,6 +560,8 @@ int configure_subsets(dic_handle* h, const dic_image* roi, int32_t subset_size, 
   h->has_results = false;
   h->n_waves = 0;
   h->n_accepted = 0;
+  h->acc_identity = true;
+  h->n_updates = 0;
   h->S = subset_size;
   h->r = (subset_size - 1) / 2;
   h->step = subset_step;
@@ -625,6 +640,7 @@ int64_t footprint(const dic_handle* cur, const dic_image* ref, const dic_image* 
     b += fft_bytes_for(cur, static_cast<int>(W), static_cast<int>(H), S, n, fft_D);
   else if (cur->fft_tw)
     b += fft_bytes_for(cur, static_cast<int>(W), static_cast<int>(H), S, 0, -1);
+  if (cur->inc_cap > 0) b += cur->inc_cap * (8 + 8 + 32 + 1 + 8 + 8 + 1) + 8 * cur->tot_p_cap;  // kept until used
   return b;
 }
 
@@ -907,6 +923,47 @@ int run_fft(dic_handle* h, int D, int subpixel, double tau, double eps, cudaStre
   return DIC_OK;
 }
 
+int ensure_increments(dic_handle* h) {
+  const int64_t n = h->npts, np = h->npts * h->nparams;
+  if (h->inc_cap >= n && h->tot_p_cap >= np) return DIC_OK;
+  int rc;
+  h->inc_cap = 0;
+  h->tot_p_cap = 0;
+  if ((rc = regrow(h, &h->acc_u, n, "accumulated warps")) || (rc = regrow(h, &h->acc_v, n, "accumulated warps")) ||
+      (rc = regrow(h, &h->acc_A, 4 * n, "accumulated warps")) ||
+      (rc = regrow(h, &h->acc_ok, n, "accumulated warps")) || (rc = regrow(h, &h->tot_u, n, "total warps")) ||
+      (rc = regrow(h, &h->tot_v, n, "total warps")) || (rc = regrow(h, &h->tot_p, np, "total warps")) ||
+      (rc = regrow(h, &h->tot_status, n, "total warps")))
+    return rc;
+  h->inc_cap = n;
+  h->tot_p_cap = np;
+  return DIC_OK;
+}
+
+int run_totals(dic_handle* h, int update, cudaStream_t s) {
+  TotalArgs a{};
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.r = h->r;
+  a.step = h->step;
+  a.nparams = h->nparams;
+  a.roi_ok = h->roi_ok;
+  a.status = h->status;
+  a.p = h->p;
+  a.identity = h->acc_identity ? 1 : 0;
+  a.acc_u = h->acc_u;
+  a.acc_v = h->acc_v;
+  a.acc_A = h->acc_A;
+  a.acc_ok = h->acc_ok;
+  a.tot_u = h->tot_u;
+  a.tot_v = h->tot_v;
+  a.tot_p = h->tot_p;
+  a.tot_status = h->tot_status;
+  a.update = update;
+  DIC_CUDA(launch_totals(a, s), "total warps");
+  return DIC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1049,7 +1106,14 @@ static int replace_image(dic_handle* h, const dic_image* im, bool is_ref) {
   return rc;
 }
 
-int dic_set_reference(dic_handle* h, const dic_image* ref) { return replace_image(h, ref, true); }
+int dic_set_reference(dic_handle* h, const dic_image* ref) {
+  const int rc = replace_image(h, ref, true);
+  if (rc == DIC_OK) {                // a new first reference: no accumulated warps
+    h->acc_identity = true;
+    h->n_updates = 0;
+  }
+  return rc;
+}
 int dic_set_deformed(dic_handle* h, const dic_image* def) { return replace_image(h, def, false); }
 
 int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void* cuda_stream) {
@@ -1106,6 +1170,8 @@ int dic_correlate(dic_handle* h, const int32_t* seeds_xy, int32_t n_seeds, void*
     h->seed_cap = n_seeds;
   }
   const bool fft_init = h->prm.init == DIC_INIT_FFT;
+  h->acc_identity = true;            // correlating from seeds: the reference is the first one
+  h->n_updates = 0;
   if (!fft_init && n_seeds * side * side > h->score_cap) {
     hfree(h, h->seed_scores);
     h->score_cap = 0;
@@ -1366,6 +1432,56 @@ int dic_mad_filter(const float* u, const float* v, const uint8_t* valid, int32_t
   if (!(eps >= 0.0) || tau != tau) return fail(DIC_EINVAL, "tau/eps invalid");
   MadArgs a{u, v, valid, nx, ny, tau, eps, u_out, v_out, replaced};
   DIC_CUDA(launch_mad(a, static_cast<cudaStream_t>(cuda_stream)), "outlier removal");
+  return DIC_OK;
+}
+
+int dic_update_reference(dic_handle* h, void* cuda_stream) {
+  if (!h) return fail(DIC_EINVAL, "handle is NULL");
+  g_last_error.clear();
+  if (!h->has_results) return fail(DIC_ESTATE, "no correlation to update the reference from");
+  if (h->shape == DIC_QUADRATIC)
+    return fail(DIC_EINVAL, "reference updating needs a rigid or affine shape function");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = s;
+  int rc = ensure_increments(h);
+  if (rc) return rc;
+  if ((rc = run_totals(h, 1, s))) return rc;
+  h->acc_identity = false;
+  ++h->n_updates;
+  // the deformed image and its coefficients become the reference's
+  if (h->ref_owned) hfree(h, h->ref_owned);
+  h->ref = h->def;
+  h->ref_owned = h->def_owned;
+  h->ref_dtype = h->def_dtype;
+  h->def_owned = nullptr;
+  void* t = h->c_ref;
+  h->c_ref = h->c_def;
+  h->c_def = t;
+  h->ref_dirty = h->def_dirty;
+  h->def_dirty = true;
+  DIC_CUDA(launch_identity_start(point_arrays(h), h->nparams, h->roi_ok, s), "identity start");
+  return DIC_OK;
+}
+
+int dic_get_total_results(dic_handle* h, dic_total_results* out, void* cuda_stream) {
+  if (!h || !out) return fail(DIC_EINVAL, "NULL argument");
+  g_last_error.clear();
+  if (!h->has_results) return fail(DIC_ESTATE, "no correlation since the handle was created or re-gridded");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int rc = ensure_increments(h);
+  if (rc) return rc;
+  if ((rc = run_totals(h, 0, s))) return rc;
+  dic_total_results r{};
+  r.n_points = h->npts;
+  r.nx = h->nx;
+  r.ny = h->ny;
+  r.n_params = h->nparams;
+  r.n_updates = h->n_updates;
+  r.u = h->tot_u;
+  r.v = h->tot_v;
+  r.p = h->tot_p;
+  r.status = h->tot_status;
+  *out = r;
   return DIC_OK;
 }
 

@@ -156,6 +156,25 @@ cudaError_t launch_fftcc_origins(const FftLevelArgs& a, cudaStream_t s);
 cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s);
 cudaError_t launch_mad(const MadArgs& a, cudaStream_t s);
 
+// ---------------------------------------------------------------- reference updating
+struct TotalArgs {
+  int nx, ny, r, step, nparams;
+  const uint8_t* roi_ok;       // NULL: every point in the ROI
+  const uint8_t* status;       // last correlation, against the current reference
+  const double* p;             // [n][nparams]
+  int identity;                // 1: no update yet (the accumulated warps are the identity)
+  double* acc_u;               // [n] accumulated warps from the first reference
+  double* acc_v;
+  double* acc_A;               // [n][4] A00 A01 A10 A11
+  uint8_t* acc_ok;             // [n]
+  double* tot_u;               // [n] outputs: total warps to the last frame
+  double* tot_v;
+  double* tot_p;               // [n][nparams]
+  uint8_t* tot_status;         // [n]
+  int update;                  // 1: the totals also become the accumulated warps
+};
+cudaError_t launch_totals(const TotalArgs& a, cudaStream_t s);
+
 // ---------------------------------------------------------------- seeds
 struct SeedArgs {
   GrayPlane ref, def;
@@ -216,6 +235,8 @@ cudaError_t launch_finalize_points(const PointArrays& pa, int nparams, int nan_r
 // (counters must be zero; counters[kCount] receives the size of front0)
 cudaError_t launch_sequence_reset(const PointArrays& pa, int nparams, const uint8_t* roi_ok,
                                   int32_t* front0, int32_t* counters, cudaStream_t s);
+// every in-ROI point starts the next sequence frame from the identity warp
+cudaError_t launch_identity_start(const PointArrays& pa, int nparams, const uint8_t* roi_ok, cudaStream_t s);
 
 // ---------------------------------------------------------------- waves
 // Shared-memory tiles of the wave kernel: the coefficient window (bxc x byc
