@@ -495,12 +495,72 @@ def sequence_leg(args, stream):
     r = c.results()
     c.close()
     lat = np.array(lat)
-    return {"frames": n, "size": [w0.width, w0.height], "subset": w0.subset_size, "step": w0.subset_step,
-            "shape": w0.shape, "points_per_frame": int(r["n_points"]),
-            "accepted_last_frame": int(r["n_accepted"]),
-            "frame_ms_p50": float(np.percentile(lat, 50)), "frame_ms_p99": float(np.percentile(lat, 99)),
-            "points_per_s": float(np.sum(acc) / (np.sum(lat) / 1e3)),
-            "note": "frame 1 from the seed (not timed); frames 2..%d timed" % n}
+    out = {"frames": n, "size": [w0.width, w0.height], "subset": w0.subset_size, "step": w0.subset_step,
+           "shape": w0.shape, "points_per_frame": int(r["n_points"]),
+           "accepted_last_frame": int(r["n_accepted"]),
+           "frame_ms_p50": float(np.percentile(lat, 50)), "frame_ms_p99": float(np.percentile(lat, 99)),
+           "points_per_s": float(np.sum(acc) / (np.sum(lat) / 1e3)),
+           "note": "frame 1 from the seed (not timed); frames 2..%d timed" % n}
+    out["updating"] = sequence_updating_leg(args, stream)
+    return out
+
+
+def sequence_updating_leg(args, stream, every=50):
+    """The same sequence with incremental reference updating: the total warps from
+    frame 0 taken after every frame (dic_get_total_results) and the reference updated
+    to the current frame every `every` frames (dic_update_reference). Two frame buffers
+    alternate: an updated reference keeps borrowing its frame's buffer."""
+    import torch
+
+    import paper_2601_12941_gb300 as P
+    import synth
+    from synth import workloads as wl
+
+    n = args.seq_frames
+    w0 = wl.sequence_frame(1)
+    ref = torch.empty((w0.height, w0.width), dtype=torch.int16, device="cuda")
+    bufs = [torch.empty_like(ref), torch.empty_like(ref)]
+    synth.render_gpu(w0.ref, ref)
+    synth.render_gpu(w0.deformed, bufs[0])
+    c = P.Correlation(ref, bufs[0], None, w0.subset_size, w0.subset_step, w0.shape, precision="mixed",
+                      search_radius=w0.search_radius, profile=0)
+    c.run(list(w0.seeds), stream.cuda_stream)
+    cur = 0
+    lat, upd, tot_ms = [], [], []
+    for k in range(2, n + 1):
+        if (k - 1) % every == 0:                        # frame k - 1 becomes the reference
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.update_reference(stream.cuda_stream)
+            b.record(stream)
+            b.synchronize()
+            upd.append(a.elapsed_time(b))
+            cur ^= 1                                    # the old frame buffer is now the reference's
+        synth.render_gpu(wl.sequence_frame(k).deformed, bufs[cur])
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        m = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c.set_deformed(bufs[cur])
+        c.run_next(stream.cuda_stream)
+        m.record(stream)
+        t = c.totals(on_device=True, stream_ptr=stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+        tot_ms.append(m.elapsed_time(b))
+    ok = int((t["status"] == 0).sum().item())
+    exx = float(t["p"][t["status"] == 0][:, 2].median().item())
+    n_up = t["n_updates"]
+    c.close()
+    return {"every": every, "updates": n_up, "frame_ms_p50": float(np.percentile(lat, 50)),
+            "frame_ms_p99": float(np.percentile(lat, 99)), "totals_ms_p50": float(np.percentile(tot_ms, 50)),
+            "update_ms_p50": float(np.percentile(upd, 50)) if upd else None,
+            "total_points_last_frame": ok, "total_exx_median_last_frame": exx,
+            "note": "per frame: deformed prefilter, waves against the current reference, total warps from "
+                    "frame 0; updates timed apart"}
 
 
 def serving_leg(args):
