@@ -264,8 +264,10 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v)
   return v;
 }
 
-// Sums of two values over the block (all threads get them).
-__device__ void block_sum2(double& a, double& b, double* scratch) {
+// Sums of two values over the block (all threads get them). FP32: the sums only set
+// the windows' means and the normalisation of R, and FP64 arithmetic in every thread
+// would bind these kernels on this GPU's FP64 pipe.
+__device__ void block_sum2(float& a, float& b, float* scratch) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   a = warp_sum(a);
   b = warp_sum(b);
@@ -275,8 +277,8 @@ __device__ void block_sum2(double& a, double& b, double* scratch) {
     scratch[2 * wid + 1] = b;
   }
   __syncthreads();
-  a = 0.0;
-  b = 0.0;
+  a = 0.f;
+  b = 0.f;
   for (int w = 0; w < nw; ++w) {
     a += scratch[2 * w];
     b += scratch[2 * w + 1];
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
   float2* A = reinterpret_cast<float2*>(smem_raw);
   float2* B = A + N;
   float2* tws = B + N;                                   // L - 1 twiddles (power of two) or the L x L DFT matrix
-  __shared__ double s_red[2 * (kSmallThreads / 32)];
+  __shared__ float s_red[2 * (kSmallThreads / 32)];
   __shared__ unsigned long long s_key[kSmallThreads / 32];
   const int tid = threadIdx.x;
   // the nested power-of-two table: stage ns <= L/2 reads tw_pow2[ns - 1 + k], k < ns,
@@ -327,8 +329,8 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       }
       continue;
     }
-    // per-thread partial sums in FP32 (a few values each), the block reduction in FP64:
-    // FP64 arithmetic per element would bind the kernel on this GPU's FP64 pipe
+    // FP32 sums (FP64 arithmetic in every thread would bind the kernel on this GPU's
+    // FP64 pipe); they set the means and the normalisation of R only
     float pf = 0.f, pg = 0.f;
     const float f00 = load_gray<float>(a.ref, o.x, o.y), g00 = load_gray<float>(a.def, o.z, o.w);
     bool vf = false, vg = false;                         // a value differs from the first
@@ -342,12 +344,12 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       vf |= f != f00;
       vg |= g != g00;
     }
-    double sf = pf, sg = pg;
+    float sf = pf, sg = pg;
     const int any_f = __syncthreads_or(vf);
     const int any_g = __syncthreads_or(vg);
     const bool flat = !any_f || !any_g;
     block_sum2(sf, sg, s_red);
-    const float mf = static_cast<float>(sf / N), mg = static_cast<float>(sg / N);
+    const float mf = sf / static_cast<float>(N), mg = sg / static_cast<float>(N);
     float pqf = 0.f, pqg = 0.f;
     for (int e = tid; e < N; e += kSmallThreads) {
       float2 v = A[e];
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       pqf = fmaf(v.x, v.x, pqf);
       pqg = fmaf(v.y, v.y, pqg);
     }
-    double qf = pqf, qg = pqg;
+    float qf = pqf, qg = pqg;
     block_sum2(qf, qg, s_red);                           // (its barriers also order the writes above)
     float2* X;
     float2* Y;
@@ -406,8 +408,7 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       }
       a.u[w] = static_cast<float>(o.z - o.x) + dx;
       a.v[w] = static_cast<float>(o.w - o.y) + dy;
-      a.peak[w] = flat ? 0.f : static_cast<float>(static_cast<double>(R[e].x) /
-                                                  (static_cast<double>(N) * sqrt(qf * qg)));
+      a.peak[w] = flat ? 0.f : R[e].x / (static_cast<float>(N) * sqrtf(qf) * sqrtf(qg));
     }
     __syncthreads();                                     // the next window reuses the buffers
   }
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
   const int lines = 2 * units;
   float2* P = reinterpret_cast<float2*>(smem_raw);
   float2* Q = P + lines * L;
-  __shared__ double s_red[2 * (kLineThreads / 32)];
+  __shared__ float s_red[2 * (kLineThreads / 32)];
   const int64_t w = blockIdx.x;
   if (!window_ok(a.org[w], L, a.W, a.H)) return;
   const int u0 = blockIdx.y * units;
@@ -497,7 +498,7 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
   __syncthreads();
   float2* X = fft_lines(P, Q, L, lines, L, 1, a.tw_pow2, false);
   float2* Y = X == P ? Q : P;
-  float pnf = 0.f, png = 0.f;                             // FP32 per thread, FP64 across the block
+  float pnf = 0.f, png = 0.f;                             // FP32 per block, FP64 across blocks
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
     const int line = e / L, ky = e - line * L;
     const int u = u0 + (line >> 1);
@@ -515,11 +516,11 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
       png = fmaf(gx, gx, fmaf(gy, gy, png));
     }
   }
-  double nf = pnf, ng = png;
+  float nf = pnf, ng = png;
   block_sum2(nf, ng, s_red);
   if (threadIdx.x == 0) {
-    atomicAdd(&a.norms[2 * w], nf);
-    atomicAdd(&a.norms[2 * w + 1], ng);
+    atomicAdd(&a.norms[2 * w], static_cast<double>(nf));
+    atomicAdd(&a.norms[2 * w + 1], static_cast<double>(ng));
   }
   float2* R = fft_lines(Y, X, L, lines, L, 1, a.tw_pow2, true);
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
