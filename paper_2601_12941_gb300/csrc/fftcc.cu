@@ -173,21 +173,29 @@ __device__ __forceinline__ void cmac(float2& acc, float2 p, float2 q) {
 
 // One pass of the 2-D DFT of odd side L as a complex matrix product with the DFT
 // matrix Wm[x][k] = exp(-2 pi i x k / L) (symmetric): along rows OUT = IN Wm, along
-// columns OUT = Wm IN; INV uses conj(Wm). Each thread accumulates a 2 x 2 tile of
-// OUT over the L terms (4 complex loads for 4 complex multiply-adds).
+// columns OUT = Wm IN; INV uses conj(Wm). Each thread accumulates a kTileR x 2 tile
+// of OUT over the L terms: kTileR + 2 complex loads (the kTileR row operands are
+// broadcast within a warp) for 2 kTileR complex multiply-adds. Only the first
+// rows_out rows of OUT are formed.
+constexpr int kTileR = 4;
 template <bool ROWS, bool INV>
 __device__ void dft_matmul(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ Wm,
                            int L, int rows_out) {
-  const int nt = (L + 1) >> 1, ntr = (rows_out + 1) >> 1;
-  for (int t = threadIdx.x; t < ntr * nt; t += blockDim.x) {
-    const int r0 = (t / nt) * 2, c0 = (t - (t / nt) * nt) * 2;
-    const int r1 = min(r0 + 1, L - 1), c1 = min(c0 + 1, L - 1);
-    float2 a00 = make_float2(0.f, 0.f), a01 = a00, a10 = a00, a11 = a00;
+  const int ntc = (L + 1) >> 1, ntr = (rows_out + kTileR - 1) / kTileR;
+  for (int t = threadIdx.x; t < ntr * ntc; t += blockDim.x) {
+    const int r0 = (t / ntc) * kTileR, c0 = (t - (t / ntc) * ntc) * 2;
+    const int c1 = min(c0 + 1, L - 1);
+    int rr[kTileR];
+#pragma unroll
+    for (int i = 0; i < kTileR; ++i) rr[i] = min(r0 + i, L - 1);
+    float2 acc0[kTileR], acc1[kTileR];
+#pragma unroll
+    for (int i = 0; i < kTileR; ++i) acc0[i] = acc1[i] = make_float2(0.f, 0.f);
     for (int x = 0; x < L; ++x) {
-      float2 p0, p1, q0, q1;
+      float2 p[kTileR], q0, q1;
       if (ROWS) {
-        p0 = in[r0 * L + x];
-        p1 = in[r1 * L + x];
+#pragma unroll
+        for (int i = 0; i < kTileR; ++i) p[i] = in[rr[i] * L + x];
         q0 = Wm[x * L + c0];
         q1 = Wm[x * L + c1];
         if (INV) {
@@ -195,25 +203,26 @@ __device__ void dft_matmul(const float2* __restrict__ in, float2* __restrict__ o
           q1.y = -q1.y;
         }
       } else {
-        p0 = Wm[r0 * L + x];
-        p1 = Wm[r1 * L + x];
+#pragma unroll
+        for (int i = 0; i < kTileR; ++i) {
+          p[i] = Wm[rr[i] * L + x];
+          if (INV) p[i].y = -p[i].y;
+        }
         q0 = in[x * L + c0];
         q1 = in[x * L + c1];
-        if (INV) {
-          p0.y = -p0.y;
-          p1.y = -p1.y;
-        }
       }
-      cmac(a00, p0, q0);
-      cmac(a01, p0, q1);
-      cmac(a10, p1, q0);
-      cmac(a11, p1, q1);
+#pragma unroll
+      for (int i = 0; i < kTileR; ++i) {
+        cmac(acc0[i], p[i], q0);
+        cmac(acc1[i], p[i], q1);
+      }
     }
-    out[r0 * L + c0] = a00;
-    if (c0 + 1 < L) out[r0 * L + c0 + 1] = a01;
-    if (r0 + 1 < rows_out) {
-      out[(r0 + 1) * L + c0] = a10;
-      if (c0 + 1 < L) out[(r0 + 1) * L + c0 + 1] = a11;
+#pragma unroll
+    for (int i = 0; i < kTileR; ++i) {
+      if (r0 + i < rows_out) {
+        out[(r0 + i) * L + c0] = acc0[i];
+        if (c0 + 1 < L) out[(r0 + i) * L + c0 + 1] = acc1[i];
+      }
     }
   }
   __syncthreads();
@@ -222,28 +231,38 @@ __device__ void dft_matmul(const float2* __restrict__ in, float2* __restrict__ o
 // The last inverse pass for a Hermitian spectrum: T holds the inverse row transforms
 // of rows ky = 0 .. (L-1)/2 only (the others are their conjugates, T[-ky] = conj T[ky]),
 // and R[y][x] = Re T[0][x] + 2 sum_{ky >= 1} Re(T[ky][x] exp(2 pi i ky y / L)), the real
-// part only (R is real). 2 x 2 tiles of R; R is written as the .x of out.
+// part only (R is real). kTileR x 2 tiles of R; R is written as the .x of out.
 __device__ void dft_inverse_columns_real(const float2* __restrict__ T, float2* __restrict__ out,
                                          const float2* __restrict__ Wm, int L) {
-  const int nt = (L + 1) >> 1, kh = (L + 1) >> 1;
-  for (int t = threadIdx.x; t < nt * nt; t += blockDim.x) {
-    const int r0 = (t / nt) * 2, c0 = (t - (t / nt) * nt) * 2;
-    const int r1 = min(r0 + 1, L - 1), c1 = min(c0 + 1, L - 1);
-    float a00 = 0.5f * T[c0].x, a01 = 0.5f * T[c1].x, a10 = a00, a11 = a01;   // the ky = 0 term, halved
-    for (int ky = 1; ky < kh; ++ky) {
-      const float2 p0 = Wm[r0 * L + ky], p1 = Wm[r1 * L + ky];                 // exp(-2 pi i ky y / L)
-      const float2 q0 = T[ky * L + c0], q1 = T[ky * L + c1];
-      // Re(q conj(p)) = q.x p.x + q.y p.y
-      a00 = fmaf(q0.x, p0.x, fmaf(q0.y, p0.y, a00));
-      a01 = fmaf(q1.x, p0.x, fmaf(q1.y, p0.y, a01));
-      a10 = fmaf(q0.x, p1.x, fmaf(q0.y, p1.y, a10));
-      a11 = fmaf(q1.x, p1.x, fmaf(q1.y, p1.y, a11));
+  const int ntc = (L + 1) >> 1, ntr = (L + kTileR - 1) / kTileR, kh = (L + 1) >> 1;
+  for (int t = threadIdx.x; t < ntr * ntc; t += blockDim.x) {
+    const int r0 = (t / ntc) * kTileR, c0 = (t - (t / ntc) * ntc) * 2;
+    const int c1 = min(c0 + 1, L - 1);
+    int rr[kTileR];
+#pragma unroll
+    for (int i = 0; i < kTileR; ++i) rr[i] = min(r0 + i, L - 1);
+    float acc0[kTileR], acc1[kTileR];
+#pragma unroll
+    for (int i = 0; i < kTileR; ++i) {                 // the ky = 0 term, halved
+      acc0[i] = 0.5f * T[c0].x;
+      acc1[i] = 0.5f * T[c1].x;
     }
-    out[r0 * L + c0].x = 2.f * a00;
-    if (c0 + 1 < L) out[r0 * L + c0 + 1].x = 2.f * a01;
-    if (r0 + 1 < L) {
-      out[(r0 + 1) * L + c0].x = 2.f * a10;
-      if (c0 + 1 < L) out[(r0 + 1) * L + c0 + 1].x = 2.f * a11;
+    for (int ky = 1; ky < kh; ++ky) {
+      const float2 q0 = T[ky * L + c0], q1 = T[ky * L + c1];
+#pragma unroll
+      for (int i = 0; i < kTileR; ++i) {
+        const float2 p = Wm[rr[i] * L + ky];           // exp(-2 pi i ky y / L)
+        // Re(q conj(p)) = q.x p.x + q.y p.y
+        acc0[i] = fmaf(q0.x, p.x, fmaf(q0.y, p.y, acc0[i]));
+        acc1[i] = fmaf(q1.x, p.x, fmaf(q1.y, p.y, acc1[i]));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kTileR; ++i) {
+      if (r0 + i < L) {
+        out[(r0 + i) * L + c0].x = 2.f * acc0[i];
+        if (c0 + 1 < L) out[(r0 + i) * L + c0 + 1].x = 2.f * acc1[i];
+      }
     }
   }
   __syncthreads();
@@ -297,8 +316,11 @@ __device__ unsigned long long block_max_key(unsigned long long v, unsigned long 
 }
 
 // ---------------------------------------------------------------- small windows
+// power-of-two windows: 256 threads; odd (the last level): 128, which the kTileR x 2
+// tiles of a 31 x 31 window fill exactly
 template <bool POW2>
-__global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a) {
+__global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftcc_small_kernel(FftccArgs a) {
+  constexpr int NT = POW2 ? kSmallThreads : kSmallThreads / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.L, N = L * L;
   float2* A = reinterpret_cast<float2*>(smem_raw);
@@ -310,9 +332,9 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
   // the nested power-of-two table: stage ns <= L/2 reads tw_pow2[ns - 1 + k], k < ns,
   // so the block keeps entries 0 .. L - 2
   if (POW2) {
-    for (int e = tid; e < L - 1; e += kSmallThreads) tws[e] = a.tw_pow2[e];
+    for (int e = tid; e < L - 1; e += NT) tws[e] = a.tw_pow2[e];
   } else {
-    for (int e = tid; e < N; e += kSmallThreads) {
+    for (int e = tid; e < N; e += NT) {
       const int x = e / L, k = e - x * L;
       tws[e] = a.tw_odd[(x * k) % L];
     }
@@ -334,7 +356,7 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
     float pf = 0.f, pg = 0.f;
     const float f00 = load_gray<float>(a.ref, o.x, o.y), g00 = load_gray<float>(a.def, o.z, o.w);
     bool vf = false, vg = false;                         // a value differs from the first
-    for (int e = tid; e < N; e += kSmallThreads) {
+    for (int e = tid; e < N; e += NT) {
       const int y = e / L, x = e - y * L;
       const float f = load_gray<float>(a.ref, o.x + x, o.y + y);
       const float g = load_gray<float>(a.def, o.z + x, o.w + y);
@@ -351,7 +373,7 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
     block_sum2(sf, sg, s_red);
     const float mf = sf / static_cast<float>(N), mg = sg / static_cast<float>(N);
     float pqf = 0.f, pqg = 0.f;
-    for (int e = tid; e < N; e += kSmallThreads) {
+    for (int e = tid; e < N; e += NT) {
       float2 v = A[e];
       v.x -= mf;
       v.y -= mg;
@@ -373,7 +395,7 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       X = A;
     }
     Y = X == A ? B : A;
-    for (int e = tid; e < N; e += kSmallThreads) {
+    for (int e = tid; e < N; e += NT) {
       const int ky = e / L, kx = e - ky * L;
       const int m = (ky == 0 ? 0 : L - ky) * L + (kx == 0 ? 0 : L - kx);
       Y[e] = e == 0 ? make_float2(0.f, 0.f) : cross_power(X[e], X[m]);
@@ -390,7 +412,7 @@ __global__ void __launch_bounds__(kSmallThreads) fftcc_small_kernel(FftccArgs a)
       R = Y;
     }
     unsigned long long best = 0ull;
-    for (int e = tid; e < N; e += kSmallThreads) {
+    for (int e = tid; e < N; e += NT) {
       const unsigned long long k = peak_key(R[e].x, e);
       best = k > best ? k : best;
     }
@@ -777,7 +799,7 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
                                                          static_cast<int>(small_smem(kFftSmallMax, false)));
       if (ok != cudaSuccess) return ok;
       const int per_sm = static_cast<int>(200 * 1024 / smem) < 8 ? static_cast<int>(200 * 1024 / smem) : 8;
-      fftcc_small_kernel<false><<<blocks_for(a.n, per_sm > 0 ? per_sm : 1), kSmallThreads, smem, s>>>(a);
+      fftcc_small_kernel<false><<<blocks_for(a.n, 2 * (per_sm > 0 ? per_sm : 1)), kSmallThreads / 2, smem, s>>>(a);
     }
     return cudaGetLastError();
   }
