@@ -288,6 +288,8 @@ def run_ours(args):
         out["strain"] = strain_leg(c, w, stream)
     if not args.no_fft:
         out["fft_init"] = fft_leg(ref, dfm, stream, reps=args.fft_reps, kernel_reps=args.fft_kernel_reps)
+    if not args.no_variants:
+        out["variants"] = variants_leg(ref, dfm, w, seeds, stream)
     if not args.no_e2e:
         out["e2e"] = e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_ranks)
     c.close()
@@ -351,6 +353,46 @@ def strain_leg(c, w, stream, window=9, basis="biquadratic", measure="green_lagra
             "ms": t, "points_per_s": n / (t / 1e3),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "peak_note": note, "algorithmic_bytes_per_point": bytes_per_point}}
+
+
+def variants_leg(ref, dfm, w, seeds, stream, steps=2):
+    """The next-row variants on the same 1.07 Gpx pair and grid as the headline step:
+    the NSSD and SSD costs (Eq. 2-3), Levenberg-Marquardt, and Keys bicubic
+    interpolation, each through the generic kernel instantiations. One warm-up step
+    and `steps` timed steps each (reference and deformed set, prefilter, seeds, every
+    wave)."""
+    import torch
+
+    import paper_2601_12941_gb300 as P
+
+    out = {}
+    for label, kw in (("nssd", dict(cost="nssd")), ("ssd", dict(cost="ssd")), ("lm", dict(optimizer="lm")),
+                      ("bicubic", dict(interp="bicubic"))):
+        interp = kw.pop("interp", "bspline3")
+        c = P.Correlation(ref, dfm, None, w.subset_size, w.subset_step, w.shape, interp=interp, precision="mixed",
+                          search_radius=w.search_radius, profile=1, **kw)
+        c.run(seeds, stream.cuda_stream)
+        stream.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        kern = 0.0
+        a.record(stream)
+        for _ in range(steps):
+            c.set_reference(ref)
+            c.set_deformed(dfm)
+            c.run(seeds, stream.cuda_stream)
+            kern += c.timing()["icgn_kernel_ms"]
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        r = c.results()
+        acc = int(r["n_accepted"])
+        out[label] = {"ms_per_step": ms, "points_per_s": acc / (ms / 1e3), "accepted": acc,
+                      "wave_kernel_ms": kern / steps,
+                      "mean_iterations": float(r["iters"][r["status"] == 0].mean()) if acc else None}
+        c.close()
+        torch.cuda.empty_cache()
+    return out
 
 
 def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel_reps=3):
@@ -726,6 +768,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-strain", action="store_true")
     ap.add_argument("--no-fft", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--fft-only", action="store_true",
                     help="run only the FFT initialiser leg on the pair of --size (profiling)")
     ap.add_argument("--fft-reps", type=int, default=3, help="timed fields of the FFT leg (after one warm-up)")
