@@ -146,6 +146,47 @@ def test_each_job_same_alone_and_in_the_mix(pkg):
     assert st["peak_busy_workers"] >= 2 and st["peak_bytes"] <= st["budget_bytes"]
 
 
+def test_device_bytes_match_estimates_with_fft_seeds_and_bicubic(pkg):
+    from paper_2601_12941_gb300 import binding as B
+
+    W, H, dt, G, sp, ref = _pool()[1]
+    dfm = synth.render(synth.ImageSpec(sp, field=synth.affine_field(W, H, u0=9.6, v0=-5.2), gray_max=G,
+                                       noise_tag=8), W, H, dt)
+    ri, _ = B.make_image(ref)
+    di, _ = B.make_image(dfm)
+    seeds = [(W // 2, H // 2)]
+    # FFT-seeded (windows up to 128 px: the global work-buffer path is allocated too)
+    prm = B.params(init="fft", max_displacement=100)
+    est = B.dic_estimate_device_bytes(ri, di, False, 21, 5, B.DIC_AFFINE, prm, 1)
+    c = pkg.Correlation(ref, dfm, None, 21, 5, "affine", init="fft", max_displacement=100)
+    c.run(seeds)
+    assert c.device_bytes() == est
+    assert (c.results()["status"] == 0).sum() > 0
+    # re-grid with the integer search: the FFT arrays stay held and are counted
+    prm2 = B.params(search_radius=12)
+    pred = B.dic_estimate_regrid_bytes(c.h, di, False, 31, 7, B.DIC_AFFINE, prm2, 2)
+    c.set_subsets(31, 7, "affine")
+    c.set_deformed(dfm)
+    c.set_params(init="search", search_radius=12)
+    c.run([(W // 2, H // 2), (W // 2 + 40, H // 2)])
+    assert c.device_bytes() == pred
+    # and back to FFT seeds with a larger window set
+    prm3 = B.params(init="fft", max_displacement=300)
+    pred = B.dic_estimate_regrid_bytes(c.h, di, False, 21, 4, B.DIC_AFFINE, prm3, 1)
+    c.set_subsets(21, 4, "affine")
+    c.set_deformed(dfm)
+    c.set_params(init="fft", max_displacement=300)
+    c.run(seeds)
+    assert c.device_bytes() == pred
+    c.close()
+    # the bicubic interpolant holds the same planes as the spline
+    est = B.dic_estimate_device_bytes(ri, di, False, 21, 5, B.DIC_AFFINE, B.params(search_radius=12), 1)
+    c = pkg.Correlation(ref, dfm, None, 21, 5, "affine", interp="bicubic", search_radius=12)
+    c.run(seeds)
+    assert c.device_bytes() == est
+    c.close()
+
+
 def test_admission_keeps_footprint_within_budget(pkg):
     from paper_2601_12941_gb300.serve import AdmissionError, Job, LibdicEngine, Server
 
