@@ -97,6 +97,41 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
     assert lib.dic_estimate_device_bytes(ctypes.byref(ri), ctypes.byref(ri), 0, 21, 5, 1, ctypes.byref(p), 1,
                                          ctypes.byref(nb)) == B.DIC_OK
     assert nb.value > 2 * 64 * 64 * 4      # at least the two FP32 coefficient planes
+    # FFT seeds: their buffers are counted, and the parameters are validated
+    pf = B.params(init="fft", max_displacement=40)
+    nf = ctypes.c_int64(0)
+    assert lib.dic_estimate_device_bytes(ctypes.byref(ri), ctypes.byref(ri), 0, 21, 5, 1, ctypes.byref(pf), 1,
+                                         ctypes.byref(nf)) == B.DIC_OK
+    assert nf.value > nb.value
+    for bad in (dict(init=2), dict(init="fft", max_displacement=4096), dict(init="fft", max_displacement=-1),
+                dict(mad_eps=-1.0)):
+        pb = B.params(**bad)
+        assert lib.dic_estimate_device_bytes(ctypes.byref(ri), ctypes.byref(ri), 0, 21, 5, 1, ctypes.byref(pb), 1,
+                                             ctypes.byref(nf)) == B.DIC_EINVAL, bad
+
+
+def test_next_row_calls_check_their_arguments_first(lib):
+    from paper_2601_12941_gb300 import binding as B
+
+    fake = ctypes.c_void_p(16)
+    fp = B.dic_fft_default_params()
+    assert (fp.max_displacement, fp.subpixel, fp.mad_tau, fp.mad_eps) == (32, 1, 3.0, 0.5)
+    assert lib.dic_fft_field(None, ctypes.byref(fp), None) == B.DIC_EINVAL
+    assert lib.dic_get_fft_results(None, ctypes.byref(B.DicFftResults())) == B.DIC_EINVAL
+    assert lib.dic_fftcc_windows(None, 31, 1, fake, 0, fake, fake, fake, None) == B.DIC_EINVAL
+    assert lib.dic_update_reference(None, None) == B.DIC_EINVAL
+    assert lib.dic_get_total_results(None, ctypes.byref(B.DicTotalResults()), None) == B.DIC_EINVAL
+    # the MAD rule: sizes, NULL arrays and in-place calls are refused before any launch;
+    # an empty field is a no-op
+    assert lib.dic_mad_filter(fake, fake, None, -1, 4, 3.0, 0.5, fake, fake, None, None) == B.DIC_EINVAL
+    assert lib.dic_mad_filter(fake, fake, None, 0, 4, 3.0, 0.5, fake, fake, None, None) == B.DIC_OK
+    assert lib.dic_mad_filter(None, fake, None, 3, 4, 3.0, 0.5, ctypes.c_void_p(32), ctypes.c_void_p(48), None,
+                              None) == B.DIC_EINVAL
+    assert lib.dic_mad_filter(fake, ctypes.c_void_p(32), None, 3, 4, 3.0, 0.5, fake, ctypes.c_void_p(48), None,
+                              None) == B.DIC_EINVAL
+    assert b"in-place" in lib.dic_last_error()
+    assert lib.dic_mad_filter(fake, ctypes.c_void_p(32), None, 3, 4, 3.0, -0.5, ctypes.c_void_p(48),
+                              ctypes.c_void_p(64), None, None) == B.DIC_EINVAL
 
 
 def test_loading_fails_loudly_without_the_library(tmp_path):
