@@ -46,8 +46,12 @@ Readings taken where the paper is silent (all of them, in one place):
   R7  Convergence: ||dp||_s = sqrt(dp0^2 + dp1^2 + r^2 sum dp2..5^2 + r^4 sum dp6..11^2)
       below the threshold; iters counts applied updates.
   R8  "Precision 0.70" is the ZNCC acceptance cut-off; "threshold 0.01" is the
-      ||dp||_s threshold. The final ZNCC is taken with one more sampling pass at
-      the final p. Accepted iff converged, ZNCC >= cut-off and in bounds.
+      ||dp||_s threshold. Accepted iff converged, ZNCC >= cut-off and in bounds. The
+      paper does not say at which warp the coefficient is taken. Gauss-Newton takes
+      it, with the in-bounds and flatness tests, from the sampling pass of the last
+      iteration (the warp the final, sub-threshold update was computed at); the
+      reported p includes that update. Levenberg-Marquardt (R13) takes it with one
+      more sampling pass at the final p.
   R9  Seed search: integer offsets |du|, |dv| <= R whose whole deformed subset is
       inside the image, scored by ZNCC from exact integer sums (float images: FP64
       sums) as C = (N Sfg - Sf Sg) / sqrt((N Sff - Sf^2)(N Sgg - Sg^2)); the best is
@@ -548,17 +552,21 @@ def icgn(ref: Plane, dfm: Plane, xc, yc, subset_size, shape, p_init, params=None
     if ratio_status is not None:
         out["status"] = ratio_status
         return out
-    wx, wy = warp(p, rs.dx, rs.dy)
-    g, valid = interpolate(dfm, xc + wx, yc + wy)
-    if not valid.all():
-        out["status"] = OUT_OF_BOUNDS
-        return out
-    g_m = g.mean()
-    gbar = g - g_m
-    delta_g = math.sqrt(np.sum(gbar ** 2))
-    if _flat(delta_g, g_m, g.size):
-        out["status"] = FLAT_SUBSET
-        return out
+    if lm:
+        # R8: Levenberg-Marquardt samples once more at the final p
+        wx, wy = warp(p, rs.dx, rs.dy)
+        g, valid = interpolate(dfm, xc + wx, yc + wy)
+        if not valid.all():
+            out["status"] = OUT_OF_BOUNDS
+            return out
+        g_m = g.mean()
+        gbar = g - g_m
+        delta_g = math.sqrt(np.sum(gbar ** 2))
+        if _flat(delta_g, g_m, g.size):
+            out["status"] = FLAT_SUBSET
+            return out
+    # R8: Gauss-Newton keeps gbar and delta_g of its last iteration's pass (already
+    # tested in bounds and not flat inside the loop)
     out["zncc"] = float(np.sum(rs.fbar * gbar) / (rs.delta_f * delta_g))
     if not out["converged"]:
         out["status"] = MAX_ITER

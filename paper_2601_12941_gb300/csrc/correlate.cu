@@ -12,8 +12,9 @@
 //      the warped pixels, reduce sum g, sum g^2 and sum SD g, solve
 //      dp = -H^-1 sum SD (f - f_m - (df/dg)(g - g_m)) in FP64, update
 //      p <- p o dp^-1, stop when ||dp|| < threshold;
-//   4. ZNCC = sum (f - f_m)(g - g_m) / (df dg) at the final p; accept when
-//      converged, in bounds and ZNCC >= cut-off;
+//   4. ZNCC = sum (f - f_m)(g - g_m) / (df dg) from the converging iteration's
+//      sampling pass (Levenberg-Marquardt: one more pass at the final p); accept
+//      when converged, in bounds and ZNCC >= cut-off;
 //   5. an accepted point claims its unvisited in-ROI 4-neighbours for the next wave.
 //
 // Threads map to pixels by column: thread t < S * bands owns column t % S and
@@ -1028,9 +1029,9 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
   constexpr int M2 = 2 * D;
   constexpr int NMOM = (M2 + 1) * (M2 + 2) / 2;
   constexpr int NV_PRE = 3 * NMOM + 2 * NP + 2;  // H moments, sum SD f', sum SD, sum f', sum f'^2
-  constexpr int NV_IT = 3 + NP + (LM ? 1 : 0);   // sum g', sum g'^2, sum SD g', bad samples (LM: sum f'g')
+  constexpr int NV_IT = 4 + NP;                  // sum g', sum g'^2, sum SD g', bad samples, sum f'g'
   constexpr int NV_FIN = 4;                      // sum g', sum g'^2, sum f' g', bad samples
-  constexpr int NACC = 2 + 2 * (D + 1) + (LM ? 1 : 0);
+  constexpr int NACC = 2 + 2 * (D + 1) + 1;
   constexpr int XALIGN = 16 / static_cast<int>(sizeof(T));   // TMA x alignment of the coefficient planes
   constexpr int NW = NT / 32;                                 // warps per block
 
@@ -1393,11 +1394,11 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
       T bad = T(0);
       if (stage != 2) {
         const T* base = s_win + (yc - 1 - w.y0) * w.w + (xc - 1 - w.x0);
-        sample_column<T, D, LM, GEN>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r,
+        sample_column<T, D, true, GEN>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r,
                                      S, col, gtile, gpitch, gdt, s_fg, final_pass, st.inside != 0, keys, acc, bad);
       } else {
         const T* base = a.c_def + static_cast<int64_t>(yc - 1) * a.ldc + (xc - 1);
-        sample_column_global<T, D, LM>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1,
+        sample_column_global<T, D, true>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1,
                                        r, S, col, gtile, gpitch, gdt, s_fg, final_pass, GEN && keys, acc, bad);
       }
       if (!final_pass) {
@@ -1407,7 +1408,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
 #pragma unroll
         for (int c = 0; c < NP; ++c) v[2 + c] = dxp[sd_i(c)] * acc[2 + sd_t(c) * (D + 1) + sd_j(c)];
         v[2 + NP] = bad;
-        if constexpr (LM) v[3 + NP] = acc[2 + 2 * (D + 1)];
+        v[3 + NP] = acc[2 + 2 * (D + 1)];
 #pragma unroll
         for (int e = NV_IT; e < pow2ceil(NV_IT); ++e) v[e] = T(0);
         parts(v, 0, NV_IT);
@@ -1435,8 +1436,25 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
             } else {
               st.iters += 1;
               if (ctl == 1) st.converged = 1;
-              st.ctl = (ctl == 1 || st.iters >= a.max_iter) ? 6 : 0;   // 6: go to the final pass
-              plan_window<C, NP>(st, xc, yc, r, a.W, a.H, tl, XALIGN);
+              const bool done = ctl == 1 || st.iters >= a.max_iter;
+              if (done && !LM) {
+                // Gauss-Newton: the coefficient of this iteration's pass, which was in
+                // bounds and not flat (the update tested both); p includes the update
+                const C sg = s_out[0], sgg = s_out[1], sfg = s_out[3 + NP];
+                const C nu = sg / static_cast<C>(N);
+                const C dg = sqrt(fmax(sgg - sg * nu, C(0)));
+                st.zncc = static_cast<double>((sfg - st.mu * sg) / (st.delta_f * dg));
+                if (!st.converged)
+                  st.status = DIC_PT_MAX_ITER;
+                else if (st.zncc < a.zncc_min)
+                  st.status = DIC_PT_LOW_ZNCC;
+                else
+                  st.status = DIC_PT_OK;
+                st.ctl = 7;
+              } else {
+                st.ctl = done ? 6 : 0;   // 6: Levenberg-Marquardt's final pass
+                plan_window<C, NP>(st, xc, yc, r, a.W, a.H, tl, XALIGN);
+              }
             }
           }
         } else if (lane == 0) {
