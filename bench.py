@@ -34,8 +34,11 @@ UNIT = "points/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-# algorithmic FP32 flops (FMA = 2): per pixel and sample pass of IC-GN, per pixel of
-# the final ZNCC pass, and per pixel of the reference precompute (n(n+1) for JtJ)
+# algorithmic FP32 flops (FMA = 2), the fixed reporting figures of the method: per pixel
+# and sample pass of IC-GN, per pixel of the final ZNCC evaluation, and per pixel of the
+# reference precompute (n(n+1) for JtJ). The Gauss-Newton kernel now takes the ZNCC
+# from its converging pass, so it executes less than this count (about 0.72 of it on
+# the 1 Gpx step)
 FLOP_ITER = {2: 64, 6: 84, 12: 108}
 FLOP_FINAL = 72
 
