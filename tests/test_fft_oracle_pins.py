@@ -243,3 +243,26 @@ def test_fft_seeds_reach_what_the_integer_search_cannot():
     # the default integer search (radius 8) finds no usable start for the seed
     b = O.correlate(ref, dfm, None, 21, 16, O.AFFINE, seeds, dict(conv_threshold=1e-6))
     assert (b["status"] == O.OK).sum() == 0
+
+
+def test_roi_points_only_and_subpixel_field_near_the_truth():
+    # only in-ROI grid points get a last-level value; with the Gaussian fit the field
+    # of a smooth sub-pixel translation lies within a fraction of a pixel of the truth
+    W = H = 256
+    fld = synth.affine_field(W, H, u0=6.3, v0=-4.6)
+    ref = _speckle(W, H, seed=21)
+    dfm = _speckle(W, H, seed=21, fld=fld)
+    roi = np.zeros((H, W), np.uint8)
+    roi[30:220, 40:200] = 1
+    out = F.multiwindow(ref, dfm, roi, 21, 8, 30, subpixel=True)
+    inroi = O.roi_points(roi, W, H, 21, 8).ravel()
+    assert np.array_equal(out["status"] == O.OK, inroi)
+    assert not out["u"][~inroi].any() and not out["peak"][~inroi].any()
+    ok = inroi & (out["peak"] > 0.5)
+    assert ok.sum() > 0.8 * inroi.sum()
+    eu, ev = np.median(np.abs(out["u"][ok] - 6.3)), np.median(np.abs(out["v"][ok] + 4.6))
+    assert eu < 0.35 and ev < 0.35          # the three-point fit locks towards integers a little
+    # without the fit the same field is integer-valued, and further from the truth
+    out_i = F.multiwindow(ref, dfm, roi, 21, 8, 30, subpixel=False)
+    assert np.array_equal(out_i["u"][inroi], np.round(out_i["u"][inroi]))
+    assert np.median(np.abs(out_i["u"][ok] - 6.3)) > eu and np.median(np.abs(out_i["v"][ok] + 4.6)) > ev

@@ -617,3 +617,34 @@ def test_pins_catch_a_planted_transposed_update(monkeypatch):
     monkeypatch.setattr(O, "compose_inverse", bad)
     with pytest.raises(AssertionError):
         test_affine_field_is_recovered_from_an_unquantised_render()
+
+
+def test_final_coefficient_is_taken_at_the_warp_of_reading_8():
+    # Gauss-Newton: the coefficient of the last iteration's pass (the warp before the
+    # final update); Levenberg-Marquardt: one more pass at the final p. Both checked
+    # against numpy's correlation coefficient of independently sampled subsets.
+    w = wl.affine_256_u8()
+    ref = synth.render(w.ref, 256, 256, "f64")
+    dfm = synth.render(w.deformed, 256, 256, "f64")
+    refp, defp = O.Plane(ref), O.Plane(dfm)
+    xc, yc, S = 120, 130, 21
+    dx, dy = O.local_coordinates(S)
+    f = ref[yc + dy.astype(int), xc + dx.astype(int)]
+    start = [2.0, -2.0, 0.0, 0.0, 0.0, 0.0]
+
+    def coefficient(p):
+        wx, wy = O.warp(np.asarray(p, float), dx, dy)
+        g, valid = O.interpolate(defp, xc + wx, yc + wy)
+        assert valid.all()
+        return np.corrcoef(f, g)[0, 1]
+
+    # one Gauss-Newton iteration: the coefficient is the start warp's, p is updated
+    one = O.icgn(refp, defp, xc, yc, S, O.AFFINE, start, dict(max_iter=1, conv_threshold=1e-12))
+    assert one["iters"] == 1 and np.abs(one["p"] - np.array(start)).max() > 0.1
+    assert abs(one["zncc"] - coefficient(start)) < 1e-12
+    # converged: the coefficient of the last pass, within the threshold of the final p's
+    full = O.icgn(refp, defp, xc, yc, S, O.AFFINE, start, dict(conv_threshold=1e-3, max_iter=100))
+    assert full["converged"] and full["status"] == O.OK
+    assert abs(full["zncc"] - coefficient(full["p"])) < 1e-5
+    lm = O.icgn(refp, defp, xc, yc, S, O.AFFINE, start, dict(conv_threshold=1e-3, max_iter=100, optimizer="lm"))
+    assert lm["converged"] and abs(lm["zncc"] - coefficient(lm["p"])) < 1e-14
