@@ -62,7 +62,8 @@ typedef enum { DIC_RIGID = 0, DIC_AFFINE = 1, DIC_QUADRATIC = 2 } dic_shape;
 /* Cost minimised per subset: ZNSSD (Eq. 4, the paper's default), NSSD (Eq. 3) or
  * SSD (Eq. 2). Each enters the IC-GN step through its residual: b = sum SD_i e_i with
  * e_i = fbar_i - (||fbar|| / ||gbar||) gbar_i, f_i - (||f|| / ||g||) g_i or f_i - g_i.
- * The reported coefficient and the acceptance test remain the ZNCC at the final p. */
+ * The reported coefficient and the acceptance test remain the ZNCC (see zncc in
+ * dic_results for the warp it is taken at). */
 typedef enum { DIC_COST_ZNSSD = 0, DIC_COST_NSSD = 1, DIC_COST_SSD = 2 } dic_cost;
 
 /* Per-subset optimiser (Sec. 2.2 names Levenberg-Marquardt and leaves the details to
@@ -90,9 +91,10 @@ typedef enum { DIC_BSPLINE3 = 0, DIC_BICUBIC = 1 } dic_interp;
  *                    integer, halves up (the paper's default MULTIWINDOW_RG). */
 typedef enum { DIC_INIT_SEARCH = 0, DIC_INIT_FFT = 1 } dic_init;
 
-/* DIC_MIXED: gray levels kept in their input type, spline coefficients, samples
- * and sums in FP32, Hessian solve, parameter update and final ZNCC in FP64.
- * DIC_FP64: FP64 everywhere. */
+/* DIC_MIXED: gray levels kept in their input type; interpolation coefficients,
+ * samples, sums, the Jacobi-scaled Hessian inverse (FP64 when a scaled pivot falls
+ * below 1e-5), the solve, the warp update and the ZNCC normalisation in FP32;
+ * results stored as FP64. DIC_FP64: FP64 everywhere. */
 typedef enum { DIC_FP64 = 0, DIC_MIXED = 1 } dic_precision;
 
 /* per-point status (dic_results.status) */
@@ -147,7 +149,10 @@ typedef struct {
   const double* u;           /* [n_points] p0: displacement at the centre, px        */
   const double* v;           /* [n_points] p1                                        */
   const double* p;           /* [n_points][n_params], Eq. 5 parameters               */
-  const float* zncc;         /* [n_points] ZNCC = 1 - ZNSSD/2 at the final p (NaN if none) */
+  const float* zncc;         /* [n_points] ZNCC = 1 - ZNSSD/2 (NaN if none): Gauss-Newton */
+                             /* takes it from its last iteration's pass (the warp the  */
+                             /* final, sub-threshold update was computed at; p includes */
+                             /* that update), Levenberg-Marquardt at the final p        */
   const int32_t* iters;      /* [n_points] parameter updates applied                 */
   const uint8_t* converged;  /* [n_points] 1 if ||dp|| < conv_threshold was met      */
   const uint8_t* status;     /* [n_points] DIC_PT_*                                  */
