@@ -7,11 +7,13 @@
 //      interpolant (cubic B-spline, or bicubic convolution) at the S x S pixels,
 //      and the Gauss-Newton Hessian
 //      H = sum SD^T SD of the steepest-descent images SD = grad f . dxi/dp,
-//      assembled from gradient moments and factorised (Cholesky) in FP64;
-//   3. inverse-compositional Gauss-Newton: sample the deformed interpolant at
-//      the warped pixels, reduce sum g, sum g^2 and sum SD g, solve
-//      dp = -H^-1 sum SD (f - f_m - (df/dg)(g - g_m)) in FP64, update
-//      p <- p o dp^-1, stop when ||dp|| < threshold;
+//      assembled from gradient moments; its Jacobi-scaled inverse by warp-parallel
+//      Gauss-Jordan (FP32 on the mixed path, with an FP64 fallback; FP64 on the
+//      FP64 path);
+//   3. inverse-compositional Gauss-Newton (or Levenberg-Marquardt): sample the
+//      deformed interpolant at the warped pixels, reduce sum g, sum g^2, sum SD g
+//      and sum f g, solve dp = -H^-1 b with b = sum SD e of the cost (Eq. 2-4),
+//      update p <- p o dp^-1, stop when ||dp|| < threshold;
 //   4. ZNCC = sum (f - f_m)(g - g_m) / (df dg) from the converging iteration's
 //      sampling pass (Levenberg-Marquardt: one more pass at the final p); accept
 //      when converged, in bounds and ZNCC >= cut-off;
