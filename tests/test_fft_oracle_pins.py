@@ -5,7 +5,9 @@ from its definition, exact recovery of circular and non-circular integer shifts
 vertex of exact Gaussian samples, bilinear reproduction of linear fields, the
 median/MAD rule on hand-built neighbourhoods, and large displacements that the
 integer ZNCC search cannot reach. CPU only."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -24,10 +26,13 @@ def _speckle(W, H, seed=11, fld=synth.IDENTITY, dtype="f64", noise=0.0):
 
 
 def test_window_sizes_follow_the_papers_example():
-    # Sec. 2.2: maximum displacement about 800 px, subset 17
-    assert F.window_sizes(800, 17, 5000, 5000) == [1024, 512, 256, 128, 64, 32, 17]
-    # Sec. 4 SEM study: maximum 2000 px, subset 31 (a 32768 px image)
-    assert F.window_sizes(2000, 31, 32768, 32768) == [2048, 1024, 512, 256, 128, 64, 32, 31]
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fft_window_sizes.json")) as fh:
+        g = json.load(fh)
+    ex = g["example"]                  # Sec. 2.2's worked example
+    assert F.window_sizes(ex["max_displacement"], ex["subset_size"], 5000, 5000) == ex["windows"]
+    sem = g["sem_study"]               # Sec. 4: the SEM study's settings on a 32768 px image
+    assert F.window_sizes(sem["max_displacement"], sem["subset_size"], 32768, 32768) == \
+        [2048, 1024, 512, 256, 128, 64, 32, 31]
     # windows larger than the image are dropped; no displacement: the subset alone
     assert F.window_sizes(800, 17, 300, 600) == [256, 128, 64, 32, 17]
     assert F.window_sizes(0, 21, 256, 256) == [21]
