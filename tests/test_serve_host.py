@@ -188,3 +188,22 @@ def test_serving_stream_recipe():
         w = j.workload
         assert 15 <= w.subset_size <= 61 and w.subset_size % 2 == 1 and 1 <= w.subset_step <= 10
         assert 512 <= w.width <= 16384 and w.width == w.height and w.dtype in ("u8", "u16")
+
+
+def test_engine_cache_key_separates_what_the_resident_reference_depends_on():
+    # the resident reference plane differs with the interpolant and the precision, so
+    # jobs that differ there must not share a cached handle; seeds, subsets and the
+    # other parameters do not enter the key (no GPU call: the key is host logic)
+    pytest.importorskip("torch")
+    from paper_2601_12941_gb300.serve import Job, LibdicEngine
+
+    eng = LibdicEngine()
+    ref = np.zeros((64, 80), np.uint8)
+    base = dict(ref=ref, deformed=ref, seeds=[(40, 32)], ref_key="r0")
+    k = eng.cache_key(Job(**base))
+    assert k == eng.cache_key(Job(**base, subset_size=31, subset_step=2, shape="quadratic",
+                                  params=dict(cost="nssd", optimizer="lm", init="fft")))
+    assert k != eng.cache_key(Job(**base, interp="bicubic"))
+    assert k != eng.cache_key(Job(**base, params=dict(precision="fp64")))
+    assert k != eng.cache_key(Job(**dict(base, ref=ref.astype(np.uint16))))
+    assert eng.cache_key(Job(**dict(base, ref_key=None))) is None
