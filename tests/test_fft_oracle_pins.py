@@ -65,6 +65,19 @@ def test_eq1_is_the_circular_zncc_computed_by_brute_force(L):
     assert np.abs(R / np.sqrt(np.sum(fb * fb) * np.sum(gb * gb)) - want).max() < 1e-12
 
 
+@pytest.mark.parametrize("L", [21, 31, 32, 64])
+def test_eq1_matches_scipys_wrapped_spatial_correlation(L):
+    # scipy's spatial correlation with periodic boundaries, its kernel origin at the
+    # centre (hence the roll by -floor(L/2)), on the mean-removed windows
+    from scipy import ndimage
+
+    f = RNG.uniform(0, 255, (L, L))
+    g = RNG.uniform(0, 255, (L, L))
+    fb, gb = f - f.mean(), g - g.mean()
+    c = np.roll(ndimage.correlate(fb, gb, mode="wrap"), (-(L // 2), -(L // 2)), (0, 1))
+    assert np.abs(F.fftcc(f, g) - c / np.sqrt(np.sum(fb * fb) * np.sum(gb * gb))).max() < 1e-12
+
+
 def test_eq1_is_invariant_to_gain_and_offset_and_zero_on_flat_windows():
     f = RNG.uniform(0, 255, (16, 16))
     g = RNG.uniform(0, 255, (16, 16))
