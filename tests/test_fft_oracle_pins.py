@@ -284,3 +284,39 @@ def test_roi_points_only_and_subpixel_field_near_the_truth():
     out_i = F.multiwindow(ref, dfm, roi, 21, 8, 30, subpixel=False)
     assert np.array_equal(out_i["u"][inroi], np.round(out_i["u"][inroi]))
     assert np.median(np.abs(out_i["u"][ok] - 6.3)) > eu and np.median(np.abs(out_i["v"][ok] + 4.6)) > ev
+
+
+def test_mad_rule_matches_scipy_filters_on_interior_points():
+    from scipy import ndimage
+
+    u = RNG.integers(-3, 4, (30, 40)).astype(float)
+    v = RNG.normal(0.0, 1.0, (30, 40))
+    u[RNG.random(u.shape) < 0.05] += 25.0
+    fu, fv, rep = F.mad_filter(u, v, np.ones(u.shape, bool))
+    mad = lambda w: np.median(np.abs(w - np.median(w)))
+    for c, f in ((u, fu), (v, fv)):
+        med = ndimage.median_filter(c, size=3, mode="nearest")
+        dev = ndimage.generic_filter(c, mad, size=3, mode="nearest")
+        out = np.abs(c - med) > 3.0 * (1.4826 * dev + 0.5)
+        inner = (slice(1, -1), slice(1, -1))
+        # outliers in either component take both medians
+        assert np.all(rep[inner] >= out[inner])
+        assert np.array_equal(f[inner][rep[inner]], med[inner][rep[inner]])
+    bu = np.abs(u - ndimage.median_filter(u, 3, mode="nearest")) > 3.0 * (
+        1.4826 * ndimage.generic_filter(u, mad, size=3, mode="nearest") + 0.5)
+    bv = np.abs(v - ndimage.median_filter(v, 3, mode="nearest")) > 3.0 * (
+        1.4826 * ndimage.generic_filter(v, mad, size=3, mode="nearest") + 0.5)
+    assert np.array_equal(rep[1:-1, 1:-1], (bu | bv)[1:-1, 1:-1])
+
+
+def test_bilinear_matches_scipys_regular_grid_interpolator_inside():
+    from scipy.interpolate import RegularGridInterpolator
+
+    ny, nx, L = 6, 9, 32
+    field = RNG.normal(0.0, 3.0, (ny, nx))
+    cx = np.arange(nx) * L + L / 2
+    cy = np.arange(ny) * L + L / 2
+    interp = RegularGridInterpolator((cy, cx), field)
+    x = RNG.uniform(cx[0], cx[-1], 300)
+    y = RNG.uniform(cy[0], cy[-1], 300)
+    assert np.abs(F.bilinear(field, L / 2, L, x, y) - interp(np.stack([y, x], 1))).max() < 1e-12
