@@ -111,3 +111,21 @@ def test_nearest_index_ties_go_low_and_out_of_range_is_none():
     assert I.nearest_index(2.5, 10) == 2 and I.nearest_index(2.51, 10) == 3 and I.nearest_index(-0.49, 10) == 0
     assert I.nearest_index(-0.5, 10) is None                 # the tie goes to -1, outside the grid
     assert I.nearest_index(9.5, 10) == 9 and I.nearest_index(9.51, 10) is None
+
+
+def test_roi_points_stay_out_and_totals_follow_the_field():
+    W = H = 200
+    frames = _frames(W, H, [0.0, 0.03, 0.06])
+    roi = np.zeros((H, W), np.uint8)
+    roi[15:185, 20:170] = 1
+    seeds = [(100, 100)]
+    inc = I.correlate_incremental(frames, roi, 21, 10, O.AFFINE, seeds, PRM, update_after=(1,))
+    inroi = O.roi_points(roi, W, H, 21, 10).ravel()
+    for res, tot in inc:
+        assert (tot["status"][~inroi] == O.NOT_IN_ROI).all() and (res["status"][~inroi] == O.NOT_IN_ROI).all()
+        assert not tot["p"][~inroi].any()
+    tot = inc[-1][1]
+    ok = tot["status"] == O.OK
+    assert ok.sum() > 0.6 * inroi.sum()
+    # the composed gradient of two 3 % steps is the 6 % field
+    assert np.abs(tot["p"][ok][:, 2] - 0.06).max() < 2e-3 and np.abs(tot["p"][ok][:, 5] + 0.024).max() < 2e-3
