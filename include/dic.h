@@ -69,8 +69,11 @@ typedef enum { DIC_COST_ZNSSD = 0, DIC_COST_NSSD = 1, DIC_COST_SSD = 2 } dic_cos
 /* Per-subset optimiser (Sec. 2.2 names Levenberg-Marquardt and leaves the details to
  * the literature): undamped inverse-compositional Gauss-Newton (default), or
  * Levenberg-Marquardt with Marquardt's diagonal damping H + lambda diag(H), lambda from
- * 1e-3, divided by 10 when a trial lowers the cost and multiplied by 10 when it does
- * not (the step is then retaken from the best warp so far). Both reach the same root. */
+ * 1e-3. A trial warp is kept when it is the first, lowers the cost (Eq. 2-4) or
+ * shortens the undamped Gauss-Newton step; keeping it divides lambda by 10, refusing
+ * it multiplies lambda by 10, and the next step is always taken from the best trial
+ * so far. A point has converged when the best trial's undamped step is below
+ * conv_threshold (that step is then applied). Both optimisers reach the same root. */
 typedef enum { DIC_OPT_GAUSS_NEWTON = 0, DIC_OPT_LEVENBERG_MARQUARDT = 1 } dic_optimizer;
 
 /* Interpolant of the gray levels at sub-pixel positions.
@@ -490,6 +493,17 @@ int dic_correlate_static(const dic_image* ref, const dic_image* def, int32_t sub
                          int32_t subset_step, int32_t shape_fn, const dic_params* params,
                          const int32_t* seeds_xy, int32_t n_seeds, const dic_static_outputs* out,
                          void* cuda_stream, char* errbuf, int32_t errlen);
+
+/* Test hook for the timeout path; the paper has no counterpart. Every wait inside a
+ * kernel is bounded: the wave kernel polls the mbarrier of a tile load at most
+ * 65,536 times, and a wait that runs out sets an error flag, lets the copy in
+ * flight land (a second bounded wait), ends its block and makes dic_correlate /
+ * dic_correlate_sequence return DIC_ETIMEOUT. on != 0 makes the first of those
+ * waits give up at once in every wave launched afterwards by this process (the
+ * second wait keeps its full bound, so no copy is left in flight); 0 restores
+ * normal waits. Results of a run that timed out are incomplete; the handle stays
+ * usable. Returns DIC_OK. Not for production use. */
+int dic_test_expire_tile_waits(int32_t on);
 
 /* Frees every buffer of the handle (NULL is ignored). */
 void dic_destroy(dic_handle* h);

@@ -42,7 +42,8 @@ EXPORTS = ("dic_default_params", "dic_create", "dic_set_params", "dic_get_params
            "dic_correlate_static", "dic_correlate_sequence", "dic_set_subsets",
            "dic_estimate_device_bytes", "dic_estimate_regrid_bytes", "dic_get_device_bytes",
            "dic_strain_field", "dic_fft_default_params", "dic_fft_field", "dic_get_fft_results",
-           "dic_fftcc_windows", "dic_mad_filter", "dic_update_reference", "dic_get_total_results")
+           "dic_fftcc_windows", "dic_mad_filter", "dic_update_reference", "dic_get_total_results",
+           "dic_test_expire_tile_waits")
 
 
 class DicImage(ctypes.Structure):
@@ -155,6 +156,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.dic_destroy.restype = None
     lib.dic_last_error.argtypes = []
     lib.dic_last_error.restype = ctypes.c_char_p
+    lib.dic_test_expire_tile_waits.argtypes = [ctypes.c_int32]
+    lib.dic_test_expire_tile_waits.restype = ctypes.c_int
     lib.dic_correlate_static.argtypes = [P(DicImage), P(DicImage), ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, P(DicParams), P(ctypes.c_int32), ctypes.c_int32,
                                          P(DicStaticOutputs), vp, ctypes.c_char_p, ctypes.c_int32]
@@ -391,16 +394,62 @@ def dic_destroy(h):
         load().dic_destroy(h)
 
 
+def dic_test_expire_tile_waits(on: bool):
+    """Test hook: tile-load waits of later wave launches give up at once (True) or
+    run normally (False)."""
+    _check(load().dic_test_expire_tile_waits(1 if on else 0))
+
+
 def dic_last_error() -> str:
     return load().dic_last_error().decode(errors="replace")
+
+
+def _device_output(t, name: str, dtype, count: int):
+    """Raises DicError unless t is a contiguous CUDA tensor of the current device with
+    the given dtype and at least count elements: the C side receives only the raw
+    pointer and writes count elements through it."""
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise DicError(DIC_EINVAL, "output %s is not a tensor" % name)
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise DicError(DIC_EINVAL, "output %s must be a CUDA tensor of the current device" % name)
+    if t.dtype != dtype:
+        raise DicError(DIC_EINVAL, "output %s has dtype %s, %s is needed" % (name, t.dtype, dtype))
+    if not t.is_contiguous():
+        raise DicError(DIC_EINVAL, "output %s must be contiguous" % name)
+    if t.numel() < count:
+        raise DicError(DIC_EINVAL, "output %s holds %d elements, %d are needed" % (name, t.numel(), count))
+
+
+def grid_size(width: int, height: int, subset_size: int, subset_step: int) -> tuple:
+    """(nx, ny) of the subset grid: centres r + k step, n = (side - 1 - 2r) // step + 1."""
+    r = (subset_size - 1) // 2
+    return (width - 1 - 2 * r) // subset_step + 1, (height - 1 - 2 * r) // subset_step + 1
 
 
 def dic_correlate_static(ref, deformed, subset_size, subset_step, shape_fn, prm: DicParams, seeds,
                          out: dict, stream_ptr: int = 0) -> int:
     """Allocation-free correlation into caller-owned CUDA tensors ``out`` (keys u, v,
-    p, zncc, iters, converged, status, wave); returns the accepted-point count."""
+    p, zncc, iters, converged, status, wave); returns the accepted-point count. Every
+    output is checked against the grid size before the call."""
+    import torch
+
     ri, rk = make_image(ref)
     di, dk = make_image(deformed)
+    if 3 <= subset_size <= min(ri.width, ri.height) and subset_step >= 1 and shape_fn in N_PARAMS:
+        nx, ny = grid_size(ri.width, ri.height, subset_size, subset_step)
+        n = max(nx, 0) * max(ny, 0)
+        for name, dt, cnt in (("u", torch.float64, n), ("v", torch.float64, n),
+                              ("p", torch.float64, n * N_PARAMS[shape_fn]), ("zncc", torch.float32, n),
+                              ("iters", torch.int32, n), ("converged", torch.uint8, n),
+                              ("status", torch.uint8, n), ("wave", torch.int32, n)):
+            _device_output(out.get(name), name, dt, cnt)
+    else:
+        # the library refuses these arguments before touching any output
+        for name in ("u", "v", "p", "zncc", "iters", "converged", "status", "wave"):
+            if not isinstance(out.get(name), torch.Tensor):
+                raise DicError(DIC_EINVAL, "output %s is not a tensor" % name)
     s = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).reshape(-1, 2))
     acc = ctypes.c_int64(0)
     o = DicStaticOutputs(*[out[k].data_ptr() for k in ("u", "v", "p", "zncc", "iters", "converged",
@@ -418,8 +467,16 @@ def dic_correlate_static(ref, deformed, subset_size, subset_step, shape_fn, prm:
 def dic_strain_field(u, v, status, nx, ny, subset_step, window, basis, measure, out: dict, stream_ptr: int = 0):
     """Sec. 2.3 strain on device arrays: u, v (float64), status (uint8) CUDA tensors of
     nx * ny points; out maps STRAIN_FIELDS to CUDA tensors (float32, valid uint8)."""
+    import torch
+
     basis = STRAIN_BASES[basis] if isinstance(basis, str) else basis
     measure = STRAIN_MEASURES[measure] if isinstance(measure, str) else measure
+    n = max(int(nx), 0) * max(int(ny), 0)
+    _device_output(u, "u", torch.float64, n)
+    _device_output(v, "v", torch.float64, n)
+    _device_output(status, "status", torch.uint8, n)
+    for k in STRAIN_FIELDS:
+        _device_output(out.get(k), k, torch.uint8 if k == "valid" else torch.float32, n)
     o = DicStrainOutputs(*[out[k].data_ptr() for k in STRAIN_FIELDS])
     _check(load().dic_strain_field(ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()),
                                    ctypes.c_void_p(status.data_ptr()), nx, ny, subset_step, window, basis, measure,
@@ -483,7 +540,12 @@ def dic_get_fft_results(h) -> dict:
 def dic_fftcc_windows(h, window: int, origins, subpixel: bool, u, v, peak, stream_ptr: int = 0):
     """Eq. 1 over explicit windows: origins an int32 CUDA tensor [n, 4] of (x0, y0,
     gx0, gy0); u, v, peak float32 CUDA tensors [n]."""
+    import torch
+
     n = int(origins.shape[0])
+    _device_output(origins, "origins", torch.int32, 4 * n)
+    for name, t in (("u", u), ("v", v), ("peak", peak)):
+        _device_output(t, name, torch.float32, n)
     _check(load().dic_fftcc_windows(h, window, n, ctypes.c_void_p(origins.data_ptr()), 1 if subpixel else 0,
                                     ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()),
                                     ctypes.c_void_p(peak.data_ptr()), ctypes.c_void_p(stream_ptr)))
@@ -492,6 +554,14 @@ def dic_fftcc_windows(h, window: int, origins, subpixel: bool, u, v, peak, strea
 def dic_mad_filter(u, v, valid, nx: int, ny: int, tau: float, eps: float, u_out, v_out, replaced=None,
                    stream_ptr: int = 0):
     """The initialiser's MAD rule on float32 CUDA tensors of nx * ny values."""
+    import torch
+
+    n = max(int(nx), 0) * max(int(ny), 0)
+    for name, t, dt in (("u", u, torch.float32), ("v", v, torch.float32), ("u_out", u_out, torch.float32),
+                        ("v_out", v_out, torch.float32), ("valid", valid, torch.uint8),
+                        ("replaced", replaced, torch.uint8)):
+        if t is not None or name in ("u", "v", "u_out", "v_out"):
+            _device_output(t, name, dt, n)
     ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
     _check(load().dic_mad_filter(ptr(u), ptr(v), ptr(valid), nx, ny, tau, eps, ptr(u_out), ptr(v_out),
                                  ptr(replaced), ctypes.c_void_p(stream_ptr)))

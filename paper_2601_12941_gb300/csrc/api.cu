@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -20,6 +21,8 @@ using namespace dic;
 namespace {
 
 thread_local std::string g_last_error;
+// dic_test_expire_tile_waits: 1 makes every later wave launch give up its tile waits
+std::atomic<int> g_expire_waits{0};
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -401,6 +404,7 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   a.interp = h->interp;
   a.conv_threshold = h->prm.conv_threshold;
   a.zncc_min = h->prm.zncc_min;
+  a.expire_waits = g_expire_waits.load();
 
   int sms = 0;
   DIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "device query");
@@ -419,10 +423,23 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   for (int i = 0; i < kBatchSlots; ++i)
     if (!batch_ev[i] && cudaEventCreateWithFlags(&batch_ev[i], cudaEventDisableTiming) != cudaSuccess)
       return fail(DIC_ECUDA, "event creation failed");
+  // A non-empty wave holds at least one point never attempted before, so at most
+  // npts waves are non-empty and the front of wave npts is empty: launching up to
+  // max_waves waves always reaches an empty front. Batches are clipped to that
+  // bound; the loop fails only when every allowed wave has been launched and the
+  // last batch still left a front.
   bool done = false;
   while (!done) {
-    if (launched + batch > max_waves) return fail(DIC_ETIMEOUT, "wave loop exceeded %lld waves", (long long)max_waves);
-    for (int b = 0; b < batch; ++b) {
+    if (launched >= max_waves) {
+      if (pending_slot >= 0) {
+        DIC_CUDA(cudaEventSynchronize(batch_ev[pending_slot]), "wave batch wait");
+        const int32_t* pc = h->h_counters + pending_slot * kNumCounters;
+        if (pc[kCount + pending_end % 3] == 0) break;
+      }
+      return fail(DIC_ETIMEOUT, "wave loop exceeded %lld waves", (long long)max_waves);
+    }
+    const int nb = static_cast<int>(batch < max_waves - launched ? batch : max_waves - launched);
+    for (int b = 0; b < nb; ++b) {
       const int64_t k = launched + b;
       a.k = static_cast<int>(k);
       a.cur = h->front[k & 1];
@@ -437,7 +454,7 @@ int run_waves(dic_handle* h, cudaStream_t s) {
         DIC_CUDA(launch_wave<T>(a, a.tiles, h->maps, h->nparams, grid, s), "wave launch");
       }
     }
-    launched += batch;
+    launched += nb;
     int32_t* hc = h->h_counters + slot * kNumCounters;
     DIC_CUDA(cudaMemcpyAsync(hc, h->counters, sizeof(int32_t) * kNumCounters, cudaMemcpyDeviceToHost, s),
              "counter read-back");
@@ -997,6 +1014,11 @@ dic_fft_params dic_fft_default_params(void) {
 }
 
 const char* dic_last_error(void) { return g_last_error.c_str(); }
+
+int dic_test_expire_tile_waits(int32_t on) {
+  g_expire_waits.store(on != 0 ? 1 : 0);
+  return DIC_OK;
+}
 
 int dic_create(const dic_image* ref, const dic_image* def, const dic_image* roi, int32_t subset_size,
                int32_t subset_step, int32_t shape_fn, int32_t interp, dic_handle** out) {

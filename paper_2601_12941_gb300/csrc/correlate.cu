@@ -1065,8 +1065,10 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
   __syncthreads();
   uint32_t bar_phase = 0;
   // every thread waits for the pending TMA transaction; a lost wait ends the block
+  // (a.expire_waits: the wait gives up without polling; the drain below still lets
+  // the copy land before the block exits)
   auto tma_wait = [&]() -> bool {
-    const bool ok = mbar_wait_bounded(&s_bar, bar_phase);
+    const bool ok = !a.expire_waits && mbar_wait_bounded(&s_bar, bar_phase);
     bar_phase ^= 1u;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {

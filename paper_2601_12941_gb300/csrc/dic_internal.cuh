@@ -281,6 +281,8 @@ struct WaveArgs {
   int interp;                // dic_interp of the coefficient planes
   double conv_threshold;
   double zncc_min;
+  int expire_waits;          // 1 (tests of the timeout path only): every tile-load wait
+                             // gives up at once, as a wait that ran out of polls would
 };
 
 // Block size of the wave kernel for subset side S: two warps up to S = 31, four

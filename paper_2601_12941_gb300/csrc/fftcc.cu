@@ -14,8 +14,9 @@
 //
 // Two paths:
 //   * L <= 64 (the subset-sized last level, and the 32 / 64 levels): one block per
-//     window, the whole window in shared memory; radix-2 Stockham FFTs along rows
-//     and columns for powers of two, a direct DFT for the odd subset size.
+//     window, the whole window in shared memory; radix-4 Stockham FFTs (one radix-2
+//     pass when log2 L is odd) along rows and columns for powers of two, a direct
+//     DFT for the odd subset size.
 //   * 128 <= L <= 4096: the window in a global work buffer; row FFTs, an in-place
 //     tile transpose, paired-row FFTs that form the cross power and transform it
 //     back, a transpose back and the inverse row FFTs with a per-window arg-max

@@ -292,13 +292,16 @@ extern "C" int dic_correlate_static(const dic_image* ref, const dic_image* def, 
   SCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
   const int grid = sms * wave_blocks_per_sm<float>(nparams, a.threads, wave_mode(a.lm, a.cost, a.interp),
                                                     static_cast<size_t>(a.tiles.smem_bytes));
+  // A non-empty wave holds at least one point never attempted before, so the front
+  // of wave npts is empty: batches are clipped to max_waves launches in all, and the
+  // loop fails only if the front is still non-empty after the last allowed wave.
   int32_t hc[kNumCounters];
   int64_t k = 0;
   const int64_t max_waves = npts + 2;
   for (;;) {
-    const int batch = 8;
-    if (k + batch > max_waves) return sfail(DIC_ETIMEOUT, "wave loop exceeded its bound");
-    for (int b = 0; b < batch; ++b, ++k) {
+    if (k >= max_waves) return sfail(DIC_ETIMEOUT, "wave loop exceeded its bound");
+    const int64_t batch = max_waves - k < 8 ? max_waves - k : 8;
+    for (int64_t b = 0; b < batch; ++b, ++k) {
       a.k = static_cast<int>(k);
       a.cur = (k & 1) ? front1 : front0;
       a.next = (k & 1) ? front0 : front1;

@@ -144,3 +144,30 @@ def test_loading_fails_loudly_without_the_library(tmp_path):
             binding.load(str(tmp_path / "missing.so"))
         finally:
             binding._lib = binding._lib_saved
+
+
+def test_pointer_entry_points_refuse_outputs_they_cannot_write(lib):
+    """The calls that take raw device pointers (the allocation-free correlation,
+    strain, FFT windows, MAD) cannot check what a pointer holds, so the binding
+    refuses host tensors, wrong dtypes and short buffers before the call."""
+    import torch
+
+    from paper_2601_12941_gb300 import binding as B
+
+    ref = np.zeros((64, 64), np.uint8)
+    n = 1
+    out = dict(u=torch.zeros(n, dtype=torch.float64), v=torch.zeros(n, dtype=torch.float64),
+               p=torch.zeros(n * 6, dtype=torch.float64), zncc=torch.zeros(n, dtype=torch.float32),
+               iters=torch.zeros(n, dtype=torch.int32), converged=torch.zeros(n, dtype=torch.uint8),
+               status=torch.zeros(n, dtype=torch.uint8), wave=torch.zeros(n, dtype=torch.int32))
+    with pytest.raises(B.DicError) as e:
+        B.dic_correlate_static(ref, ref, 21, 40, B.DIC_AFFINE, B.params(), [(32, 32)], out)
+    assert e.value.code == B.DIC_EINVAL and "CUDA" in str(e.value)
+    with pytest.raises(B.DicError):
+        B.dic_strain_field(torch.zeros(4, dtype=torch.float64), torch.zeros(4, dtype=torch.float64),
+                           torch.zeros(4, dtype=torch.uint8), 2, 2, 5, 3, "bilinear", "green_lagrange",
+                           {k: torch.zeros(4) for k in B.STRAIN_FIELDS})
+    with pytest.raises(B.DicError):
+        B.dic_mad_filter(torch.zeros(4), torch.zeros(4), None, 2, 2, 3.0, 0.5, torch.zeros(4), torch.zeros(4))
+    assert B.grid_size(256, 256, 21, 5) == (48, 48)
+    assert B.grid_size(32768, 32768, 41, 10) == (3273, 3273)

@@ -63,13 +63,39 @@ def _dev(a):
     return torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).cuda()
 
 
-def test_sine_2048_u16_quadratic_full_size(pkg):
+def _sine_taylor_start(fld, xc, yc, h=0.5):
+    """The analytic field's second-order expansion at the centre in Eq. 5's
+    parameters (no 1/2 factor on the quadratic terms), by central differences."""
+    X = np.array([xc, xc + h, xc - h, xc, xc, xc + h, xc - h, xc + h, xc - h], float)
+    Y = np.array([yc, yc, yc, yc + h, yc - h, yc + h, yc + h, yc - h, yc - h], float)
+    out = []
+    for f in synth.displacement(fld, X, Y):
+        fx, fy = (f[1] - f[2]) / (2 * h), (f[3] - f[4]) / (2 * h)
+        fxx, fyy = (f[1] - 2 * f[0] + f[2]) / h ** 2, (f[3] - 2 * f[0] + f[4]) / h ** 2
+        fxy = (f[5] - f[6] - f[7] + f[8]) / (4 * h * h)
+        out.append((f[0], fx, fy, 0.5 * fxx, fxy, 0.5 * fyy))
+    (u, ux, uy, uxx, uxy, uyy), (v, vx, vy, vxx, vxy, vyy) = out
+    return [u, v, ux, uy, vx, vy, uxx, uxy, uyy, vxx, vxy, vyy]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sine_2048_u16_quadratic_full_size(pkg, precision):
+    """The 2048^2 quadratic workload in both precisions. Periods above ~80 px
+    (x > 500): the 12-parameter warp follows the sine and the minimum near the
+    analytic start is unique, so the oracle, started there, must give the GPU's
+    status and parameters. Shorter periods (150 < x <= 500, T 31-80 px): the cost
+    has several minima within a fraction of a pixel (the oracle's roots from the
+    analytic start move by up to 0.5 px), so which one a point reaches depends on
+    its start (the neighbour's warp on the GPU); there each accepted GPU point is
+    checked to be a valid answer: a stationary point of the cost (one oracle
+    Gauss-Newton step from it moves it by less than the parity tolerances) whose
+    correlation coefficient clears the cut-off."""
     w = wl.sine_2048_u16()
     W, H, S = w.width, w.height, w.subset_size
     ref = synth.render(w.ref, W, H, "u16")
     dfm = synth.render(w.deformed, W, H, "u16")
-    c = pkg.Correlation(_dev(ref), _dev(dfm), None, S, w.subset_step, w.shape, precision="mixed",
-                        search_radius=w.search_radius, **GPU_PARAMS["mixed"])
+    c = pkg.Correlation(_dev(ref), _dev(dfm), None, S, w.subset_step, w.shape, precision=precision,
+                        search_radius=w.search_radius, **GPU_PARAMS[precision])
     c.run(list(w.seeds))
     res = c.results()
     c.close()
@@ -78,7 +104,6 @@ def test_sine_2048_u16_quadratic_full_size(pkg):
     assert ok.mean() > 0.95
     refp, defp = O.Plane(ref), O.Plane(dfm)
     rng = np.random.default_rng(7)
-    # periods above ~80 px: the 12-parameter warp follows the sine and the minimum is unique
     cand = np.flatnonzero((res["x"] > 500) & (res["wave"] >= 0))
     pick = rng.choice(cand, 40, replace=False)
     errs = []
@@ -91,8 +116,23 @@ def test_sine_2048_u16_quadratic_full_size(pkg):
         if ora["status"] == O.OK:
             d = np.abs(res["p"][q] - ora["p"])
             assert d[:2].max() <= TOL_UV and d[2:].max() <= TOL_P, (q, d)
+            assert abs(float(res["zncc"][q]) - ora["zncc"]) <= 1e-5, q
             errs.append(d[:2].max())
-    print("sine 2048: %d accepted of %d, sampled max |du,dv| %.2e" % (ok.sum(), ok.size, max(errs)))
+    # short periods: validity of the GPU's root
+    short = np.flatnonzero((res["x"] > 150) & (res["x"] <= 500) & ok)
+    n_moved = 0
+    for q in rng.choice(short, 30, replace=False):
+        xc, yc = int(res["x"][q]), int(res["y"][q])
+        one = O.icgn(refp, defp, xc, yc, S, "quadratic", list(res["p"][q]), dict(ORACLE_PARAMS, max_iter=1))
+        assert one["status"] in (O.OK, O.MAX_ITER), (q, one["status"])
+        d = np.abs(one["p"] - res["p"][q])
+        assert d[:2].max() <= TOL_UV and d[2:].max() <= TOL_P, (q, d)
+        assert one["zncc"] >= 0.70 and abs(float(res["zncc"][q]) - one["zncc"]) <= 1e-5, q
+        # and the oracle's own start lands on a root of the same quality
+        ana = O.icgn(refp, defp, xc, yc, S, "quadratic", _sine_taylor_start(w.field, xc, yc), ORACLE_PARAMS)
+        n_moved += int(ana["status"] != O.OK or np.abs(ana["p"][:2] - res["p"][q][:2]).max() > TOL_UV)
+    print("sine 2048 %s: %d accepted of %d, sampled max |du,dv| %.2e; short periods: 30 valid roots, "
+          "%d of them not the root the analytic start reaches" % (precision, ok.sum(), ok.size, max(errs), n_moved))
 
 
 def test_gigapixel_32768_u8_full_size(pkg):

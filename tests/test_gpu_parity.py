@@ -91,7 +91,7 @@ def test_affine_256_u8_matches_oracle(pkg, precision):
     ora = _oracle("affine256", ref, dfm, None, w.subset_size, w.subset_step, w.shape, w.seeds, prm)
     gpu = _run(pkg, ref, dfm, None, w.subset_size, w.subset_step, w.shape, w.seeds, precision,
                search_radius=w.search_radius)
-    stats = compare(gpu, ora, w.width, w.height, w.subset_size)
+    stats = compare(gpu, ora, w.width, w.height, w.subset_size, precision=precision)
     assert stats["accepted"] > 2000
     if precision == "fp64":
         assert stats["max_uv"] < 1e-8 and stats["max_p"] < 1e-9
@@ -109,7 +109,7 @@ def test_quadratic_sine_u16_matches_oracle(pkg, precision):
     ora = _oracle("sine230", ref, dfm, None, S, step, "quadratic", w.seeds, prm)
     gpu = _run(pkg, ref, dfm, None, S, step, "quadratic", w.seeds, precision,
                search_radius=w.search_radius)
-    stats = compare(gpu, ora, W, H, S)
+    stats = compare(gpu, ora, W, H, S, precision=precision)
     assert stats["accepted"] > 0.8 * stats["points"]
     print(precision, stats)
 
@@ -121,7 +121,7 @@ def test_rigid_matches_oracle(pkg, precision):
     prm = dict(ORACLE_PARAMS, search_radius=6)
     ora = _oracle("rigid150", ref, dfm, None, 15, 4, "rigid", [(75, 66)], prm)
     gpu = _run(pkg, ref, dfm, None, 15, 4, "rigid", [(75, 66)], precision, search_radius=6)
-    compare(gpu, ora, W, H, 15)
+    compare(gpu, ora, W, H, 15, precision=precision)
 
 
 def test_roi_hole_two_seeds_and_out_of_roi_seed(pkg):
@@ -210,6 +210,84 @@ def test_large_strain_uses_global_fallback_and_matches_oracle(pkg, precision):
     prm = dict(ORACLE_PARAMS, search_radius=3)
     ora = _oracle("strain160", ref, dfm, None, 21, 6, "affine", [(80, 75)], prm)
     gpu = _run(pkg, ref, dfm, None, 21, 6, "affine", [(80, 75)], precision, search_radius=3)
-    stats = compare(gpu, ora, W, H, 21)
+    stats = compare(gpu, ora, W, H, 21, precision=precision)
     assert stats["accepted"] >= 4
     print(precision, stats)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bf16_gray_levels_equal_the_u8_run_and_match_oracle(pkg, precision):
+    """Gray levels stored as BF16 (the gigapixel workload's storage type): a BF16
+    tensor holding u8 values represents them exactly, so every result equals the u8
+    run's bit for bit, and both match the oracle."""
+    W, H = 190, 170
+    fld = synth.affine_field(W, H, u0=-1.3, v0=2.1, exx=1.2e-3, eyy=-6e-4, exy=3e-4, eyx=3e-4)
+    ref, dfm = _pair(W, H, fld, dtype="u8", seed=202, noise=2.0)
+    seeds = [(95, 85)]
+    prm = dict(ORACLE_PARAMS, search_radius=4)
+    ora = _oracle("bf16_190", ref, dfm, None, 21, 5, "affine", seeds, prm)
+    a = _run(pkg, ref, dfm, None, 21, 5, "affine", seeds, precision, search_radius=4)
+    rb = torch.from_numpy(ref).cuda().to(torch.bfloat16)
+    db = torch.from_numpy(dfm).cuda().to(torch.bfloat16)
+    assert torch.equal(rb.float(), torch.from_numpy(ref).cuda().float())
+    c = pkg.Correlation(rb, db, None, 21, 5, "affine", precision=precision, search_radius=4,
+                        **GPU_PARAMS[precision])
+    c.run(seeds)
+    b = c.results()
+    c.close()
+    for k in ("p", "zncc", "status", "wave", "iters"):
+        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k]), equal_nan=k == "zncc"), k
+    stats = compare(b, ora, W, H, 21, precision=precision)
+    assert stats["accepted"] > 0.9 * stats["points"]
+    print(precision, stats)
+
+
+@pytest.mark.parametrize("W,H,S,step,seed", [
+    (40, 40, 21, 10, (20, 20)),      # 2 x 2 grid
+    (25, 25, 21, 10, (12, 12)),      # one point
+    (260, 26, 21, 6, (12, 12)),      # one row of 40 points, seeded at its left end: 40 waves
+    (24, 200, 21, 5, (12, 190)),     # one column of 36 points, seeded at its bottom end
+])
+def test_tiny_grids_and_one_row_strips_match_oracle(pkg, W, H, S, step, seed):
+    """Grids with fewer points than the first wave batches, and strips with as many
+    waves as points: the wave loop must finish on the empty front. The field moves
+    every subset at least 1.3 px away from the top and left edges (centres start at
+    r, so an unmoved subset there starts at row or column 0, outside the sampling
+    bounds)."""
+    fld = synth.affine_field(W, H, u0=1.5, v0=1.5, exx=1e-3)
+    ref, dfm = _pair(W, H, fld, dtype="u8", seed=303)
+    prm = dict(ORACLE_PARAMS, search_radius=2)
+    ora = oracle.correlate(ref, dfm, None, S, step, "affine", [seed], prm)
+    assert (ora["status"] == O.OK).sum() >= max(1, 0.9 * len(ora["status"]))
+    for precision in ("fp64", "mixed"):
+        gpu = _run(pkg, ref, dfm, None, S, step, "affine", [seed], precision, search_radius=2)
+        stats = compare(gpu, ora, W, H, S, precision=precision)
+        assert stats["accepted"] >= max(1, 0.9 * stats["points"]), stats
+
+
+def test_acceptance_is_decided_at_the_warp_of_the_last_pass(pkg):
+    """Reading 8: the in-bounds test belongs to the last iteration's sampling pass. A
+    point whose single pass lies inside the bounds is accepted although the update
+    carries its subset past the right edge; the GPU agrees with the oracle."""
+    from scipy import ndimage
+
+    W, H = 64, 40
+    rng = np.random.default_rng(3)
+    base = ndimage.gaussian_filter(rng.random((H, W + 8)), 1.5) * 200.0
+    ref = np.ascontiguousarray(base[:, 4:4 + W]).astype(np.float32)
+    dfm = np.ascontiguousarray(base[:, 1:1 + W]).astype(np.float32)
+    S, r = 11, 5
+    step = 17                            # centres x = 5, 22, 39, 56 and y = 5, 22
+    seed = (W - 2 - r - 1, 22)           # x = 56: at p = 0 its last column is x = W - 3
+    prm = dict(max_iter=1, conv_threshold=10.0, zncc_min=-1.0, search_radius=0)
+    ora = oracle.correlate(ref.astype(np.float64), dfm.astype(np.float64), None, S, step, "affine", [seed], prm)
+    q = int(np.flatnonzero(np.asarray(ora["wave"]) == 0)[0])
+    assert ora["status"][q] == O.OK and ora["p"][q][0] > 1.0
+    for precision in ("fp64", "mixed"):
+        c = pkg.Correlation(torch.from_numpy(ref).cuda(), torch.from_numpy(dfm).cuda(), None, S, step, "affine",
+                            precision=precision, **prm)
+        c.run([seed])
+        g = c.results()
+        c.close()
+        assert g["status"][q] == O.OK and g["iters"][q] == 1
+        assert abs(g["p"][q][0] - ora["p"][q][0]) < 1e-4

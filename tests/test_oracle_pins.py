@@ -648,3 +648,116 @@ def test_final_coefficient_is_taken_at_the_warp_of_reading_8():
     assert abs(full["zncc"] - coefficient(full["p"])) < 1e-5
     lm = O.icgn(refp, defp, xc, yc, S, O.AFFINE, start, dict(conv_threshold=1e-3, max_iter=100, optimizer="lm"))
     assert lm["converged"] and abs(lm["zncc"] - coefficient(lm["p"])) < 1e-14
+
+
+# --------------------------------------------------------------------------- ROI rule
+# Sec. 2.1 gives the region of interest as a boolean mask; the rule read from it is
+# that a grid point is in the ROI when every pixel of its S x S reference subset is
+# in the mask. The expected flags below are worked out by hand from that rule (they
+# are not computed by the oracle).
+
+def _mask(W, H, value=True):
+    return np.full((H, W), value, dtype=bool)
+
+
+def test_roi_rule_one_hole_pixel_removes_exactly_the_subsets_that_cover_it():
+    # 12 x 12, S = 5 (r = 2), step 1: centres 2..9 on both axes (8 x 8 points). A hole
+    # at (x, y) = (5, 5) lies in the subsets with centres 3..7 on both axes.
+    m = _mask(12, 12)
+    m[5, 5] = False
+    got = O.roi_points(m, 12, 12, 5, 1)
+    want = np.ones((8, 8), bool)
+    want[1:6, 1:6] = False            # centres 3..7 are indices 1..5
+    assert got.shape == (8, 8)
+    assert np.array_equal(got, want)
+    assert got.sum() == 39
+    # the hole at each corner of a subset: centre (7, 7) has it at its top-left
+    # corner, (3, 3) at its bottom-right, (7, 3) at its bottom-left, (3, 7) at its
+    # top-right; one step further out the subset misses it
+    for xc, yc in ((7, 7), (3, 3), (7, 3), (3, 7)):
+        assert not got[yc - 2, xc - 2], (xc, yc)
+    for xc, yc in ((8, 7), (2, 3), (7, 8), (3, 2)):
+        assert got[yc - 2, xc - 2], (xc, yc)
+
+
+def test_roi_rule_mask_edge_exactly_at_the_subset_edge():
+    # mask true for x <= 7 only: centre xc is in when xc + r <= 7, i.e. xc <= 5 (r = 2)
+    m = _mask(12, 12)
+    m[:, 8:] = False
+    got = O.roi_points(m, 12, 12, 5, 1)
+    want = np.zeros((8, 8), bool)
+    want[:, :4] = True                # centres 2, 3, 4, 5
+    assert np.array_equal(got, want)
+    # the same edge along y: true for y >= 4 only, so yc - r >= 4, yc >= 6
+    m = _mask(12, 12)
+    m[:4, :] = False
+    got = O.roi_points(m, 12, 12, 5, 1)
+    want = np.zeros((8, 8), bool)
+    want[4:, :] = True                # centres 6, 7, 8, 9
+    assert np.array_equal(got, want)
+
+
+def test_roi_rule_narrow_regions():
+    # a one-pixel-wide ROI holds no subset of side 3 or more
+    m = _mask(12, 12, False)
+    m[:, 6] = True
+    assert not O.roi_points(m, 12, 12, 3, 1).any()
+    assert not O.roi_points(m, 12, 12, 5, 1).any()
+    # a band exactly S wide (columns 3..7, S = 5) holds one column of centres, xc = 5
+    m = _mask(12, 12, False)
+    m[:, 3:8] = True
+    got = O.roi_points(m, 12, 12, 5, 1)
+    want = np.zeros((8, 8), bool)
+    want[:, 3] = True
+    assert np.array_equal(got, want)
+
+
+def test_roi_rule_with_a_step():
+    # 10 x 10, S = 3 (r = 1), step 3: centres 1, 4, 7 per axis; subsets cover
+    # columns (and rows) 0..2, 3..5 and 6..8. A hole at (4, 4) lies in the subset of
+    # centre (4, 4) only; so does a hole at (x, y) = (3, 5).
+    m = _mask(10, 10)
+    m[4, 4] = False
+    got = O.roi_points(m, 10, 10, 3, 3)
+    want = np.ones((3, 3), bool)
+    want[1, 1] = False
+    assert np.array_equal(got, want)
+    m = _mask(10, 10)
+    m[5, 3] = False                   # row y = 5, column x = 3
+    assert np.array_equal(O.roi_points(m, 10, 10, 3, 3), want)
+    # a hole at (2, 0) lies in the subset of centre (1, 1) only
+    m = _mask(10, 10)
+    m[0, 2] = False
+    want = np.ones((3, 3), bool)
+    want[0, 0] = False
+    assert np.array_equal(O.roi_points(m, 10, 10, 3, 3), want)
+    # row 9 and column 9 lie in no subset: a hole there removes nothing
+    m = _mask(10, 10)
+    m[9, :] = False
+    m[:, 9] = False
+    assert O.roi_points(m, 10, 10, 3, 3).all()
+
+
+def test_out_of_bounds_test_applies_to_the_warp_of_the_last_pass():
+    # Reading 8: Gauss-Newton takes the coefficient, the in-bounds test and the
+    # flatness test from the sampling pass of its last iteration, whose warp is the one
+    # before the final update. A point whose last pass lies inside the sampling bounds
+    # is accepted even when the final update carries its subset outside them.
+    W, H = 64, 40
+    rng = np.random.default_rng(3)
+    base = ndimage.gaussian_filter(rng.random((H, W + 8)), 1.5) * 200.0
+    ref = np.ascontiguousarray(base[:, 4:4 + W])
+    dfm = np.ascontiguousarray(base[:, 1:1 + W])        # the content moves 3 px to +x
+    refp, defp = O.Plane(ref), O.Plane(dfm)
+    S, r = 11, 5
+    xc, yc = W - 2 - r - 1, 20                          # at p = 0 the last column is x = W - 3
+    prm = dict(max_iter=1, conv_threshold=10.0, zncc_min=-1.0)
+    res = O.icgn(refp, defp, xc, yc, S, O.AFFINE, [0.0] * 6, prm)
+    assert res["iters"] == 1 and res["converged"] and res["status"] == O.OK
+    assert res["p"][0] > 1.0                            # the update moved the subset right
+    dx, dy = O.local_coordinates(S)
+    wx, wy = O.warp(res["p"], dx, dy)
+    _, valid = O.interpolate(defp, xc + wx, yc + wy)
+    assert not valid.all()                              # the final warp leaves the bounds
+    _, valid0 = O.interpolate(defp, xc + dx, yc + dy)
+    assert valid0.all()                                 # the pass that decided was inside
