@@ -31,36 +31,89 @@ if ROOT not in sys.path:
 METRIC = ("converged subset-points/sec (1 Gpx pair, affine) vs plain FP64 GPU; "
           "p50/p99 pair latency")
 UNIT = "points/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-# algorithmic FP32 flops (FMA = 2), the fixed reporting figures of the method: per pixel
-# and sample pass of IC-GN, per pixel of the final ZNCC evaluation, and per pixel of the
-# reference precompute (n(n+1) for JtJ). The Gauss-Newton kernel now takes the ZNCC
-# from its converging pass, so it executes less than this count (about 0.72 of it on
-# the 1 Gpx step)
+# Algorithmic FP32 flops of the wave kernel (FMA = 2), the method's reporting count:
+# per pixel and sampling pass of IC-GN (warp, B-spline weights, the 4 x 4 contraction,
+# sum g and sum g^2, sum SD g: 64 rigid, 84 affine, 108 quadratic), per pixel of a
+# separate final ZNCC pass (72), and n(n+1) per pixel for the reference precompute
+# (J^T J). The Gauss-Newton kernel takes the ZNCC from its converging pass instead of
+# a separate pass, with one more sum (sum f'g', 2 flops) in every pass: the executed
+# count is n(n+1) + passes x (count + 2) per pixel, passes = iterations (+1 for a pass
+# that left the sampling bounds).
 FLOP_ITER = {2: 64, 6: 84, 12: 108}
 FLOP_FINAL = 72
+FLOP_COEFF_SUM = 2
+PT_OUT_OF_BOUNDS = 3
+
+# DRAM bytes (read + write) per attempted point of the wave kernel, from one ncu
+# capture of the current kernel (None: not captured since the kernel last changed)
+WAVE_DRAM_BYTES_PER_POINT = None
 
 
-# DRAM bytes (read + write) per point of the wave kernel as last captured by ncu (a
-# full capture of two mid-run waves of 2,560 points on the 6144^2 version of the
-# workload: 31.37 MB per launch), or None when the kernel has changed since (the
-# roofline then reports no traffic)
-WAVE_DRAM_BYTES_PER_POINT = None   # the kernel changed after the last capture (12,250 B per point then)
+def sm_count():
+    """Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount)."""
+    import torch
+
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 
-def fp32_peak_tflops():
-    """152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz maximum SM clock."""
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+def sm_max_mhz():
+    """Maximum SM clock: the generated peaks file, else nvidia-smi, else 2070 MHz."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except (OSError, KeyError, ValueError):
+        pass
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
+        return float(out[0]), "nvidia-smi clocks.max.sm"
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return 2070.0, "nominal"
 
 
-def algorithmic_flops(iters, status, wave, S, nparams):
+def fp32_peak():
+    """FP32 peak in TFLOP/s: SM count (from the device) x 128 FP32 lanes x 2 (FMA) x
+    the maximum SM clock; derived from unit counts and clocks (no measured FP32
+    peak exists for this pool). Returns (peak, note, sms, mhz)."""
+    sms = sm_count()
+    mhz, src = sm_max_mhz()
+    return (sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
+            "derived: %d SMs (device attribute) x %d FP32 lanes x 2 (FMA) x %.0f MHz (%s)"
+            % (sms, FP32_LANES_PER_SM, mhz, src), sms, mhz)
+
+
+def survey_flops(iters, status, wave, S, nparams):
+    """The method's fixed reporting count: (iters x per-pass + final pass) S^2 + n(n+1) S^2."""
     attempted = wave >= 0
     it = iters[attempted].astype(np.float64)
     px = float(S * S)
-    pre = px * nparams * (nparams + 1)
-    return float(np.sum((it * FLOP_ITER[nparams] + FLOP_FINAL) * px + pre))
+    return float(np.sum((it * FLOP_ITER[nparams] + FLOP_FINAL) * px + px * nparams * (nparams + 1)))
+
+
+def executed_flops(iters, status, wave, S, nparams, final_pass=False):
+    """Work the Gauss-Newton kernel executes: n(n+1) S^2 per attempted point plus
+    (per-pass count + 2) S^2 per sampling pass; final_pass: one more pass per
+    attempted point (Levenberg-Marquardt)."""
+    attempted = wave >= 0
+    passes = iters[attempted].astype(np.float64) + (status[attempted] == PT_OUT_OF_BOUNDS)
+    if final_pass:
+        passes = passes + 1.0
+    px = float(S * S)
+    return float(np.sum(passes * (FLOP_ITER[nparams] + FLOP_COEFF_SUM) * px + px * nparams * (nparams + 1)))
+
+
+def wave_roofline(res, S, nparams, kernel_ms, final_pass=False):
+    """Roofline of the wave kernels of one correlation: executed TFLOP/s over the
+    summed wave-kernel time, against the derived FP32 peak; the fixed reporting
+    count beside it."""
+    peak, note, sms, mhz = fp32_peak()
+    ex = executed_flops(res["iters"], res["status"], res["wave"], S, nparams, final_pass)
+    sv = survey_flops(res["iters"], res["status"], res["wave"], S, nparams)
+    t = kernel_ms / 1e3
+    return {"bound": "alu", "achieved": ex / t / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": ex / t / 1e12 / peak,
+            "frac_survey_count": sv / t / 1e12 / peak, "kernel_ms": kernel_ms, "sm_count": sms, "sm_max_mhz": mhz,
+            "peak_note": note, "algorithmic_gflop": ex / 1e9, "survey_count_gflop": sv / 1e9}
 
 
 class Clocks:
@@ -243,11 +296,22 @@ def run_ours(args):
     res = c.results()
     accepted = int(res["n_accepted"])
     attempted = int((res["wave"] >= 0).sum())
-    flops = algorithmic_flops(res["iters"], res["status"], res["wave"], w.subset_size, nparams)
     ms_per_step, value = aggregate(ranks, total_ms / args.steps, accepted)
     kern_avg = kern_ms / args.steps
-    achieved = flops / (kern_avg / 1e3) / 1e12
     tm = c.timing()
+    roof = wave_roofline(res, w.subset_size, nparams, kern_avg)
+    per_launch = attempted / (sum(wave_launches) / len(wave_launches))
+    roof.update({"kernel": "wave_kernel<float, 6, 128, 0> (fused reference precompute, IC-GN, ZNCC, claims)",
+                 "traffic": WAVE_DRAM_BYTES_PER_POINT * per_launch if WAVE_DRAM_BYTES_PER_POINT else None,
+                 "traffic_note": "bytes per launch: DRAM bytes per attempted point (ncu capture of the 6144^2 "
+                                 "case) x attempted points per wave launch; the kernel is ALU-bound",
+                 "kernel_ms_per_step": kern_avg, "share_of_step": kern_avg / (total_ms / args.steps),
+                 "achieved_note": "achieved = executed FP32 flops of the step's wave kernels / their summed "
+                                  "CUDA-event durations (%d launches per step)" % (sum(wave_launches) / len(wave_launches))})
+    # prefilter of both images: HBM-bound, 1 B read + 4 B written per pixel and image
+    hbm, hbm_note = hbm_peak_gbs()
+    pf_bytes = 2.0 * (1 + 4) * w.width * w.height
+    pf_gbs = pf_bytes / (tm["prefilter_ms"] / 1e3) / 1e9 if tm["prefilter_ms"] > 0 else None
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -258,22 +322,20 @@ def run_ours(args):
                                   % (w.width, w.height, w.subset_size, w.subset_step, len(seeds),
                                      w.search_radius),
                       "points": int(res["n_points"]), "accepted": accepted, "attempted": attempted,
-                      "waves": int(res["n_waves"]), "precision": "mixed (u8 gray; f32 spline, sums, Jacobi-scaled solve and ZNCC)",
+                      "waves": int(res["n_waves"]),
+                      "precision": "DIC_MIXED: u8 gray levels; FP32 spline coefficients, samples, sums, "
+                                   "Jacobi-scaled Hessian inverse, solve and ZNCC normalisation; FP64 results "
+                                   "(config 3 as written, BF16 gray and FP64 solves: see config3_as_written)",
                       "controls": "max_iter 40, threshold 0.01, zncc_min 0.70",
                       "l2": "no flush: each step reads two 1.07 GB gray planes and writes two 4.3 GB coefficient planes, above the 129 MB L2",
                       "parallelism": "replicas x%d" % world},
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
            "gpu_launches": launches,
-           "roofline": {"bound": "alu", "kernel": "wave_kernel (fused reference precompute, IC-GN, ZNCC, claims)",
-                        "achieved": achieved, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
-                        "frac": achieved / fp32_peak_tflops(),
-                        "traffic": (WAVE_DRAM_BYTES_PER_POINT * attempted / (sum(wave_launches) / len(wave_launches))
-                                    if WAVE_DRAM_BYTES_PER_POINT else None),
-                        "traffic_note": "bytes per launch: DRAM bytes per point (ncu, 6144^2 case) x attempted "
-                                        "points per wave launch; algorithmic bytes are not the bound (ALU)",
-                        "peak_note": "FP32 peak from 152 SMs x 128 lanes x 2 x 2070 MHz (no measured FP32 peak)",
-                        "kernel_ms_per_step": kern_avg, "share_of_step": kern_avg / (total_ms / args.steps),
-                        "algorithmic_gflop_per_step": flops / 1e9},
+           "roofline": roof,
+           "prefilter": {"bound": "hbm", "kernel": "prefilter_iir_kernel<u8> (2 images)", "ms_per_step": tm["prefilter_ms"],
+                         "achieved": pf_gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": pf_gbs / hbm if pf_gbs else None, "peak_note": hbm_note,
+                         "algorithmic_bytes_per_pixel": 5},
            "stages_ms": {k: tm[k] for k in ("prefilter_ms", "setup_ms", "waves_ms", "seed_kernel_ms")},
            "clocks": clocks}
 
@@ -288,12 +350,20 @@ def run_ours(args):
     if not args.no_fp64:
         c64 = P.Correlation(ref, dfm, None, w.subset_size, w.subset_step, w.shape, precision="fp64",
                             search_radius=w.search_radius, profile=1)
-        t64, lat64, _, _ = timed_steps(c64, 1, 1)
+        t64, lat64, k64, _ = timed_steps(c64, args.fp64_steps, 1)
         r64 = c64.results()
-        v64 = sum_over_ranks(int(r64["n_accepted"])) / (max_over_ranks(t64) / 1e3)
-        out["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": t64,
+        v64 = sum_over_ranks(int(r64["n_accepted"])) / (max_over_ranks(t64 / args.fp64_steps) / 1e3)
+        out["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": t64 / args.fp64_steps,
+                             "steps": args.fp64_steps, "wave_kernel_ms": k64 / args.fp64_steps,
                              "speedup_of_mixed": value / v64 if v64 else None}
+        out["vs_fp64_plain"] = value / v64 if v64 else None
         c64.close()
+    if not args.no_variants:
+        out["config3_as_written"] = config3_leg(args, P, ref, dfm, w, seeds, stream, timed_steps)
+
+    if rank == 0 and not args.no_oracle_error:
+        # the oracle's error report of the headline step's result (host work, after the timing)
+        out["oracle_error"] = oracle_error_gigapixel(res, w, args.oracle_points)
 
     if not args.no_strain:
         out["strain"] = strain_leg(c, w, stream)
@@ -305,17 +375,259 @@ def run_ours(args):
     del ref, dfm
     torch.cuda.empty_cache()
 
+    if not args.no_configs:
+        out["config1"] = config1_leg(P, stream, rank == 0 and not args.no_oracle_error)
+        out["config2"] = config2_leg(P, stream, rank == 0 and not args.no_oracle_error)
     if args.seq_frames > 0:
         out["sequence"] = sequence_leg(args, stream)
+        if not args.no_configs:
+            out["sequence_subsets"] = [sequence_variant_leg(args, stream, S, shape, frames)
+                                       for S, shape, frames in ((31, "affine", 100), (41, "affine", 100),
+                                                                (21, "quadratic", 100), (41, "quadratic", 50))]
     if args.serve_jobs > 0 and world == 1:
         out["serving"] = serving_leg(args)
 
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(w, out["cpu_baseline"])
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def config3_leg(args, P, ref, dfm, w, seeds, stream, timed_steps):
+    """Config 3 as its description reads: gray levels in BF16 (the u8 pair converted on
+    the device, outside the timed region; u8 values are exact in BF16), coefficients
+    in FP32, and the Hessian inverse, the solve and the final ZNCC normalisation in
+    FP64 (DIC_MIXED_FP64_SOLVE). Same grid, seeds and controls as the headline."""
+    import torch
+
+    rb = ref.to(torch.bfloat16)
+    db = dfm.to(torch.bfloat16)
+    torch.cuda.synchronize()
+    c = P.Correlation(rb, db, None, w.subset_size, w.subset_step, w.shape, precision="mixed_fp64_solve",
+                      search_radius=w.search_radius, profile=1)
+    steps = max(2, min(args.steps, 5))
+    t, lat, kern, _ = timed_steps(c, steps, 1)
+    r = c.results()
+    tm = c.timing()
+    c.close()
+    acc = int(r["n_accepted"])
+    out = {"precision": "DIC_MIXED_FP64_SOLVE: BF16 gray levels, FP32 coefficients, samples and sums; FP64 Hessian "
+                        "inverse, solve (one refinement step) and ZNCC normalisation",
+           "steps": steps, "ms_per_step": t / steps, "points_per_s": acc / (t / steps / 1e3), "accepted": acc,
+           "prefilter_ms": tm["prefilter_ms"],
+           "roofline": wave_roofline(r, w.subset_size, 6, kern / steps)}
+    if not args.no_oracle_error:
+        out["oracle_error"] = oracle_error_gigapixel(r, w, max(60, args.oracle_points // 4))
+    del rb, db
+    return out
+
+
+def oracle_error_gigapixel(res, w, n_points, seed=2026):
+    """Error of a 1 Gpx result against the FP64 oracle on a seeded sample of points:
+    each sampled point is correlated by the oracle from the analytic field (start:
+    the field's displacement and gradient at the centre) on host-rendered crops, to
+    its converged root (threshold 1e-8, 100 iterations); the GPU result was taken at
+    the bench's controls. Three fifths of the sample lie away from the slip line, the
+    rest near it (their subsets just clear it); subsets that cross the line have no
+    single affine root and are counted apart (status agreement only)."""
+    import oracle
+    import synth
+    from oracle import dic_oracle as O
+
+    fld = w.field
+    S, r = w.subset_size, (w.subset_size - 1) // 2
+    X = res["x"].astype(np.float64) - fld.cx
+    Y = res["y"].astype(np.float64) - fld.cy
+    dist = np.abs(Y - X) / np.sqrt(2.0)
+    clear = r * np.sqrt(2.0) + 1.0
+    inside = (res["x"] > 200) & (res["x"] < w.width - 200) & (res["y"] > 200) & (res["y"] < w.height - 200)
+    att = res["wave"] >= 0
+    rng = np.random.default_rng(seed)
+    far = np.flatnonzero(inside & att & (dist > clear + 40))
+    near = np.flatnonzero(inside & att & (dist > clear) & (dist <= clear + 40))
+    cross = np.flatnonzero(inside & att & (dist <= clear - 2.0))
+    n_near = n_points * 2 // 5
+    pick = np.concatenate([rng.choice(far, n_points - n_near, replace=False),
+                           rng.choice(near, min(n_near, len(near)), replace=False)])
+    pad = 48 + r + 16
+    du, dp, agree, both = [], [], 0, 0
+    t0 = time.perf_counter()
+
+    def run_point(q, p0):
+        xc, yc = int(res["x"][q]), int(res["y"][q])
+        x0, y0, side = xc - pad, yc - pad, 2 * pad + 1
+        rc, roff = synth.render_crop(w.ref, w.width, w.height, x0, y0, side, side, w.dtype)
+        dc, doff = synth.render_crop(w.deformed, w.width, w.height, x0, y0, side, side, w.dtype)
+        refp = O.Plane(rc, roff[0], roff[1], w.width, w.height)
+        defp = O.Plane(dc, doff[0], doff[1], w.width, w.height)
+        return O.icgn(refp, defp, xc, yc, S, "affine", p0, dict(conv_threshold=1e-8, max_iter=100))
+
+    for q in pick:
+        xc, yc = float(res["x"][q]), float(res["y"][q])
+        u, v = synth.displacement(fld, np.array([xc]), np.array([yc]))
+        ora = run_point(q, [u[0], v[0], fld.exx, fld.exy, fld.eyx, fld.eyy])
+        g_ok = res["status"][q] == 0
+        o_ok = ora["status"] == O.OK
+        agree += int(g_ok == o_ok)
+        if g_ok and o_ok:
+            both += 1
+            d = np.abs(np.asarray(res["p"][q]) - ora["p"])
+            du.append(d[:2].max())
+            dp.append(d[2:].max())
+    cross_pick = rng.choice(cross, min(20, len(cross)), replace=False) if len(cross) else []
+    cross_agree = 0
+    for q in cross_pick:
+        xc, yc = float(res["x"][q]), float(res["y"][q])
+        u, v = synth.displacement(fld, np.array([xc]), np.array([yc]))
+        ora = run_point(q, [u[0], v[0], fld.exx, fld.exy, fld.eyx, fld.eyy])
+        cross_agree += int((res["status"][q] == 0) == (ora["status"] == O.OK))
+    du, dp = np.array(du), np.array(dp)
+    return {"sample": "%d points (%d away from the slip line, %d near it), oracle from the analytic field on "
+                      "host-rendered crops, converged to 1e-8" % (len(pick), n_points - n_near, len(pick) - (n_points - n_near)),
+            "both_accepted": both, "status_agreement": "%d/%d" % (agree, len(pick)),
+            "max_uv_px": float(du.max()) if both else None, "mean_uv_px": float(du.mean()) if both else None,
+            "max_p2_5": float(dp.max()) if both else None, "mean_p2_5": float(dp.mean()) if both else None,
+            "crossing_slip_line_status_agreement": "%d/%d" % (cross_agree, len(cross_pick)),
+            "note": "the GPU stopped at the bench's threshold (0.01 on ||dp||), the oracle at 1e-8: the error "
+                    "includes the unconverged remainder the paper's threshold leaves",
+            "oracle_seconds": time.perf_counter() - t0}
+
+
+def pair_leg(P, ref, dfm, w, precision, stream, steps, warmup=2):
+    """One workload pair timed on the device (reference and deformed set, prefilter,
+    seed search, every wave), results left on the device; returns the last result."""
+    import torch
+
+    c = P.Correlation(ref, dfm, None, w.subset_size, w.subset_step, w.shape, precision=precision,
+                      search_radius=w.search_radius, profile=1)
+    for _ in range(warmup):
+        c.set_reference(ref)
+        c.set_deformed(dfm)
+        c.run(list(w.seeds), stream.cuda_stream)
+    stream.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    kern = 0.0
+    lat = []
+    a.record(stream)
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.set_reference(ref)
+        c.set_deformed(dfm)
+        c.run(list(w.seeds), stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        lat.append(e0.elapsed_time(e1))
+        kern += c.timing()["icgn_kernel_ms"]
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    r = c.results()
+    c.close()
+    nparams = P.N_PARAMS[P.SHAPES[w.shape]]
+    acc = int(r["n_accepted"])
+    return r, {"precision": precision, "steps": steps, "ms_per_step": ms, "points_per_s": acc / (ms / 1e3),
+               "accepted": acc, "points": int(r["n_points"]), "waves": int(r["n_waves"]),
+               "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+               "roofline": wave_roofline(r, w.subset_size, nparams, kern / steps)}
+
+
+def _parity_stats(gpu, ora):
+    """Status agreement and parameter errors of a whole-grid GPU result against the
+    oracle's correlation of the same pair (same controls)."""
+    sg, so = np.asarray(gpu["status"]).astype(int), np.asarray(ora["status"]).astype(int)
+    both = (sg == 0) & (so == 0)
+    pg, po = np.asarray(gpu["p"])[both], np.asarray(ora["p"])[both]
+    d = np.abs(pg - po)
+    return {"status_agreement": "%d/%d" % (int((sg == so).sum()), len(so)), "both_accepted": int(both.sum()),
+            "max_uv_px": float(d[:, :2].max()) if both.any() else None,
+            "mean_uv_px": float(d[:, :2].mean()) if both.any() else None,
+            "max_p2": float(d[:, 2:].max()) if both.any() and d.shape[1] > 2 else None,
+            "max_zncc": float(np.abs(np.asarray(gpu["zncc"], np.float64)[both] - ora["zncc"][both]).max())
+            if both.any() else None}
+
+
+def config1_leg(P, stream, with_oracle):
+    """Config 1: the 256^2 u8 affine pair (2,304 points, subset 21, step 5, one seed),
+    the plain FP64 form and the mixed form, each against the oracle's correlation of
+    the whole pair at the same (Sec. 4 default) controls."""
+    import torch
+
+    import oracle
+    import synth
+    from synth import workloads as wl
+
+    w = wl.affine_256_u8()
+    ref_h = synth.render(w.ref, w.width, w.height, "u8")
+    dfm_h = synth.render(w.deformed, w.width, w.height, "u8")
+    ref, dfm = torch.from_numpy(ref_h).cuda(), torch.from_numpy(dfm_h).cuda()
+    out = {"workload": "%s: %dx%d u8, subset %d, step %d, affine, 1 seed, Sec. 4 default controls"
+                       % (w.name, w.width, w.height, w.subset_size, w.subset_step)}
+    ora = None
+    if with_oracle:
+        t0 = time.perf_counter()
+        ora = oracle.correlate(ref_h, dfm_h, None, w.subset_size, w.subset_step, w.shape, list(w.seeds),
+                               dict(search_radius=w.search_radius))
+        out["oracle_seconds"] = time.perf_counter() - t0
+    for prec in ("fp64", "mixed"):
+        r, d = pair_leg(P, ref, dfm, w, prec, stream, steps=20)
+        if ora is not None:
+            d["oracle_error"] = _parity_stats(r, ora)
+        out[prec] = d
+    return out
+
+
+def config2_leg(P, stream, with_oracle, n_oracle=40):
+    """Config 2: the 2048^2 u16 sine pair (1,018,081 points, subset 31, step 2,
+    quadratic), FP64 and mixed; oracle error on a seeded sample of points with periods
+    above 80 px (x > 500), each correlated by the oracle from the analytic field's
+    rounded displacement to its converged root."""
+    import torch
+
+    import synth
+    from oracle import dic_oracle as O
+    from synth import workloads as wl
+
+    w = wl.sine_2048_u16()
+    ref_h = synth.render(w.ref, w.width, w.height, "u16")
+    dfm_h = synth.render(w.deformed, w.width, w.height, "u16")
+    ref = torch.from_numpy(ref_h.view(np.int16)).cuda()
+    dfm = torch.from_numpy(dfm_h.view(np.int16)).cuda()
+    out = {"workload": "%s: %dx%d u16 (12-bit), v = 0.5 sin(2 pi y / T(x)), T 10-300 px, 1%% noise, subset %d, "
+                       "step %d, quadratic, Sec. 4 default controls"
+                       % (w.name, w.width, w.height, w.subset_size, w.subset_step)}
+    refp = dfp = None
+    if with_oracle:
+        refp, dfp = O.Plane(ref_h), O.Plane(dfm_h)
+    for prec, steps in (("fp64", 2), ("mixed", 5)):
+        r, d = pair_leg(P, ref, dfm, w, prec, stream, steps=steps, warmup=1)
+        if refp is not None:
+            rng = np.random.default_rng(17)
+            cand = np.flatnonzero((r["x"] > 500) & (r["status"] == 0))
+            errs, perr, agree = [], [], 0
+            for q in rng.choice(cand, n_oracle, replace=False):
+                xc, yc = int(r["x"][q]), int(r["y"][q])
+                u, v = synth.displacement(w.field, np.array([float(xc)]), np.array([float(yc)]))
+                ora = O.icgn(refp, dfp, xc, yc, w.subset_size, "quadratic", [round(u[0]), round(v[0])],
+                             dict(conv_threshold=1e-8, max_iter=100))
+                agree += int(ora["status"] == O.OK)
+                if ora["status"] == O.OK:
+                    dd = np.abs(np.asarray(r["p"][q]) - ora["p"])
+                    errs.append(dd[:2].max())
+                    perr.append(dd[2:].max())
+            d["oracle_error"] = {"sample": "%d accepted points with x > 500, oracle converged to 1e-8" % n_oracle,
+                                 "oracle_accepts": "%d/%d" % (agree, n_oracle),
+                                 "max_uv_px": float(max(errs)) if errs else None,
+                                 "mean_uv_px": float(np.mean(errs)) if errs else None,
+                                 "max_p2_11": float(max(perr)) if perr else None}
+        out[prec] = d
+    out["speedup_of_mixed"] = out["mixed"]["points_per_s"] / out["fp64"]["points_per_s"]
+    return out
 
 
 def hbm_peak_gbs():
@@ -472,9 +784,9 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel
             "gpu_launches": launches,
             "last_level_ms": k, "last_level_share": k / t,
             "roofline": {"bound": "alu", "kernel": "fftcc_small_kernel<odd> (direct DFT, one window per block)",
-                         "achieved": achieved, "peak": fp32_peak_tflops(), "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak_tflops(), "algorithmic_flops_per_window": 22 * S ** 3 + 2 * S ** 2,
-                         "peak_note": "FP32 peak from 152 SMs x 128 lanes x 2 x 2070 MHz"}}
+                         "achieved": achieved, "peak": fp32_peak()[0], "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak()[0], "algorithmic_flops_per_window": 22 * S ** 3 + 2 * S ** 2,
+                         "peak_note": fp32_peak()[1]}}
 
 
 def e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_ranks):
@@ -509,30 +821,35 @@ def e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_
             "d2h_bytes_per_step": int(d2h), "points": n}
 
 
-def sequence_leg(args, stream):
+def run_sequence(stream, S, shape, frames, oracle_points=20):
     """Frames of the incremental uniaxial sequence (4096 x 3000 u16, strain ramping
-    to 2e-2 over 200 frames, 1% noise), subset 21, step 10, affine: frame 1 from the
-    seed, every later frame from the previous frame's field (dic_correlate_sequence)
-    against the resident frame-0 reference. Per-frame latency covers the deformed
-    prefilter and every wave; frames are rendered outside the timed region."""
+    to 2e-2 over 200 frames, 1% noise), step 10, subset S and shape function given:
+    frame 1 from the seed, every later frame from the previous frame's field
+    (dic_correlate_sequence) against the resident frame-0 reference. Per-frame
+    latency covers the deformed prefilter and every wave; frames are rendered outside
+    the timed region. The frames of a shorter run are those of the 200-frame ramp
+    (frame k has strain 0.02 k / 199). Oracle error: a seeded sample of points of the
+    last frame, each correlated by the oracle from the analytic field on
+    host-rendered crops to its converged root."""
     import torch
 
     import paper_2601_12941_gb300 as P
     import synth
+    from oracle import dic_oracle as O
     from synth import workloads as wl
 
-    n = args.seq_frames
-    w0 = wl.sequence_frame(1)
+    w0 = wl.sequence_frame(1, subset_size=S, shape=shape)
     ref = torch.empty((w0.height, w0.width), dtype=torch.int16, device="cuda")
     dfm = torch.empty_like(ref)
     synth.render_gpu(w0.ref, ref)
     synth.render_gpu(w0.deformed, dfm)
     c = P.Correlation(ref, dfm, None, w0.subset_size, w0.subset_step, w0.shape, precision="mixed",
-                      search_radius=w0.search_radius, profile=0)
+                      search_radius=w0.search_radius, profile=1)
     c.run(list(w0.seeds), stream.cuda_stream)
-    lat, acc = [], []
-    for k in range(2, n + 1):
-        synth.render_gpu(wl.sequence_frame(k).deformed, dfm)
+    nparams = P.N_PARAMS[P.SHAPES[shape]]
+    lat, acc, kern, flops = [], [], [], []
+    for k in range(2, frames + 1):
+        synth.render_gpu(wl.sequence_frame(k, subset_size=S, shape=shape).deformed, dfm)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -542,18 +859,67 @@ def sequence_leg(args, stream):
         b.record(stream)
         b.synchronize()
         lat.append(a.elapsed_time(b))
-        acc.append(c.results(on_device=True)["n_accepted"])
+        kern.append(c.timing()["icgn_kernel_ms"])
+        rr = c.results()
+        acc.append(int(rr["n_accepted"]))
+        flops.append(executed_flops(rr["iters"], rr["status"], rr["wave"], S, nparams))
     r = c.results()
     c.close()
     lat = np.array(lat)
-    out = {"frames": n, "size": [w0.width, w0.height], "subset": w0.subset_size, "step": w0.subset_step,
-           "shape": w0.shape, "points_per_frame": int(r["n_points"]),
-           "accepted_last_frame": int(r["n_accepted"]),
+    peak, note, _, _ = fp32_peak()
+    achieved = float(np.sum(flops)) / (float(np.sum(kern)) / 1e3) / 1e12
+    out = {"frames": frames, "size": [w0.width, w0.height], "subset": S, "step": w0.subset_step,
+           "shape": shape, "points_per_frame": int(r["n_points"]), "accepted_last_frame": int(r["n_accepted"]),
            "frame_ms_p50": float(np.percentile(lat, 50)), "frame_ms_p99": float(np.percentile(lat, 99)),
            "points_per_s": float(np.sum(acc) / (np.sum(lat) / 1e3)),
-           "note": "frame 1 from the seed (not timed); frames 2..%d timed" % n}
+           "wave_kernel_ms_p50": float(np.percentile(kern, 50)),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                        "frac": achieved / peak, "peak_note": note},
+           "note": "frame 1 from the seed (not timed); frames 2..%d timed" % frames}
+    if oracle_points:
+        wl_last = wl.sequence_frame(frames, subset_size=S, shape=shape)
+        fld = wl_last.field
+        rng = np.random.default_rng(31 + S)
+        ok = np.flatnonzero((r["status"] == 0) & (r["x"] > 100) & (r["x"] < w0.width - 100)
+                            & (r["y"] > 100) & (r["y"] < w0.height - 100))
+        pad = (S - 1) // 2 + 80
+        errs, perr, agree = [], [], 0
+        pick = rng.choice(ok, min(oracle_points, len(ok)), replace=False)
+        for q in pick:
+            xc, yc = int(r["x"][q]), int(r["y"][q])
+            x0, y0, side = xc - pad, yc - pad, 2 * pad + 1
+            rc, roff = synth.render_crop(wl_last.ref, w0.width, w0.height, x0, y0, side, side, "u16")
+            dc, doff = synth.render_crop(wl_last.deformed, w0.width, w0.height, x0, y0, side, side, "u16")
+            u, v = synth.displacement(fld, np.array([float(xc)]), np.array([float(yc)]))
+            p0 = [u[0], v[0], fld.exx, fld.exy, fld.eyx, fld.eyy] + [0.0] * (nparams - 6)
+            ora = O.icgn(O.Plane(rc, roff[0], roff[1], w0.width, w0.height),
+                         O.Plane(dc, doff[0], doff[1], w0.width, w0.height), xc, yc, S, shape, p0,
+                         dict(conv_threshold=1e-8, max_iter=100))
+            agree += int(ora["status"] == O.OK)
+            if ora["status"] == O.OK:
+                d = np.abs(np.asarray(r["p"][q]) - ora["p"])
+                errs.append(d[:2].max())
+                perr.append(d[2:].max())
+        out["oracle_error"] = {"sample": "%d accepted points of frame %d, oracle from the analytic field, "
+                                         "converged to 1e-8" % (len(pick), frames),
+                               "oracle_accepts": "%d/%d" % (agree, len(pick)),
+                               "max_uv_px": float(max(errs)) if errs else None,
+                               "mean_uv_px": float(np.mean(errs)) if errs else None,
+                               "max_p2": float(max(perr)) if perr else None}
+    return out
+
+
+def sequence_leg(args, stream):
+    """Config 4 at subset 21, affine, 200 frames (see run_sequence), and the same
+    sequence with incremental reference updating."""
+    out = run_sequence(stream, 21, "affine", args.seq_frames, 0 if args.no_oracle_error else 20)
     out["updating"] = sequence_updating_leg(args, stream)
     return out
+
+
+def sequence_variant_leg(args, stream, S, shape, frames):
+    """Config 4 at another subset size or shape function (see run_sequence)."""
+    return run_sequence(stream, S, shape, min(frames, args.seq_frames), 0 if args.no_oracle_error else 10)
 
 
 def sequence_updating_leg(args, stream, every=50):
@@ -711,12 +1077,73 @@ def cpu_baseline(w, seconds):
                                [(side // 2, side // 2)], dict(search_radius=w.search_radius))
         el = time.perf_counter() - t
         acc = int((res["status"] == 0).sum())
-        best = dict(value=acc / el, unit=UNIT, cores=1, kind="oracle",
+        best = dict(value=acc / el, unit=UNIT, cores=1, kind="oracle", nproc=os.cpu_count(), cpu_model=cpu_model(),
                     sample="%dx%d crop centred on the first seed of the same pair, %d points, %d accepted, %.1f s"
                     % (side, side, len(res["status"]), acc, el), seconds=el)
         if el >= seconds or side >= 1600:
             return best
         side = int(side * min(2.0, max(1.2, (seconds / max(el, 1e-3)) ** 0.5)))
+
+
+def _oracle_crop_job(job):
+    """One crop of the 1 Gpx pair through the oracle (runs in a spawned worker)."""
+    import oracle
+    import synth
+    from synth import workloads as wl
+
+    size, cx, cy, side = job
+    w = wl.gigapixel_u8(size)
+    x0, y0 = cx - side // 2, cy - side // 2
+    ref, _ = synth.render_crop(w.ref, w.width, w.height, x0, y0, side, side, w.dtype)
+    dfm, _ = synth.render_crop(w.deformed, w.width, w.height, x0, y0, side, side, w.dtype)
+    t = time.perf_counter()
+    res = oracle.correlate(ref, dfm, None, w.subset_size, w.subset_step, w.shape, [(side // 2, side // 2)],
+                           dict(search_radius=w.search_radius))
+    return int((res["status"] == 0).sum()), time.perf_counter() - t
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu or /proc/cpuinfo), or the platform's."""
+    import platform
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_all_cores(w, single):
+    """The oracle on every host core: one crop per core (the single-thread leg's crop
+    size, centred on different blocks of the pair), in a pool of spawned processes
+    (no fork after the GPU was used); value = accepted points of all crops / wall
+    time of the batch, pool start-up excluded."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    side = int(single["sample"].split("x")[0])
+    b = w.width // 8
+    centres = [(b // 2 + (i % 8) * b, b // 2 + ((i // 8) % 8) * b) for i in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_crop_job, [(w.width, cx, cy, 64) for cx, cy in centres])   # warm the workers
+        t = time.perf_counter()
+        res = pool.map(_oracle_crop_job, [(w.width, cx, cy, side) for cx, cy in centres])
+        wall = time.perf_counter() - t
+    acc = sum(a for a, _ in res)
+    return {"value": acc / wall, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "nproc": cores, "sample": "%d crops of %dx%d (one per core, centred on different blocks of the same "
+                                      "pair), %d accepted points, %.1f s wall" % (cores, side, side, acc, wall),
+            "speedup_over_one_core": (acc / wall) / single["value"] if single.get("value") else None}
 
 
 def run_reference(args):
@@ -784,7 +1211,13 @@ def main():
     ap.add_argument("--fft-kernel-reps", type=int, default=3,
                     help="timed runs of the last level alone (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serve-jobs", type=int, default=40,
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the plain FP64 comparator")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 256^2, 2048^2 and extra sequence legs")
+    ap.add_argument("--no-oracle-error", action="store_true", help="skip the oracle error reports")
+    ap.add_argument("--oracle-points", type=int, default=200,
+                    help="sampled points of the 1 Gpx oracle error report")
+    ap.add_argument("--serve-jobs", type=int, default=500,
                     help="jobs in the serving stream (0: skip the serving leg)")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="Poisson arrival rate, jobs/s")
     ap.add_argument("--serve-workers", type=int, default=4)

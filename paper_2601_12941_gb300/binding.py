@@ -17,7 +17,8 @@ DIC_U8, DIC_U16, DIC_BF16, DIC_F32, DIC_F64 = range(5)
 DIC_RIGID, DIC_AFFINE, DIC_QUADRATIC = range(3)
 DIC_BSPLINE3, DIC_BICUBIC = 0, 1
 INTERPS = {"bspline3": DIC_BSPLINE3, "bicubic": DIC_BICUBIC}
-DIC_FP64, DIC_MIXED = 0, 1
+DIC_FP64, DIC_MIXED, DIC_MIXED_FP64_SOLVE = 0, 1, 2
+PRECISIONS = {"fp64": DIC_FP64, "mixed": DIC_MIXED, "mixed_fp64_solve": DIC_MIXED_FP64_SOLVE}
 DIC_COST_ZNSSD, DIC_COST_NSSD, DIC_COST_SSD = 0, 1, 2
 COSTS = {"znssd": DIC_COST_ZNSSD, "nssd": DIC_COST_NSSD, "ssd": DIC_COST_SSD}
 DIC_OPT_GAUSS_NEWTON, DIC_OPT_LEVENBERG_MARQUARDT = 0, 1
@@ -582,7 +583,7 @@ def _apply(p: DicParams, kw: dict) -> DicParams:
         if k not in fields:
             raise TypeError("unknown parameter %r" % k)
         if k == "precision" and isinstance(v, str):
-            v = {"fp64": DIC_FP64, "mixed": DIC_MIXED}[v]
+            v = PRECISIONS[v]
         if k == "cost" and isinstance(v, str):
             v = COSTS[v]
         if k == "optimizer" and isinstance(v, str):

@@ -302,8 +302,12 @@ void free_planes(dic_handle* h) {
   h->plane_prec = -1;
 }
 
+// Element type of the coefficient planes of a precision: DIC_FP64 (double) or
+// DIC_MIXED (float; also for DIC_MIXED_FP64_SOLVE).
+int plane_kind(int precision) { return precision == DIC_FP64 ? DIC_FP64 : DIC_MIXED; }
+
 int ensure_planes(dic_handle* h) {
-  const int prec = h->prm.precision;
+  const int prec = plane_kind(h->prm.precision);
   if (h->plane_prec == prec) return DIC_OK;
   free_planes(h);
   const size_t es = prec == DIC_FP64 ? sizeof(double) : sizeof(float);
@@ -405,11 +409,14 @@ int run_waves(dic_handle* h, cudaStream_t s) {
   a.conv_threshold = h->prm.conv_threshold;
   a.zncc_min = h->prm.zncc_min;
   a.expire_waits = g_expire_waits.load();
+  a.solve64 = h->prm.precision == DIC_MIXED_FP64_SOLVE ? 1 : 0;
+  if (a.solve64 && h->interp != DIC_BSPLINE3)
+    return fail(DIC_EINVAL, "DIC_MIXED_FP64_SOLVE runs on the B-spline interpolant only");
 
   int sms = 0;
   DIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "device query");
   const size_t smem = static_cast<size_t>(a.tiles.smem_bytes);
-  const int per_sm = wave_blocks_per_sm<T>(h->nparams, a.threads, wave_mode(a.lm, a.cost, a.interp), smem);
+  const int per_sm = wave_blocks_per_sm<T>(h->nparams, a.threads, wave_mode(a.lm, a.cost, a.interp, a.solve64), smem);
   const int grid = sms * per_sm;
 
   const bool prof = h->prm.profile != 0;
@@ -644,7 +651,7 @@ int64_t footprint(const dic_handle* cur, const dic_image* ref, const dic_image* 
     b += (cur->def_owned && dtype_size(def->dtype) == dtype_size(cur->def_dtype))
              ? owned_bytes(cur, cur->def_owned)
              : static_cast<int64_t>(owned_pitch(def)) * H;
-  b += cur->plane_prec == precision ? owned_bytes(cur, cur->c_ref) + owned_bytes(cur, cur->c_def) : plane_bytes;
+  b += cur->plane_prec == plane_kind(precision) ? owned_bytes(cur, cur->c_ref) + owned_bytes(cur, cur->c_def) : plane_bytes;
   b += points_bytes(n > cur->pts_cap ? n : cur->pts_cap);
   b += 8 * (n * np > cur->p_cap ? n * np : cur->p_cap);
   const int64_t sc = static_cast<int64_t>(n_seeds) > static_cast<int64_t>(cur->seed_cap)
@@ -668,8 +675,10 @@ int validate_params(const dic_params* p) {
   if (!(p->zncc_min >= -1.0 && p->zncc_min <= 1.0)) return fail(DIC_EINVAL, "zncc_min must be in [-1, 1]");
   if (p->search_radius < 0 || p->search_radius > 256)
     return fail(DIC_EINVAL, "search_radius %d out of range", p->search_radius);
-  if (p->precision != DIC_FP64 && p->precision != DIC_MIXED)
+  if (p->precision != DIC_FP64 && p->precision != DIC_MIXED && p->precision != DIC_MIXED_FP64_SOLVE)
     return fail(DIC_EINVAL, "unknown precision %d", p->precision);
+  if (p->precision == DIC_MIXED_FP64_SOLVE && (p->cost != DIC_COST_ZNSSD || p->optimizer != DIC_OPT_GAUSS_NEWTON))
+    return fail(DIC_EINVAL, "DIC_MIXED_FP64_SOLVE runs Gauss-Newton with ZNSSD only");
   if (p->cost != DIC_COST_ZNSSD && p->cost != DIC_COST_NSSD && p->cost != DIC_COST_SSD)
     return fail(DIC_EINVAL, "unknown cost %d", p->cost);
   if (p->optimizer != DIC_OPT_GAUSS_NEWTON && p->optimizer != DIC_OPT_LEVENBERG_MARQUARDT)
@@ -1231,7 +1240,7 @@ int dic_correlate_sequence(dic_handle* h, void* cuda_stream) {
   if (!h->has_results) return fail(DIC_ESTATE, "dic_correlate_sequence needs an earlier correlation");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   h->last_stream = s;
-  if (h->plane_prec != h->prm.precision)
+  if (h->plane_prec != plane_kind(h->prm.precision))
     return fail(DIC_ESTATE, "the precision changed since the last correlation; correlate with seeds");
   h->timing = dic_timing{};
   const bool prof = h->prm.profile != 0;

@@ -281,6 +281,8 @@ struct WaveArgs {
   int interp;                // dic_interp of the coefficient planes
   double conv_threshold;
   double zncc_min;
+  int solve64;               // 1: FP64 Hessian inverse, solve and ZNCC normalisation on the
+                             // FP32 path (DIC_MIXED_FP64_SOLVE; kernel variant 3)
   int expire_waits;          // 1 (tests of the timeout path only): every tile-load wait
                              // gives up at once, as a wait that ran out of polls would
 };
@@ -330,9 +332,13 @@ template <typename T>
 int wave_blocks_per_sm(int nparams, int threads, int mode, size_t smem);
 
 // Kernel variant: 0 Gauss-Newton with ZNSSD on the B-spline (the default, leanest
-// instantiation); 1 Gauss-Newton with any cost or interpolant; 2 Levenberg-Marquardt.
-inline int wave_mode(int lm, int cost, int interp) {
-  return lm ? 2 : (cost == DIC_COST_ZNSSD && interp == DIC_BSPLINE3 ? 0 : 1);
+// instantiation); 1 Gauss-Newton with any cost or interpolant; 2 Levenberg-Marquardt;
+// 3 variant 0 with the Hessian inverse, the solve and the ZNCC normalisation in FP64
+// (FP32 coefficients only).
+inline int wave_mode(int lm, int cost, int interp, int solve64 = 0) {
+  if (lm) return 2;
+  if (cost == DIC_COST_ZNSSD && interp == DIC_BSPLINE3) return solve64 ? 3 : 0;
+  return 1;
 }
 
 }  // namespace dic

@@ -11,14 +11,16 @@ TOL_P = 1e-5
 # stores it as FP32 (half an ulp of a value near 1 is 3e-8); the mixed path sums
 # f' g' in FP32 over up to 61^2 pixels before normalising (relative error of a few
 # 1e-7 per sum, amplified where sum f'g' and mu sum g' nearly cancel)
-TOL_ZNCC = {"fp64": 1e-6, "mixed": 1e-5}
+TOL_ZNCC = {"fp64": 1e-6, "mixed": 1e-5, "mixed_fp64_solve": 1e-5}
 # controls of the parity runs: the oracle converges tightly; the FP32 path stops at
 # 1e-5: ||dp|| weighs dp2..5 by r, so a 1e-4 stop could leave the last step of the
 # strain-like parameters at ~1e-5 (seen: 1.1e-5), while the FP32 fixed point
 # itself sits within ~1e-7 of the FP64 root
 ORACLE_PARAMS = dict(conv_threshold=1e-8, max_iter=100)
 GPU_PARAMS = {"fp64": dict(conv_threshold=1e-8, max_iter=100),
-              "mixed": dict(conv_threshold=1e-5, max_iter=100)}
+              "mixed": dict(conv_threshold=1e-5, max_iter=100),
+              # FP64 solves on the FP32 sums: the root is still fixed by FP32 sums
+              "mixed_fp64_solve": dict(conv_threshold=1e-5, max_iter=100)}
 
 
 def borderline(ora, W, H, S, zncc_min=0.70, max_iter=100):

@@ -103,8 +103,16 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
     assert lib.dic_estimate_device_bytes(ctypes.byref(ri), ctypes.byref(ri), 0, 21, 5, 1, ctypes.byref(pf), 1,
                                          ctypes.byref(nf)) == B.DIC_OK
     assert nf.value > nb.value
+    # the mixed path with FP64 solves: estimated like the mixed path (FP32 planes);
+    # Gauss-Newton with ZNSSD only
+    p2 = B.params(precision="mixed_fp64_solve")
+    n2 = ctypes.c_int64(0)
+    assert lib.dic_estimate_device_bytes(ctypes.byref(ri), ctypes.byref(ri), 0, 21, 5, 1, ctypes.byref(p2), 1,
+                                         ctypes.byref(n2)) == B.DIC_OK
+    assert n2.value == nb.value
     for bad in (dict(init=2), dict(init="fft", max_displacement=4096), dict(init="fft", max_displacement=-1),
-                dict(mad_eps=-1.0)):
+                dict(mad_eps=-1.0), dict(precision=3), dict(precision="mixed_fp64_solve", cost="nssd"),
+                dict(precision="mixed_fp64_solve", optimizer="lm")):
         pb = B.params(**bad)
         assert lib.dic_estimate_device_bytes(ctypes.byref(ri), ctypes.byref(ri), 0, 21, 5, 1, ctypes.byref(pb), 1,
                                              ctypes.byref(nf)) == B.DIC_EINVAL, bad

@@ -82,7 +82,37 @@ def test_prefilter_matches_oracle_coefficients(pkg, precision, dtype):
     c.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("dtype", ["u8", "u16", "bf16", "f32", "f64"])
+def test_prefilter_strips_match_oracle_for_every_gray_type(pkg, dtype):
+    """The FP32 prefilter on an image wide and tall enough for interior strips (16-byte
+    vector loads), edge strips (mirrored columns) and a partial last block of rows,
+    for every gray type the library reads; a width of 700 (rows not 16-byte aligned)
+    takes the element-by-element path everywhere."""
+    from paper_2601_12941_gb300 import binding as B
+
+    for W, H in ((704, 600), (700, 531)):
+        gray = 4095.0 if dtype == "u16" else 255.0
+        kind = {"u8": "u8", "bf16": "u8", "u16": "u16", "f32": "f32", "f64": "f64"}[dtype]
+        ref, dfm = _pair(W, H, synth.affine_field(W, H, u0=0.5), dtype=kind, gray=gray, noise=0.01 * gray)
+        if dtype == "bf16":
+            dev_ref = torch.from_numpy(ref).cuda().to(torch.bfloat16)
+            dev_dfm = torch.from_numpy(dfm).cuda().to(torch.bfloat16)
+        else:
+            dev_ref = torch.from_numpy(ref.view(np.int16) if ref.dtype == np.uint16 else ref).cuda()
+            dev_dfm = torch.from_numpy(dfm.view(np.int16) if dfm.dtype == np.uint16 else dfm).cuda()
+        c = pkg.Correlation(dev_ref, dev_dfm, None, 21, 9, "affine", precision="mixed")
+        c.run([(W // 2, H // 2)])
+        for which, img in ((0, ref), (1, dfm)):
+            ptr, ld, es = pkg.dic_get_coefficients(c.h, which)
+            dev = torch.as_tensor(B._DeviceArray(ptr, (H, ld), np.dtype(np.float32).str), device="cuda")
+            got = dev[:, :W].double().cpu().numpy()
+            want = O.bspline_coefficients(img.astype(np.float64))
+            rel = np.abs(got - want).max() / np.abs(want).max()
+            assert rel < 2e-6, (W, H, which, rel)
+        c.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_fp64_solve"])
 def test_affine_256_u8_matches_oracle(pkg, precision):
     w = wl.affine_256_u8()
     ref = synth.render(w.ref, w.width, w.height, w.dtype)
@@ -98,7 +128,7 @@ def test_affine_256_u8_matches_oracle(pkg, precision):
     print(precision, stats)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_fp64_solve"])
 def test_quadratic_sine_u16_matches_oracle(pkg, precision):
     W, H = 230, 190
     w = wl.sine_2048_u16(W, H)
@@ -114,7 +144,7 @@ def test_quadratic_sine_u16_matches_oracle(pkg, precision):
     print(precision, stats)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_fp64_solve"])
 def test_rigid_matches_oracle(pkg, precision):
     W, H = 150, 133
     ref, dfm = _pair(W, H, synth.affine_field(W, H, u0=-3.4, v0=1.3), dtype="u8")
@@ -215,7 +245,7 @@ def test_large_strain_uses_global_fallback_and_matches_oracle(pkg, precision):
     print(precision, stats)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_fp64_solve"])
 def test_bf16_gray_levels_equal_the_u8_run_and_match_oracle(pkg, precision):
     """Gray levels stored as BF16 (the gigapixel workload's storage type): a BF16
     tensor holding u8 values represents them exactly, so every result equals the u8
