@@ -255,14 +255,23 @@ __device__ __forceinline__ bool is_flat(C delta, C mean, int count) {
   return delta / sqrt(static_cast<C>(count)) <= C(1e-6) * fmax(fabs(mean), C(1));
 }
 
+// n < 2^23 as a float, exactly, on the integer and FP32 pipes (0x4B000000 | n is the
+// float 2^23 + n)
+__device__ __forceinline__ float small_uint_to_float(uint32_t n) {
+  return __uint_as_float(0x4B000000u | n) - 8388608.0f;
+}
+
 // Gray level at subset column c, row r of a staged gray tile (row pitch in bytes).
 template <typename T>
 __device__ __forceinline__ T tile_gray(const unsigned char* tile, int pitch, int dtype, int c, int r) {
   const unsigned char* row = tile + r * pitch;
   switch (dtype) {
     case DIC_U8:
+      if constexpr (sizeof(T) == sizeof(float)) return small_uint_to_float(row[c]);
       return static_cast<T>(row[c]);
     case DIC_U16:
+      if constexpr (sizeof(T) == sizeof(float))
+        return small_uint_to_float(reinterpret_cast<const uint16_t*>(row)[c]);
       return static_cast<T>(reinterpret_cast<const uint16_t*>(row)[c]);
     case DIC_BF16:
       return static_cast<T>(__uint_as_float(static_cast<uint32_t>(reinterpret_cast<const uint16_t*>(row)[c]) << 16));
@@ -831,6 +840,28 @@ __device__ __forceinline__ Pair<float> psub<float>(Pair<float> a, Pair<float> b)
   return bits_pair(d);
 }
 
+// floor of both values and their integer parts. FP32 (|x| < 2^22): x + 1.5 * 2^23
+// rounded toward minus infinity is floor(x) + 1.5 * 2^23 exactly, an integer whose
+// low mantissa bits hold floor(x); one packed add, one packed subtract and two
+// integer subtracts replace two roundings and two conversions. FP64: floor().
+template <typename T>
+__device__ __forceinline__ Pair<T> pfloor(Pair<T> x, int& ix, int& iy) {
+  const T fx = floor(x.x), fy = floor(x.y);
+  ix = static_cast<int>(fx);
+  iy = static_cast<int>(fy);
+  return Pair<T>{fx, fy};
+}
+template <>
+__device__ __forceinline__ Pair<float> pfloor<float>(Pair<float> x, int& ix, int& iy) {
+  constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23
+  unsigned long long d;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pair_bits(x)), "l"(pair_bits(Pair<float>{kMagic, kMagic})));
+  const Pair<float> t = bits_pair(d);
+  ix = __float_as_int(t.x) - 0x4B400000;
+  iy = __float_as_int(t.y) - 0x4B400000;
+  return psub(t, Pair<float>{kMagic, kMagic});
+}
+
 // bspline_weights6 of two offsets at once (x in .x, y in .y), the same arithmetic
 template <typename T>
 __device__ __forceinline__ void bspline_weights6_pair(Pair<T> t, Pair<T>& w0, Pair<T>& w1, Pair<T>& w2,
@@ -895,8 +926,16 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
   for (int j = 0; j <= D; ++j) sd[j] = pair(T(0), T(0));
   const Pair<T> a2 = pair(ax, ay), b2 = pair(bx, by), cq2 = pair(cxq, cyq);
   int pix_ix = -0x40000000, pix_iy = -0x40000000;
-  auto step = [&](T (&A)[4], T (&B)[4], T (&Cc)[4], T (&Dn)[4], int row) {
-    const T dyv = static_cast<T>(row - r);
+  T dyr = static_cast<T>(row0 - r);                  // dy of the next row, counted in T (exact)
+  const Pair<T>* fgp = s_fg + row0 * S + col;       // gradients of the next row's pixel
+  const unsigned char* grow = gtile + row0 * gpitch; // its gray tile row
+  auto step = [&](T (&A)[4], T (&B)[4], T (&Cc)[4], T (&Dn)[4]) {
+    const T dyv = dyr;
+    dyr += T(1);
+    const Pair<T> fg = *fgp;
+    fgp += S;
+    const unsigned char* gr = grow;
+    grow += gpitch;
     const Pair<T> dy2 = pair(dyv, dyv);
     const Pair<T> xy = D >= 2 ? pfma(dy2, pfma(cq2, dy2, b2), a2) : pfma(dy2, b2, a2);
     const T xl = xy.x, yl = xy.y;
@@ -905,8 +944,8 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
       pix_ix = -0x40000000;
       return;
     }
-    const T xf = floor(xl), yf = floor(yl);
-    const int ix = static_cast<int>(xf), iy = static_cast<int>(yf);
+    int ix, iy;
+    const Pair<T> fl = pfloor<T>(xy, ix, iy);
     const T* b = base + (iy * ld + ix);
     if (!(ix == pix_ix && iy == pix_iy + 1)) {
 #pragma unroll
@@ -922,9 +961,9 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
     pix_iy = iy;
     Pair<T> w0, w1, w2, w3;
     if (GEN && keys)
-      keys_weights2_pair<T>(psub(xy, pair(xf, yf)), w0, w1, w2, w3);
+      keys_weights2_pair<T>(psub(xy, fl), w0, w1, w2, w3);
     else
-      bspline_weights6_pair<T>(psub(xy, pair(xf, yf)), w0, w1, w2, w3);
+      bspline_weights6_pair<T>(psub(xy, fl), w0, w1, w2, w3);
     const T wx0 = w0.x, wx1 = w1.x, wx2 = w2.x, wx3 = w3.x;
     const T wy0 = w0.y, wy1 = w1.y, wy2 = w2.y, wy3 = w3.y;
     const T r0 = wx0 * A[0] + wx1 * A[1] + wx2 * A[2] + wx3 * A[3];
@@ -935,10 +974,10 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
     acc[0] += gp;
     acc[1] += gp * gp;
     if (fin) {
-      acc[2] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
+      acc[2] += gp * (tile_gray<T>(gr, 0, gdtype, col, 0) - f0);
     } else {
-      const Pair<T> g2 = pmul(pair(gp, gp), s_fg[row * S + col]);   // (fx g', fy g')
-      if (FG) acc[2 + 2 * (D + 1)] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
+      const Pair<T> g2 = pmul(pair(gp, gp), fg);   // (fx g', fy g')
+      if (FG) acc[2 + 2 * (D + 1)] += gp * (tile_gray<T>(gr, 0, gdtype, col, 0) - f0);
       sd[0] = padd(sd[0], g2);
       Pair<T> dyp = dy2;
 #pragma unroll
@@ -949,10 +988,10 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
     }
   };
   for (int row = row0; row < row1; row += 4) {
-    step(c0, c1, c2, c3, row);
-    if (row + 1 < row1) step(c1, c2, c3, c0, row + 1);
-    if (row + 2 < row1) step(c2, c3, c0, c1, row + 2);
-    if (row + 3 < row1) step(c3, c0, c1, c2, row + 3);
+    step(c0, c1, c2, c3);
+    if (row + 1 < row1) step(c1, c2, c3, c0);
+    if (row + 2 < row1) step(c2, c3, c0, c1);
+    if (row + 3 < row1) step(c3, c0, c1, c2);
   }
   if (!fin) {
 #pragma unroll
@@ -1126,57 +1165,76 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
     __syncwarp();
   };
 
-  for (;;) {
-    // ---- 1. next point and its starting warp (warp 0)
-    if (warp == 0) {
-      int item = 0;
-      if (lane == 0) item = atomicAdd(&a.counters[kWork + cur], 1);
-      item = __shfl_sync(0xffffffffu, item, 0);
-      if (item < n_front) {
-        const int q = a.cur[item];
-        const int gi = q % a.nx, gj = q / a.nx;
-        int best = -1;
-        if (a.k == 0) {
-          best = q;
-        } else {
-          // the accepted neighbour from an earlier wave with the highest ZNCC
-          // (ties to the lower index); lanes 0-3 look at left, right, up, down
-          int nb = -1;
-          if (lane == 0 && gi > 0) nb = q - 1;
-          if (lane == 1 && gi < a.nx - 1) nb = q + 1;
-          if (lane == 2 && gj > 0) nb = q - a.nx;
-          if (lane == 3 && gj < a.ny - 1) nb = q + a.nx;
-          float z = -3.0f;
-          int cand = 0x7fffffff;
-          if (nb >= 0) {
-            const int64_t rec = a.pts.accept[nb];
-            if (rec >= 0 && static_cast<int>(rec >> 32) < a.k) {
-              z = __int_as_float(static_cast<int>(rec & 0xffffffffLL));
-              cand = nb;
-            }
+  // The next point of the front and its starting warp, fetched one point ahead by
+  // warp NW - 1 while warp 0 runs the current point's serial solve (the start depends
+  // only on points accepted in earlier waves): an item index from the wave's atomic
+  // cursor; for wave 0 the seed's own warp, otherwise the warp of the accepted
+  // 4-neighbour from an earlier wave with the highest ZNCC (ties to the lower index;
+  // lanes 0-3 look at left, right, up, down), re-expanded about this centre.
+  __shared__ int nx_item, nx_q;
+  __shared__ C nx_dp[kMaxParams], nx_p[kMaxParams];
+  auto fetch_next = [&]() {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&a.counters[kWork + cur], 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item < n_front) {
+      const int q = a.cur[item];
+      const int gi = q % a.nx, gj = q / a.nx;
+      int best = -1;
+      if (a.k == 0) {
+        best = q;
+      } else {
+        int nb = -1;
+        if (lane == 0 && gi > 0) nb = q - 1;
+        if (lane == 1 && gi < a.nx - 1) nb = q + 1;
+        if (lane == 2 && gj > 0) nb = q - a.nx;
+        if (lane == 3 && gj < a.ny - 1) nb = q + a.nx;
+        float z = -3.0f;
+        int cand = 0x7fffffff;
+        if (nb >= 0) {
+          const int64_t rec = a.pts.accept[nb];
+          if (rec >= 0 && static_cast<int>(rec >> 32) < a.k) {
+            z = __int_as_float(static_cast<int>(rec & 0xffffffffLL));
+            cand = nb;
           }
-#pragma unroll
-          for (int o = 1; o <= 2; o <<= 1) {
-            const float oz = __shfl_xor_sync(0xffffffffu, z, o);
-            const int oc = __shfl_xor_sync(0xffffffffu, cand, o);
-            if (oz > z || (oz == z && oc < cand)) {
-              z = oz;
-              cand = oc;
-            }
-          }
-          best = __shfl_sync(0xffffffffu, cand, 0);
-          if (best == 0x7fffffff) best = -1;
         }
-        if (lane < NP)
-          st.dp[lane] = best >= 0 ? static_cast<C>(a.pts.p[static_cast<int64_t>(best) * NP + lane]) : C(0);
-        __syncwarp();
+#pragma unroll
+        for (int o = 1; o <= 2; o <<= 1) {
+          const float oz = __shfl_xor_sync(0xffffffffu, z, o);
+          const int oc = __shfl_xor_sync(0xffffffffu, cand, o);
+          if (oz > z || (oz == z && oc < cand)) {
+            z = oz;
+            cand = oc;
+          }
+        }
+        best = __shfl_sync(0xffffffffu, cand, 0);
+        if (best == 0x7fffffff) best = -1;
+      }
+      if (lane < NP)
+        nx_dp[lane] = best >= 0 ? static_cast<C>(a.pts.p[static_cast<int64_t>(best) * NP + lane]) : C(0);
+      __syncwarp();
+      if (lane == 0) {
+        if (a.k > 0 && best >= 0)
+          transfer_warp<C, NP>(nx_dp, static_cast<C>((gi - best % a.nx) * a.step),
+                               static_cast<C>((gj - best / a.nx) * a.step), nx_p);
+        else
+          for (int c = 0; c < NP; ++c) nx_p[c] = nx_dp[c];
+        nx_q = q;
+      }
+    }
+    if (lane == 0) nx_item = item;
+  };
+  if (warp == NW - 1) fetch_next();
+  __syncthreads();
+
+  for (;;) {
+    // ---- 1. the prefetched point becomes the current one (warp 0)
+    if (warp == 0) {
+      const int item = nx_item;
+      if (item < n_front) {
+        if (lane < NP) st.p[lane] = nx_p[lane];
         if (lane == 0) {
-          if (a.k > 0 && best >= 0)
-            transfer_warp<C, NP>(st.dp, static_cast<C>((gi - best % a.nx) * a.step),
-                                 static_cast<C>((gj - best / a.nx) * a.step), st.p);
-          else
-            for (int c = 0; c < NP; ++c) st.p[c] = st.dp[c];
-          st.q = q;
+          st.q = nx_q;
           st.win.w = 0;
           st.iters = 0;
           st.converged = 0;
@@ -1342,6 +1400,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
       }
     }
     __syncthreads();
+    if (warp == NW - 1) fetch_next();   // the next point, beside warp 0's serial steps
     if (warp == 0) {
       gather(NV_PRE);
       finish_reference<C, NP, NMOM, M2, ANYCOST, SC>(st, s_out, N, lane, a.cost);
