@@ -302,10 +302,18 @@ template <int NP>
 struct SolveState<float, NP> {
   float X[NP * NP];         // H^-1 = D (D H D)^-1 D, column-major
 };
+// FP64 solves on the FP32 path (kernel variant 3): the FP64 Hessian and the FP32
+// inverse of the mixed path, which preconditions an FP64 iterative refinement
+struct Refined64 {};
+template <int NP>
+struct SolveState<Refined64, NP> {
+  float X[NP * NP];         // H^-1 = D (D H D)^-1 D in FP32, column-major
+  double H[NP * NP];        // Gauss-Newton Hessian in FP64 (from the FP32 moment sums)
+};
 
 // Per-block state of the point being correlated; C is the working precision
 // (float on the mixed path, double on the FP64 path), SC the precision of the
-// Hessian inverse and the solve (C, or double on the mixed path with FP64 solves).
+// Hessian inverse and the solve (C, or Refined64 on the mixed path with FP64 solves).
 template <typename C, int NP, typename SC = C>
 struct PointState {
   SolveState<SC, NP> sv;
@@ -522,7 +530,13 @@ __device__ void finish_reference(PointState<C, NP, SC>& st, const C* out, int N,
     return out[(sd_t(ca) + sd_t(cb)) * NMOM + mono(sd_i(ca) + sd_i(cb), sd_j(ca) + sd_j(cb), M2)];
   };
   double ratio;
-  if constexpr (sizeof(SC) == sizeof(double)) {
+  if constexpr (std::is_same<SC, Refined64>::value) {
+    for (int e = lane; e < NP * NP; e += 32) st.sv.H[e] = static_cast<double>(hget(e / NP, e % NP));
+    float rf;
+    if (invert_scaled_warp<float, NP>(hget, st.sv.X, lane, &rf) < 1e-5f)
+      invert_scaled_fp64<NP, NMOM, M2>(out, st.sv.X, lane, &rf);
+    ratio = rf;
+  } else if constexpr (sizeof(SC) == sizeof(double)) {
     for (int e = lane; e < NP * NP; e += 32) st.sv.H[e] = static_cast<double>(hget(e / NP, e % NP));
     __syncwarp();
     ratio = invert_spd_warp<SC, NP>(st.sv.H, st.sv.X, lane);
@@ -540,7 +554,7 @@ __device__ void finish_reference(PointState<C, NP, SC>& st, const C* out, int N,
   if (lane == 0) {
     st.mu = mu;
     st.delta_f = df;
-    if constexpr (sizeof(SC) == sizeof(double) && sizeof(C) != sizeof(double)) {
+    if constexpr (std::is_same<SC, Refined64>::value) {
       const double mu64 = static_cast<double>(sf) / static_cast<double>(N);
       st.mu64 = mu64;
       st.delta_f64 = sqrt(fmax(static_cast<double>(sff) - static_cast<double>(sf) * mu64, 0.0));
@@ -591,7 +605,29 @@ __device__ int gauss_newton_update(PointState<C, NP, SC>& st, const C* out, int 
     kc = f0 * ((out[1] - st.sff) + C(2) * f0 * (out[0] - st.sf)) / (ng * (ng + nf));
   }
   C d;
-  if constexpr (sizeof(SC) == sizeof(double)) {
+  if constexpr (std::is_same<SC, Refined64>::value) {
+    // H dp = -b to FP64 accuracy: x = -X b, then x <- x - X (b + H x) twice with the
+    // residual in FP64 (each step multiplies the error by about |I - X H|, a few
+    // FP32 roundings times the scaled condition number)
+    const double bc = lane < NP ? static_cast<double>(st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]))
+                                : 0.0;
+    const int row = lane < NP ? lane : 0;
+    double x = 0.0;
+#pragma unroll
+    for (int m = 0; m < NP; ++m) x -= static_cast<double>(st.sv.X[m * NP + row]) * __shfl_sync(0xffffffffu, bc, m);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      double res = bc;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) res += st.sv.H[row * NP + m] * __shfl_sync(0xffffffffu, x, m);
+      double dx = 0.0;
+#pragma unroll
+      for (int m = 0; m < NP; ++m)
+        dx -= static_cast<double>(st.sv.X[m * NP + row]) * __shfl_sync(0xffffffffu, res, m);
+      x += dx;
+    }
+    d = lane < NP ? static_cast<C>(x) : C(0);
+  } else if constexpr (sizeof(SC) == sizeof(double)) {
     double bc = 0.0;
     if (lane < NP)
       bc = static_cast<double>(ANYCOST ? st.sdf[lane] - kg * out[2 + lane] + kc * st.sds[lane]
@@ -1080,7 +1116,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
   constexpr bool ANYCOST = MODE == 1 || MODE == 2;
   constexpr bool GEN = MODE == 1 || MODE == 2;       // the interpolant is a runtime choice
   constexpr bool S64 = MODE == 3;                    // mixed path with FP64 solves and ZNCC
-  using SC = typename std::conditional<S64, double, C>::type;
+  using SC = typename std::conditional<S64, Refined64, C>::type;
   const bool keys = GEN && a.interp == DIC_BICUBIC;
   constexpr int D = Shape<NP>::D;
   constexpr int M2 = 2 * D;
@@ -1165,76 +1201,57 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
     __syncwarp();
   };
 
-  // The next point of the front and its starting warp, fetched one point ahead by
-  // warp NW - 1 while warp 0 runs the current point's serial solve (the start depends
-  // only on points accepted in earlier waves): an item index from the wave's atomic
-  // cursor; for wave 0 the seed's own warp, otherwise the warp of the accepted
-  // 4-neighbour from an earlier wave with the highest ZNCC (ties to the lower index;
-  // lanes 0-3 look at left, right, up, down), re-expanded about this centre.
-  __shared__ int nx_item, nx_q;
-  __shared__ C nx_dp[kMaxParams], nx_p[kMaxParams];
-  auto fetch_next = [&]() {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(&a.counters[kWork + cur], 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item < n_front) {
-      const int q = a.cur[item];
-      const int gi = q % a.nx, gj = q / a.nx;
-      int best = -1;
-      if (a.k == 0) {
-        best = q;
-      } else {
-        int nb = -1;
-        if (lane == 0 && gi > 0) nb = q - 1;
-        if (lane == 1 && gi < a.nx - 1) nb = q + 1;
-        if (lane == 2 && gj > 0) nb = q - a.nx;
-        if (lane == 3 && gj < a.ny - 1) nb = q + a.nx;
-        float z = -3.0f;
-        int cand = 0x7fffffff;
-        if (nb >= 0) {
-          const int64_t rec = a.pts.accept[nb];
-          if (rec >= 0 && static_cast<int>(rec >> 32) < a.k) {
-            z = __int_as_float(static_cast<int>(rec & 0xffffffffLL));
-            cand = nb;
-          }
-        }
-#pragma unroll
-        for (int o = 1; o <= 2; o <<= 1) {
-          const float oz = __shfl_xor_sync(0xffffffffu, z, o);
-          const int oc = __shfl_xor_sync(0xffffffffu, cand, o);
-          if (oz > z || (oz == z && oc < cand)) {
-            z = oz;
-            cand = oc;
-          }
-        }
-        best = __shfl_sync(0xffffffffu, cand, 0);
-        if (best == 0x7fffffff) best = -1;
-      }
-      if (lane < NP)
-        nx_dp[lane] = best >= 0 ? static_cast<C>(a.pts.p[static_cast<int64_t>(best) * NP + lane]) : C(0);
-      __syncwarp();
-      if (lane == 0) {
-        if (a.k > 0 && best >= 0)
-          transfer_warp<C, NP>(nx_dp, static_cast<C>((gi - best % a.nx) * a.step),
-                               static_cast<C>((gj - best / a.nx) * a.step), nx_p);
-        else
-          for (int c = 0; c < NP; ++c) nx_p[c] = nx_dp[c];
-        nx_q = q;
-      }
-    }
-    if (lane == 0) nx_item = item;
-  };
-  if (warp == NW - 1) fetch_next();
-  __syncthreads();
-
   for (;;) {
-    // ---- 1. the prefetched point becomes the current one (warp 0)
+    // ---- 1. next point and its starting warp (warp 0)
     if (warp == 0) {
-      const int item = nx_item;
+      int item = 0;
+      if (lane == 0) item = atomicAdd(&a.counters[kWork + cur], 1);
+      item = __shfl_sync(0xffffffffu, item, 0);
       if (item < n_front) {
-        if (lane < NP) st.p[lane] = nx_p[lane];
+        const int q = a.cur[item];
+        const int gi = q % a.nx, gj = q / a.nx;
+        int best = -1;
+        if (a.k == 0) {
+          best = q;
+        } else {
+          // the accepted neighbour from an earlier wave with the highest ZNCC
+          // (ties to the lower index); lanes 0-3 look at left, right, up, down
+          int nb = -1;
+          if (lane == 0 && gi > 0) nb = q - 1;
+          if (lane == 1 && gi < a.nx - 1) nb = q + 1;
+          if (lane == 2 && gj > 0) nb = q - a.nx;
+          if (lane == 3 && gj < a.ny - 1) nb = q + a.nx;
+          float z = -3.0f;
+          int cand = 0x7fffffff;
+          if (nb >= 0) {
+            const int64_t rec = a.pts.accept[nb];
+            if (rec >= 0 && static_cast<int>(rec >> 32) < a.k) {
+              z = __int_as_float(static_cast<int>(rec & 0xffffffffLL));
+              cand = nb;
+            }
+          }
+#pragma unroll
+          for (int o = 1; o <= 2; o <<= 1) {
+            const float oz = __shfl_xor_sync(0xffffffffu, z, o);
+            const int oc = __shfl_xor_sync(0xffffffffu, cand, o);
+            if (oz > z || (oz == z && oc < cand)) {
+              z = oz;
+              cand = oc;
+            }
+          }
+          best = __shfl_sync(0xffffffffu, cand, 0);
+          if (best == 0x7fffffff) best = -1;
+        }
+        if (lane < NP)
+          st.dp[lane] = best >= 0 ? static_cast<C>(a.pts.p[static_cast<int64_t>(best) * NP + lane]) : C(0);
+        __syncwarp();
         if (lane == 0) {
-          st.q = nx_q;
+          if (a.k > 0 && best >= 0)
+            transfer_warp<C, NP>(st.dp, static_cast<C>((gi - best % a.nx) * a.step),
+                                 static_cast<C>((gj - best / a.nx) * a.step), st.p);
+          else
+            for (int c = 0; c < NP; ++c) st.p[c] = st.dp[c];
+          st.q = q;
           st.win.w = 0;
           st.iters = 0;
           st.converged = 0;
@@ -1400,7 +1417,6 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
       }
     }
     __syncthreads();
-    if (warp == NW - 1) fetch_next();   // the next point, beside warp 0's serial steps
     if (warp == 0) {
       gather(NV_PRE);
       finish_reference<C, NP, NMOM, M2, ANYCOST, SC>(st, s_out, N, lane, a.cost);
