@@ -133,10 +133,10 @@ WaveTiles wave_tiles(int S, int gray_dtype) {
   t.bxg = ((S + galign - 1 + galign - 1) / galign) * galign;
   const int SS = ((S * S + 31) / 32) * 32;
   auto al = [](int x) { return (x + 127) & ~127; };
-  // reference gradients: (fx, fy) pairs of T per subset pixel
-  t.off_fx = 0;
-  t.off_fy = 0;
-  t.off_win = al(2 * SS * static_cast<int>(sizeof(T)));
+  // reference gradients: (fx, fy) pairs of T per subset pixel; then f - f0 in T
+  t.off_fg = 0;
+  t.off_f = al(2 * SS * static_cast<int>(sizeof(T)));
+  t.off_win = al(t.off_f + SS * static_cast<int>(sizeof(T)));
   t.off_gray = al(t.off_win + t.bxc * t.byc * static_cast<int>(sizeof(T)));
   t.smem_bytes = al(t.off_gray + t.bxg * S * t.gray_es);
   return t;

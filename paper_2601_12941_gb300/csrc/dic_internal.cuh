@@ -239,7 +239,8 @@ cudaError_t launch_sequence_reset(const PointArrays& pa, int nparams, const uint
 cudaError_t launch_identity_start(const PointArrays& pa, int nparams, const uint8_t* roi_ok, cudaStream_t s);
 
 // ---------------------------------------------------------------- waves
-// Shared-memory tiles of the wave kernel: the coefficient window (bxc x byc
+// Shared-memory tiles of the wave kernel: the reference gradients (fx, fy) and
+// gray levels f - f0 of the subset pixels, the coefficient window (bxc x byc
 // elements, also the TMA box of the coefficient planes), the reference gray tile
 // (bxg x S elements of gray_es bytes, the TMA box of the gray plane) and where
 // each region starts in dynamic shared memory (128-byte aligned).
@@ -247,7 +248,7 @@ struct WaveTiles {
   int bxc, byc;
   int bxg, gray_es;
   int coef_tma, gray_tma;    // 1: tiles arrive by TMA; 0: cooperative copies
-  int off_fx, off_fy, off_win, off_gray;
+  int off_fg, off_f, off_win, off_gray;
   int smem_bytes;
 };
 

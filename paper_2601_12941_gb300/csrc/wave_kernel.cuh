@@ -381,7 +381,12 @@ template <typename V, int N, typename HGet>
 __device__ __forceinline__ float invert_scaled_warp(HGet hget, float* X, int lane, float* ratio) {
   // lane i < N: d_i = H_ii^-1/2 (shared by shuffles)
   const V hii = lane < N ? static_cast<V>(hget(lane, lane)) : V(0);
-  const V dl = hii > V(0) ? V(1) / sqrt(hii) : V(0);
+  V dl = V(0);
+  if constexpr (sizeof(V) == sizeof(float)) {
+    dl = hii > V(0) ? rsqrtf(hii) : V(0);
+  } else {
+    dl = hii > V(0) ? V(1) / sqrt(hii) : V(0);
+  }
   V hmax = hii;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -401,15 +406,18 @@ __device__ __forceinline__ float invert_scaled_warp(HGet hget, float* X, int lan
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const V piv = __shfl_sync(0xffffffffu, col[k], k);
-    const V dk = __shfl_sync(0xffffffffu, dl, k);
+    const V hkk = __shfl_sync(0xffffffffu, hii, k);
     pmin = piv < pmin ? piv : pmin;
-    const V up = dk > V(0) ? piv / (dk * dk) : V(0);
+    const V up = piv * hkk;   // the pivot of H itself: the scaled pivot times H_kk
     rmin = up < rmin ? up : rmin;
     if (!(piv > V(0))) {
       *ratio = 0.0f;
       return 0.0f;
     }
-    col[k] *= V(1) / piv;
+    if constexpr (sizeof(V) == sizeof(float))
+      col[k] *= __frcp_rn(piv);
+    else
+      col[k] *= V(1) / piv;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       if (i == k) continue;
@@ -953,9 +961,8 @@ template <typename T, int D, bool FG, bool GEN>
 __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld, T ax, T bx, T cxq,
                                               T ay, T by, T cyq, T xlo, T xhi, T ylo, T yhi, T f0,
                                               int row0, int row1, int r, int S, int col,
-                                              const unsigned char* gtile, int gpitch, int gdtype,
-                                              const Pair<T>* s_fg, bool fin, bool inside, bool keys, T* acc,
-                                              T& bad) {
+                                              const T* s_f, const Pair<T>* s_fg, bool fin, bool inside,
+                                              bool keys, T* acc, T& bad) {
   T c0[4], c1[4], c2[4], c3[4];
   Pair<T> sd[D + 1];   // sum fx g' dy^j in .x, sum fy g' dy^j in .y
 #pragma unroll
@@ -964,14 +971,14 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
   int pix_ix = -0x40000000, pix_iy = -0x40000000;
   T dyr = static_cast<T>(row0 - r);                  // dy of the next row, counted in T (exact)
   const Pair<T>* fgp = s_fg + row0 * S + col;       // gradients of the next row's pixel
-  const unsigned char* grow = gtile + row0 * gpitch; // its gray tile row
+  const T* fpp = s_f + row0 * S + col;            // its reference gray level f - f0
   auto step = [&](T (&A)[4], T (&B)[4], T (&Cc)[4], T (&Dn)[4]) {
     const T dyv = dyr;
     dyr += T(1);
     const Pair<T> fg = *fgp;
     fgp += S;
-    const unsigned char* gr = grow;
-    grow += gpitch;
+    const T fr = *fpp;
+    fpp += S;
     const Pair<T> dy2 = pair(dyv, dyv);
     const Pair<T> xy = D >= 2 ? pfma(dy2, pfma(cq2, dy2, b2), a2) : pfma(dy2, b2, a2);
     const T xl = xy.x, yl = xy.y;
@@ -1010,10 +1017,10 @@ __device__ __forceinline__ void sample_column(const T* __restrict__ base, int ld
     acc[0] += gp;
     acc[1] += gp * gp;
     if (fin) {
-      acc[2] += gp * (tile_gray<T>(gr, 0, gdtype, col, 0) - f0);
+      acc[2] += gp * fr;
     } else {
       const Pair<T> g2 = pmul(pair(gp, gp), fg);   // (fx g', fy g')
-      if (FG) acc[2 + 2 * (D + 1)] += gp * (tile_gray<T>(gr, 0, gdtype, col, 0) - f0);
+      if (FG) acc[2 + 2 * (D + 1)] += gp * fr;
       sd[0] = padd(sd[0], g2);
       Pair<T> dyp = dy2;
 #pragma unroll
@@ -1045,9 +1052,8 @@ template <typename T, int D, bool FG>
 __device__ __noinline__ void sample_column_global(const T* __restrict__ base, int64_t ld, T ax,
                                                      T bx, T cxq, T ay, T by, T cyq, T xlo, T xhi,
                                                      T ylo, T yhi, T f0, int row0, int row1, int r,
-                                                     int S, int col, const unsigned char* gtile,
-                                                     int gpitch, int gdtype, const Pair<T>* s_fg, bool fin,
-                                                     bool keys, T* acc, T& bad) {
+                                                     int S, int col, const T* s_f, const Pair<T>* s_fg,
+                                                     bool fin, bool keys, T* acc, T& bad) {
   for (int row = row0; row < row1; ++row) {
     const T dyv = static_cast<T>(row - r);
     const T xl = ax + dyv * (bx + cxq * dyv);
@@ -1077,11 +1083,11 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
     acc[0] += gp;
     acc[1] += gp * gp;
     if (fin) {
-      acc[2] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
+      acc[2] += gp * s_f[row * S + col];
     } else {
       const Pair<T> fg = s_fg[row * S + col];
       const T gxv = gp * fg.x, gyv = gp * fg.y;
-      if (FG) acc[2 + 2 * (D + 1)] += gp * (tile_gray<T>(gtile, gpitch, gdtype, col, row) - f0);
+      if (FG) acc[2 + 2 * (D + 1)] += gp * s_f[row * S + col];
       T dyp = T(1);
 #pragma unroll
       for (int j = 0; j <= D; ++j) {
@@ -1097,7 +1103,7 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
 template <typename T, int NT>
 struct WaveOccupancy;
 template <>
-struct WaveOccupancy<float, 128> { static constexpr int kBlocks = 7; };
+struct WaveOccupancy<float, 128> { static constexpr int kBlocks = 6; };
 template <>
 struct WaveOccupancy<float, 64> { static constexpr int kBlocks = 14; };
 template <>
@@ -1132,7 +1138,8 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
   const WaveTiles& tl = a.tiles;
   const int S = a.S, r = a.r, N = S * S;
   // reference gradients (fx, fy) of the subset pixels, interleaved
-  Pair<T>* s_fg = reinterpret_cast<Pair<T>*>(smem_raw + tl.off_fx);
+  Pair<T>* s_fg = reinterpret_cast<Pair<T>*>(smem_raw + tl.off_fg);
+  T* s_f = reinterpret_cast<T*>(smem_raw + tl.off_f);   // f - f0 of the subset pixels
   T* s_win = reinterpret_cast<T*>(smem_raw + tl.off_win);
   unsigned char* s_gray = smem_raw + tl.off_gray;
   const int gdt = a.ref_gray.dtype;
@@ -1342,6 +1349,33 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
         z2 = cm[tl.bxc + 2];
       }
       T z1 = row0 < row1 ? wref[(row0 + 1) * tl.bxc + col + 1] : T(0);
+      // f - f0 of this thread's pixels, converted from the gray tile by one loop per
+      // element type (the type is the same for every pixel)
+      {
+        T* fo = s_f + row0 * S + col;
+        const unsigned char* gi = gtile + row0 * gpitch + col * tl.gray_es;
+        auto conv = [&](auto load) {
+          for (int row = row0; row < row1; ++row, fo += S, gi += gpitch) *fo = load(gi) - f0;
+        };
+        switch (gdt) {
+          case DIC_U8:
+            conv([](const unsigned char* g) { return tile_gray<T>(g, 0, DIC_U8, 0, 0); });
+            break;
+          case DIC_U16:
+            conv([](const unsigned char* g) { return tile_gray<T>(g, 0, DIC_U16, 0, 0); });
+            break;
+          case DIC_BF16:
+            conv([](const unsigned char* g) { return tile_gray<T>(g, 0, DIC_BF16, 0, 0); });
+            break;
+          case DIC_F32:
+            conv([](const unsigned char* g) { return tile_gray<T>(g, 0, DIC_F32, 0, 0); });
+            break;
+          default:
+            conv([](const unsigned char* g) { return tile_gray<T>(g, 0, DIC_F64, 0, 0); });
+            break;
+        }
+      }
+      T dyv = static_cast<T>(row0 - r);   // dy of the row, counted in T (exact)
       for (int row = row0; row < row1; ++row) {
         const int pix = row * S + col;
         // exact derivative of the reference spline at the pixel:
@@ -1364,14 +1398,14 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
         z1 = p1;
         z2 = p2;
         s_fg[pix] = pair(fx, fy);
-        const T fp = tile_gray<T>(gtile, gpitch, gdt, col, row) - f0;
+        const T fp = s_f[pix];
         sf += fp;
         sff += fp * fp;
-        const T dyv = static_cast<T>(row - r);
         T dyp[M2 + 1];
         dyp[0] = T(1);
 #pragma unroll
         for (int j = 1; j <= M2; ++j) dyp[j] = dyp[j - 1] * dyv;
+        dyv += T(1);
         const T wxx = fx * fx, wxy = fx * fy, wyy = fy * fy;
 #pragma unroll
         for (int j = 0; j <= M2; ++j) {
@@ -1490,11 +1524,11 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
       if (stage != 2) {
         const T* base = s_win + (yc - 1 - w.y0) * w.w + (xc - 1 - w.x0);
         sample_column<T, D, true, GEN>(base, w.w, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1, r,
-                                     S, col, gtile, gpitch, gdt, s_fg, final_pass, st.inside != 0, keys, acc, bad);
+                                     S, col, s_f, s_fg, LM && final_pass, st.inside != 0, keys, acc, bad);
       } else {
         const T* base = a.c_def + static_cast<int64_t>(yc - 1) * a.ldc + (xc - 1);
         sample_column_global<T, D, true>(base, a.ldc, ax, bx, cxq, ay, by, cyq, xlo, xhi, ylo, yhi, f0, row0, row1,
-                                       r, S, col, gtile, gpitch, gdt, s_fg, final_pass, GEN && keys, acc, bad);
+                                       r, S, col, s_f, s_fg, LM && final_pass, GEN && keys, acc, bad);
       }
       if (!final_pass) {
         T v[pow2ceil(NV_IT)];

@@ -296,7 +296,7 @@ def test_tiny_grids_and_one_row_strips_match_oracle(pkg, W, H, S, step, seed):
 
 
 def test_acceptance_is_decided_at_the_warp_of_the_last_pass(pkg):
-    """Reading 8: the in-bounds test belongs to the last iteration's sampling pass. A
+    """R8: the in-bounds test belongs to the last iteration's sampling pass. A
     point whose single pass lies inside the bounds is accepted although the update
     carries its subset past the right edge; the GPU agrees with the oracle."""
     from scipy import ndimage

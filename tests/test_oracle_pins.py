@@ -739,7 +739,7 @@ def test_roi_rule_with_a_step():
 
 
 def test_out_of_bounds_test_applies_to_the_warp_of_the_last_pass():
-    # Reading 8: Gauss-Newton takes the coefficient, the in-bounds test and the
+    # R8: Gauss-Newton takes the coefficient, the in-bounds test and the
     # flatness test from the sampling pass of its last iteration, whose warp is the one
     # before the final update. A point whose last pass lies inside the sampling bounds
     # is accepted even when the final update carries its subset outside them.
