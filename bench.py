@@ -807,18 +807,26 @@ def e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_
     r = c.results(copy=False)
     barrier()
     t0 = time.perf_counter()
+    parts = np.zeros(3)
     for _ in range(steps):
+        ta = time.perf_counter()
         c.set_reference(nref)
         c.set_deformed(ndef)
+        tb = time.perf_counter()
         c.run(seeds, stream.cuda_stream)
+        tc = time.perf_counter()
         r = c.results(copy=False)   # the handle's pinned host buffers, filled by the C call
+        parts += (tb - ta, tc - tb, time.perf_counter() - tc)
     barrier()
     el = max_over_ranks((time.perf_counter() - t0) / steps)
     n = int(r["n_points"])
     d2h = sum(np.asarray(r[k]).nbytes for k in ("x", "y", "u", "v", "p", "zncc", "iters", "converged", "status", "wave"))
+    up, run, back = parts / steps
     return {"value": sum_over_ranks(int(r["n_accepted"])) / el, "unit": UNIT,
             "ms_per_step": el * 1e3, "h2d_bytes_per_step": int(nref.nbytes + ndef.nbytes),
-            "d2h_bytes_per_step": int(d2h), "points": n}
+            "d2h_bytes_per_step": int(d2h), "points": n,
+            "split_ms": {"upload": up * 1e3, "correlate": run * 1e3, "readback": back * 1e3},
+            "h2d_gbs": (nref.nbytes + ndef.nbytes) / up / 1e9, "d2h_gbs": d2h / back / 1e9}
 
 
 def run_sequence(stream, S, shape, frames, oracle_points=20):

@@ -98,10 +98,11 @@ typedef enum { DIC_INIT_SEARCH = 0, DIC_INIT_FFT = 1 } dic_init;
  * samples, sums, the Jacobi-scaled Hessian inverse (FP64 when a scaled pivot falls
  * below 1e-5), the solve, the warp update and the ZNCC normalisation in FP32;
  * results stored as FP64. DIC_FP64: FP64 everywhere. DIC_MIXED_FP64_SOLVE: as
- * DIC_MIXED, except that each Gauss-Newton step solves H dp = -b to FP64 accuracy
- * (the Hessian in FP64 from the FP32 moment sums; two steps of FP64 iterative
- * refinement preconditioned by the FP32 inverse) and the final ZNCC is normalised in
- * FP64 from the FP32 sums; Gauss-Newton with ZNSSD on the B-spline only. */
+ * DIC_MIXED, except that each Gauss-Newton step solves H dp = -b beyond FP32
+ * accuracy (the Hessian in FP64 from the FP32 moment sums; one step of iterative
+ * refinement whose residual is evaluated in FP64, the FP32 inverse supplying the
+ * first solution and the correction) and the final ZNCC is normalised in FP64 from
+ * the FP32 sums; Gauss-Newton with ZNSSD on the B-spline only. */
 typedef enum { DIC_FP64 = 0, DIC_MIXED = 1, DIC_MIXED_FP64_SOLVE = 2 } dic_precision;
 
 /* per-point status (dic_results.status) */

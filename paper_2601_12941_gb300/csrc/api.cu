@@ -286,8 +286,14 @@ int bind_image(dic_handle* h, const dic_image* im, GrayPlane* plane, void** owne
       if (rc) return rc;
       *owned = buf;
     }
-    DIC_CUDA(cudaMemcpy2D(*owned, pitch, im->data, stride, row_bytes, im->height, cudaMemcpyHostToDevice),
-             "image upload");
+    // one linear copy when the rows are contiguous on both sides (a 2-D copy moves
+    // the image row by row)
+    if (stride == static_cast<int64_t>(pitch)) {
+      DIC_CUDA(cudaMemcpy(*owned, im->data, pitch * im->height, cudaMemcpyHostToDevice), "image upload");
+    } else {
+      DIC_CUDA(cudaMemcpy2D(*owned, pitch, im->data, stride, row_bytes, im->height, cudaMemcpyHostToDevice),
+               "image upload");
+    }
     plane->data = *owned;
     plane->stride = static_cast<int64_t>(pitch);
   }

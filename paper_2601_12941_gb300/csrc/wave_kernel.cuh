@@ -614,27 +614,24 @@ __device__ int gauss_newton_update(PointState<C, NP, SC>& st, const C* out, int 
   }
   C d;
   if constexpr (std::is_same<SC, Refined64>::value) {
-    // H dp = -b to FP64 accuracy: x = -X b, then x <- x - X (b + H x) twice with the
-    // residual in FP64 (each step multiplies the error by about |I - X H|, a few
-    // FP32 roundings times the scaled condition number)
-    const double bc = lane < NP ? static_cast<double>(st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]))
-                                : 0.0;
+    // H dp = -b by one step of iterative refinement: x0 = -X b with the FP32 inverse,
+    // the residual r = b + H x0 in FP64 against the FP64 Hessian, x = x0 - X r; the
+    // error of x is about the square of x0's relative error (a few FP32 roundings times
+    // the scaled condition number), far below FP32 rounding
+    const C bcf = lane < NP ? st.sdf[lane] - ratio * (out[2 + lane] - nu * st.sds[lane]) : C(0);
     const int row = lane < NP ? lane : 0;
-    double x = 0.0;
+    C x0 = C(0);
 #pragma unroll
-    for (int m = 0; m < NP; ++m) x -= static_cast<double>(st.sv.X[m * NP + row]) * __shfl_sync(0xffffffffu, bc, m);
+    for (int m = 0; m < NP; ++m) x0 -= st.sv.X[m * NP + row] * __shfl_sync(0xffffffffu, bcf, m);
+    double res = static_cast<double>(bcf);
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      double res = bc;
+    for (int m = 0; m < NP; ++m)
+      res += st.sv.H[row * NP + m] * static_cast<double>(__shfl_sync(0xffffffffu, x0, m));
+    const C rf = static_cast<C>(res);
+    C dx = C(0);
 #pragma unroll
-      for (int m = 0; m < NP; ++m) res += st.sv.H[row * NP + m] * __shfl_sync(0xffffffffu, x, m);
-      double dx = 0.0;
-#pragma unroll
-      for (int m = 0; m < NP; ++m)
-        dx -= static_cast<double>(st.sv.X[m * NP + row]) * __shfl_sync(0xffffffffu, res, m);
-      x += dx;
-    }
-    d = lane < NP ? static_cast<C>(x) : C(0);
+    for (int m = 0; m < NP; ++m) dx -= st.sv.X[m * NP + row] * __shfl_sync(0xffffffffu, rf, m);
+    d = lane < NP ? static_cast<C>(static_cast<double>(x0) + static_cast<double>(dx)) : C(0);
   } else if constexpr (sizeof(SC) == sizeof(double)) {
     double bc = 0.0;
     if (lane < NP)
