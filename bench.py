@@ -46,8 +46,9 @@ FLOP_COEFF_SUM = 2
 PT_OUT_OF_BOUNDS = 3
 
 # DRAM bytes (read + write) per attempted point of the wave kernel, from one ncu
-# capture of the current kernel (None: not captured since the kernel last changed)
-WAVE_DRAM_BYTES_PER_POINT = None
+# capture of the current kernel (a mid-run wave of 2,560 points on the 6144^2 version
+# of the workload: 31.26 MB per launch); None when the kernel has changed since
+WAVE_DRAM_BYTES_PER_POINT = 12212
 
 
 def sm_count():
