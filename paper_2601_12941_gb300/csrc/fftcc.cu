@@ -437,6 +437,313 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
   }
 }
 
+// ---------------------------------------------------------------- odd windows on the tensor cores
+// Odd windows up to 31 px (the subset-sized last level): the four DFT matrix products
+// of a window on the tensor cores (mma.sync m16n8k8, TF32 operands, FP32
+// accumulators), each operand split into a TF32 high part and a TF32 remainder so that
+// hi*hi + hi*lo + lo*hi keeps FP32 accuracy (3xTF32). The window is padded to 32; a
+// complex product A B is the real product [Ar Ai] [[Br, Bi], [-Bi, Br]]. With W the
+// DFT matrix (symmetric) and Z the packed window:
+//   1. Y = Z W              rows, forward       (32 x 64) x (64 x 64), stored transposed
+//   2. X^T = Y^T W          columns, forward    (32 x 64) x (64 x 64)
+//   3. P = cross power of X(k), X(-k)
+//   4. T = P conj(W)        rows ky <= 15 of the Hermitian half, (16 x 64) x (64 x 64);
+//                           conj(W) in block form is the transpose of W's
+//   5. R = A6 [Tr; Ti]      R[y][x] = sum_ky c_ky (Tr cos(2 pi ky y / L) - Ti sin(...)),
+//                           c_0 = 1, c_ky = 2: (32 x 32) x (32 x 32)
+// 128 threads (four warps) per block, one window at a time; warp w takes its share of
+// the 16 x 8 output tiles of each product.
+constexpr int kTcP = 32;                 // padded window side
+constexpr int kTcSA = 2 * kTcP + 4;      // row stride (floats) of the 32 x 64 operand buffers
+constexpr int kTcSW = kTcP + 8;          // row stride of the 32 x 32 parts of W (and of [Tr; Ti])
+constexpr int kTcS6 = kTcP + 4;          // row stride of A6
+constexpr int kTcThreads = 128;
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// c += a b, m16n8k8, TF32 operands (bit patterns), FP32 accumulators
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The A fragment of rows m0.., columns k0.. of a row-major FP32 buffer, split into
+// TF32 high parts and remainders: lane (g, t) holds rows g, g + 8 and columns t, t + 4.
+__device__ __forceinline__ void a_frag_split(const float* A, int sa, int m0, int k0, int g, int t, uint32_t (&hi)[4],
+                                             uint32_t (&lo)[4]) {
+  const float v[4] = {A[(m0 + g) * sa + k0 + t], A[(m0 + g + 8) * sa + k0 + t], A[(m0 + g) * sa + k0 + t + 4],
+                      A[(m0 + g + 8) * sa + k0 + t + 4]};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    hi[i] = tf32_bits(v[i]);
+    lo[i] = tf32_bits(v[i] - __uint_as_float(hi[i]));
+  }
+}
+
+// B fragment (rows k0.., columns n0..) of the 64 x 64 block matrix [[Wr, Wi], [-Wi, Wr]]
+// (TRANS: of its transpose, which is the block matrix of conj(W)), from the split
+// 32 x 32 parts: wp[0] = Wr, wp[1] = Wi (high or low parts, TF32 bits). A 8 x 8 tile lies
+// in one quadrant; a negated quadrant flips the sign bits. Lane (g, t): rows t, t + 4,
+// column g.
+template <bool TRANS>
+__device__ __forceinline__ void w_frag(const uint32_t* const (&wp)[2], int k0, int n0, int g, int t, uint32_t& b0,
+                                       uint32_t& b1) {
+  // block row/column of the element (k, n): the quadrant of the stored matrix
+  const int qr = (TRANS ? n0 : k0) >> 5, qc = (TRANS ? k0 : n0) >> 5;
+  const uint32_t* part = wp[qr == qc ? 0 : 1];
+  const uint32_t neg = (qr == 1 && qc == 0) ? 0x80000000u : 0u;
+  const int r0 = (TRANS ? n0 : k0) & 31, c0 = (TRANS ? k0 : n0) & 31;
+  if (TRANS) {   // element (k, n) of the transpose is stored element (n, k)
+    b0 = part[(r0 + g) * kTcSW + c0 + t] ^ neg;
+    b1 = part[(r0 + g) * kTcSW + c0 + t + 4] ^ neg;
+  } else {
+    b0 = part[(r0 + t) * kTcSW + c0 + g] ^ neg;
+    b1 = part[(r0 + t + 4) * kTcSW + c0 + g] ^ neg;
+  }
+}
+
+// acc[j] += A (rows m0..m0+15, k in [0, K)) x Wblock (columns n0 + 8 j), 3xTF32
+template <bool TRANS, int NJ>
+__device__ __forceinline__ void gemm_w(const float* A, int sa, int m0, int K, const uint32_t* const (&wh)[2],
+                                       const uint32_t* const (&wl)[2], const int (&n0)[NJ], int g, int t,
+                                       float (&acc)[NJ][4]) {
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    uint32_t ah[4], al[4];
+    a_frag_split(A, sa, m0, k0, g, t, ah, al);
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      uint32_t bh0, bh1, bl0, bl1;
+      w_frag<TRANS>(wh, k0, n0[j], g, t, bh0, bh1);
+      w_frag<TRANS>(wl, k0, n0[j], g, t, bl0, bl1);
+      mma_tf32(acc[j], ah, bh0, bh1);
+      mma_tf32(acc[j], ah, bl0, bl1);
+      mma_tf32(acc[j], al, bh0, bh1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTcThreads) fftcc_odd_tc_kernel(FftccArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L = a.L, N = L * L, kh = (L + 1) / 2;
+  uint32_t* wrh = reinterpret_cast<uint32_t*>(smem_raw);   // [32][kTcSW] TF32 bits
+  uint32_t* wih = wrh + kTcP * kTcSW;
+  uint32_t* wrl = wih + kTcP * kTcSW;
+  uint32_t* wil = wrl + kTcP * kTcSW;
+  uint32_t* a6h = wil + kTcP * kTcSW;                        // [32][kTcS6]
+  uint32_t* a6l = a6h + kTcP * kTcS6;
+  float* buf0 = reinterpret_cast<float*>(a6l + kTcP * kTcS6);   // [32][kTcSA]
+  float* buf1 = buf0 + kTcP * kTcSA;
+  __shared__ float s_red[2 * (kTcThreads / 32)];
+  __shared__ unsigned long long s_key[kTcThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const uint32_t* const wh[2] = {wrh, wih};
+  const uint32_t* const wl[2] = {wrl, wil};
+
+  // W (x, k < L: exp(-2 pi i x k / L), else 0) and A6, each as TF32 high part and remainder
+  for (int e = tid; e < kTcP * kTcP; e += kTcThreads) {
+    const int x = e >> 5, k = e & 31;
+    const float2 w = (x < L && k < L) ? a.tw_odd[(x * k) % L] : make_float2(0.f, 0.f);
+    const uint32_t rh = tf32_bits(w.x), ih = tf32_bits(w.y);
+    wrh[x * kTcSW + k] = rh;
+    wih[x * kTcSW + k] = ih;
+    wrl[x * kTcSW + k] = tf32_bits(w.x - __uint_as_float(rh));
+    wil[x * kTcSW + k] = tf32_bits(w.y - __uint_as_float(ih));
+    // A6[y][kp]: kp < 16 the cosine column of ky = kp, else the sine column of kp - 16
+    const int y = x, ky = k & 15;
+    float v = 0.f;
+    if (y < L && ky < kh) {
+      const float2 q = a.tw_odd[(ky * y) % L];            // (cos, -sin) of 2 pi ky y / L
+      const float c = ky == 0 ? 1.f : 2.f;
+      v = k < 16 ? c * q.x : c * q.y;
+    }
+    const uint32_t vh = tf32_bits(v);
+    a6h[y * kTcS6 + k] = vh;
+    a6l[y * kTcS6 + k] = tf32_bits(v - __uint_as_float(vh));
+  }
+  __syncthreads();
+
+  for (int64_t win = blockIdx.x; win < a.n; win += gridDim.x) {
+    const int4 o = a.org[win];
+    if (!window_ok(o, L, a.W, a.H)) {                       // skipped (outside the ROI)
+      if (tid == 0) {
+        a.u[win] = 0.f;
+        a.v[win] = 0.f;
+        a.peak[win] = 0.f;
+      }
+      continue;
+    }
+    // the packed window [f | g] in buf0 (rows y, columns x and 32 + x; zero padding)
+    float pf = 0.f, pg = 0.f;
+    const float f00 = load_gray<float>(a.ref, o.x, o.y), g00 = load_gray<float>(a.def, o.z, o.w);
+    bool vf = false, vg = false;
+    for (int e = tid; e < kTcP * kTcP; e += kTcThreads) {
+      const int y = e >> 5, x = e & 31;
+      float f = 0.f, gv = 0.f;
+      if (y < L && x < L) {
+        f = load_gray<float>(a.ref, o.x + x, o.y + y);
+        gv = load_gray<float>(a.def, o.z + x, o.w + y);
+        vf |= f != f00;
+        vg |= gv != g00;
+      }
+      buf0[y * kTcSA + x] = f;
+      buf0[y * kTcSA + kTcP + x] = gv;
+      pf += f;
+      pg += gv;
+    }
+    float sf = pf, sg = pg;
+    const int any_f = __syncthreads_or(vf);
+    const int any_g = __syncthreads_or(vg);
+    const bool flat = !any_f || !any_g;
+    block_sum2(sf, sg, s_red);
+    const float mf = sf / static_cast<float>(N), mg = sg / static_cast<float>(N);
+    float pqf = 0.f, pqg = 0.f;
+    for (int e = tid; e < N; e += kTcThreads) {
+      const int y = e / L, x = e - y * L;
+      const float f = buf0[y * kTcSA + x] - mf, gv = buf0[y * kTcSA + kTcP + x] - mg;
+      buf0[y * kTcSA + x] = f;
+      buf0[y * kTcSA + kTcP + x] = gv;
+      pqf = fmaf(f, f, pqf);
+      pqg = fmaf(gv, gv, pqg);
+    }
+    float qf = pqf, qg = pqg;
+    block_sum2(qf, qg, s_red);                              // (its barriers also order the writes above)
+
+    // 1. Y = Z W; warp w: rows 16 (w & 1).., columns 32 (w >> 1) + 8 j; stored as
+    //    Y^T in buf1 ([x][y | 32 + y])
+    {
+      const int m0 = (warp & 1) * 16;
+      const int n0[4] = {(warp >> 1) * 32, (warp >> 1) * 32 + 8, (warp >> 1) * 32 + 16, (warp >> 1) * 32 + 24};
+      float acc[4][4] = {};
+      gemm_w<false, 4>(buf0, kTcSA, m0, 2 * kTcP, wh, wl, n0, g, t, acc);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int m = m0 + g + (i >> 1) * 8, n = n0[j] + 2 * t + (i & 1);
+          buf1[(n & 31) * kTcSA + m + (n >> 5) * kTcP] = acc[j][i];
+        }
+    }
+    __syncthreads();
+    // 2. X^T = Y^T W into buf0 ([kx][ky | 32 + ky])
+    {
+      const int m0 = (warp & 1) * 16;
+      const int n0[4] = {(warp >> 1) * 32, (warp >> 1) * 32 + 8, (warp >> 1) * 32 + 16, (warp >> 1) * 32 + 24};
+      float acc[4][4] = {};
+      gemm_w<false, 4>(buf1, kTcSA, m0, 2 * kTcP, wh, wl, n0, g, t, acc);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int m = m0 + g + (i >> 1) * 8, n = n0[j] + 2 * t + (i & 1);
+          buf0[m * kTcSA + n] = acc[j][i];
+        }
+    }
+    __syncthreads();
+    // 3. the cross power P(ky, kx) of rows ky < 16 into buf1 ([ky][kx | 32 + kx]); the
+    //    zero frequency and the padding are zero
+    for (int e = tid; e < 16 * kTcP; e += kTcThreads) {
+      const int ky = e >> 5, kx = e & 31;
+      float2 p = make_float2(0.f, 0.f);
+      if (ky < kh && kx < L && (ky | kx) != 0) {
+        const int mkx = kx == 0 ? 0 : L - kx, mky = ky == 0 ? 0 : L - ky;
+        const float2 zk = make_float2(buf0[kx * kTcSA + ky], buf0[kx * kTcSA + kTcP + ky]);
+        const float2 zm = make_float2(buf0[mkx * kTcSA + mky], buf0[mkx * kTcSA + kTcP + mky]);
+        p = cross_power(zk, zm);
+      }
+      buf1[ky * kTcSA + kx] = p.x;
+      buf1[ky * kTcSA + kTcP + kx] = p.y;
+    }
+    __syncthreads();
+    // 4. T = P conj(W), rows ky < 16; warp w: columns 16 w + 8 j; stored as [Tr; Ti]
+    //    (32 x 32, row ky for Tr and 16 + ky for Ti) in buf0
+    {
+      const int n0[2] = {16 * warp, 16 * warp + 8};
+      float acc[2][4] = {};
+      gemm_w<true, 2>(buf1, kTcSA, 0, 2 * kTcP, wh, wl, n0, g, t, acc);
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int m = g + (i >> 1) * 8, n = n0[j] + 2 * t + (i & 1);
+          buf0[(m + (n >> 5) * 16) * kTcSW + (n & 31)] = acc[j][i];
+        }
+    }
+    __syncthreads();
+    // 5. R = A6 [Tr; Ti] into buf1 ([y][x], row stride 32); warp w: rows 16 (w & 1)..,
+    //    columns 16 (w >> 1) + 8 j
+    {
+      const int m0 = (warp & 1) * 16;
+      float acc[2][4] = {};
+      for (int k0 = 0; k0 < kTcP; k0 += 8) {
+        uint32_t ah[4], al[4];
+        ah[0] = a6h[(m0 + g) * kTcS6 + k0 + t];
+        ah[1] = a6h[(m0 + g + 8) * kTcS6 + k0 + t];
+        ah[2] = a6h[(m0 + g) * kTcS6 + k0 + t + 4];
+        ah[3] = a6h[(m0 + g + 8) * kTcS6 + k0 + t + 4];
+        al[0] = a6l[(m0 + g) * kTcS6 + k0 + t];
+        al[1] = a6l[(m0 + g + 8) * kTcS6 + k0 + t];
+        al[2] = a6l[(m0 + g) * kTcS6 + k0 + t + 4];
+        al[3] = a6l[(m0 + g + 8) * kTcS6 + k0 + t + 4];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int n0 = (warp >> 1) * 16 + 8 * j;
+          const float v0 = buf0[(k0 + t) * kTcSW + n0 + g], v1 = buf0[(k0 + t + 4) * kTcSW + n0 + g];
+          const uint32_t h0 = tf32_bits(v0), h1 = tf32_bits(v1);
+          const uint32_t l0 = tf32_bits(v0 - __uint_as_float(h0)), l1 = tf32_bits(v1 - __uint_as_float(h1));
+          mma_tf32(acc[j], ah, h0, h1);
+          mma_tf32(acc[j], ah, l0, l1);
+          mma_tf32(acc[j], al, h0, h1);
+        }
+      }
+      __syncthreads();   // buf1 (P) is no longer read
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int m = m0 + g + (i >> 1) * 8, n = (warp >> 1) * 16 + 8 * j + 2 * t + (i & 1);
+          buf1[m * kTcP + n] = acc[j][i];
+        }
+    }
+    __syncthreads();
+    // arg-max over the L x L values (ties to the lower row-major index y L + x)
+    unsigned long long best = 0ull;
+    for (int e = tid; e < N; e += kTcThreads) {
+      const int y = e / L, x = e - y * L;
+      const unsigned long long k = peak_key(buf1[y * kTcP + x], e);
+      best = k > best ? k : best;
+    }
+    best = block_max_key(best, s_key);
+    if (tid == 0) {
+      const int e = flat ? 0 : key_index(best);
+      const int ky = e / L, kx = e - ky * L;
+      float dx = static_cast<float>(shift_of_peak(kx, L)), dy = static_cast<float>(shift_of_peak(ky, L));
+      const float r0 = buf1[ky * kTcP + kx];
+      if (a.subpixel && !flat) {
+        const int xm = kx == 0 ? L - 1 : kx - 1, xp = kx == L - 1 ? 0 : kx + 1;
+        const int ym = ky == 0 ? L - 1 : ky - 1, yp = ky == L - 1 ? 0 : ky + 1;
+        dx -= gauss3(buf1[ky * kTcP + xm], r0, buf1[ky * kTcP + xp]);
+        dy -= gauss3(buf1[ym * kTcP + kx], r0, buf1[yp * kTcP + kx]);
+      }
+      a.u[win] = static_cast<float>(o.z - o.x) + dx;
+      a.v[win] = static_cast<float>(o.w - o.y) + dy;
+      a.peak[win] = flat ? 0.f : r0 / (static_cast<float>(N) * sqrtf(qf) * sqrtf(qg));
+    }
+    __syncthreads();                                     // the next window reuses the buffers
+  }
+}
+
+size_t odd_tc_smem() {
+  return sizeof(uint32_t) * (4 * kTcP * kTcSW + 2 * kTcP * kTcS6) + sizeof(float) * 2 * kTcP * kTcSA;
+}
+
 // ---------------------------------------------------------------- large windows
 // Rows of the packed windows, transformed along x: work[w][y][kx]. Also marks the
 // windows whose f or g is not constant (an exactly flat window correlates to 0).
@@ -799,6 +1106,15 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          static_cast<int>(small_smem(kFftSmallMax, false)));
       if (ok != cudaSuccess) return ok;
+      if (L <= kTcP) {
+        // odd windows up to 32: the DFT products on the tensor cores
+        static const cudaError_t ok_tc = cudaFuncSetAttribute(
+            fftcc_odd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(odd_tc_smem()));
+        if (ok_tc != cudaSuccess) return ok_tc;
+        const int per_tc = static_cast<int>(220 * 1024 / (odd_tc_smem() + 1024));
+        fftcc_odd_tc_kernel<<<blocks_for(a.n, per_tc > 0 ? per_tc : 1), kTcThreads, odd_tc_smem(), s>>>(a);
+        return cudaGetLastError();
+      }
       const int per_sm = static_cast<int>(200 * 1024 / smem) < 8 ? static_cast<int>(200 * 1024 / smem) : 8;
       fftcc_small_kernel<false><<<blocks_for(a.n, 2 * (per_sm > 0 ? per_sm : 1)), kSmallThreads / 2, smem, s>>>(a);
     }

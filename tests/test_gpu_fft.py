@@ -84,7 +84,8 @@ def _random_origins(rng, W, H, L, n, spread):
     return org
 
 
-@pytest.mark.parametrize("L,n,subpixel", [(21, 300, True), (31, 200, True), (41, 120, False), (61, 40, True),
+@pytest.mark.parametrize("L,n,subpixel", [(3, 200, False), (9, 200, True), (21, 300, True), (31, 200, True),
+                                          (41, 120, False), (61, 40, True),
                                           (16, 300, True), (32, 200, True), (64, 60, True),
                                           (128, 12, False), (256, 6, False), (512, 3, False)])
 def test_eq1_over_windows_matches_oracle(pkg, L, n, subpixel):
