@@ -50,6 +50,26 @@ PT_OUT_OF_BOUNDS = 3
 # of the workload: 31.26 MB per launch); None when the kernel has changed since
 WAVE_DRAM_BYTES_PER_POINT = 12212
 
+# Tensor work of the odd-window FFT kernel per window (3xTF32 products of the 32-padded
+# window: 384 + 384 for the forward rows and columns, 192 for the inverse rows, 96 for
+# the real column pass), FLOPs per m16n8k8 product, and the nominal TF32 / bf16 dense
+# ratio that turns the measured bf16 peak into a TF32 one.
+TC_MMAS_PER_WINDOW = 1056
+TC_FLOPS_PER_MMA = 2 * 16 * 8 * 8
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def measured_peaks():
+    """The generated peaks file ({} when absent)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+MEASURED = measured_peaks()
+
 
 def sm_count():
     """Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount)."""
@@ -721,12 +741,15 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel
     """Multi-window FFT initialiser (Sec. 2.2, Eq. 1; MAD) on the 1 Gpx pair with the
     SEM study's settings (Sec. 4): subset 31, step 15, maximum displacement 2000 px
     (windows 2048 .. 32, then 31), a 1000 px border outside the ROI, Gaussian
-    sub-pixel fit. The last level (one 31 x 31 window per grid point, direct DFT) is
-    the dominant kernel: algorithmic FLOPs per window 22 S^3 + 2 S^2 (the forward 2-D
-    DFT, 2 S^3 complex multiply-adds of 8 FLOPs; the inverse of the Hermitian cross
-    power, (S+1)/2 rows of S^2 complex multiply-adds and a real column pass of
-    S^2 (S-1)/2 two-FMA terms); it is timed alone through dic_fftcc_windows on the
-    same number of windows."""
+    sub-pixel fit. The last level (one 31 x 31 window per grid point: the DFT matrix
+    products on the tensor cores, 3xTF32 mma.sync) is timed alone through
+    dic_fftcc_windows on the same number of windows. Its roofline counts the tensor
+    work it executes, TC_MMAS_PER_WINDOW m16n8k8 products of 2 x 16 x 8 x 8 FLOPs,
+    against the TF32 dense peak (the measured bf16 peak x the nominal TF32 / bf16
+    ratio 1.1 / 2.25); the method's own count, 22 S^3 + 2 S^2 FP32 FLOPs per window
+    (the forward 2-D DFT, 2 S^3 complex multiply-adds of 8 FLOPs; the inverse of the
+    Hermitian cross power, (S+1)/2 rows of S^2 complex multiply-adds and a real
+    column pass of S^2 (S-1)/2 two-FMA terms), is given beside it."""
     import torch
 
     import paper_2601_12941_gb300 as P
@@ -775,6 +798,9 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel
     k = float(np.median(kms)) if kms else float("nan")
     flops = (22.0 * S ** 3 + 2.0 * S ** 2) * n
     achieved = flops / (k / 1e3) / 1e12
+    tc_flops = float(TC_MMAS_PER_WINDOW * TC_FLOPS_PER_MMA) * n
+    tc_achieved = tc_flops / (k / 1e3) / 1e12
+    tf32_peak = MEASURED.get("bf16_tflops", 1900.0) * TF32_PER_BF16
     levels = g["windows"]
     launches = 1 + 3 * len(levels) + 5 * sum(1 for L in levels if L > 64)   # origins, fftcc (6 when > 64 px), MAD; status
     c.close()
@@ -784,10 +810,15 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel
             "windows": levels, "points_in_roi": n_ok, "ms": t, "points_per_s": n_ok / (t / 1e3),
             "gpu_launches": launches,
             "last_level_ms": k, "last_level_share": k / t,
-            "roofline": {"bound": "alu", "kernel": "fftcc_small_kernel<odd> (direct DFT, one window per block)",
-                         "achieved": achieved, "peak": fp32_peak()[0], "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak()[0], "algorithmic_flops_per_window": 22 * S ** 3 + 2 * S ** 2,
-                         "peak_note": fp32_peak()[1]}}
+            "roofline": {"bound": "tensor",
+                         "kernel": "fftcc_tc_kernel (3xTF32 mma.sync m16n8k8, one warp per window)",
+                         "achieved": tc_achieved, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc_achieved / tf32_peak,
+                         "executed_flops_per_window": TC_MMAS_PER_WINDOW * TC_FLOPS_PER_MMA,
+                         "peak_note": "TF32 dense, of measured: bf16 burst %.1f TFLOP/s (MEASURED_PEAKS.json) x "
+                                      "nominal TF32/bf16 1.1/2.25" % MEASURED.get("bf16_tflops", float("nan")),
+                         "algorithmic_fp32": {"flops_per_window": 22 * S ** 3 + 2 * S ** 2, "achieved": achieved,
+                                              "peak": fp32_peak()[0], "frac": achieved / fp32_peak()[0],
+                                              "peak_note": fp32_peak()[1]}}}
 
 
 def e2e_leg(args, c, ref, dfm, seeds, stream, barrier, max_over_ranks, sum_over_ranks):

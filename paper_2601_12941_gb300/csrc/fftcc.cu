@@ -24,6 +24,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "dic_internal.cuh"
 
 namespace dic {
@@ -437,27 +439,30 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
   }
 }
 
-// ---------------------------------------------------------------- odd windows on the tensor cores
-// Odd windows up to 31 px (the subset-sized last level): the four DFT matrix products
-// of a window on the tensor cores (mma.sync m16n8k8, TF32 operands, FP32
+// ---------------------------------------------------------------- windows up to 32 px on the tensor cores
+// Windows up to 32 px (the subset-sized last level and the 32 px level): the four DFT
+// matrix products of a window on the tensor cores (mma.sync m16n8k8, TF32 operands, FP32
 // accumulators), each operand split into a TF32 high part and a TF32 remainder so that
 // hi*hi + hi*lo + lo*hi keeps FP32 accuracy (3xTF32). The window is padded to 32; a
 // complex product A B is the real product [Ar Ai] [[Br, Bi], [-Bi, Br]]. With W the
 // DFT matrix (symmetric) and Z the packed window:
 //   1. Y = Z W              rows, forward       (32 x 64) x (64 x 64), stored transposed
 //   2. X^T = Y^T W          columns, forward    (32 x 64) x (64 x 64)
-//   3. P = cross power of X(k), X(-k)
-//   4. T = P conj(W)        rows ky <= 15 of the Hermitian half, (16 x 64) x (64 x 64);
-//                           conj(W) in block form is the transpose of W's
+//   3. P = cross power of X(k), X(-k), rows ky <= 15 of the Hermitian half, stored
+//      conjugated
+//   4. T = P conj(W) = conj(conj(P) W)          (16 x 64) x (64 x 64)
 //   5. R = A6 [Tr; Ti]      R[y][x] = sum_ky c_ky (Tr cos(2 pi ky y / L) - Ti sin(...)),
-//                           c_0 = 1, c_ky = 2: (32 x 32) x (32 x 32)
-// 128 threads (four warps) per block, one window at a time; warp w takes its share of
-// the 16 x 8 output tiles of each product.
+//                           c_0 = 1, c_ky = 2, and c_{L/2} = 1 for even L: (32 x 32) x (32 x 32)
+// For L = 32 the Hermitian half has a 17th row, the Nyquist row ky = 16, whose inverse
+// row transform T16 is real: it is formed with shuffles (FP32 FMA) and adds
+// T16[x] (-1)^y to R.
+// One warp per window, with its own 32 x kTcSA buffer in shared memory, so a window
+// needs no block-wide barrier: 16 warps per block (one block per SM, 128 registers a
+// thread), the W and A6 operands held once per block in fragment order (one 16-byte
+// shared load per lane gives the high and low parts of a B fragment).
 constexpr int kTcP = 32;                 // padded window side
 constexpr int kTcSA = 2 * kTcP + 4;      // row stride (floats) of the 32 x 64 operand buffers
-constexpr int kTcSW = kTcP + 8;          // row stride of the 32 x 32 parts of W (and of [Tr; Ti])
-constexpr int kTcS6 = kTcP + 4;          // row stride of A6
-constexpr int kTcThreads = 128;
+constexpr int kTcSW = kTcP + 8;          // row stride of [Tr; Ti] and of R
 
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
   uint32_t r;
@@ -487,261 +492,377 @@ __device__ __forceinline__ void a_frag_split(const float* A, int sa, int m0, int
   }
 }
 
-// B fragment (rows k0.., columns n0..) of the 64 x 64 block matrix [[Wr, Wi], [-Wi, Wr]]
-// (TRANS: of its transpose, which is the block matrix of conj(W)), from the split
-// 32 x 32 parts: wp[0] = Wr, wp[1] = Wi (high or low parts, TF32 bits). A 8 x 8 tile lies
-// in one quadrant; a negated quadrant flips the sign bits. Lane (g, t): rows t, t + 4,
-// column g.
-template <bool TRANS>
-__device__ __forceinline__ void w_frag(const uint32_t* const (&wp)[2], int k0, int n0, int g, int t, uint32_t& b0,
-                                       uint32_t& b1) {
-  // block row/column of the element (k, n): the quadrant of the stored matrix
-  const int qr = (TRANS ? n0 : k0) >> 5, qc = (TRANS ? k0 : n0) >> 5;
-  const uint32_t* part = wp[qr == qc ? 0 : 1];
-  const uint32_t neg = (qr == 1 && qc == 0) ? 0x80000000u : 0u;
-  const int r0 = (TRANS ? n0 : k0) & 31, c0 = (TRANS ? k0 : n0) & 31;
-  if (TRANS) {   // element (k, n) of the transpose is stored element (n, k)
-    b0 = part[(r0 + g) * kTcSW + c0 + t] ^ neg;
-    b1 = part[(r0 + g) * kTcSW + c0 + t + 4] ^ neg;
+// Gray levels of a column of the window: rows y < L of pixel column x (lanes x >= L
+// and rows y >= L give 0), the element type fixed once per window.
+struct Bf16Bits {   // a bfloat16 gray level: the high half of a float
+  uint16_t bits;
+};
+
+template <typename G>
+__device__ __forceinline__ float gray_at(const char* p) {
+  if constexpr (sizeof(G) == 1) {
+    return static_cast<float>(*reinterpret_cast<const uint8_t*>(p));
+  } else if constexpr (std::is_same<G, Bf16Bits>::value) {
+    return __uint_as_float(static_cast<uint32_t>(*reinterpret_cast<const uint16_t*>(p)) << 16);
   } else {
-    b0 = part[(r0 + t) * kTcSW + c0 + g] ^ neg;
-    b1 = part[(r0 + t + 4) * kTcSW + c0 + g] ^ neg;
+    return static_cast<float>(*reinterpret_cast<const G*>(p));
   }
 }
 
-// acc[j] += A (rows m0..m0+15, k in [0, K)) x Wblock (columns n0 + 8 j), 3xTF32
-template <bool TRANS, int NJ>
-__device__ __forceinline__ void gemm_w(const float* A, int sa, int m0, int K, const uint32_t* const (&wh)[2],
-                                       const uint32_t* const (&wl)[2], const int (&n0)[NJ], int g, int t,
-                                       float (&acc)[NJ][4]) {
-  for (int k0 = 0; k0 < K; k0 += 8) {
-    uint32_t ah[4], al[4];
-    a_frag_split(A, sa, m0, k0, g, t, ah, al);
+// Column `lane` of the window at (x0, y0) into col[y * ld] (zero padded to 32 rows),
+// returning the column sum; *varies: a pixel differs from v00.
+template <typename G>
+__device__ __forceinline__ float window_column(const GrayPlane& pl, int x0, int y0, int L, int lane, float* col,
+                                               int ld, float v00, bool* varies) {
+  const bool in = lane < L;
+  const char* p = static_cast<const char*>(pl.data) + static_cast<int64_t>(y0) * pl.stride +
+                  static_cast<int64_t>(x0 + (in ? lane : 0)) * sizeof(G);
+  float s = 0.f;
+  bool vary = false;
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      uint32_t bh0, bh1, bl0, bl1;
-      w_frag<TRANS>(wh, k0, n0[j], g, t, bh0, bh1);
-      w_frag<TRANS>(wl, k0, n0[j], g, t, bl0, bl1);
-      mma_tf32(acc[j], ah, bh0, bh1);
-      mma_tf32(acc[j], ah, bl0, bl1);
-      mma_tf32(acc[j], al, bh0, bh1);
+  for (int y = 0; y < kTcP; ++y) {
+    float v = 0.f;
+    if (in && y < L) {
+      v = gray_at<G>(p + static_cast<int64_t>(y) * pl.stride);
+      vary |= v != v00;
+    }
+    col[y * ld] = v;
+    s += v;
+  }
+  *varies = vary;
+  return s;
+}
+
+__device__ __forceinline__ float load_window_column(const GrayPlane& pl, int x0, int y0, int L, int lane, float* col,
+                                                    int ld, float v00, bool* varies) {
+  switch (pl.dtype) {
+    case DIC_U8:
+      return window_column<uint8_t>(pl, x0, y0, L, lane, col, ld, v00, varies);
+    case DIC_U16:
+      return window_column<uint16_t>(pl, x0, y0, L, lane, col, ld, v00, varies);
+    case DIC_BF16:
+      return window_column<Bf16Bits>(pl, x0, y0, L, lane, col, ld, v00, varies);
+    case DIC_F32:
+      return window_column<float>(pl, x0, y0, L, lane, col, ld, v00, varies);
+    default:
+      return window_column<double>(pl, x0, y0, L, lane, col, ld, v00, varies);
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// acc[m][j] += A (rows 16 m.., 64 columns) x Wblock (64 x 64), 3xTF32; MT row tiles of
+// 16, the 8 column tiles of 8. wf: the B fragments of the block matrix in fragment
+// order, entry (k-step, column tile, lane) = (high b0, high b1, low b0, low b1).
+template <int MT>
+__device__ __forceinline__ void warp_gemm_w(const float* A, int sa, const uint4* __restrict__ wf, int lane, int g,
+                                            int t, float (&acc)[MT][8][4]) {
+#pragma unroll 1
+  for (int ks = 0; ks < 8; ++ks) {
+    uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m) a_frag_split(A, sa, 16 * m, 8 * ks, g, t, ah[m], al[m]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint4 b = wf[(ks * 8 + j) * 32 + lane];
+#pragma unroll
+      for (int m = 0; m < MT; ++m) {
+        mma_tf32(acc[m][j], ah[m], b.x, b.y);
+        mma_tf32(acc[m][j], ah[m], b.z, b.w);
+        mma_tf32(acc[m][j], al[m], b.x, b.y);
+      }
     }
   }
 }
 
-__global__ void __launch_bounds__(kTcThreads) fftcc_odd_tc_kernel(FftccArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = a.L, N = L * L, kh = (L + 1) / 2;
-  uint32_t* wrh = reinterpret_cast<uint32_t*>(smem_raw);   // [32][kTcSW] TF32 bits
-  uint32_t* wih = wrh + kTcP * kTcSW;
-  uint32_t* wrl = wih + kTcP * kTcSW;
-  uint32_t* wil = wrl + kTcP * kTcSW;
-  uint32_t* a6h = wil + kTcP * kTcSW;                        // [32][kTcS6]
-  uint32_t* a6l = a6h + kTcP * kTcS6;
-  float* buf0 = reinterpret_cast<float*>(a6l + kTcP * kTcS6);   // [32][kTcSA]
-  float* buf1 = buf0 + kTcP * kTcSA;
-  __shared__ float s_red[2 * (kTcThreads / 32)];
-  __shared__ unsigned long long s_key[kTcThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const uint32_t* const wh[2] = {wrh, wih};
-  const uint32_t* const wl[2] = {wrl, wil};
+// Element (r, c) of the 64 x 64 block matrix [[Wr, Wi], [-Wi, Wr]] of the DFT matrix
+// W[x][k] = exp(-2 pi i x k / L) (x, k < L; 0 in the padding); tw[m] = exp(-2 pi i m / L).
+__device__ __forceinline__ float w_block(const float2* __restrict__ tw, int L, int r, int c) {
+  const int qr = r >> 5, qc = c >> 5, x = r & 31, k = c & 31;
+  if (x >= L || k >= L) return 0.f;
+  const float2 w = tw[(x * k) % L];
+  return qr == qc ? w.x : (qr == 0 ? w.y : -w.y);
+}
 
-  // W (x, k < L: exp(-2 pi i x k / L), else 0) and A6, each as TF32 high part and remainder
-  for (int e = tid; e < kTcP * kTcP; e += kTcThreads) {
-    const int x = e >> 5, k = e & 31;
-    const float2 w = (x < L && k < L) ? a.tw_odd[(x * k) % L] : make_float2(0.f, 0.f);
-    const uint32_t rh = tf32_bits(w.x), ih = tf32_bits(w.y);
-    wrh[x * kTcSW + k] = rh;
-    wih[x * kTcSW + k] = ih;
-    wrl[x * kTcSW + k] = tf32_bits(w.x - __uint_as_float(rh));
-    wil[x * kTcSW + k] = tf32_bits(w.y - __uint_as_float(ih));
-    // A6[y][kp]: kp < 16 the cosine column of ky = kp, else the sine column of kp - 16
-    const int y = x, ky = k & 15;
-    float v = 0.f;
-    if (y < L && ky < kh) {
-      const float2 q = a.tw_odd[(ky * y) % L];            // (cos, -sin) of 2 pi ky y / L
-      const float c = ky == 0 ? 1.f : 2.f;
-      v = k < 16 ? c * q.x : c * q.y;
+// Entry e = (k-step, column tile, lane) of the fragment-ordered block matrix.
+__device__ __forceinline__ uint4 w_fragment(const float2* __restrict__ tw, int L, int e) {
+  const int ks = e >> 8, j = (e >> 5) & 7, ln = e & 31;
+  const int k = 8 * ks + (ln & 3), n = 8 * j + (ln >> 2);
+  const float v0 = w_block(tw, L, k, n), v1 = w_block(tw, L, k + 4, n);
+  const uint32_t h0 = tf32_bits(v0), h1 = tf32_bits(v1);
+  return make_uint4(h0, h1, tf32_bits(v0 - __uint_as_float(h0)), tf32_bits(v1 - __uint_as_float(h1)));
+}
+
+constexpr int kTcWarps = 16;
+constexpr int kTcBlockThreads = 32 * kTcWarps;
+constexpr int kTcBuf = kTcP * kTcSA;      // floats per warp
+constexpr int kTcFrags = 8 * 8 * 32;      // B fragments of a 64 x 64 block matrix: k-steps x column tiles x lanes
+constexpr int kTcA6Frags = 2 * 4 * 2 * 32;   // A fragments of A6: row tiles x k-steps x (high, low) x lanes
+
+__global__ void __launch_bounds__(kTcBlockThreads, 1) fftcc_tc_kernel(FftccArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 s_root[kTcP];                           // exp(-2 pi i m / L), m < L
+  const int L = a.L, N = L * L, kh = L / 2 + 1;             // rows 0 .. L/2 of the Hermitian half
+  const bool nyquist = L == 32;                             // row ky = 16, outside the 16-row tile
+  uint4* wf = reinterpret_cast<uint4*>(smem_raw);          // B fragments of the block W
+  uint4* a6f = wf + kTcFrags;                               // A fragments of A6
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* buf = reinterpret_cast<float*>(a6f + kTcA6Frags) + warp * kTcBuf;
+  const int g = lane >> 2, t = lane & 3;
+
+  // W's block matrices and A6 in fragment order, TF32 high parts and remainders.
+  // A6[y][kp] (y < L): kp < 16 the cosine column of ky = kp, else the sine column of
+  // kp - 16, weighted c_0 = 1, c_ky = 2, c_{L/2} = 1 (ky <= L / 2; else 0)
+  const bool pow2 = (L & (L - 1)) == 0;
+  for (int e = tid; e < L; e += kTcBlockThreads) s_root[e] = pow2 ? twiddle(a.tw_pow2, e, L, false) : a.tw_odd[e];
+  __syncthreads();
+  for (int e = tid; e < kTcFrags; e += kTcBlockThreads) {
+    wf[e] = w_fragment(s_root, L, e);
+  }
+  for (int e = tid; e < kTcA6Frags / 2; e += kTcBlockThreads) {
+    const int mt = e >> 7, ks = (e >> 5) & 3, ln = e & 31;
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int y = 16 * mt + (ln >> 2) + (i & 1) * 8, kp = 8 * ks + (ln & 3) + (i >> 1) * 4, ky = kp & 15;
+      v[i] = 0.f;
+      if (y < L && ky < kh) {
+        const float2 q = s_root[(ky * y) % L];            // (cos, -sin) of 2 pi ky y / L
+        const float c = (ky == 0 || 2 * ky == L) ? 1.f : 2.f;
+        v[i] = kp < 16 ? c * q.x : c * q.y;
+      }
     }
-    const uint32_t vh = tf32_bits(v);
-    a6h[y * kTcS6 + k] = vh;
-    a6l[y * kTcS6 + k] = tf32_bits(v - __uint_as_float(vh));
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      h[i] = tf32_bits(v[i]);
+      l[i] = tf32_bits(v[i] - __uint_as_float(h[i]));
+    }
+    a6f[2 * e - ln] = make_uint4(h[0], h[1], h[2], h[3]);        // entry ((mt, ks), hi, lane)
+    a6f[2 * e - ln + 32] = make_uint4(l[0], l[1], l[2], l[3]);   // entry ((mt, ks), lo, lane)
   }
   __syncthreads();
 
-  for (int64_t win = blockIdx.x; win < a.n; win += gridDim.x) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * kTcWarps;
+  for (int64_t win = static_cast<int64_t>(blockIdx.x) * kTcWarps + warp; win < a.n; win += stride) {
     const int4 o = a.org[win];
     if (!window_ok(o, L, a.W, a.H)) {                       // skipped (outside the ROI)
-      if (tid == 0) {
+      if (lane == 0) {
         a.u[win] = 0.f;
         a.v[win] = 0.f;
         a.peak[win] = 0.f;
       }
       continue;
     }
-    // the packed window [f | g] in buf0 (rows y, columns x and 32 + x; zero padding)
-    float pf = 0.f, pg = 0.f;
+    // the packed window [f | g] in buf (rows y, columns x and 32 + x; zero padding),
+    // lane x loading pixel column x; then centred by the means
     const float f00 = load_gray<float>(a.ref, o.x, o.y), g00 = load_gray<float>(a.def, o.z, o.w);
-    bool vf = false, vg = false;
-    for (int e = tid; e < kTcP * kTcP; e += kTcThreads) {
-      const int y = e >> 5, x = e & 31;
-      float f = 0.f, gv = 0.f;
-      if (y < L && x < L) {
-        f = load_gray<float>(a.ref, o.x + x, o.y + y);
-        gv = load_gray<float>(a.def, o.z + x, o.w + y);
-        vf |= f != f00;
-        vg |= gv != g00;
-      }
-      buf0[y * kTcSA + x] = f;
-      buf0[y * kTcSA + kTcP + x] = gv;
-      pf += f;
-      pg += gv;
-    }
-    float sf = pf, sg = pg;
-    const int any_f = __syncthreads_or(vf);
-    const int any_g = __syncthreads_or(vg);
-    const bool flat = !any_f || !any_g;
-    block_sum2(sf, sg, s_red);
+    bool vf, vg;
+    float sf = load_window_column(a.ref, o.x, o.y, L, lane, buf + lane, kTcSA, f00, &vf);
+    float sg = load_window_column(a.def, o.z, o.w, L, lane, buf + kTcP + lane, kTcSA, g00, &vg);
+    const bool flat = !__any_sync(0xffffffffu, vf) || !__any_sync(0xffffffffu, vg);
+    sf = warp_sum(sf);
+    sg = warp_sum(sg);
     const float mf = sf / static_cast<float>(N), mg = sg / static_cast<float>(N);
-    float pqf = 0.f, pqg = 0.f;
-    for (int e = tid; e < N; e += kTcThreads) {
-      const int y = e / L, x = e - y * L;
-      const float f = buf0[y * kTcSA + x] - mf, gv = buf0[y * kTcSA + kTcP + x] - mg;
-      buf0[y * kTcSA + x] = f;
-      buf0[y * kTcSA + kTcP + x] = gv;
-      pqf = fmaf(f, f, pqf);
-      pqg = fmaf(gv, gv, pqg);
+    float qf = 0.f, qg = 0.f;
+    if (lane < L) {
+      for (int y = 0; y < L; ++y) {
+        const float f = buf[y * kTcSA + lane] - mf, gv = buf[y * kTcSA + kTcP + lane] - mg;
+        buf[y * kTcSA + lane] = f;
+        buf[y * kTcSA + kTcP + lane] = gv;
+        qf = fmaf(f, f, qf);
+        qg = fmaf(gv, gv, qg);
+      }
     }
-    float qf = pqf, qg = pqg;
-    block_sum2(qf, qg, s_red);                              // (its barriers also order the writes above)
+    qf = warp_sum(qf);
+    qg = warp_sum(qg);
+    __syncwarp();
 
-    // 1. Y = Z W; warp w: rows 16 (w & 1).., columns 32 (w >> 1) + 8 j; stored as
-    //    Y^T in buf1 ([x][y | 32 + y])
+    // 1. Y = Z W, stored as Y^T ([x][y | 32 + y])
     {
-      const int m0 = (warp & 1) * 16;
-      const int n0[4] = {(warp >> 1) * 32, (warp >> 1) * 32 + 8, (warp >> 1) * 32 + 16, (warp >> 1) * 32 + 24};
-      float acc[4][4] = {};
-      gemm_w<false, 4>(buf0, kTcSA, m0, 2 * kTcP, wh, wl, n0, g, t, acc);
+      float acc[2][8][4] = {};
+      warp_gemm_w<2>(buf, kTcSA, wf, lane, g, t, acc);
+      __syncwarp();
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int m = 16 * mt + g + (i >> 1) * 8, n = 8 * j + 2 * t + (i & 1);
+            buf[(n & 31) * kTcSA + m + (n >> 5) * kTcP] = acc[mt][j][i];
+          }
+      __syncwarp();
+    }
+    // 2. X^T = Y^T W ([kx][ky | 32 + ky])
+    {
+      float acc[2][8][4] = {};
+      warp_gemm_w<2>(buf, kTcSA, wf, lane, g, t, acc);
+      __syncwarp();
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int m = 16 * mt + g + (i >> 1) * 8, n = 8 * j + 2 * t + (i & 1);
+            buf[m * kTcSA + n] = acc[mt][j][i];
+          }
+      __syncwarp();
+    }
+    // 3. the cross power P(ky, kx) of rows ky < 16 ([ky][kx | 32 + kx]); the zero
+    //    frequency and the padding are zero. All of X is read before P is written.
+    float t16 = 0.f;
+    {
+      const int ky = lane & 15;
+      float2 p[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int kx = 2 * j + (lane >> 4);
+        p[j] = make_float2(0.f, 0.f);
+        if (ky < kh && kx < L && (ky | kx) != 0) {
+          const int mkx = kx == 0 ? 0 : L - kx, mky = ky == 0 ? 0 : L - ky;
+          const float2 zk = make_float2(buf[kx * kTcSA + ky], buf[kx * kTcSA + kTcP + ky]);
+          const float2 zm = make_float2(buf[mkx * kTcSA + mky], buf[mkx * kTcSA + kTcP + mky]);
+          p[j] = cross_power(zk, zm);
+        }
+      }
+      float2 p16 = make_float2(0.f, 0.f);                // the Nyquist row's P(16, kx), kx = lane
+      if (nyquist) {
+        const int mkx = lane == 0 ? 0 : L - lane;
+        p16 = cross_power(make_float2(buf[lane * kTcSA + 16], buf[lane * kTcSA + kTcP + 16]),
+                          make_float2(buf[mkx * kTcSA + 16], buf[mkx * kTcSA + kTcP + 16]));
+      }
+      __syncwarp();
+      if (nyquist) {                                     // T16[x] = Re sum_kx P(16, kx) exp(2 pi i kx x / L), x = lane
+#pragma unroll 8
+        for (int kx = 0; kx < 32; ++kx) {
+          const float pr = __shfl_sync(0xffffffffu, p16.x, kx), pi = __shfl_sync(0xffffffffu, p16.y, kx);
+          const float2 w = s_root[(lane * kx) & 31];
+          t16 = fmaf(pr, w.x, fmaf(pi, w.y, t16));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int kx = 2 * j + (lane >> 4);
+        buf[ky * kTcSA + kx] = p[j].x;
+        buf[ky * kTcSA + kTcP + kx] = -p[j].y;           // conj(P): T = conj(conj(P) W)
+      }
+      __syncwarp();
+    }
+    // 4. T = P conj(W), rows ky < 16, stored as [Tr; Ti] (32 x 32, row ky for Tr and
+    //    16 + ky for Ti, row stride kTcSW)
+    {
+      float acc[1][8][4] = {};
+      warp_gemm_w<1>(buf, kTcSA, wf, lane, g, t, acc);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int m = g + (i >> 1) * 8, n = 8 * j + 2 * t + (i & 1);
+          buf[(m + (n >> 5) * 16) * kTcSW + (n & 31)] = (n >> 5) ? -acc[0][j][i] : acc[0][j][i];
+        }
+      __syncwarp();
+    }
+    // 5. R = A6 [Tr; Ti] (32 x 32), then the arg-max over the L x L values (ties to
+    //    the lower row-major index y L + x) straight from the accumulators
+    float acc[2][4][4] = {};
+#pragma unroll 1
+    for (int k0 = 0; k0 < kTcP; k0 += 8) {
+      uint32_t ah[2][4], al[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const uint4 h = a6f[((mt * 4 + (k0 >> 3)) * 2) * 32 + lane], l = a6f[((mt * 4 + (k0 >> 3)) * 2 + 1) * 32 + lane];
+        ah[mt][0] = h.x;
+        ah[mt][1] = h.y;
+        ah[mt][2] = h.z;
+        ah[mt][3] = h.w;
+        al[mt][0] = l.x;
+        al[mt][1] = l.y;
+        al[mt][2] = l.z;
+        al[mt][3] = l.w;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float v0 = buf[(k0 + t) * kTcSW + 8 * j + g], v1 = buf[(k0 + t + 4) * kTcSW + 8 * j + g];
+        const uint32_t h0 = tf32_bits(v0), h1 = tf32_bits(v1);
+        const uint32_t l0 = tf32_bits(v0 - __uint_as_float(h0)), l1 = tf32_bits(v1 - __uint_as_float(h1));
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          mma_tf32(acc[mt][j], ah[mt], h0, h1);
+          mma_tf32(acc[mt][j], ah[mt], l0, l1);
+          mma_tf32(acc[mt][j], al[mt], h0, h1);
+        }
+      }
+    }
+    if (nyquist) {                                       // R[y][x] += T16[x] (-1)^y
 #pragma unroll
       for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int m = m0 + g + (i >> 1) * 8, n = n0[j] + 2 * t + (i & 1);
-          buf1[(n & 31) * kTcSA + m + (n >> 5) * kTcP] = acc[j][i];
+        for (int c = 0; c < 2; ++c) {
+          const float tv = __shfl_sync(0xffffffffu, t16, 8 * j + 2 * t + c);
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            acc[mt][j][c] += (g & 1) ? -tv : tv;         // row 16 mt + g
+            acc[mt][j][2 + c] += (g & 1) ? -tv : tv;     // row 16 mt + g + 8
+          }
         }
     }
-    __syncthreads();
-    // 2. X^T = Y^T W into buf0 ([kx][ky | 32 + ky])
-    {
-      const int m0 = (warp & 1) * 16;
-      const int n0[4] = {(warp >> 1) * 32, (warp >> 1) * 32 + 8, (warp >> 1) * 32 + 16, (warp >> 1) * 32 + 24};
-      float acc[4][4] = {};
-      gemm_w<false, 4>(buf1, kTcSA, m0, 2 * kTcP, wh, wl, n0, g, t, acc);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int m = m0 + g + (i >> 1) * 8, n = n0[j] + 2 * t + (i & 1);
-          buf0[m * kTcSA + n] = acc[j][i];
-        }
-    }
-    __syncthreads();
-    // 3. the cross power P(ky, kx) of rows ky < 16 into buf1 ([ky][kx | 32 + kx]); the
-    //    zero frequency and the padding are zero
-    for (int e = tid; e < 16 * kTcP; e += kTcThreads) {
-      const int ky = e >> 5, kx = e & 31;
-      float2 p = make_float2(0.f, 0.f);
-      if (ky < kh && kx < L && (ky | kx) != 0) {
-        const int mkx = kx == 0 ? 0 : L - kx, mky = ky == 0 ? 0 : L - ky;
-        const float2 zk = make_float2(buf0[kx * kTcSA + ky], buf0[kx * kTcSA + kTcP + ky]);
-        const float2 zm = make_float2(buf0[mkx * kTcSA + mky], buf0[mkx * kTcSA + kTcP + mky]);
-        p = cross_power(zk, zm);
-      }
-      buf1[ky * kTcSA + kx] = p.x;
-      buf1[ky * kTcSA + kTcP + kx] = p.y;
-    }
-    __syncthreads();
-    // 4. T = P conj(W), rows ky < 16; warp w: columns 16 w + 8 j; stored as [Tr; Ti]
-    //    (32 x 32, row ky for Tr and 16 + ky for Ti) in buf0
-    {
-      const int n0[2] = {16 * warp, 16 * warp + 8};
-      float acc[2][4] = {};
-      gemm_w<true, 2>(buf1, kTcSA, 0, 2 * kTcP, wh, wl, n0, g, t, acc);
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int m = g + (i >> 1) * 8, n = n0[j] + 2 * t + (i & 1);
-          buf0[(m + (n >> 5) * 16) * kTcSW + (n & 31)] = acc[j][i];
-        }
-    }
-    __syncthreads();
-    // 5. R = A6 [Tr; Ti] into buf1 ([y][x], row stride 32); warp w: rows 16 (w & 1)..,
-    //    columns 16 (w >> 1) + 8 j
-    {
-      const int m0 = (warp & 1) * 16;
-      float acc[2][4] = {};
-      for (int k0 = 0; k0 < kTcP; k0 += 8) {
-        uint32_t ah[4], al[4];
-        ah[0] = a6h[(m0 + g) * kTcS6 + k0 + t];
-        ah[1] = a6h[(m0 + g + 8) * kTcS6 + k0 + t];
-        ah[2] = a6h[(m0 + g) * kTcS6 + k0 + t + 4];
-        ah[3] = a6h[(m0 + g + 8) * kTcS6 + k0 + t + 4];
-        al[0] = a6l[(m0 + g) * kTcS6 + k0 + t];
-        al[1] = a6l[(m0 + g + 8) * kTcS6 + k0 + t];
-        al[2] = a6l[(m0 + g) * kTcS6 + k0 + t + 4];
-        al[3] = a6l[(m0 + g + 8) * kTcS6 + k0 + t + 4];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int n0 = (warp >> 1) * 16 + 8 * j;
-          const float v0 = buf0[(k0 + t) * kTcSW + n0 + g], v1 = buf0[(k0 + t + 4) * kTcSW + n0 + g];
-          const uint32_t h0 = tf32_bits(v0), h1 = tf32_bits(v1);
-          const uint32_t l0 = tf32_bits(v0 - __uint_as_float(h0)), l1 = tf32_bits(v1 - __uint_as_float(h1));
-          mma_tf32(acc[j], ah, h0, h1);
-          mma_tf32(acc[j], ah, l0, l1);
-          mma_tf32(acc[j], al, h0, h1);
-        }
-      }
-      __syncthreads();   // buf1 (P) is no longer read
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int m = m0 + g + (i >> 1) * 8, n = (warp >> 1) * 16 + 8 * j + 2 * t + (i & 1);
-          buf1[m * kTcP + n] = acc[j][i];
-        }
-    }
-    __syncthreads();
-    // arg-max over the L x L values (ties to the lower row-major index y L + x)
     unsigned long long best = 0ull;
-    for (int e = tid; e < N; e += kTcThreads) {
-      const int y = e / L, x = e - y * L;
-      const unsigned long long k = peak_key(buf1[y * kTcP + x], e);
-      best = k > best ? k : best;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int y = 16 * mt + g + (i >> 1) * 8, x = 8 * j + 2 * t + (i & 1);
+          if (y < L && x < L) {
+            const unsigned long long k = peak_key(acc[mt][j][i], y * L + x);
+            best = k > best ? k : best;
+          }
+        }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, best, off);
+      best = o2 > best ? o2 : best;
     }
-    best = block_max_key(best, s_key);
-    if (tid == 0) {
+    __syncwarp();                                        // [Tr; Ti] is no longer read
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int y = 16 * mt + g + (i >> 1) * 8, x = 8 * j + 2 * t + (i & 1);
+          buf[y * kTcSW + x] = acc[mt][j][i];
+        }
+    __syncwarp();
+    if (lane == 0) {
       const int e = flat ? 0 : key_index(best);
       const int ky = e / L, kx = e - ky * L;
       float dx = static_cast<float>(shift_of_peak(kx, L)), dy = static_cast<float>(shift_of_peak(ky, L));
-      const float r0 = buf1[ky * kTcP + kx];
+      const float r0 = buf[ky * kTcSW + kx];
       if (a.subpixel && !flat) {
         const int xm = kx == 0 ? L - 1 : kx - 1, xp = kx == L - 1 ? 0 : kx + 1;
         const int ym = ky == 0 ? L - 1 : ky - 1, yp = ky == L - 1 ? 0 : ky + 1;
-        dx -= gauss3(buf1[ky * kTcP + xm], r0, buf1[ky * kTcP + xp]);
-        dy -= gauss3(buf1[ym * kTcP + kx], r0, buf1[yp * kTcP + kx]);
+        dx -= gauss3(buf[ky * kTcSW + xm], r0, buf[ky * kTcSW + xp]);
+        dy -= gauss3(buf[ym * kTcSW + kx], r0, buf[yp * kTcSW + kx]);
       }
       a.u[win] = static_cast<float>(o.z - o.x) + dx;
       a.v[win] = static_cast<float>(o.w - o.y) + dy;
       a.peak[win] = flat ? 0.f : r0 / (static_cast<float>(N) * sqrtf(qf) * sqrtf(qg));
     }
-    __syncthreads();                                     // the next window reuses the buffers
+    __syncwarp();                                        // the next window reuses the buffer
   }
 }
 
-size_t odd_tc_smem() {
-  return sizeof(uint32_t) * (4 * kTcP * kTcSW + 2 * kTcP * kTcS6) + sizeof(float) * 2 * kTcP * kTcSA;
+size_t tc_smem() {
+  return sizeof(uint4) * (kTcFrags + kTcA6Frags) + sizeof(float) * kTcWarps * kTcBuf;
 }
 
 // ---------------------------------------------------------------- large windows
@@ -1092,6 +1213,14 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
   if (a.n == 0) return cudaSuccess;
   const int L = a.L;
   const bool pow2 = (L & (L - 1)) == 0;
+  if (L <= kTcP) {
+    // windows up to 32: the DFT products on the tensor cores
+    static const cudaError_t ok_tc = cudaFuncSetAttribute(fftcc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          static_cast<int>(tc_smem()));
+    if (ok_tc != cudaSuccess) return ok_tc;
+    fftcc_tc_kernel<<<blocks_for((a.n + kTcWarps - 1) / kTcWarps, 1), kTcBlockThreads, tc_smem(), s>>>(a);
+    return cudaGetLastError();
+  }
   if (L <= kFftSmallMax) {
     const size_t smem = small_smem(L, pow2);
     if (pow2) {
@@ -1106,15 +1235,6 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          static_cast<int>(small_smem(kFftSmallMax, false)));
       if (ok != cudaSuccess) return ok;
-      if (L <= kTcP) {
-        // odd windows up to 32: the DFT products on the tensor cores
-        static const cudaError_t ok_tc = cudaFuncSetAttribute(
-            fftcc_odd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(odd_tc_smem()));
-        if (ok_tc != cudaSuccess) return ok_tc;
-        const int per_tc = static_cast<int>(220 * 1024 / (odd_tc_smem() + 1024));
-        fftcc_odd_tc_kernel<<<blocks_for(a.n, per_tc > 0 ? per_tc : 1), kTcThreads, odd_tc_smem(), s>>>(a);
-        return cudaGetLastError();
-      }
       const int per_sm = static_cast<int>(200 * 1024 / smem) < 8 ? static_cast<int>(200 * 1024 / smem) : 8;
       fftcc_small_kernel<false><<<blocks_for(a.n, 2 * (per_sm > 0 ? per_sm : 1)), kSmallThreads / 2, smem, s>>>(a);
     }
