@@ -102,65 +102,118 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int m, 
   return w;
 }
 
-// Stockham passes (radix 4, then one radix-2 pass when log2 L is odd) over `lines`
-// lines of length L (a power of two): element i of line l at p[l * ls + i * es];
-// ping-pong between p and q, the result in the returned buffer. A pass of radix R
-// after sub-transforms of size ns takes butterfly j's inputs at j + r L / R,
-// twiddles them by exp(-2 pi i r (j mod ns) / (R ns)) and writes output r at
-// (j - j mod ns) R + j mod ns + r ns.
-__device__ float2* fft_lines(float2* p, float2* q, int L, int lines, int ls, int es, const float2* __restrict__ tw,
-                             bool inv) {
-  int ns = 1;
-  const int quarter = L >> 2;
-  if (quarter > 0) {
-    const int lgq = __ffs(quarter) - 1;
-    const int total = lines * quarter;
-    for (; ns * 4 <= L; ns <<= 2) {
-      for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int l = t >> lgq, j = t & (quarter - 1);
-        const float2* in = p + l * ls;
-        float2* out = q + l * ls;
-        const int k = j & (ns - 1);
-        float2 v0 = in[j * es], v1 = in[(j + quarter) * es], v2 = in[(j + 2 * quarter) * es],
-               v3 = in[(j + 3 * quarter) * es];
-        if (ns > 1) {
-          const int M = ns << 2;
-          v1 = cmul(v1, twiddle(tw, k, M, inv));
-          v2 = cmul(v2, twiddle(tw, 2 * k, M, inv));
-          v3 = cmul(v3, twiddle(tw, 3 * k, M, inv));
-        }
-        const float2 a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = csub(v1, v3);
-        const float2 rot = inv ? make_float2(-a3.y, a3.x) : make_float2(a3.y, -a3.x);   // +-i a3
-        const int d = ((j - k) << 2) + k;
-        out[d * es] = cadd(a0, a2);
-        out[(d + ns) * es] = cadd(a1, rot);
-        out[(d + 2 * ns) * es] = csub(a0, a2);
-        out[(d + 3 * ns) * es] = csub(a1, rot);
-      }
-      __syncthreads();
-      float2* t = p;
-      p = q;
-      q = t;
-    }
+// Shared-memory slot of element e of a transform buffer: one pad slot after every 8, so
+// that the stride-R stores of the first Stockham passes and the strided column
+// accesses fall on distinct banks. A buffer of n elements takes fft_slots(n) slots.
+__host__ __device__ __forceinline__ int fsl(int e) { return e + (e >> 3); }
+__host__ __device__ __forceinline__ int fft_slots(int n) { return n + (n >> 3); }
+
+// DFT of 4 points in place, forward (exp(-2 pi i n k / 4)) or inverse.
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& y0, float2& y1, float2& y2, float2& y3) {
+  const float2 t0 = cadd(y0, y2), t1 = csub(y0, y2), t2 = cadd(y1, y3), t3 = csub(y1, y3);
+  const float2 rt = INV ? make_float2(-t3.y, t3.x) : make_float2(t3.y, -t3.x);   // +-i t3
+  y0 = cadd(t0, t2);
+  y2 = csub(t0, t2);
+  y1 = cadd(t1, rt);
+  y3 = csub(t1, rt);
+}
+
+// DFT of 8 points in place: the 4-point DFTs of the even and odd samples combined
+// with exp(-+2 pi i k / 8).
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+  constexpr float h = 0.70710678118654752f;             // sqrt(1/2)
+  dft4<INV>(v[0], v[2], v[4], v[6]);
+  dft4<INV>(v[1], v[3], v[5], v[7]);
+  float2 b1 = v[3], b2 = v[5], b3 = v[7];               // odd DFT's outputs 1, 2, 3
+  if (INV) {
+    b1 = make_float2(h * (b1.x - b1.y), h * (b1.x + b1.y));       // x exp(i pi / 4)
+    b2 = make_float2(-b2.y, b2.x);                                // x i
+    b3 = make_float2(-h * (b3.x + b3.y), h * (b3.x - b3.y));      // x exp(3 i pi / 4)
+  } else {
+    b1 = make_float2(h * (b1.x + b1.y), h * (b1.y - b1.x));       // x exp(-i pi / 4)
+    b2 = make_float2(b2.y, -b2.x);                                // x -i
+    b3 = make_float2(h * (b3.y - b3.x), -h * (b3.x + b3.y));      // x exp(-3 i pi / 4)
   }
-  if (ns < L) {                                           // one radix-2 pass, ns = L / 2
-    const int half = L >> 1;
-    const int lg = __ffs(half) - 1;
-    const int total = lines * half;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int l = t >> lg, j = t & (half - 1);
-      const float2* in = p + l * ls;
-      float2* out = q + l * ls;
-      const int k = j & (ns - 1);
-      float2 w = tw[ns - 1 + k];
-      if (inv) w.y = -w.y;
-      const float2 a0 = in[j * es];
-      const float2 b = cmul(in[(j + half) * es], w);
-      const int d = ((j - k) << 1) + k;
-      out[d * es] = cadd(a0, b);
-      out[(d + ns) * es] = csub(a0, b);
+  const float2 a0 = v[0], a1 = v[2], a2 = v[4], a3 = v[6], b0 = v[1];
+  v[0] = cadd(a0, b0);
+  v[4] = csub(a0, b0);
+  v[1] = cadd(a1, b1);
+  v[5] = csub(a1, b1);
+  v[2] = cadd(a2, b2);
+  v[6] = csub(a2, b2);
+  v[3] = cadd(a3, b3);
+  v[7] = csub(a3, b3);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2 (&v)[R]) {
+  if constexpr (R == 8) {
+    dft8<INV>(v);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+  } else {
+    const float2 a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  }
+}
+
+// One Stockham pass of radix R after sub-transforms of size ns over `lines` lines of
+// length L: butterfly j takes its inputs at j + r L / R, twiddles them by
+// exp(-+2 pi i r (j mod ns) / (R ns)) and writes output r at
+// (j - j mod ns) R + j mod ns + r ns. Element i of line l sits at slot
+// fsl(l * ls + i * es). Along rows (es = 1) consecutive threads take consecutive j;
+// along columns, consecutive lines.
+template <int R, bool INV>
+__device__ __forceinline__ void stockham_pass(const float2* __restrict__ in, float2* __restrict__ out, int L,
+                                              int lines, int ls, int es, int ns, const float2* __restrict__ tw) {
+  const int nb = L / R, lgb = __ffs(nb) - 1, lgl = __ffs(lines) - 1;
+  const int total = lines * nb;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int l, j;
+    if (es == 1) {
+      l = t >> lgb;
+      j = t & (nb - 1);
+    } else {
+      j = t >> lgl;
+      l = t & (lines - 1);
     }
-    __syncthreads();
+    const int base = l * ls, k = j & (ns - 1);
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[fsl(base + (j + r * nb) * es)];
+    if (ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, r * k, R * ns, INV));
+    }
+    dft_r<R, INV>(v);
+    const int d = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[fsl(base + (d + r * ns) * es)] = v[r];
+  }
+  __syncthreads();
+}
+
+// Transforms `lines` lines of length L (a power of two >= 2; `lines` a power of two):
+// radix-8 Stockham passes, then one radix-4 or radix-2 pass for the rest; ping-pong
+// between p and q (fft_slots(...) each, padded slots), the result in the returned buffer.
+template <bool INV>
+__device__ float2* fft_lines(float2* p, float2* q, int L, int lines, int ls, int es, const float2* __restrict__ tw) {
+  int ns = 1;
+  for (; ns * 8 <= L; ns *= 8) {
+    stockham_pass<8, INV>(p, q, L, lines, ls, es, ns, tw);
+    float2* t = p;
+    p = q;
+    q = t;
+  }
+  if (ns < L) {
+    if (L / ns == 4) {
+      stockham_pass<4, INV>(p, q, L, lines, ls, es, ns, tw);
+    } else {
+      stockham_pass<2, INV>(p, q, L, lines, ls, es, ns, tw);
+    }
     float2* t = p;
     p = q;
     q = t;
@@ -325,10 +378,11 @@ template <bool POW2>
 __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftcc_small_kernel(FftccArgs a) {
   constexpr int NT = POW2 ? kSmallThreads : kSmallThreads / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = a.L, N = L * L;
-  float2* A = reinterpret_cast<float2*>(smem_raw);
-  float2* B = A + N;
-  float2* tws = B + N;                                   // L - 1 twiddles (power of two) or the L x L DFT matrix
+  const int L = a.L, N = L * L, NS = POW2 ? fft_slots(N) : N;
+  float2* A = reinterpret_cast<float2*>(smem_raw);      // element e at slot sl(e): padded for the FFT passes
+  float2* B = A + NS;
+  float2* tws = B + NS;                                  // L - 1 twiddles (power of two) or the L x L DFT matrix
+  auto sl = [](int e) { return POW2 ? fsl(e) : e; };
   __shared__ float s_red[2 * (kSmallThreads / 32)];
   __shared__ unsigned long long s_key[kSmallThreads / 32];
   const int tid = threadIdx.x;
@@ -363,7 +417,7 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
       const int y = e / L, x = e - y * L;
       const float f = load_gray<float>(a.ref, o.x + x, o.y + y);
       const float g = load_gray<float>(a.def, o.z + x, o.w + y);
-      A[e] = make_float2(f, g);
+      A[sl(e)] = make_float2(f, g);
       pf += f;
       pg += g;
       vf |= f != f00;
@@ -377,10 +431,10 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
     const float mf = sf / static_cast<float>(N), mg = sg / static_cast<float>(N);
     float pqf = 0.f, pqg = 0.f;
     for (int e = tid; e < N; e += NT) {
-      float2 v = A[e];
+      float2 v = A[sl(e)];
       v.x -= mf;
       v.y -= mg;
-      A[e] = v;
+      A[sl(e)] = v;
       pqf = fmaf(v.x, v.x, pqf);
       pqg = fmaf(v.y, v.y, pqg);
     }
@@ -389,9 +443,9 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
     float2* X;
     float2* Y;
     if (POW2) {
-      X = fft_lines(A, B, L, L, L, 1, tws, false);       // rows
+      X = fft_lines<false>(A, B, L, L, L, 1, tws);       // rows
       Y = X == A ? B : A;
-      X = fft_lines(X, Y, L, L, 1, L, tws, false);       // columns
+      X = fft_lines<false>(X, Y, L, L, 1, L, tws);       // columns
     } else {
       dft_matmul<true, false>(A, B, tws, L, L);
       dft_matmul<false, false>(B, A, tws, L, L);
@@ -401,14 +455,14 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
     for (int e = tid; e < N; e += NT) {
       const int ky = e / L, kx = e - ky * L;
       const int m = (ky == 0 ? 0 : L - ky) * L + (kx == 0 ? 0 : L - kx);
-      Y[e] = e == 0 ? make_float2(0.f, 0.f) : cross_power(X[e], X[m]);
+      Y[sl(e)] = e == 0 ? make_float2(0.f, 0.f) : cross_power(X[sl(e)], X[sl(m)]);
     }
     __syncthreads();
     float2* R;
     if (POW2) {
-      R = fft_lines(Y, X, L, L, L, 1, tws, true);
+      R = fft_lines<true>(Y, X, L, L, L, 1, tws);
       float2* S2 = R == A ? B : A;
-      R = fft_lines(R, S2, L, L, 1, L, tws, true);
+      R = fft_lines<true>(R, S2, L, L, 1, L, tws);
     } else {
       dft_matmul<true, true>(Y, X, tws, L, (L + 1) / 2);   // rows ky <= (L-1)/2 of the Hermitian half
       dft_inverse_columns_real(X, Y, tws, L);
@@ -416,7 +470,7 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
     }
     unsigned long long best = 0ull;
     for (int e = tid; e < N; e += NT) {
-      const unsigned long long k = peak_key(R[e].x, e);
+      const unsigned long long k = peak_key(R[sl(e)].x, e);
       best = k > best ? k : best;
     }
     best = block_max_key(best, s_key);
@@ -427,13 +481,13 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
       if (a.subpixel && !flat) {
         const int xm = kx == 0 ? L - 1 : kx - 1, xp = kx == L - 1 ? 0 : kx + 1;
         const int ym = ky == 0 ? L - 1 : ky - 1, yp = ky == L - 1 ? 0 : ky + 1;
-        const float r0 = R[e].x;
-        dx -= gauss3(R[ky * L + xm].x, r0, R[ky * L + xp].x);
-        dy -= gauss3(R[ym * L + kx].x, r0, R[yp * L + kx].x);
+        const float r0 = R[sl(e)].x;
+        dx -= gauss3(R[sl(ky * L + xm)].x, r0, R[sl(ky * L + xp)].x);
+        dy -= gauss3(R[sl(ym * L + kx)].x, r0, R[sl(yp * L + kx)].x);
       }
       a.u[w] = static_cast<float>(o.z - o.x) + dx;
       a.v[w] = static_cast<float>(o.w - o.y) + dy;
-      a.peak[w] = flat ? 0.f : R[e].x / (static_cast<float>(N) * sqrtf(qf) * sqrtf(qg));
+      a.peak[w] = flat ? 0.f : R[sl(e)].x / (static_cast<float>(N) * sqrtf(qf) * sqrtf(qg));
     }
     __syncthreads();                                     // the next window reuses the buffers
   }
@@ -872,8 +926,8 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_rows_fwd_kernel(FftccArgs 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.L;
   const int rows = kLineElems / L;                       // L >= 128: 1 .. 32 rows per block
-  float2* P = reinterpret_cast<float2*>(smem_raw);
-  float2* Q = P + kLineElems;
+  float2* P = reinterpret_cast<float2*>(smem_raw);      // element e at slot fsl(e)
+  float2* Q = P + fft_slots(kLineElems);
   const int64_t w = blockIdx.x;
   const int4 o = a.org[w];
   if (!window_ok(o, L, a.W, a.H)) return;                // uniform: the whole block
@@ -887,13 +941,13 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_rows_fwd_kernel(FftccArgs 
     const float g = load_gray<float>(a.def, o.z + x, o.w + y0 + r);
     vf |= f != f00;
     vg |= g != g00;
-    P[e] = make_float2(f, g);
+    P[fsl(e)] = make_float2(f, g);
   }
   if (__syncthreads_or(vf) && threadIdx.x == 0) atomicOr(&a.nonflat[2 * w], 1);
   if (__syncthreads_or(vg) && threadIdx.x == 0) atomicOr(&a.nonflat[2 * w + 1], 1);
-  const float2* R = fft_lines(P, Q, L, rows, L, 1, a.tw_pow2, false);
+  const float2* R = fft_lines<false>(P, Q, L, rows, L, 1, a.tw_pow2);
   float2* dst = a.work + w * static_cast<int64_t>(L) * L + static_cast<int64_t>(y0) * L;
-  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) dst[e] = R[e];
+  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) dst[e] = R[fsl(e)];
 }
 
 // In-place transpose of every L x L window: the block of tile (ti, tj), ti <= tj,
@@ -928,8 +982,8 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
   const int L = a.L;
   const int units = L <= kLineElems / 2 ? kLineElems / 2 / L : 1;   // 2 lines each: 4096 elements (8192 at L = 4096)
   const int lines = 2 * units;
-  float2* P = reinterpret_cast<float2*>(smem_raw);
-  float2* Q = P + lines * L;
+  float2* P = reinterpret_cast<float2*>(smem_raw);      // element e at slot fsl(e)
+  float2* Q = P + fft_slots(lines * L);
   __shared__ float s_red[2 * (kLineThreads / 32)];
   const int64_t w = blockIdx.x;
   if (!window_ok(a.org[w], L, a.W, a.H)) return;
@@ -944,10 +998,10 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
       const int row = (line & 1) ? (L - u) & (L - 1) : u;
       v = base[static_cast<int64_t>(row) * L + y];
     }
-    P[e] = v;
+    P[fsl(e)] = v;
   }
   __syncthreads();
-  float2* X = fft_lines(P, Q, L, lines, L, 1, a.tw_pow2, false);
+  float2* X = fft_lines<false>(P, Q, L, lines, L, 1, a.tw_pow2);
   float2* Y = X == P ? Q : P;
   float pnf = 0.f, png = 0.f;                             // FP32 per block, FP64 across blocks
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
@@ -955,9 +1009,9 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
     const int u = u0 + (line >> 1);
     const int mline = line ^ 1;                          // the mirror row's line
     const int mky = ky == 0 ? 0 : L - ky;
-    const float2 zk = X[e], zm = X[mline * L + mky];
+    const float2 zk = X[fsl(e)], zm = X[fsl(mline * L + mky)];
     const bool dc = u == 0 && ky == 0;
-    Y[e] = dc ? make_float2(0.f, 0.f) : cross_power(zk, zm);
+    Y[fsl(e)] = dc ? make_float2(0.f, 0.f) : cross_power(zk, zm);
     // each frequency once: line 0 of the unit, and line 1 only when its row differs
     const bool count = u < nunits && !dc && ((line & 1) == 0 || (u != 0 && 2 * u != L));
     if (count) {
@@ -973,14 +1027,14 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
     atomicAdd(&a.norms[2 * w], static_cast<double>(nf));
     atomicAdd(&a.norms[2 * w + 1], static_cast<double>(ng));
   }
-  float2* R = fft_lines(Y, X, L, lines, L, 1, a.tw_pow2, true);
+  float2* R = fft_lines<true>(Y, X, L, lines, L, 1, a.tw_pow2);
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
     const int line = e / L, y = e - line * L;
     const int u = u0 + (line >> 1);
     if (u >= nunits) continue;
     if ((line & 1) && (u == 0 || 2 * u == L)) continue;   // a self-paired row is written once
     const int row = (line & 1) ? (L - u) & (L - 1) : u;
-    base[static_cast<int64_t>(row) * L + y] = R[e];
+    base[static_cast<int64_t>(row) * L + y] = R[fsl(e)];
   }
 }
 
@@ -989,19 +1043,19 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_rows_inv_kernel(FftccArgs 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.L;
   const int rows = kLineElems / L;
-  float2* P = reinterpret_cast<float2*>(smem_raw);
-  float2* Q = P + kLineElems;
+  float2* P = reinterpret_cast<float2*>(smem_raw);      // element e at slot fsl(e)
+  float2* Q = P + fft_slots(kLineElems);
   __shared__ unsigned long long s_key[kLineThreads / 32];
   const int64_t w = blockIdx.x;
   if (!window_ok(a.org[w], L, a.W, a.H)) return;
   const int y0 = blockIdx.y * rows;
   const float2* src = a.work + w * static_cast<int64_t>(L) * L + static_cast<int64_t>(y0) * L;
-  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) P[e] = src[e];
+  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) P[fsl(e)] = src[e];
   __syncthreads();
-  const float2* R = fft_lines(P, Q, L, rows, L, 1, a.tw_pow2, true);
+  const float2* R = fft_lines<true>(P, Q, L, rows, L, 1, a.tw_pow2);
   unsigned long long best = 0ull;
   for (int e = threadIdx.x; e < rows * L; e += kLineThreads) {
-    const unsigned long long k = peak_key(R[e].x, y0 * L + e);
+    const unsigned long long k = peak_key(R[fsl(e)].x, y0 * L + e);
     best = k > best ? k : best;
   }
   best = block_max_key(best, s_key);
@@ -1170,7 +1224,8 @@ __global__ void fft_status_kernel(const uint8_t* roi_ok, uint8_t* status, int64_
 }
 
 size_t small_smem(int L, bool pow2) {
-  return sizeof(float2) * (2 * static_cast<size_t>(L) * L + (pow2 ? L - 1 : static_cast<size_t>(L) * L));
+  if (pow2) return sizeof(float2) * (2 * static_cast<size_t>(fft_slots(L * L)) + L - 1);
+  return sizeof(float2) * 3 * static_cast<size_t>(L) * L;
 }
 
 int blocks_for(int64_t n, int per_sm) {
@@ -1228,7 +1283,9 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          static_cast<int>(small_smem(kFftSmallMax, true)));
       if (ok != cudaSuccess) return ok;
-      const int per_sm = static_cast<int>(200 * 1024 / smem) < 8 ? static_cast<int>(200 * 1024 / smem) : 8;
+      // blocks per SM within 224 KB of shared memory (1 KB reserved per block)
+      const int fit = static_cast<int>(224 * 1024 / (smem + 1024));
+      const int per_sm = fit < 8 ? fit : 8;
       fftcc_small_kernel<true><<<blocks_for(a.n, per_sm > 0 ? per_sm : 1), kSmallThreads, smem, s>>>(a);
     } else {
       static const cudaError_t ok = cudaFuncSetAttribute(fftcc_small_kernel<false>,
@@ -1243,13 +1300,13 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
   // large windows: a power of two in [128, 4096] (checked by the caller)
   static const cudaError_t ok1 = cudaFuncSetAttribute(fftcc_rows_fwd_kernel,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      static_cast<int>(2 * kLineElems * sizeof(float2)));
+                                                      static_cast<int>(2 * fft_slots(kLineElems) * sizeof(float2)));
   static const cudaError_t ok2 = cudaFuncSetAttribute(fftcc_pairs_kernel,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      static_cast<int>(4 * kLineElems * sizeof(float2)));
+                                                      static_cast<int>(2 * fft_slots(2 * kLineElems) * sizeof(float2)));
   static const cudaError_t ok3 = cudaFuncSetAttribute(fftcc_rows_inv_kernel,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      static_cast<int>(2 * kLineElems * sizeof(float2)));
+                                                      static_cast<int>(2 * fft_slots(kLineElems) * sizeof(float2)));
   if (ok1 != cudaSuccess) return ok1;
   if (ok2 != cudaSuccess) return ok2;
   if (ok3 != cudaSuccess) return ok3;
@@ -1259,13 +1316,13 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
   if ((e = cudaMemsetAsync(a.keys, 0, sizeof(unsigned long long) * a.n, s)) != cudaSuccess) return e;
   const unsigned nw = static_cast<unsigned>(a.n);
   const int rows = kLineElems / L;
-  const size_t line_smem = 2 * kLineElems * sizeof(float2);
+  const size_t line_smem = 2 * fft_slots(kLineElems) * sizeof(float2);
   fftcc_rows_fwd_kernel<<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
   const int T = L / kTransposeTile;
   fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
   const int units = L <= kLineElems / 2 ? kLineElems / 2 / L : 1;
   const int nunits = L / 2 + 1;
-  const size_t pair_smem = 2 * sizeof(float2) * 2 * units * L;
+  const size_t pair_smem = 2 * sizeof(float2) * fft_slots(2 * units * L);
   fftcc_pairs_kernel<<<dim3(nw, (nunits + units - 1) / units), kLineThreads, pair_smem, s>>>(a);
   fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
   fftcc_rows_inv_kernel<<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
