@@ -185,8 +185,21 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ in, flo
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[fsl(base + (j + r * nb) * es)];
     if (ns > 1) {
+      if constexpr (R == 8) {   // w^1, w^2, w^4 from the table, the other powers as products
+        const float2 w1 = twiddle(tw, k, 8 * ns, INV), w2 = twiddle(tw, 2 * k, 8 * ns, INV),
+                     w4 = twiddle(tw, 4 * k, 8 * ns, INV);
+        const float2 w3 = cmul(w1, w2);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        v[4] = cmul(v[4], w4);
+        v[5] = cmul(v[5], cmul(w1, w4));
+        v[6] = cmul(v[6], cmul(w2, w4));
+        v[7] = cmul(v[7], cmul(w3, w4));
+      } else {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, r * k, R * ns, INV));
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, r * k, R * ns, INV));
+      }
     }
     dft_r<R, INV>(v);
     const int d = (j - k) * R + k;
@@ -383,6 +396,8 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
   float2* B = A + NS;
   float2* tws = B + NS;                                  // L - 1 twiddles (power of two) or the L x L DFT matrix
   auto sl = [](int e) { return POW2 ? fsl(e) : e; };
+  const int lg = __ffs(L) - 1;                           // POW2: e / L = e >> lg
+  auto row_of = [&](int e) { return POW2 ? e >> lg : e / L; };
   __shared__ float s_red[2 * (kSmallThreads / 32)];
   __shared__ unsigned long long s_key[kSmallThreads / 32];
   const int tid = threadIdx.x;
@@ -414,7 +429,7 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
     const float f00 = load_gray<float>(a.ref, o.x, o.y), g00 = load_gray<float>(a.def, o.z, o.w);
     bool vf = false, vg = false;                         // a value differs from the first
     for (int e = tid; e < N; e += NT) {
-      const int y = e / L, x = e - y * L;
+      const int y = row_of(e), x = e - y * L;
       const float f = load_gray<float>(a.ref, o.x + x, o.y + y);
       const float g = load_gray<float>(a.def, o.z + x, o.w + y);
       A[sl(e)] = make_float2(f, g);
@@ -453,7 +468,7 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
     }
     Y = X == A ? B : A;
     for (int e = tid; e < N; e += NT) {
-      const int ky = e / L, kx = e - ky * L;
+      const int ky = row_of(e), kx = e - ky * L;
       const int m = (ky == 0 ? 0 : L - ky) * L + (kx == 0 ? 0 : L - kx);
       Y[sl(e)] = e == 0 ? make_float2(0.f, 0.f) : cross_power(X[sl(e)], X[sl(m)]);
     }
@@ -476,7 +491,7 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
     best = block_max_key(best, s_key);
     if (tid == 0) {
       const int e = flat ? 0 : key_index(best);
-      const int ky = e / L, kx = e - ky * L;
+      const int ky = row_of(e), kx = e - ky * L;
       float dx = static_cast<float>(shift_of_peak(kx, L)), dy = static_cast<float>(shift_of_peak(ky, L));
       if (a.subpixel && !flat) {
         const int xm = kx == 0 ? L - 1 : kx - 1, xp = kx == L - 1 ? 0 : kx + 1;
@@ -920,9 +935,44 @@ size_t tc_smem() {
 }
 
 // ---------------------------------------------------------------- large windows
+// Gray levels of elements e = threadIdx.x + i kLineThreads of the block's rows of a
+// window (row e / L, column e mod L from (x0, y0)), all loads issued before use.
+template <typename G>
+__device__ __forceinline__ void line_grays_t(const GrayPlane& pl, int x0, int y0, int L,
+                                             float (&v)[kLineElems / kLineThreads]) {
+  const char* base = static_cast<const char*>(pl.data) + static_cast<int64_t>(y0) * pl.stride +
+                     static_cast<int64_t>(x0) * sizeof(G);
+  const int lg = __ffs(L) - 1;
+#pragma unroll
+  for (int i = 0; i < kLineElems / kLineThreads; ++i) {
+    const int e = threadIdx.x + i * kLineThreads;
+    v[i] = gray_at<G>(base + static_cast<int64_t>(e >> lg) * pl.stride + static_cast<int64_t>(e & (L - 1)) * sizeof(G));
+  }
+}
+
+__device__ __forceinline__ void line_grays(const GrayPlane& pl, int x0, int y0, int L,
+                                           float (&v)[kLineElems / kLineThreads]) {
+  switch (pl.dtype) {
+    case DIC_U8:
+      line_grays_t<uint8_t>(pl, x0, y0, L, v);
+      break;
+    case DIC_U16:
+      line_grays_t<uint16_t>(pl, x0, y0, L, v);
+      break;
+    case DIC_BF16:
+      line_grays_t<Bf16Bits>(pl, x0, y0, L, v);
+      break;
+    case DIC_F32:
+      line_grays_t<float>(pl, x0, y0, L, v);
+      break;
+    default:
+      line_grays_t<double>(pl, x0, y0, L, v);
+  }
+}
+
 // Rows of the packed windows, transformed along x: work[w][y][kx]. Also marks the
 // windows whose f or g is not constant (an exactly flat window correlates to 0).
-__global__ void __launch_bounds__(kLineThreads) fftcc_rows_fwd_kernel(FftccArgs a) {
+__global__ void __launch_bounds__(kLineThreads, 3) fftcc_rows_fwd_kernel(FftccArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.L;
   const int rows = kLineElems / L;                       // L >= 128: 1 .. 32 rows per block
@@ -935,13 +985,14 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_rows_fwd_kernel(FftccArgs 
   const float f00 = load_gray<float>(a.ref, o.x, o.y);
   const float g00 = load_gray<float>(a.def, o.z, o.w);
   bool vf = false, vg = false;
-  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) {
-    const int r = e / L, x = e - r * L;
-    const float f = load_gray<float>(a.ref, o.x + x, o.y + y0 + r);
-    const float g = load_gray<float>(a.def, o.z + x, o.w + y0 + r);
-    vf |= f != f00;
-    vg |= g != g00;
-    P[fsl(e)] = make_float2(f, g);
+  float fv[kLineElems / kLineThreads], gv[kLineElems / kLineThreads];
+  line_grays(a.ref, o.x, o.y + y0, L, fv);
+  line_grays(a.def, o.z, o.w + y0, L, gv);
+#pragma unroll
+  for (int i = 0; i < kLineElems / kLineThreads; ++i) {
+    vf |= fv[i] != f00;
+    vg |= gv[i] != g00;
+    P[fsl(threadIdx.x + i * kLineThreads)] = make_float2(fv[i], gv[i]);
   }
   if (__syncthreads_or(vf) && threadIdx.x == 0) atomicOr(&a.nonflat[2 * w], 1);
   if (__syncthreads_or(vg) && threadIdx.x == 0) atomicOr(&a.nonflat[2 * w + 1], 1);
@@ -977,11 +1028,11 @@ __global__ void __launch_bounds__(kTransposeTile * 8) fftcc_transpose_kernel(Fft
 // (u, L - u) (rows 0 and L/2 pair with themselves): FFT both along y, form the cross
 // power of each frequency with its mirror, accumulate the norms of F and G (zero
 // frequency excluded), transform back along y, write both rows back.
-__global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) {
+__global__ void __launch_bounds__(kLineThreads, 3) fftcc_pairs_kernel(FftccArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.L;
   const int units = L <= kLineElems / 2 ? kLineElems / 2 / L : 1;   // 2 lines each: 4096 elements (8192 at L = 4096)
-  const int lines = 2 * units;
+  const int lines = 2 * units, lg = __ffs(L) - 1;
   float2* P = reinterpret_cast<float2*>(smem_raw);      // element e at slot fsl(e)
   float2* Q = P + fft_slots(lines * L);
   __shared__ float s_red[2 * (kLineThreads / 32)];
@@ -991,7 +1042,7 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
   const int nunits = L / 2 + 1;
   float2* base = a.work + w * static_cast<int64_t>(L) * L;
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
-    const int line = e / L, y = e - line * L;
+    const int line = e >> lg, y = e & (L - 1);
     const int u = u0 + (line >> 1);
     float2 v = make_float2(0.f, 0.f);
     if (u < nunits) {
@@ -1005,7 +1056,7 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
   float2* Y = X == P ? Q : P;
   float pnf = 0.f, png = 0.f;                             // FP32 per block, FP64 across blocks
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
-    const int line = e / L, ky = e - line * L;
+    const int line = e >> lg, ky = e & (L - 1);
     const int u = u0 + (line >> 1);
     const int mline = line ^ 1;                          // the mirror row's line
     const int mky = ky == 0 ? 0 : L - ky;
@@ -1029,7 +1080,7 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
   }
   float2* R = fft_lines<true>(Y, X, L, lines, L, 1, a.tw_pow2);
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
-    const int line = e / L, y = e - line * L;
+    const int line = e >> lg, y = e & (L - 1);
     const int u = u0 + (line >> 1);
     if (u >= nunits) continue;
     if ((line & 1) && (u == 0 || 2 * u == L)) continue;   // a self-paired row is written once
@@ -1039,7 +1090,7 @@ __global__ void __launch_bounds__(kLineThreads) fftcc_pairs_kernel(FftccArgs a) 
 }
 
 // Inverse transform of the rows along kx and the per-window arg-max of R.
-__global__ void __launch_bounds__(kLineThreads) fftcc_rows_inv_kernel(FftccArgs a) {
+__global__ void __launch_bounds__(kLineThreads, 3) fftcc_rows_inv_kernel(FftccArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.L;
   const int rows = kLineElems / L;
