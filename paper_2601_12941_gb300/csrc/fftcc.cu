@@ -541,7 +541,7 @@ __device__ __forceinline__ uint32_t tf32_bits(float x) {
 
 // c += a b, m16n8k8, TF32 operands (bit patterns), FP32 accumulators
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
       "{%0, %1, %2, %3};"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -635,15 +635,23 @@ __device__ __forceinline__ void warp_gemm_w(const float* A, int sa, const uint4*
     uint32_t ah[MT][4], al[MT][4];
 #pragma unroll
     for (int m = 0; m < MT; ++m) a_frag_split(A, sa, 16 * m, 8 * ks, g, t, ah[m], al[m]);
+    // two column tiles at a time, the three partial products of a tile issued
+    // 2 MT products apart, so that no product waits on the one just before it
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const uint4 b = wf[(ks * 8 + j) * 32 + lane];
+    for (int j = 0; j < 8; j += 2) {
+      const uint4 b[2] = {wf[(ks * 8 + j) * 32 + lane], wf[(ks * 8 + j + 1) * 32 + lane]};
 #pragma unroll
-      for (int m = 0; m < MT; ++m) {
-        mma_tf32(acc[m][j], ah[m], b.x, b.y);
-        mma_tf32(acc[m][j], ah[m], b.z, b.w);
-        mma_tf32(acc[m][j], al[m], b.x, b.y);
-      }
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int m = 0; m < MT; ++m) mma_tf32(acc[m][j + h], ah[m], b[h].x, b[h].y);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int m = 0; m < MT; ++m) mma_tf32(acc[m][j + h], ah[m], b[h].z, b[h].w);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int m = 0; m < MT; ++m) mma_tf32(acc[m][j + h], al[m], b[h].x, b[h].y);
     }
   }
 }
@@ -856,18 +864,27 @@ __global__ void __launch_bounds__(kTcBlockThreads, 1) fftcc_tc_kernel(FftccArgs 
         al[mt][2] = l.z;
         al[mt][3] = l.w;
       }
+      uint32_t bh[4][2], bl[4][2];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float v0 = buf[(k0 + t) * kTcSW + 8 * j + g], v1 = buf[(k0 + t + 4) * kTcSW + 8 * j + g];
-        const uint32_t h0 = tf32_bits(v0), h1 = tf32_bits(v1);
-        const uint32_t l0 = tf32_bits(v0 - __uint_as_float(h0)), l1 = tf32_bits(v1 - __uint_as_float(h1));
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          mma_tf32(acc[mt][j], ah[mt], h0, h1);
-          mma_tf32(acc[mt][j], ah[mt], l0, l1);
-          mma_tf32(acc[mt][j], al[mt], h0, h1);
-        }
+        bh[j][0] = tf32_bits(v0);
+        bh[j][1] = tf32_bits(v1);
+        bl[j][0] = tf32_bits(v0 - __uint_as_float(bh[j][0]));
+        bl[j][1] = tf32_bits(v1 - __uint_as_float(bh[j][1]));
       }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) mma_tf32(acc[mt][j], ah[mt], bh[j][0], bh[j][1]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) mma_tf32(acc[mt][j], ah[mt], bl[j][0], bl[j][1]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) mma_tf32(acc[mt][j], al[mt], bh[j][0], bh[j][1]);
     }
     if (nyquist) {                                       // R[y][x] += T16[x] (-1)^y
 #pragma unroll
