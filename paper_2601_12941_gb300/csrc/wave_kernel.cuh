@@ -1334,6 +1334,15 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
       for (int j = 0; j <= M2; ++j) A[0][j] = A[1][j] = A[2][j] = T(0);
 #pragma unroll
       for (int j = 0; j <= D; ++j) Bf[0][j] = Bf[1][j] = Bs[0][j] = Bs[1][j] = T(0);
+      // PACKM: the fx and fy terms of a moment summed as one packed pair,
+      // A02[j] = (A[0][j], A[2][j]), Bf2[j] = (Bf[0][j], Bf[1][j]), Bs2[j] = (Bs[0][j], Bs[1][j])
+      // (128-thread FP32 blocks of up to 6 parameters, where the registers allow it)
+      constexpr bool PACKM = NT == 128 && NP <= 6 && sizeof(T) == 4;
+      Pair<T> A02[M2 + 1], Bf2[D + 1], Bs2[D + 1];
+#pragma unroll
+      for (int j = 0; j <= M2; ++j) A02[j] = pair(T(0), T(0));
+#pragma unroll
+      for (int j = 0; j <= D; ++j) Bf2[j] = Bs2[j] = pair(T(0), T(0));
       // the column walk keeps the three coefficient rows around the pixel in
       // registers: each row loads only the row below
       T m0 = T(0), m1 = T(0), m2 = T(0), z0 = T(0), z2 = T(0);
@@ -1403,20 +1412,55 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
 #pragma unroll
         for (int j = 1; j <= M2; ++j) dyp[j] = dyp[j - 1] * dyv;
         dyv += T(1);
-        const T wxx = fx * fx, wxy = fx * fy, wyy = fy * fy;
+        if constexpr (PACKM) {
+          const Pair<T> fg = pair(fx, fy);
+          const Pair<T> w2 = pmul(fg, fg);                // (fx^2, fy^2)
+          const Pair<T> fb = pmul(fg, pair(fp, fp));      // (fx f', fy f')
+          const T wxy = fx * fy;
+          A02[0] = padd(A02[0], w2);
+          A[1][0] += wxy;
+#pragma unroll
+          for (int j = 1; j <= M2; ++j) {
+            A02[j] = pfma(w2, pair(dyp[j], dyp[j]), A02[j]);
+            A[1][j] += wxy * dyp[j];
+          }
+          Bf2[0] = padd(Bf2[0], fb);
+          Bs2[0] = padd(Bs2[0], fg);
+#pragma unroll
+          for (int j = 1; j <= D; ++j) {
+            Bf2[j] = pfma(fb, pair(dyp[j], dyp[j]), Bf2[j]);
+            Bs2[j] = pfma(fg, pair(dyp[j], dyp[j]), Bs2[j]);
+          }
+        } else {
+          const T wxx = fx * fx, wxy = fx * fy, wyy = fy * fy;
+#pragma unroll
+          for (int j = 0; j <= M2; ++j) {
+            A[0][j] += wxx * dyp[j];
+            A[1][j] += wxy * dyp[j];
+            A[2][j] += wyy * dyp[j];
+          }
+          const T fxb = fx * fp, fyb = fy * fp;
+#pragma unroll
+          for (int j = 0; j <= D; ++j) {
+            Bf[0][j] += fxb * dyp[j];
+            Bf[1][j] += fyb * dyp[j];
+            Bs[0][j] += fx * dyp[j];
+            Bs[1][j] += fy * dyp[j];
+          }
+        }
+      }
+      if constexpr (PACKM) {
 #pragma unroll
         for (int j = 0; j <= M2; ++j) {
-          A[0][j] += wxx * dyp[j];
-          A[1][j] += wxy * dyp[j];
-          A[2][j] += wyy * dyp[j];
+          A[0][j] = A02[j].x;
+          A[2][j] = A02[j].y;
         }
-        const T fxb = fx * fp, fyb = fy * fp;
 #pragma unroll
         for (int j = 0; j <= D; ++j) {
-          Bf[0][j] += fxb * dyp[j];
-          Bf[1][j] += fyb * dyp[j];
-          Bs[0][j] += fx * dyp[j];
-          Bs[1][j] += fy * dyp[j];
+          Bf[0][j] = Bf2[j].x;
+          Bf[1][j] = Bf2[j].y;
+          Bs[0][j] = Bs2[j].x;
+          Bs[1][j] = Bs2[j].y;
         }
       }
 #pragma unroll
