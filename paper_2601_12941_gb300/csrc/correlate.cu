@@ -125,8 +125,8 @@ template <typename T>
 WaveTiles wave_tiles(int S, int gray_dtype) {
   WaveTiles t{};
   const int xalign = 16 / static_cast<int>(sizeof(T));
-  t.bxc = ((S + 12 + xalign - 1) / xalign) * xalign;
-  t.byc = S + 9;
+  t.bxc = ((S + 8 + xalign - 1) / xalign) * xalign;
+  t.byc = S + 7;
   static const int es_of[5] = {1, 2, 2, 4, 8};
   t.gray_es = es_of[gray_dtype];
   const int galign = 16 / t.gray_es;
@@ -137,8 +137,12 @@ WaveTiles wave_tiles(int S, int gray_dtype) {
   t.off_fg = 0;
   t.off_f = al(2 * SS * static_cast<int>(sizeof(T)));
   t.off_win = al(t.off_f + SS * static_cast<int>(sizeof(T)));
-  t.off_gray = al(t.off_win + t.bxc * t.byc * static_cast<int>(sizeof(T)));
-  t.smem_bytes = al(t.off_gray + t.bxg * S * t.gray_es);
+  const int win_end = al(t.off_win + t.bxc * t.byc * static_cast<int>(sizeof(T)));
+  // the gray tile is read only before the gradients are written: it shares their
+  // region when it fits
+  t.gray_alias = t.bxg * S * t.gray_es <= 2 * SS * static_cast<int>(sizeof(T));
+  t.off_gray = t.gray_alias ? t.off_fg : win_end;
+  t.smem_bytes = t.gray_alias ? win_end : al(win_end + t.bxg * S * t.gray_es);
   return t;
 }
 

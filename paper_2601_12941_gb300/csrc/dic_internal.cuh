@@ -249,6 +249,7 @@ struct WaveTiles {
   int bxg, gray_es;
   int coef_tma, gray_tma;    // 1: tiles arrive by TMA; 0: cooperative copies
   int off_fg, off_f, off_win, off_gray;
+  int gray_alias;            // 1: the gray tile lies in the gradient region
   int smem_bytes;
 };
 

@@ -1100,7 +1100,7 @@ __device__ __noinline__ void sample_column_global(const T* __restrict__ base, in
 template <typename T, int NT>
 struct WaveOccupancy;
 template <>
-struct WaveOccupancy<float, 128> { static constexpr int kBlocks = 6; };
+struct WaveOccupancy<float, 128> { static constexpr int kBlocks = 7; };   // 72 registers (12 parameters: 6, below)
 template <>
 struct WaveOccupancy<float, 64> { static constexpr int kBlocks = 14; };
 template <>
@@ -1110,8 +1110,16 @@ struct WaveOccupancy<double, 64> { static constexpr int kBlocks = 8; };
 
 // MODE 0: Gauss-Newton, ZNSSD only (the default, leanest); 1: Gauss-Newton, any cost;
 // 2: Levenberg-Marquardt, any cost
+// Resident blocks the registers are sized for: the quadratic FP32 kernel keeps 6
+// blocks of 128 threads (at 7 its register cap costs more in spills than the extra
+// block gains)
+template <typename T, int NP, int NT>
+constexpr int wave_min_blocks() {
+  return (sizeof(T) == 4 && NT == 128 && NP == 12) ? 6 : WaveOccupancy<T, NT>::kBlocks;
+}
+
 template <typename T, int NP, int NT, int MODE>
-__global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
+__global__ void __launch_bounds__(NT, wave_min_blocks<T, NP, NT>())
     wave_kernel(WaveArgs<T> a, const __grid_constant__ CUtensorMap tm_cref,
                 const __grid_constant__ CUtensorMap tm_cdef, const __grid_constant__ CUtensorMap tm_gray) {
   using C = T;  // working precision of the per-point control arithmetic
@@ -1381,6 +1389,7 @@ __global__ void __launch_bounds__(NT, WaveOccupancy<T, NT>::kBlocks)
             break;
         }
       }
+      if (tl.gray_alias) __syncthreads();   // every gray level read before the gradients overwrite them
       T dyv = static_cast<T>(row0 - r);   // dy of the row, counted in T (exact)
       for (int row = row0; row < row1; ++row) {
         const int pix = row * S + col;
