@@ -163,35 +163,41 @@ __device__ void strain_from_gradient(int measure, float h11, float h12, float h2
   spectral(d11, d12, d22, m, 1.0f / (r1 + r2), e);
 }
 
-constexpr int kTileX = 32, kTileY = 8;   // grid points per block (one per thread)
+constexpr int kTileX = 32, kTileY = 16;   // grid points per block (one per thread; a warp per tile row)
+// staged points per thread for a half-window h: kernels for h <= 4 (2 each) and for
+// h <= 15, the largest window (6 each)
+constexpr int staged_per_thread(int h) {
+  return ((kTileX + 2 * h) * (kTileY + 2 * h) + kTileX * kTileY - 1) / (kTileX * kTileY);
+}
+constexpr int kSmallHalf = 4, kMaxHalf = 15;
 
 // Block of kTileX x kTileY grid points. The block stages the displacements of its
 // points and of a halo of h = (window - 1) / 2 points as FP32 offsets from one
-// accepted point of the tile (points outside the grid or not accepted become NaN),
-// then applies the full-window slope filter separably: along each staged row the
-// sums sum_i i d, sum_i d and sum_i i^2 d over the window's columns, then down each
-// point's column the x slope sum_j (a + b j^2) (sum_i i d)_j and the y slope
-// sum_j j (a (sum_i d)_j + b (sum_i i^2 d)_j). A NaN anywhere in a window reaches
-// its sums (even through a zero weight), which sends the point to the general fit.
-__global__ void __launch_bounds__(kTileX * kTileY, 4) strain_kernel(StrainArgs a) {
+// accepted point of the tile, the first in row-major order (points outside the grid
+// or not accepted become NaN), then applies the full-window slope filter separably:
+// along each staged row the sums sum_i i d, sum_i d and sum_i i^2 d over the window's
+// columns, then down each point's column the x slope sum_j (a + b j^2) (sum_i i d)_j
+// and the y slope sum_j j (a (sum_i d)_j + b (sum_i i^2 d)_j). A NaN anywhere in a
+// window reaches its sums (even through a zero weight), which sends the point to the
+// general fit. Every load of a thread is issued before the first barrier; the
+// reference point comes from one ballot per warp; three barriers in all.
+template <int kStagedPerThread>
+__global__ void __launch_bounds__(kTileX * kTileY, 2) strain_kernel(StrainArgs a) {
   extern __shared__ __align__(16) float sm[];
   const int h = (a.window - 1) / 2, N = a.window;
-  const int SX = kTileX + 2 * h, SY = kTileY + 2 * h;
+  const int SX = kTileX + 2 * h, SY = kTileY + 2 * h, NS = SX * SY;
   float* su = sm;                 // [SY][SX] staged offsets of u
-  float* sv = su + SY * SX;       // ... of v
-  float* fx = sv + SY * SX;       // [2][SY][kTileX] row sums: sum i d   (u, v)
+  float* sv = su + NS;            // ... of v
+  float* fx = sv + NS;            // [2][SY][kTileX] row sums: sum i d   (u, v)
   float* f0 = fx + 2 * SY * kTileX;   // sum d
   float* f2 = f0 + 2 * SY * kTileX;   // sum i^2 d
-  __shared__ float s_ref[2];
-  __shared__ int s_first;
-  const int tid = threadIdx.x;
+  __shared__ int s_first[kTileY];     // per tile row: lane of its first accepted point, or 32
+  __shared__ float2 s_ref[kTileY];    // ... and that point's (u, v) in FP32
+  const int tid = threadIdx.x, tx = tid & (kTileX - 1), ty = tid / kTileX;
   const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
-  const int tx = tid % kTileX, ty = tid / kTileX;
   const int ic = x0 + tx, jc = y0 + ty;
   const bool inside = ic < a.nx && jc < a.ny;
   const int64_t q = static_cast<int64_t>(jc) * a.nx + ic;
-  // the thread's own point; the tile's first accepted point is the reference of the
-  // staged offsets (which keeps them small)
   uint8_t st_c = 1;
   double uc = 0.0, vc = 0.0;
   if (inside) {
@@ -199,41 +205,54 @@ __global__ void __launch_bounds__(kTileX * kTileY, 4) strain_kernel(StrainArgs a
     uc = a.u[q];
     vc = a.v[q];
   }
-  if (tid == 0) s_first = kTileX * kTileY;
-  __syncthreads();
-  if (inside && st_c == 0) atomicMin(&s_first, tid);
-  __syncthreads();
-  if (tid == s_first) {
-    s_ref[0] = static_cast<float>(uc);
-    s_ref[1] = static_cast<float>(vc);
+  // the staged points of this thread: status and displacements, loaded now
+  uint8_t sst[kStagedPerThread];
+  double suq[kStagedPerThread], svq[kStagedPerThread];
+#pragma unroll
+  for (int k = 0; k < kStagedPerThread; ++k) {
+    const int e = tid + k * kTileX * kTileY;
+    sst[k] = 1;
+    suq[k] = svq[k] = 0.0;
+    if (e < NS) {
+      const int i = x0 - h + e % SX, j = y0 - h + e / SX;
+      if (i >= 0 && i < a.nx && j >= 0 && j < a.ny) {
+        const int64_t qs = static_cast<int64_t>(j) * a.nx + i;
+        sst[k] = a.status[qs];
+        suq[k] = a.u[qs];
+        svq[k] = a.v[qs];
+      }
+    }
   }
-  if (s_first == kTileX * kTileY && tid == 0) s_ref[0] = s_ref[1] = 0.0f;
+  // the tile's reference: the first accepted point in row-major order
+  const unsigned acc = __ballot_sync(0xffffffffu, inside && st_c == 0);
+  const int first = acc ? __ffs(acc) - 1 : kTileX;
+  if (tx == 0) s_first[ty] = first;
+  if (tx == first) s_ref[ty] = make_float2(static_cast<float>(uc), static_cast<float>(vc));
   __syncthreads();
+  float2 ref = make_float2(0.0f, 0.0f);
+  for (int r = 0; r < kTileY; ++r) {
+    if (s_first[r] < kTileX) {
+      ref = s_ref[r];
+      break;
+    }
+  }
   // offsets are formed in FP32 after one conversion per value (FP64 arithmetic runs at a
   // small fraction of the FP32 rate here); exact when the displacements are FP32 values,
   // as the mixed path produces them
-  const float ur = s_ref[0], vr = s_ref[1];
   const float nan_ = __int_as_float(0x7fc00000);
-  for (int e = tid; e < SY * SX; e += blockDim.x) {
-    const int i = x0 - h + e % SX, j = y0 - h + e / SX;
-    float du = nan_, dv = nan_;
-    if (i >= 0 && i < a.nx && j >= 0 && j < a.ny) {
-      // the three loads are issued together; status then selects
-      const int64_t q = static_cast<int64_t>(j) * a.nx + i;
-      const uint8_t st = a.status[q];
-      const double uq = a.u[q], vq = a.v[q];
-      if (st == 0) {
-        du = static_cast<float>(uq) - ur;
-        dv = static_cast<float>(vq) - vr;
-      }
+#pragma unroll
+  for (int k = 0; k < kStagedPerThread; ++k) {
+    const int e = tid + k * kTileX * kTileY;
+    if (e < NS) {
+      const bool ok = sst[k] == 0;
+      su[e] = ok ? static_cast<float>(suq[k]) - ref.x : nan_;
+      sv[e] = ok ? static_cast<float>(svq[k]) - ref.y : nan_;
     }
-    su[e] = du;
-    sv[e] = dv;
   }
   __syncthreads();
   for (int e = tid; e < 2 * SY * kTileX; e += blockDim.x) {
-    const int comp = e / (SY * kTileX), rc = e % (SY * kTileX);
-    const int row = rc / kTileX, c = rc % kTileX;
+    const int comp = e >= SY * kTileX, rc = e - comp * SY * kTileX;
+    const int row = rc / kTileX, c = rc & (kTileX - 1);
     const float* src = (comp == 0 ? su : sv) + row * SX + c;   // window columns c .. c + 2h
     float sx = 0.0f, s0 = 0.0f, s2 = 0.0f;
     for (int k = 0; k < N; ++k) {
@@ -296,12 +315,16 @@ cudaError_t launch_strain(const StrainArgs& a, cudaStream_t s) {
   const int h = (a.window - 1) / 2;
   const int SX = kTileX + 2 * h, SY = kTileY + 2 * h;
   const size_t smem = sizeof(float) * (2 * static_cast<size_t>(SY) * SX + 6 * static_cast<size_t>(SY) * kTileX);
-  // the largest window (31) needs about 48 KB; the limit is raised once (thread-safe)
-  static const cudaError_t configured =
-      cudaFuncSetAttribute(strain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-  if (configured != cudaSuccess) return configured;
   dim3 grid((a.nx + kTileX - 1) / kTileX, (a.ny + kTileY - 1) / kTileY);
-  strain_kernel<<<grid, kTileX * kTileY, smem, s>>>(a);
+  if (h <= kSmallHalf) {
+    strain_kernel<staged_per_thread(kSmallHalf)><<<grid, kTileX * kTileY, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  // the largest window (31) needs about 58 KB; the limit is raised once (thread-safe)
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      strain_kernel<staged_per_thread(kMaxHalf)>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+  if (configured != cudaSuccess) return configured;
+  strain_kernel<staged_per_thread(kMaxHalf)><<<grid, kTileX * kTileY, smem, s>>>(a);
   return cudaGetLastError();
 }
 

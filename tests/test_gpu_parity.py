@@ -154,6 +154,23 @@ def test_rigid_matches_oracle(pkg, precision):
     compare(gpu, ora, W, H, 15, precision=precision)
 
 
+@pytest.mark.parametrize("S", [41, 21])
+@pytest.mark.parametrize("dtype", ["u16", "f32", "f64"])
+def test_gray_types_at_both_block_sizes_match_oracle(pkg, dtype, S):
+    """Gray levels of each element type through the 128-thread kernel (subset 41: the
+    u16 and f32 gray tiles share the gradient region, the f64 tile has its own) and the
+    64-thread kernel (subset 21)."""
+    W, H = 170, 150
+    gray = 4095.0 if dtype == "u16" else 255.0
+    fld = synth.affine_field(W, H, u0=1.3, v0=-0.8, exx=1.5e-3, eyy=-1e-3, exy=4e-4)
+    ref, dfm = _pair(W, H, fld, dtype=dtype, gray=gray, noise=0.01 * gray)
+    prm = dict(ORACLE_PARAMS, search_radius=4)
+    seeds = [(W // 2, H // 2)]
+    ora = oracle.correlate(ref, dfm, None, S, 7, "affine", seeds, prm)
+    gpu = _run(pkg, ref, dfm, None, S, 7, "affine", seeds, "mixed", search_radius=4)
+    compare(gpu, ora, W, H, S)
+
+
 def test_roi_hole_two_seeds_and_out_of_roi_seed(pkg):
     W, H = 180, 160
     fld = synth.affine_field(W, H, u0=1.6, v0=-2.2, exx=2e-3, eyy=-1e-3, exy=5e-4, eyx=5e-4)
