@@ -21,8 +21,6 @@ namespace {
 
 constexpr float kMinScaledPivot = 1e-5f;
 
-__device__ __forceinline__ int basis_terms(int basis) { return basis == DIC_STRAIN_BILINEAR ? 3 : 8; }
-
 // P(x, y) for the basis (Eq. 9, as printed)
 __device__ __forceinline__ void basis_row(int basis, float x, float y, float* P) {
   P[0] = 1.0f;
@@ -38,68 +36,82 @@ __device__ __forceinline__ void basis_row(int basis, float x, float y, float* P)
 }
 
 // General least squares over the valid points of the window (out of line: windows with
-// missing points are the rare case): returns false when the
-// design is not well posed; else the x and y slopes (grid units) of u and v.
-__device__ __noinline__ bool fit_window(const StrainArgs& a, int ic, int jc, double uc, double vc, float* g) {
-  const int K = basis_terms(a.basis);
-  const int h = (a.window - 1) / 2;
-  float M[8][8], ru[8], rv[8];
+// missing points are the rare case) for a basis of K terms: returns false when the
+// design is not well posed; else the x and y slopes (grid units) of u and v. Which
+// points are present comes from the block's staged offsets su (row pitch SX; NaN where
+// a point is missing or outside the grid; centre at slot ec); the offsets from the
+// centre are formed in FP64 from the staged displacements ud, vd and rounded once.
+// Normal equations with
+// unit-diagonal scaling, then elimination without exchanges, indexed at compile time
+// (K fixed) so that the matrix lives in registers.
+template <int K>
+__device__ __noinline__ bool fit_window(const StrainArgs& a, int h, const float* su, const double* ud,
+                                        const double* vd, int SX, int ec, double uc, double vc, float* g) {
+  float M[K][K], ru[K], rv[K];
+#pragma unroll
   for (int r = 0; r < K; ++r) {
     ru[r] = rv[r] = 0.0f;
+#pragma unroll
     for (int c = 0; c < K; ++c) M[r][c] = 0.0f;
   }
   int count = 0;
   for (int dj = -h; dj <= h; ++dj) {
-    const int j = jc + dj;
-    if (j < 0 || j >= a.ny) continue;
     for (int di = -h; di <= h; ++di) {
-      const int i = ic + di;
-      if (i < 0 || i >= a.nx) continue;
-      const int64_t q = static_cast<int64_t>(j) * a.nx + i;
-      if (a.status[q] != 0) continue;
+      const int e = ec + dj * SX + di;
+      if (su[e] != su[e]) continue;                  // missing: not accepted, or outside the grid
       float P[8];
       basis_row(a.basis, static_cast<float>(di), static_cast<float>(dj), P);
-      const float du = static_cast<float>(a.u[q] - uc), dv = static_cast<float>(a.v[q] - vc);
+      const float du = static_cast<float>(ud[e] - uc), dv = static_cast<float>(vd[e] - vc);
+#pragma unroll
       for (int r = 0; r < K; ++r) {
         ru[r] += P[r] * du;
         rv[r] += P[r] * dv;
+#pragma unroll
         for (int c = r; c < K; ++c) M[r][c] += P[r] * P[c];
       }
       ++count;
     }
   }
   if (count < K) return false;
-  // unit-diagonal scaling, then elimination without exchanges
-  float d[8];
+  float d[K];
+#pragma unroll
   for (int r = 0; r < K; ++r) {
     if (!(M[r][r] > 0.0f)) return false;
     d[r] = rsqrtf(M[r][r]);
   }
+#pragma unroll
   for (int r = 0; r < K; ++r) {
+#pragma unroll
     for (int c = r; c < K; ++c) M[r][c] *= d[r] * d[c];
+#pragma unroll
     for (int c = 0; c < r; ++c) M[r][c] = M[c][r];
     ru[r] *= d[r];
     rv[r] *= d[r];
   }
+#pragma unroll
   for (int k = 0; k < K; ++k) {
     const float piv = M[k][k];
     if (!(piv > kMinScaledPivot)) return false;
     const float inv = 1.0f / piv;
+#pragma unroll
     for (int r = k + 1; r < K; ++r) {
       const float f = M[r][k] * inv;
+#pragma unroll
       for (int c = k + 1; c < K; ++c) M[r][c] -= f * M[k][c];
       ru[r] -= f * ru[k];
       rv[r] -= f * rv[k];
     }
   }
+#pragma unroll
   for (int r = K - 1; r >= 0; --r) {
-    float su = ru[r], sv = rv[r];
+    float xu = ru[r], xv = rv[r];
+#pragma unroll
     for (int c = r + 1; c < K; ++c) {
-      su -= M[r][c] * ru[c];
-      sv -= M[r][c] * rv[c];
+      xu -= M[r][c] * ru[c];
+      xv -= M[r][c] * rv[c];
     }
-    ru[r] = su / M[r][r];
-    rv[r] = sv / M[r][r];
+    ru[r] = xu / M[r][r];
+    rv[r] = xv / M[r][r];
   }
   // undo the scaling: coefficient r is d[r] z[r]
   g[0] = d[1] * ru[1];
@@ -183,10 +195,12 @@ constexpr int kSmallHalf = 4, kMaxHalf = 15;
 // reference point comes from one ballot per warp; three barriers in all.
 template <int kStagedPerThread>
 __global__ void __launch_bounds__(kTileX * kTileY, 2) strain_kernel(StrainArgs a) {
-  extern __shared__ __align__(16) float sm[];
+  extern __shared__ __align__(16) double smd[];
   const int h = (a.window - 1) / 2, N = a.window;
   const int SX = kTileX + 2 * h, SY = kTileY + 2 * h, NS = SX * SY;
-  float* su = sm;                 // [SY][SX] staged offsets of u
+  double* ud = smd;               // [SY][SX] staged displacements (for the general fit)
+  double* vd = ud + NS;
+  float* su = reinterpret_cast<float*>(vd + NS);   // [SY][SX] staged offsets of u
   float* sv = su + NS;            // ... of v
   float* fx = sv + NS;            // [2][SY][kTileX] row sums: sum i d   (u, v)
   float* f0 = fx + 2 * SY * kTileX;   // sum d
@@ -247,6 +261,8 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2) strain_kernel(StrainArgs a
       const bool ok = sst[k] == 0;
       su[e] = ok ? static_cast<float>(suq[k]) - ref.x : nan_;
       sv[e] = ok ? static_cast<float>(svq[k]) - ref.y : nan_;
+      ud[e] = suq[k];
+      vd[e] = svq[k];
     }
   }
   __syncthreads();
@@ -287,7 +303,9 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2) strain_kernel(StrainArgs a
       g[2] = svx;
       g[3] = svy;
     } else {
-      ok = fit_window(a, ic, jc, uc, vc, g);
+      const int ec = (ty + h) * SX + tx + h;
+      ok = a.basis == DIC_STRAIN_BILINEAR ? fit_window<3>(a, h, su, ud, vd, SX, ec, uc, vc, g)
+                                          : fit_window<8>(a, h, su, ud, vd, SX, ec, uc, vc, g);
     }
   }
   if (ok) {
@@ -314,15 +332,16 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2) strain_kernel(StrainArgs a
 cudaError_t launch_strain(const StrainArgs& a, cudaStream_t s) {
   const int h = (a.window - 1) / 2;
   const int SX = kTileX + 2 * h, SY = kTileY + 2 * h;
-  const size_t smem = sizeof(float) * (2 * static_cast<size_t>(SY) * SX + 6 * static_cast<size_t>(SY) * kTileX);
+  const size_t smem = (sizeof(double) + sizeof(float)) * 2 * static_cast<size_t>(SY) * SX +
+                      sizeof(float) * 6 * static_cast<size_t>(SY) * kTileX;
   dim3 grid((a.nx + kTileX - 1) / kTileX, (a.ny + kTileY - 1) / kTileY);
   if (h <= kSmallHalf) {
     strain_kernel<staged_per_thread(kSmallHalf)><<<grid, kTileX * kTileY, smem, s>>>(a);
     return cudaGetLastError();
   }
-  // the largest window (31) needs about 58 KB; the limit is raised once (thread-safe)
+  // the largest window (31) needs about 103 KB; the limit is raised once (thread-safe)
   static const cudaError_t configured = cudaFuncSetAttribute(
-      strain_kernel<staged_per_thread(kMaxHalf)>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      strain_kernel<staged_per_thread(kMaxHalf)>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
   if (configured != cudaSuccess) return configured;
   strain_kernel<staged_per_thread(kMaxHalf)><<<grid, kTileX * kTileY, smem, s>>>(a);
   return cudaGetLastError();
