@@ -36,7 +36,7 @@ __device__ __forceinline__ void basis_row(int basis, float x, float y, float* P)
 }
 
 // General least squares over the valid points of the window (out of line: windows with
-// missing points are the rare case) for a basis of K terms: returns false when the
+// missing points are the rare case) for a basis of K terms: returns NaN in .x when the
 // design is not well posed; else the x and y slopes (grid units) of u and v. Which
 // points are present comes from the block's staged offsets su (row pitch SX; NaN where
 // a point is missing or outside the grid; centre at slot ec); the offsets from the
@@ -45,8 +45,9 @@ __device__ __forceinline__ void basis_row(int basis, float x, float y, float* P)
 // unit-diagonal scaling, then elimination without exchanges, indexed at compile time
 // (K fixed) so that the matrix lives in registers.
 template <int K>
-__device__ __noinline__ bool fit_window(const StrainArgs& a, int h, const float* su, const double* ud,
-                                        const double* vd, int SX, int ec, double uc, double vc, float* g) {
+__device__ __noinline__ float4 fit_window(const StrainArgs& a, int h, const float* su, const double* ud,
+                                          const double* vd, int SX, int ec, double uc, double vc) {
+  const float4 fail = make_float4(__int_as_float(0x7fc00000), 0.0f, 0.0f, 0.0f);
   float M[K][K], ru[K], rv[K];
 #pragma unroll
   for (int r = 0; r < K; ++r) {
@@ -72,11 +73,11 @@ __device__ __noinline__ bool fit_window(const StrainArgs& a, int h, const float*
       ++count;
     }
   }
-  if (count < K) return false;
+  if (count < K) return fail;
   float d[K];
 #pragma unroll
   for (int r = 0; r < K; ++r) {
-    if (!(M[r][r] > 0.0f)) return false;
+    if (!(M[r][r] > 0.0f)) return fail;
     d[r] = rsqrtf(M[r][r]);
   }
 #pragma unroll
@@ -91,7 +92,7 @@ __device__ __noinline__ bool fit_window(const StrainArgs& a, int h, const float*
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const float piv = M[k][k];
-    if (!(piv > kMinScaledPivot)) return false;
+    if (!(piv > kMinScaledPivot)) return fail;
     const float inv = 1.0f / piv;
 #pragma unroll
     for (int r = k + 1; r < K; ++r) {
@@ -114,11 +115,7 @@ __device__ __noinline__ bool fit_window(const StrainArgs& a, int h, const float*
     rv[r] = xv / M[r][r];
   }
   // undo the scaling: coefficient r is d[r] z[r]
-  g[0] = d[1] * ru[1];
-  g[1] = d[2] * ru[2];
-  g[2] = d[1] * rv[1];
-  g[3] = d[2] * rv[2];
-  return true;
+  return make_float4(d[1] * ru[1], d[2] * ru[2], d[1] * rv[1], d[2] * rv[2]);
 }
 
 // eigenvalues mu1 >= mu2 of the symmetric [[d11, d12], [d12, d22]]
@@ -140,7 +137,8 @@ __device__ __forceinline__ void spectral(float d11, float d12, float d22, float 
 
 // Sec. 2.3: strain (exx, eyy, exy) from H = grad u, formed from the small parts of
 // F^T F = I + D or F F^T = I + D' so that no 1 is subtracted from a near-1 value.
-__device__ void strain_from_gradient(int measure, float h11, float h12, float h21, float h22, float* e) {
+__device__ __forceinline__ void strain_from_gradient(int measure, float h11, float h12, float h21, float h22,
+                                                     float* e) {
   const bool left = measure == DIC_EULER_ALMANSI || measure == DIC_BIOT_LEFT;
   // D = H + H^T + H^T H (right) or D' = H + H^T + H H^T (left)
   const float d11 = left ? 2.0f * h11 + h11 * h11 + h12 * h12 : 2.0f * h11 + h11 * h11 + h21 * h21;
@@ -271,8 +269,9 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2) strain_kernel(StrainArgs a
     const int row = rc / kTileX, c = rc & (kTileX - 1);
     const float* src = (comp == 0 ? su : sv) + row * SX + c;   // window columns c .. c + 2h
     float sx = 0.0f, s0 = 0.0f, s2 = 0.0f;
-    for (int k = 0; k < N; ++k) {
-      const float di = static_cast<float>(k - h), d = src[k];
+    float di = static_cast<float>(-h);                 // k - h, counted in FP32 (exact)
+    for (int k = 0; k < N; ++k, di += 1.0f) {
+      const float d = src[k];
       sx += di * d;
       s0 += d;
       s2 += di * di * d;
@@ -283,13 +282,13 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2) strain_kernel(StrainArgs a
   }
   __syncthreads();
   if (!inside) return;
-  float g[4];
+  float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   bool ok = st_c == 0;
   if (ok) {
     float sux = 0.0f, suy = 0.0f, svx = 0.0f, svy = 0.0f;
     const int o = ty * kTileX + tx, ov = SY * kTileX;
-    for (int k = 0; k < N; ++k) {
-      const float dj = static_cast<float>(k - h);
+    float dj = static_cast<float>(-h);                 // k - h, counted in FP32 (exact)
+    for (int k = 0; k < N; ++k, dj += 1.0f) {
       const float wxj = a.wa + a.wb * dj * dj;
       const int r = o + k * kTileX;
       sux += wxj * fx[r];
@@ -298,19 +297,17 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2) strain_kernel(StrainArgs a
       svy += dj * (a.wa * f0[ov + r] + a.wb * f2[ov + r]);
     }
     if (isfinite(sux) && isfinite(suy) && isfinite(svx) && isfinite(svy)) {
-      g[0] = sux;
-      g[1] = suy;
-      g[2] = svx;
-      g[3] = svy;
+      g = make_float4(sux, suy, svx, svy);
     } else {
       const int ec = (ty + h) * SX + tx + h;
-      ok = a.basis == DIC_STRAIN_BILINEAR ? fit_window<3>(a, h, su, ud, vd, SX, ec, uc, vc, g)
-                                          : fit_window<8>(a, h, su, ud, vd, SX, ec, uc, vc, g);
+      g = a.basis == DIC_STRAIN_BILINEAR ? fit_window<3>(a, h, su, ud, vd, SX, ec, uc, vc)
+                                         : fit_window<8>(a, h, su, ud, vd, SX, ec, uc, vc);
+      ok = g.x == g.x;
     }
   }
   if (ok) {
     const float inv_s = 1.0f / static_cast<float>(a.step);   // grid units -> pixels
-    const float h11 = g[0] * inv_s, h12 = g[1] * inv_s, h21 = g[2] * inv_s, h22 = g[3] * inv_s;
+    const float h11 = g.x * inv_s, h12 = g.y * inv_s, h21 = g.z * inv_s, h22 = g.w * inv_s;
     float e[3];
     strain_from_gradient(a.measure, h11, h12, h21, h22, e);
     a.dudx[q] = h11;
