@@ -1110,12 +1110,14 @@ struct WaveOccupancy<double, 64> { static constexpr int kBlocks = 8; };
 
 // MODE 0: Gauss-Newton, ZNSSD only (the default, leanest); 1: Gauss-Newton, any cost;
 // 2: Levenberg-Marquardt, any cost
-// Resident blocks the registers are sized for: the quadratic FP32 kernel keeps 6
-// blocks of 128 threads (at 7 its register cap costs more in spills than the extra
-// block gains)
+// Resident blocks the registers are sized for. The quadratic FP32 kernels take fewer
+// blocks than the others, for registers that spare them spills: 6 of 128 threads (at
+// 7 its register cap costs more in spills than the extra block gains) and 10 of 64
+// (96 registers; at 14 they spill about 100 bytes a thread)
 template <typename T, int NP, int NT>
 constexpr int wave_min_blocks() {
-  return (sizeof(T) == 4 && NT == 128 && NP == 12) ? 6 : WaveOccupancy<T, NT>::kBlocks;
+  if (sizeof(T) == 4 && NP == 12) return NT == 128 ? 6 : 10;
+  return WaveOccupancy<T, NT>::kBlocks;
 }
 
 template <typename T, int NP, int NT, int MODE>
