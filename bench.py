@@ -47,8 +47,8 @@ PT_OUT_OF_BOUNDS = 3
 
 # DRAM bytes (read + write) per attempted point of the wave kernel, from one ncu
 # capture of the current kernel (a mid-run wave of 2,560 points on the 6144^2 version
-# of the workload: 31.26 MB per launch); None when the kernel has changed since
-WAVE_DRAM_BYTES_PER_POINT = 12212
+# of the workload: 30.65 MB per launch); None when the kernel has changed since
+WAVE_DRAM_BYTES_PER_POINT = 11972
 
 # Tensor work of the odd-window FFT kernel per window (3xTF32 products of the 32-padded
 # window: 384 + 384 for the forward rows and columns, 192 for the inverse rows, 96 for
