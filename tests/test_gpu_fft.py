@@ -116,6 +116,42 @@ def test_eq1_over_windows_matches_oracle(pkg, L, n, subpixel):
     assert ties <= max(2, n // 50)
 
 
+@pytest.mark.parametrize("L", [31, 32, 64, 128])
+@pytest.mark.parametrize("dtype", ["u16", "bf16", "f32", "f64"])
+def test_gray_types_over_windows_match_oracle(pkg, dtype, L):
+    """Every gray element type through each window path: the tensor-core windows (31,
+    32), the shared-memory FFT (64) and the row kernels of the work-buffer path (128)
+    load the window with the element type fixed once per window or row."""
+    W, H = 420, 380
+    fld = synth.affine_field(W, H, u0=2.6, v0=-1.9, exx=3e-3, eyy=-2e-3, exy=1e-3)
+    kind = "u8" if dtype == "bf16" else dtype
+    ref = _speckle(W, H, 31, dtype=kind)
+    dfm = _speckle(W, H, 31, fld=fld, dtype=kind, tag=2)
+    if dtype == "bf16":                  # integer gray levels below 256 are exact in BF16
+        ref_in = torch.from_numpy(ref.astype(np.float32)).to(torch.bfloat16).cuda()
+        dfm_in = torch.from_numpy(dfm.astype(np.float32)).to(torch.bfloat16).cuda()
+    else:
+        ref_in, dfm_in = ref, dfm
+    rng = np.random.default_rng(100 + L)
+    origins = _random_origins(rng, W, H, L, 40, spread=min(L // 3, 10))
+    subpixel = L <= 64
+    c = pkg.Correlation(ref_in, dfm_in, None, 21, 10, "affine")
+    gu, gv, gp = _gpu_windows(pkg, c, L, origins, subpixel)
+    c.close()
+    ora = _oracle_windows(ref, dfm, L, origins, subpixel)
+    ties = 0
+    for k, (ou, ov, opk, tie, R) in enumerate(ora):
+        if tie:
+            ties += 1
+            continue
+        if subpixel:
+            assert abs(gu[k] - ou) < 1e-4 and abs(gv[k] - ov) < 1e-4, (k, gu[k], ou, gv[k], ov)
+        else:
+            assert (gu[k], gv[k]) == (ou, ov), (k, gu[k], ou, gv[k], ov)
+        assert abs(gp[k] - opk) < 2e-5, (k, gp[k], opk)
+    assert ties <= 2
+
+
 def test_flat_and_skipped_windows(pkg):
     W, H = 400, 360
     ref = _speckle(W, H, 5)
