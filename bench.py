@@ -50,13 +50,13 @@ PT_OUT_OF_BOUNDS = 3
 # of the workload: 30.65 MB per launch); None when the kernel has changed since
 WAVE_DRAM_BYTES_PER_POINT = 11972
 
-# Tensor work of the odd-window FFT kernel per window (3xTF32 products of the 32-padded
-# window: 384 + 384 for the forward rows and columns, 192 for the inverse rows, 96 for
-# the real column pass), FLOPs per m16n8k8 product, and the nominal TF32 / bf16 dense
-# ratio that turns the measured bf16 peak into a TF32 one.
-TC_MMAS_PER_WINDOW = 1056
-TC_FLOPS_PER_MMA = 2 * 16 * 8 * 8
-TF32_PER_BF16 = 1.1 / 2.25
+# Tensor work of the FFT window kernel per window (split-FP16 products, three per
+# m16n8k16 step, of the 32-padded window: 192 for the forward rows, 192 for the
+# columns, 96 for the inverse rows, 48 for the real column pass) and FLOPs per
+# m16n8k16 product; FP16 runs at the bf16 dense rate, so the measured bf16 peak is the
+# denominator.
+TC_MMAS_PER_WINDOW = 528
+TC_FLOPS_PER_MMA = 2 * 16 * 8 * 16
 
 
 def measured_peaks():
@@ -742,11 +742,11 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel
     SEM study's settings (Sec. 4): subset 31, step 15, maximum displacement 2000 px
     (windows 2048 .. 32, then 31), a 1000 px border outside the ROI, Gaussian
     sub-pixel fit. The last level (one 31 x 31 window per grid point: the DFT matrix
-    products on the tensor cores, 3xTF32 mma.sync) is timed alone through
+    products on the tensor cores, split-FP16 mma.sync) is timed alone through
     dic_fftcc_windows on the same number of windows. Its roofline counts the tensor
-    work it executes, TC_MMAS_PER_WINDOW m16n8k8 products of 2 x 16 x 8 x 8 FLOPs,
-    against the TF32 dense peak (the measured bf16 peak x the nominal TF32 / bf16
-    ratio 1.1 / 2.25); the method's own count, 22 S^3 + 2 S^2 FP32 FLOPs per window
+    work it executes, TC_MMAS_PER_WINDOW m16n8k16 products of 2 x 16 x 8 x 16 FLOPs,
+    against the measured bf16 dense peak (FP16 and bf16 share the rate); the method's
+    own count, 22 S^3 + 2 S^2 FP32 FLOPs per window
     (the forward 2-D DFT, 2 S^3 complex multiply-adds of 8 FLOPs; the inverse of the
     Hermitian cross power, (S+1)/2 rows of S^2 complex multiply-adds and a real
     column pass of S^2 (S-1)/2 two-FMA terms), is given beside it."""
@@ -800,7 +800,7 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel
     achieved = flops / (k / 1e3) / 1e12
     tc_flops = float(TC_MMAS_PER_WINDOW * TC_FLOPS_PER_MMA) * n
     tc_achieved = tc_flops / (k / 1e3) / 1e12
-    tf32_peak = MEASURED.get("bf16_tflops", 1900.0) * TF32_PER_BF16
+    f16_peak = MEASURED.get("bf16_tflops", 1912.3)
     levels = g["windows"]
     launches = 1 + 3 * len(levels) + 5 * sum(1 for L in levels if L > 64)   # origins, fftcc (6 when > 64 px), MAD; status
     c.close()
@@ -811,11 +811,11 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel
             "gpu_launches": launches,
             "last_level_ms": k, "last_level_share": k / t,
             "roofline": {"bound": "tensor",
-                         "kernel": "fftcc_tc_kernel (3xTF32 mma.sync m16n8k8, one warp per window)",
-                         "achieved": tc_achieved, "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc_achieved / tf32_peak,
+                         "kernel": "fftcc_tc_kernel (split-FP16 mma.sync m16n8k16, one warp per window)",
+                         "achieved": tc_achieved, "peak": f16_peak, "unit": "TFLOP/s", "frac": tc_achieved / f16_peak,
                          "executed_flops_per_window": TC_MMAS_PER_WINDOW * TC_FLOPS_PER_MMA,
-                         "peak_note": "TF32 dense, of measured: bf16 burst %.1f TFLOP/s (MEASURED_PEAKS.json) x "
-                                      "nominal TF32/bf16 1.1/2.25" % MEASURED.get("bf16_tflops", float("nan")),
+                         "peak_note": "FP16 dense at the bf16 rate, of measured: bf16 burst %.1f TFLOP/s "
+                                      "(MEASURED_PEAKS.json)" % MEASURED.get("bf16_tflops", float("nan")),
                          "algorithmic_fp32": {"flops_per_window": 22 * S ** 3 + 2 * S ** 2, "achieved": achieved,
                                               "peak": fp32_peak()[0], "frac": achieved / fp32_peak()[0],
                                               "peak_note": fp32_peak()[1]}}}

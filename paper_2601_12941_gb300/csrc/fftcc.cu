@@ -12,17 +12,21 @@
 //   norms of the transforms in the denominator). The peak of R sits at minus the
 //   shift of the deformed window's content.
 //
-// Two paths:
-//   * L <= 64 (the subset-sized last level, and the 32 / 64 levels): one block per
-//     window, the whole window in shared memory; radix-4 Stockham FFTs (one radix-2
-//     pass when log2 L is odd) along rows and columns for powers of two, a direct
-//     DFT for the odd subset size.
+// Three paths:
+//   * L <= 32 (the subset-sized last level and the 32 px level): one warp per window,
+//     the 2-D DFT as matrix products on the tensor cores (split FP16 operands).
+//   * L <= 64 otherwise (the 64 px level, odd sizes 33-63): one block per window, the
+//     whole window in shared memory; radix-8 Stockham FFTs (then one radix-4 or
+//     radix-2 pass) along rows and columns for powers of two, a direct DFT for odd
+//     sizes.
 //   * 128 <= L <= 4096: the window in a global work buffer; row FFTs, an in-place
 //     tile transpose, paired-row FFTs that form the cross power and transform it
 //     back, a transpose back and the inverse row FFTs with a per-window arg-max
 //     (packed 64-bit keys: the larger R, ties to the lower row-major index).
 #include <math.h>
 #include <stdint.h>
+
+#include <cuda_fp16.h>
 
 #include <type_traits>
 
@@ -509,57 +513,42 @@ __global__ void __launch_bounds__(POW2 ? kSmallThreads : kSmallThreads / 2) fftc
 }
 
 // ---------------------------------------------------------------- windows up to 32 px on the tensor cores
-// Windows up to 32 px (the subset-sized last level and the 32 px level): the four DFT
-// matrix products of a window on the tensor cores (mma.sync m16n8k8, TF32 operands, FP32
-// accumulators), each operand split into a TF32 high part and a TF32 remainder so that
-// hi*hi + hi*lo + lo*hi keeps FP32 accuracy (3xTF32). The window is padded to 32; a
-// complex product A B is the real product [Ar Ai] [[Br, Bi], [-Bi, Br]]. With W the
-// DFT matrix (symmetric) and Z the packed window:
-//   1. Y = Z W              rows, forward       (32 x 64) x (64 x 64), stored transposed
+// Windows up to 32 px (the subset-sized last level and the 32 px level): the DFT matrix
+// products of a window on the tensor cores, mma.sync m16n8k16 with FP16 operands and
+// FP32 accumulators, each operand split into an FP16 high part and an FP16 remainder so
+// that hi*hi + hi*lo + lo*hi keeps about FP32 accuracy (22 significant bits). Data
+// operands are scaled by powers of two before the split (exact) to stay inside the FP16
+// range: the window by 2^E1 from its largest centred value, the row transforms by 2^-7
+// (|Y| < 2^20), the cross power by 2^E3 from its largest entry, the inverse row
+// transforms by 2^-7; the peak value undoes the product of the scales. The window is
+// padded to 32; a complex product is a real product in block form ([[Ar, -Ai], [Ai, Ar]]
+// on the left, [[Br, Bi], [-Bi, Br]] on the right). With W the DFT matrix (symmetric) and
+// Z the packed window:
+//   1. Y^T = W Z^T          rows, forward       (64 x 64) x (64 x 32), stored [Yr^T | Yi^T]
 //   2. X^T = Y^T W          columns, forward    (32 x 64) x (64 x 64)
 //   3. P = cross power of X(k), X(-k), rows ky <= 15 of the Hermitian half, stored
 //      conjugated
-//   4. T = P conj(W) = conj(conj(P) W)          (16 x 64) x (64 x 64)
+//   4. U^T = W conj(P)^T    inverse rows        (64 x 64) x (64 x 16); T = conj(U) = P conj(W),
+//                           stored as T^T
 //   5. R = A6 [Tr; Ti]      R[y][x] = sum_ky c_ky (Tr cos(2 pi ky y / L) - Ti sin(...)),
 //                           c_0 = 1, c_ky = 2, and c_{L/2} = 1 for even L: (32 x 32) x (32 x 32)
-// For L = 32 the Hermitian half has a 17th row, the Nyquist row ky = 16, whose inverse
-// row transform T16 is real: it is formed with shuffles (FP32 FMA) and adds
-// T16[x] (-1)^y to R.
-// One warp per window, with its own 32 x kTcSA buffer in shared memory, so a window
-// needs no block-wide barrier: 16 warps per block (one block per SM, 128 registers a
-// thread), the W and A6 operands held once per block in fragment order (one 16-byte
-// shared load per lane gives the high and low parts of a B fragment).
-constexpr int kTcP = 32;                 // padded window side
-constexpr int kTcSA = 2 * kTcP + 4;      // row stride (floats) of the 32 x 64 operand buffers
-constexpr int kTcSW = kTcP + 8;          // row stride of [Tr; Ti] and of R
-
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-// c += a b, m16n8k8, TF32 operands (bit patterns), FP32 accumulators
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// The A fragment of rows m0.., columns k0.. of a row-major FP32 buffer, split into
-// TF32 high parts and remainders: lane (g, t) holds rows g, g + 8 and columns t, t + 4.
-__device__ __forceinline__ void a_frag_split(const float* A, int sa, int m0, int k0, int g, int t, uint32_t (&hi)[4],
-                                             uint32_t (&lo)[4]) {
-  const float v[4] = {A[(m0 + g) * sa + k0 + t], A[(m0 + g + 8) * sa + k0 + t], A[(m0 + g) * sa + k0 + t + 4],
-                      A[(m0 + g + 8) * sa + k0 + t + 4]};
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    hi[i] = tf32_bits(v[i]);
-    lo[i] = tf32_bits(v[i] - __uint_as_float(hi[i]));
-  }
-}
+// Every product reads its data operand in the layout the stage before wrote (pairs along
+// the summed index), so no stage stores transposed. For L = 32 the Hermitian half has a
+// 17th row, the Nyquist row ky = 16, whose inverse row transform T16 is real: it is
+// formed with shuffles (FP32 FMA) and adds T16[x] (-1)^y to R.
+// One warp per window, with its own 32 x kH16SA buffer of FP32 values in shared memory,
+// so a window needs no block-wide barrier: 16 warps per block (one block per SM, 128
+// registers a thread); W and A6 are held once per block as split fragments in fragment
+// order (one 16-byte shared load per lane gives a B fragment's high and low parts).
+constexpr int kTcP = 32;                  // padded window side
+constexpr int kTcSW = kTcP + 8;           // row stride of T^T and of R
+constexpr int kTcWarps = 16;
+constexpr int kTcBlockThreads = 32 * kTcWarps;
+constexpr int kH16SA = 2 * kTcP + 8;      // row stride (floats) of the 32 x 64 data buffers
+constexpr int kH16Buf = kTcP * kH16SA;    // floats per warp
+constexpr int kWaFrags = 4 * 4 * 2 * 32;  // A fragments of [[Wr, -Wi], [Wi, Wr]]: row tiles x k-steps x (hi, lo) x lanes
+constexpr int kWbFrags = 4 * 8 * 32;      // B fragments of [[Wr, Wi], [-Wi, Wr]]: k-steps x column tiles x lanes
+constexpr int kA6hFrags = 2 * 2 * 2 * 32; // A fragments of A6: row tiles x k-steps x (hi, lo) x lanes
 
 // Gray levels of a column of the window: rows y < L of pixel column x (lanes x >= L
 // and rows y >= L give 0), the element type fixed once per window.
@@ -624,103 +613,114 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// acc[m][j] += A (rows 16 m.., 64 columns) x Wblock (64 x 64), 3xTF32; MT row tiles of
-// 16, the 8 column tiles of 8. wf: the B fragments of the block matrix in fragment
-// order, entry (k-step, column tile, lane) = (high b0, high b1, low b0, low b1).
-template <int MT>
-__device__ __forceinline__ void warp_gemm_w(const float* A, int sa, const uint4* __restrict__ wf, int lane, int g,
-                                            int t, float (&acc)[MT][8][4]) {
-#pragma unroll 1
-  for (int ks = 0; ks < 8; ++ks) {
-    uint32_t ah[MT][4], al[MT][4];
-#pragma unroll
-    for (int m = 0; m < MT; ++m) a_frag_split(A, sa, 16 * m, 8 * ks, g, t, ah[m], al[m]);
-    // two column tiles at a time, the three partial products of a tile issued
-    // 2 MT products apart, so that no product waits on the one just before it
-#pragma unroll
-    for (int j = 0; j < 8; j += 2) {
-      const uint4 b[2] = {wf[(ks * 8 + j) * 32 + lane], wf[(ks * 8 + j + 1) * 32 + lane]};
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int m = 0; m < MT; ++m) mma_tf32(acc[m][j + h], ah[m], b[h].x, b[h].y);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int m = 0; m < MT; ++m) mma_tf32(acc[m][j + h], ah[m], b[h].z, b[h].w);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int m = 0; m < MT; ++m) mma_tf32(acc[m][j + h], al[m], b[h].x, b[h].y);
-    }
-  }
+// c += a b, m16n8k16, FP16 operands (f16x2 registers), FP32 accumulators
+__device__ __forceinline__ void mma_f16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Element (r, c) of the 64 x 64 block matrix [[Wr, Wi], [-Wi, Wr]] of the DFT matrix
-// W[x][k] = exp(-2 pi i x k / L) (x, k < L; 0 in the padding); tw[m] = exp(-2 pi i m / L).
-__device__ __forceinline__ float w_block(const float2* __restrict__ tw, int L, int r, int c) {
-  const int qr = r >> 5, qc = c >> 5, x = r & 31, k = c & 31;
-  if (x >= L || k >= L) return 0.f;
-  const float2 w = tw[(x * k) % L];
-  return qr == qc ? w.x : (qr == 0 ? w.y : -w.y);
+// (x0 s, x1 s) as an f16x2 high part and an f16x2 remainder (x0 in the low half)
+__device__ __forceinline__ void split_h2(float x0, float x1, float s, uint32_t& hi, uint32_t& lo) {
+  const float y0 = x0 * s, y1 = x1 * s;
+  const __half2 h = __floats2half2_rn(y0, y1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(y0 - hf.x, y1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Entry e = (k-step, column tile, lane) of the fragment-ordered block matrix.
-__device__ __forceinline__ uint4 w_fragment(const float2* __restrict__ tw, int L, int e) {
-  const int ks = e >> 8, j = (e >> 5) & 7, ln = e & 31;
-  const int k = 8 * ks + (ln & 3), n = 8 * j + (ln >> 2);
-  const float v0 = w_block(tw, L, k, n), v1 = w_block(tw, L, k + 4, n);
-  const uint32_t h0 = tf32_bits(v0), h1 = tf32_bits(v1);
-  return make_uint4(h0, h1, tf32_bits(v0 - __uint_as_float(h0)), tf32_bits(v1 - __uint_as_float(h1)));
+// 2^E with E = 13 - floor(log2(m)): m scaled by it lies in [2^13, 2^14); 1 for m = 0
+__device__ __forceinline__ int f16_scale_exp(float m) {
+  if (!(m > 0.f)) return 0;
+  const int e = static_cast<int>((__float_as_uint(m) >> 23) & 0xffu) - 127;
+  const int E = 13 - e;
+  return E < -100 ? -100 : (E > 100 ? 100 : E);
+}
+__device__ __forceinline__ float pow2f(int E) { return __uint_as_float(static_cast<uint32_t>(127 + E) << 23); }
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
-constexpr int kTcWarps = 16;
-constexpr int kTcBlockThreads = 32 * kTcWarps;
-constexpr int kTcBuf = kTcP * kTcSA;      // floats per warp
-constexpr int kTcFrags = 8 * 8 * 32;      // B fragments of a 64 x 64 block matrix: k-steps x column tiles x lanes
-constexpr int kTcA6Frags = 2 * 4 * 2 * 32;   // A fragments of A6: row tiles x k-steps x (high, low) x lanes
+// A fragments (row tile mt, k-step ks) of an M x K row-major operand given by el(r, c),
+// split: lane (g, t) holds rows g, g + 8 and columns 2t, 2t + 1, 2t + 8, 2t + 9.
+template <typename F>
+__device__ __forceinline__ void a16_fragment(F el, int mt, int ks, int ln, uint4& hi, uint4& lo) {
+  const int g = ln >> 2, t = ln & 3, r0 = 16 * mt + g, c0 = 16 * ks + 2 * t;
+  uint32_t h[4], l[4];
+  split_h2(el(r0, c0), el(r0, c0 + 1), 1.f, h[0], l[0]);
+  split_h2(el(r0 + 8, c0), el(r0 + 8, c0 + 1), 1.f, h[1], l[1]);
+  split_h2(el(r0, c0 + 8), el(r0, c0 + 9), 1.f, h[2], l[2]);
+  split_h2(el(r0 + 8, c0 + 8), el(r0 + 8, c0 + 9), 1.f, h[3], l[3]);
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// The DFT matrix W[x][k] = exp(-2 pi i x k / L) (x, k < L; else 0) from the root table
+__device__ __forceinline__ float2 w_entry(const float2* __restrict__ tw, int L, int x, int k) {
+  return (x < L && k < L) ? tw[(x * k) % L] : make_float2(0.f, 0.f);
+}
 
 __global__ void __launch_bounds__(kTcBlockThreads, 1) fftcc_tc_kernel(FftccArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float2 s_root[kTcP];                           // exp(-2 pi i m / L), m < L
   const int L = a.L, N = L * L, kh = L / 2 + 1;             // rows 0 .. L/2 of the Hermitian half
   const bool nyquist = L == 32;                             // row ky = 16, outside the 16-row tile
-  uint4* wf = reinterpret_cast<uint4*>(smem_raw);          // B fragments of the block W
-  uint4* a6f = wf + kTcFrags;                               // A fragments of A6
+  uint4* wa = reinterpret_cast<uint4*>(smem_raw);          // A fragments of [[Wr, -Wi], [Wi, Wr]]
+  uint4* wb = wa + kWaFrags;                                // B fragments of [[Wr, Wi], [-Wi, Wr]]
+  uint4* a6f = wb + kWbFrags;                               // A fragments of A6
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* buf = reinterpret_cast<float*>(a6f + kTcA6Frags) + warp * kTcBuf;
+  float* buf = reinterpret_cast<float*>(a6f + kA6hFrags) + warp * kH16Buf;
   const int g = lane >> 2, t = lane & 3;
 
-  // W's block matrices and A6 in fragment order, TF32 high parts and remainders.
-  // A6[y][kp] (y < L): kp < 16 the cosine column of ky = kp, else the sine column of
-  // kp - 16, weighted c_0 = 1, c_ky = 2, c_{L/2} = 1 (ky <= L / 2; else 0)
   const bool pow2 = (L & (L - 1)) == 0;
   for (int e = tid; e < L; e += kTcBlockThreads) s_root[e] = pow2 ? twiddle(a.tw_pow2, e, L, false) : a.tw_odd[e];
   __syncthreads();
-  for (int e = tid; e < kTcFrags; e += kTcBlockThreads) {
-    wf[e] = w_fragment(s_root, L, e);
-  }
-  for (int e = tid; e < kTcA6Frags / 2; e += kTcBlockThreads) {
+  // [[Wr, -Wi], [Wi, Wr]] as A fragments: entry ((mt, ks), hi/lo, lane)
+  for (int e = tid; e < kWaFrags / 2; e += kTcBlockThreads) {
     const int mt = e >> 7, ks = (e >> 5) & 3, ln = e & 31;
-    float v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int y = 16 * mt + (ln >> 2) + (i & 1) * 8, kp = 8 * ks + (ln & 3) + (i >> 1) * 4, ky = kp & 15;
-      v[i] = 0.f;
-      if (y < L && ky < kh) {
-        const float2 q = s_root[(ky * y) % L];            // (cos, -sin) of 2 pi ky y / L
-        const float c = (ky == 0 || 2 * ky == L) ? 1.f : 2.f;
-        v[i] = kp < 16 ? c * q.x : c * q.y;
-      }
-    }
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      h[i] = tf32_bits(v[i]);
-      l[i] = tf32_bits(v[i] - __uint_as_float(h[i]));
-    }
-    a6f[2 * e - ln] = make_uint4(h[0], h[1], h[2], h[3]);        // entry ((mt, ks), hi, lane)
-    a6f[2 * e - ln + 32] = make_uint4(l[0], l[1], l[2], l[3]);   // entry ((mt, ks), lo, lane)
+    uint4 hi, lo;
+    a16_fragment([&](int r, int c) {
+      const float2 w = w_entry(s_root, L, r & 31, c & 31);
+      const int qr = r >> 5, qc = c >> 5;
+      return qr == qc ? w.x : (qr == 0 ? -w.y : w.y);
+    }, mt, ks, ln, hi, lo);
+    wa[2 * e - ln] = hi;
+    wa[2 * e - ln + 32] = lo;
+  }
+  // [[Wr, Wi], [-Wi, Wr]] as B fragments: entry (ks, nt, lane) = (hi b01, hi b23, lo b01, lo b23);
+  // lane (g, t) holds rows 2t, 2t + 1, 2t + 8, 2t + 9 of column g
+  for (int e = tid; e < kWbFrags; e += kTcBlockThreads) {
+    const int ks = e >> 8, nt = (e >> 5) & 7, ln = e & 31;
+    const int n = 8 * nt + (ln >> 2), k0 = 16 * ks + 2 * (ln & 3);
+    auto el = [&](int r, int c) {
+      const float2 w = w_entry(s_root, L, r & 31, c & 31);
+      const int qr = r >> 5, qc = c >> 5;
+      return qr == qc ? w.x : (qr == 0 ? w.y : -w.y);
+    };
+    uint32_t h0, l0, h1, l1;
+    split_h2(el(k0, n), el(k0 + 1, n), 1.f, h0, l0);
+    split_h2(el(k0 + 8, n), el(k0 + 9, n), 1.f, h1, l1);
+    wb[e] = make_uint4(h0, h1, l0, l1);
+  }
+  // A6[y][kp] (y < L): kp < 16 the cosine column of ky = kp, else the sine column of
+  // kp - 16, weighted c_0 = 1, c_ky = 2, c_{L/2} = 1 (ky <= L / 2; else 0)
+  for (int e = tid; e < kA6hFrags / 2; e += kTcBlockThreads) {
+    const int mt = e >> 6, ks = (e >> 5) & 1, ln = e & 31;
+    uint4 hi, lo;
+    a16_fragment([&](int y, int kp) {
+      const int ky = kp & 15;
+      if (!(y < L && ky < kh)) return 0.f;
+      const float2 q = s_root[(ky * y) % L];              // (cos, -sin) of 2 pi ky y / L
+      const float c = (ky == 0 || 2 * ky == L) ? 1.f : 2.f;
+      return kp < 16 ? c * q.x : c * q.y;
+    }, mt, ks, ln, hi, lo);
+    a6f[2 * e - ln] = hi;
+    a6f[2 * e - ln + 32] = lo;
   }
   __syncthreads();
 
@@ -735,65 +735,123 @@ __global__ void __launch_bounds__(kTcBlockThreads, 1) fftcc_tc_kernel(FftccArgs 
       }
       continue;
     }
-    // the packed window [f | g] in buf (rows y, columns x and 32 + x; zero padding),
-    // lane x loading pixel column x; then centred by the means
+    // the packed window Z = [f | g] in buf (rows y, columns x and 32 + x; zero
+    // padding), lane x loading pixel column x; then centred by the means
     const float f00 = load_gray<float>(a.ref, o.x, o.y), g00 = load_gray<float>(a.def, o.z, o.w);
     bool vf, vg;
-    float sf = load_window_column(a.ref, o.x, o.y, L, lane, buf + lane, kTcSA, f00, &vf);
-    float sg = load_window_column(a.def, o.z, o.w, L, lane, buf + kTcP + lane, kTcSA, g00, &vg);
+    float sf = load_window_column(a.ref, o.x, o.y, L, lane, buf + lane, kH16SA, f00, &vf);
+    float sg = load_window_column(a.def, o.z, o.w, L, lane, buf + kTcP + lane, kH16SA, g00, &vg);
     const bool flat = !__any_sync(0xffffffffu, vf) || !__any_sync(0xffffffffu, vg);
     sf = warp_sum(sf);
     sg = warp_sum(sg);
     const float mf = sf / static_cast<float>(N), mg = sg / static_cast<float>(N);
-    float qf = 0.f, qg = 0.f;
+    float qf = 0.f, qg = 0.f, zmax = 0.f;
     if (lane < L) {
       for (int y = 0; y < L; ++y) {
-        const float f = buf[y * kTcSA + lane] - mf, gv = buf[y * kTcSA + kTcP + lane] - mg;
-        buf[y * kTcSA + lane] = f;
-        buf[y * kTcSA + kTcP + lane] = gv;
+        const float f = buf[y * kH16SA + lane] - mf, gv = buf[y * kH16SA + kTcP + lane] - mg;
+        buf[y * kH16SA + lane] = f;
+        buf[y * kH16SA + kTcP + lane] = gv;
         qf = fmaf(f, f, qf);
         qg = fmaf(gv, gv, qg);
+        zmax = fmaxf(zmax, fmaxf(fabsf(f), fabsf(gv)));
       }
     }
     qf = warp_sum(qf);
     qg = warp_sum(qg);
+    const int E1 = f16_scale_exp(warp_max(zmax));
+    const float s1 = pow2f(E1);
     __syncwarp();
 
-    // 1. Y = Z W, stored as Y^T ([x][y | 32 + y])
+    // 1. Y^T = W Z^T: [Yr^T; Yi^T] = [[Wr, -Wi], [Wi, Wr]] [Zr^T; Zi^T] (64 x 64 by 64 x 32);
+    //    stored as [Yr^T | Yi^T] ([kx][y | 32 + y])
+    {
+      float acc[4][4][4] = {};
+#pragma unroll 1
+      for (int ks = 0; ks < 4; ++ks) {
+        uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const float* p = buf + (8 * nt + g) * kH16SA + 16 * ks + 2 * t;   // Z row y = 8 nt + g
+          const float2 v0 = *reinterpret_cast<const float2*>(p), v1 = *reinterpret_cast<const float2*>(p + 8);
+          split_h2(v0.x, v0.y, s1, bh[nt][0], bl[nt][0]);
+          split_h2(v1.x, v1.y, s1, bh[nt][1], bl[nt][1]);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+          const uint4 h = wa[((mt * 4 + ks) * 2) * 32 + lane], l = wa[((mt * 4 + ks) * 2 + 1) * 32 + lane];
+          const uint32_t ah[4] = {h.x, h.y, h.z, h.w}, al[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_f16(acc[mt][nt], ah, bh[nt][0], bh[nt][1]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_f16(acc[mt][nt], ah, bl[nt][0], bl[nt][1]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_f16(acc[mt][nt], al, bh[nt][0], bh[nt][1]);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int hr = 0; hr < 2; ++hr) {
+            const int m = 16 * mt + g + 8 * hr, n = 8 * nt + 2 * t;
+            *reinterpret_cast<float2*>(buf + (m & 31) * kH16SA + (m >> 5) * kTcP + n) =
+                make_float2(acc[mt][nt][2 * hr], acc[mt][nt][2 * hr + 1]);
+          }
+      __syncwarp();
+    }
+    // 2. X^T = Y^T W: [Xr^T | Xi^T] = [Yr^T | Yi^T] [[Wr, Wi], [-Wi, Wr]] ([kx][ky | 32 + ky]);
+    //    Y^T enters scaled by 2^-7 (|Y| < 2^20)
     {
       float acc[2][8][4] = {};
-      warp_gemm_w<2>(buf, kTcSA, wf, lane, g, t, acc);
+      const float s2 = pow2f(-7);
+#pragma unroll 1
+      for (int ks = 0; ks < 4; ++ks) {
+        uint32_t ah[2][4], al[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const float* p = buf + (16 * mt + g) * kH16SA + 16 * ks + 2 * t;
+          const float2 v0 = *reinterpret_cast<const float2*>(p), v1 = *reinterpret_cast<const float2*>(p + 8 * kH16SA);
+          const float2 v2 = *reinterpret_cast<const float2*>(p + 8),
+                       v3 = *reinterpret_cast<const float2*>(p + 8 * kH16SA + 8);
+          split_h2(v0.x, v0.y, s2, ah[mt][0], al[mt][0]);
+          split_h2(v1.x, v1.y, s2, ah[mt][1], al[mt][1]);
+          split_h2(v2.x, v2.y, s2, ah[mt][2], al[mt][2]);
+          split_h2(v3.x, v3.y, s2, ah[mt][3], al[mt][3]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; nt += 2) {
+          const uint4 b[2] = {wb[(ks * 8 + nt) * 32 + lane], wb[(ks * 8 + nt + 1) * 32 + lane]};
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) mma_f16(acc[mt][nt + h], ah[mt], b[h].x, b[h].y);
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) mma_f16(acc[mt][nt + h], ah[mt], b[h].z, b[h].w);
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) mma_f16(acc[mt][nt + h], al[mt], b[h].x, b[h].y);
+        }
+      }
       __syncwarp();
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+        for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int m = 16 * mt + g + (i >> 1) * 8, n = 8 * j + 2 * t + (i & 1);
-            buf[(n & 31) * kTcSA + m + (n >> 5) * kTcP] = acc[mt][j][i];
+          for (int hr = 0; hr < 2; ++hr) {
+            const int m = 16 * mt + g + 8 * hr, n = 8 * nt + 2 * t;
+            *reinterpret_cast<float2*>(buf + m * kH16SA + n) = make_float2(acc[mt][nt][2 * hr], acc[mt][nt][2 * hr + 1]);
           }
       __syncwarp();
     }
-    // 2. X^T = Y^T W ([kx][ky | 32 + ky])
-    {
-      float acc[2][8][4] = {};
-      warp_gemm_w<2>(buf, kTcSA, wf, lane, g, t, acc);
-      __syncwarp();
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int m = 16 * mt + g + (i >> 1) * 8, n = 8 * j + 2 * t + (i & 1);
-            buf[m * kTcSA + n] = acc[mt][j][i];
-          }
-      __syncwarp();
-    }
-    // 3. the cross power P(ky, kx) of rows ky < 16 ([ky][kx | 32 + kx]); the zero
-    //    frequency and the padding are zero. All of X is read before P is written.
-    float t16 = 0.f;
+    // 3. the cross power P(ky, kx) of rows ky < 16, stored conjugated ([ky][kx | 32 + kx]);
+    //    the zero frequency and the padding are zero. All of X is read before P is written.
+    float t16 = 0.f, pmax = 0.f;
     {
       const int ky = lane & 15;
       float2 p[16];
@@ -803,16 +861,17 @@ __global__ void __launch_bounds__(kTcBlockThreads, 1) fftcc_tc_kernel(FftccArgs 
         p[j] = make_float2(0.f, 0.f);
         if (ky < kh && kx < L && (ky | kx) != 0) {
           const int mkx = kx == 0 ? 0 : L - kx, mky = ky == 0 ? 0 : L - ky;
-          const float2 zk = make_float2(buf[kx * kTcSA + ky], buf[kx * kTcSA + kTcP + ky]);
-          const float2 zm = make_float2(buf[mkx * kTcSA + mky], buf[mkx * kTcSA + kTcP + mky]);
+          const float2 zk = make_float2(buf[kx * kH16SA + ky], buf[kx * kH16SA + kTcP + ky]);
+          const float2 zm = make_float2(buf[mkx * kH16SA + mky], buf[mkx * kH16SA + kTcP + mky]);
           p[j] = cross_power(zk, zm);
+          pmax = fmaxf(pmax, fmaxf(fabsf(p[j].x), fabsf(p[j].y)));
         }
       }
       float2 p16 = make_float2(0.f, 0.f);                // the Nyquist row's P(16, kx), kx = lane
       if (nyquist) {
         const int mkx = lane == 0 ? 0 : L - lane;
-        p16 = cross_power(make_float2(buf[lane * kTcSA + 16], buf[lane * kTcSA + kTcP + 16]),
-                          make_float2(buf[mkx * kTcSA + 16], buf[mkx * kTcSA + kTcP + 16]));
+        p16 = cross_power(make_float2(buf[lane * kH16SA + 16], buf[lane * kH16SA + kTcP + 16]),
+                          make_float2(buf[mkx * kH16SA + 16], buf[mkx * kH16SA + kTcP + 16]));
       }
       __syncwarp();
       if (nyquist) {                                     // T16[x] = Re sum_kx P(16, kx) exp(2 pi i kx x / L), x = lane
@@ -826,72 +885,90 @@ __global__ void __launch_bounds__(kTcBlockThreads, 1) fftcc_tc_kernel(FftccArgs 
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int kx = 2 * j + (lane >> 4);
-        buf[ky * kTcSA + kx] = p[j].x;
-        buf[ky * kTcSA + kTcP + kx] = -p[j].y;           // conj(P): T = conj(conj(P) W)
+        buf[ky * kH16SA + kx] = p[j].x;
+        buf[ky * kH16SA + kTcP + kx] = -p[j].y;          // conj(P)
       }
       __syncwarp();
     }
-    // 4. T = P conj(W), rows ky < 16, stored as [Tr; Ti] (32 x 32, row ky for Tr and
-    //    16 + ky for Ti, row stride kTcSW)
+    const int E3 = f16_scale_exp(warp_max(pmax));
+    // 4. U^T = W conj(P)^T: [Ur^T; Ui^T] = [[Wr, -Wi], [Wi, Wr]] [Pr^T; -Pi^T] (64 x 64 by
+    //    64 x 16), conj(P) entering scaled by 2^E3; T = conj(U) is stored as T^T
+    //    ([x][ky | 16 + ky], row stride kTcSW)
     {
-      float acc[1][8][4] = {};
-      warp_gemm_w<1>(buf, kTcSA, wf, lane, g, t, acc);
-      __syncwarp();
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int m = g + (i >> 1) * 8, n = 8 * j + 2 * t + (i & 1);
-          buf[(m + (n >> 5) * 16) * kTcSW + (n & 31)] = (n >> 5) ? -acc[0][j][i] : acc[0][j][i];
-        }
-      __syncwarp();
-    }
-    // 5. R = A6 [Tr; Ti] (32 x 32), then the arg-max over the L x L values (ties to
-    //    the lower row-major index y L + x) straight from the accumulators
-    float acc[2][4][4] = {};
+      float acc[4][2][4] = {};
+      const float s3 = pow2f(E3);
 #pragma unroll 1
-    for (int k0 = 0; k0 < kTcP; k0 += 8) {
-      uint32_t ah[2][4], al[2][4];
+      for (int ks = 0; ks < 4; ++ks) {
+        uint32_t bh[2][2], bl[2][2];
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const uint4 h = a6f[((mt * 4 + (k0 >> 3)) * 2) * 32 + lane], l = a6f[((mt * 4 + (k0 >> 3)) * 2 + 1) * 32 + lane];
-        ah[mt][0] = h.x;
-        ah[mt][1] = h.y;
-        ah[mt][2] = h.z;
-        ah[mt][3] = h.w;
-        al[mt][0] = l.x;
-        al[mt][1] = l.y;
-        al[mt][2] = l.z;
-        al[mt][3] = l.w;
+        for (int nt = 0; nt < 2; ++nt) {
+          const float* p = buf + (8 * nt + g) * kH16SA + 16 * ks + 2 * t;   // conj(P) row ky = 8 nt + g
+          const float2 v0 = *reinterpret_cast<const float2*>(p), v1 = *reinterpret_cast<const float2*>(p + 8);
+          split_h2(v0.x, v0.y, s3, bh[nt][0], bl[nt][0]);
+          split_h2(v1.x, v1.y, s3, bh[nt][1], bl[nt][1]);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+          const uint4 h = wa[((mt * 4 + ks) * 2) * 32 + lane], l = wa[((mt * 4 + ks) * 2 + 1) * 32 + lane];
+          const uint32_t ah[4] = {h.x, h.y, h.z, h.w}, al[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) mma_f16(acc[mt][nt], ah, bh[nt][0], bh[nt][1]);
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) mma_f16(acc[mt][nt], ah, bl[nt][0], bl[nt][1]);
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) mma_f16(acc[mt][nt], al, bh[nt][0], bh[nt][1]);
+        }
       }
-      uint32_t bh[4][2], bl[4][2];
+      __syncwarp();
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float v0 = buf[(k0 + t) * kTcSW + 8 * j + g], v1 = buf[(k0 + t + 4) * kTcSW + 8 * j + g];
-        bh[j][0] = tf32_bits(v0);
-        bh[j][1] = tf32_bits(v1);
-        bl[j][0] = tf32_bits(v0 - __uint_as_float(bh[j][0]));
-        bl[j][1] = tf32_bits(v1 - __uint_as_float(bh[j][1]));
-      }
+      for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+        for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) mma_tf32(acc[mt][j], ah[mt], bh[j][0], bh[j][1]);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) mma_tf32(acc[mt][j], ah[mt], bl[j][0], bl[j][1]);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) mma_tf32(acc[mt][j], al[mt], bh[j][0], bh[j][1]);
+          for (int hr = 0; hr < 2; ++hr) {
+            const int m = 16 * mt + g + 8 * hr, n = 8 * nt + 2 * t;
+            const float sg2 = m < 32 ? 1.f : -1.f;     // Ti = -Ui
+            *reinterpret_cast<float2*>(buf + (m & 31) * kTcSW + (m >> 5) * 16 + n) =
+                make_float2(sg2 * acc[mt][nt][2 * hr], sg2 * acc[mt][nt][2 * hr + 1]);
+          }
+      __syncwarp();
     }
-    if (nyquist) {                                       // R[y][x] += T16[x] (-1)^y
+    // 5. R = A6 [Tr; Ti] (32 x 32 by 32 x 32), [Tr; Ti] entering scaled by 2^-7; then the
+    //    arg-max over the L x L values (ties to the lower row-major index y L + x)
+    //    straight from the accumulators
+    float acc[2][4][4] = {};
+    {
+      const float s4 = pow2f(-7);
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          const float* p = buf + (8 * nt + g) * kTcSW + 16 * ks + 2 * t;   // T^T row x = 8 nt + g
+          const float2 v0 = *reinterpret_cast<const float2*>(p), v1 = *reinterpret_cast<const float2*>(p + 8);
+          split_h2(v0.x, v0.y, s4, bh[nt][0], bl[nt][0]);
+          split_h2(v1.x, v1.y, s4, bh[nt][1], bl[nt][1]);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          const uint4 h = a6f[((mt * 2 + ks) * 2) * 32 + lane], l = a6f[((mt * 2 + ks) * 2 + 1) * 32 + lane];
+          const uint32_t ah[4] = {h.x, h.y, h.z, h.w}, al[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_f16(acc[mt][nt], ah, bh[nt][0], bh[nt][1]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_f16(acc[mt][nt], ah, bl[nt][0], bl[nt][1]);
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_f16(acc[mt][nt], al, bh[nt][0], bh[nt][1]);
+        }
+      }
+    }
+    if (nyquist) {                                       // R[y][x] += T16[x] (-1)^y, in R's scale
+      const float sn = pow2f(E3 - 7);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const float tv = __shfl_sync(0xffffffffu, t16, 8 * j + 2 * t + c);
+          const float tv = sn * __shfl_sync(0xffffffffu, t16, 8 * j + 2 * t + c);
 #pragma unroll
           for (int mt = 0; mt < 2; ++mt) {
             acc[mt][j][c] += (g & 1) ? -tv : tv;         // row 16 mt + g
@@ -917,7 +994,7 @@ __global__ void __launch_bounds__(kTcBlockThreads, 1) fftcc_tc_kernel(FftccArgs 
       const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, best, off);
       best = o2 > best ? o2 : best;
     }
-    __syncwarp();                                        // [Tr; Ti] is no longer read
+    __syncwarp();                                        // T^T is no longer read
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -941,14 +1018,16 @@ __global__ void __launch_bounds__(kTcBlockThreads, 1) fftcc_tc_kernel(FftccArgs 
       }
       a.u[win] = static_cast<float>(o.z - o.x) + dx;
       a.v[win] = static_cast<float>(o.w - o.y) + dy;
-      a.peak[win] = flat ? 0.f : r0 / (static_cast<float>(N) * sqrtf(qf) * sqrtf(qg));
+      // R here is the correlation times 2^(2 E1 - 7 - 7 + E3 - 7): X carries s1 2^-7, P its
+      // square, T the factor 2^E3 and the 2^-7 of step 5
+      a.peak[win] = flat ? 0.f : ldexpf(r0, 21 - 2 * E1 - E3) / (static_cast<float>(N) * sqrtf(qf) * sqrtf(qg));
     }
     __syncwarp();                                        // the next window reuses the buffer
   }
 }
 
 size_t tc_smem() {
-  return sizeof(uint4) * (kTcFrags + kTcA6Frags) + sizeof(float) * kTcWarps * kTcBuf;
+  return sizeof(uint4) * (kWaFrags + kWbFrags + kA6hFrags) + sizeof(float) * kTcWarps * kH16Buf;
 }
 
 // ---------------------------------------------------------------- large windows
