@@ -802,7 +802,8 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel
     tc_achieved = tc_flops / (k / 1e3) / 1e12
     f16_peak = MEASURED.get("bf16_tflops", 1912.3)
     levels = g["windows"]
-    launches = 1 + 3 * len(levels) + 5 * sum(1 for L in levels if L > 64)   # origins, fftcc (6 when > 64 px), MAD; status
+    # origins, fftcc, MAD per level (fftcc: 4 launches for 128-512 px, 6 above); status
+    launches = 1 + 3 * len(levels) + sum(3 if L <= 512 else 5 for L in levels if L > 64)
     c.close()
     del roi
     return {"workload": "sem_fft_%d_u8: %dx%d u8 pair, subset %d, step %d, max displacement %d px, %d px border "

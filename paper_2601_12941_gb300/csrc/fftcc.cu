@@ -39,6 +39,7 @@ constexpr int kSmallThreads = 256;
 constexpr int kLineThreads = 512;
 constexpr int kLineElems = 4096;       // complex elements per block of the line kernels
 constexpr int kTransposeTile = 32;
+constexpr int kTrRun = 8;              // rows per column run of the transposed work-buffer I/O
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -1068,6 +1069,10 @@ __device__ __forceinline__ void line_grays(const GrayPlane& pl, int x0, int y0, 
 
 // Rows of the packed windows, transformed along x: work[w][y][kx]. Also marks the
 // windows whose f or g is not constant (an exactly flat window correlates to 0).
+// TR: the output goes to the work buffer transposed (work[w][kx][y]), in runs of
+// kTrRun rows (64 bytes) per column, so no transpose kernel is needed (L <= 512: at
+// least kTrRun rows per block).
+template <bool TR>
 __global__ void __launch_bounds__(kLineThreads, 3) fftcc_rows_fwd_kernel(FftccArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.L;
@@ -1093,8 +1098,22 @@ __global__ void __launch_bounds__(kLineThreads, 3) fftcc_rows_fwd_kernel(FftccAr
   if (__syncthreads_or(vf) && threadIdx.x == 0) atomicOr(&a.nonflat[2 * w], 1);
   if (__syncthreads_or(vg) && threadIdx.x == 0) atomicOr(&a.nonflat[2 * w + 1], 1);
   const float2* R = fft_lines<false>(P, Q, L, rows, L, 1, a.tw_pow2);
-  float2* dst = a.work + w * static_cast<int64_t>(L) * L + static_cast<int64_t>(y0) * L;
-  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) dst[e] = R[fsl(e)];
+  if (TR) {
+    const int lg = __ffs(L) - 1;
+    float2* base = a.work + w * static_cast<int64_t>(L) * L + y0;
+    for (int it = threadIdx.x; it < (rows / kTrRun) * L; it += kLineThreads) {
+      const int kx = it & (L - 1), r = kTrRun * (it >> lg);
+      float4* d = reinterpret_cast<float4*>(base + static_cast<int64_t>(kx) * L + r);
+#pragma unroll
+      for (int i = 0; i < kTrRun / 2; ++i) {
+        const float2 v0 = R[fsl((r + 2 * i) * L + kx)], v1 = R[fsl((r + 2 * i + 1) * L + kx)];
+        d[i] = make_float4(v0.x, v0.y, v1.x, v1.y);
+      }
+    }
+  } else {
+    float2* dst = a.work + w * static_cast<int64_t>(L) * L + static_cast<int64_t>(y0) * L;
+    for (int e = threadIdx.x; e < rows * L; e += kLineThreads) dst[e] = R[fsl(e)];
+  }
 }
 
 // In-place transpose of every L x L window: the block of tile (ti, tj), ti <= tj,
@@ -1185,7 +1204,9 @@ __global__ void __launch_bounds__(kLineThreads, 3) fftcc_pairs_kernel(FftccArgs 
   }
 }
 
-// Inverse transform of the rows along kx and the per-window arg-max of R.
+// Inverse transform of the rows along kx and the per-window arg-max of R. TR: the work
+// buffer holds the transposed layout (work[w][kx][y]), read in runs of kTrRun rows.
+template <bool TR>
 __global__ void __launch_bounds__(kLineThreads, 3) fftcc_rows_inv_kernel(FftccArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = a.L;
@@ -1196,8 +1217,25 @@ __global__ void __launch_bounds__(kLineThreads, 3) fftcc_rows_inv_kernel(FftccAr
   const int64_t w = blockIdx.x;
   if (!window_ok(a.org[w], L, a.W, a.H)) return;
   const int y0 = blockIdx.y * rows;
-  const float2* src = a.work + w * static_cast<int64_t>(L) * L + static_cast<int64_t>(y0) * L;
-  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) P[fsl(e)] = src[e];
+  if (TR) {
+    const int lg = __ffs(L) - 1;
+    const float2* base = a.work + w * static_cast<int64_t>(L) * L + y0;
+    for (int it = threadIdx.x; it < (rows / kTrRun) * L; it += kLineThreads) {
+      const int kx = it & (L - 1), r = kTrRun * (it >> lg);
+      const float4* sp = reinterpret_cast<const float4*>(base + static_cast<int64_t>(kx) * L + r);
+      float4 v[kTrRun / 2];
+#pragma unroll
+      for (int i = 0; i < kTrRun / 2; ++i) v[i] = sp[i];
+#pragma unroll
+      for (int i = 0; i < kTrRun / 2; ++i) {
+        P[fsl((r + 2 * i) * L + kx)] = make_float2(v[i].x, v[i].y);
+        P[fsl((r + 2 * i + 1) * L + kx)] = make_float2(v[i].z, v[i].w);
+      }
+    }
+  } else {
+    const float2* src = a.work + w * static_cast<int64_t>(L) * L + static_cast<int64_t>(y0) * L;
+    for (int e = threadIdx.x; e < rows * L; e += kLineThreads) P[fsl(e)] = src[e];
+  }
   __syncthreads();
   const float2* R = fft_lines<true>(P, Q, L, rows, L, 1, a.tw_pow2);
   unsigned long long best = 0ull;
@@ -1444,35 +1482,49 @@ cudaError_t launch_fftcc(const FftccArgs& a, cudaStream_t s) {
     }
     return cudaGetLastError();
   }
-  // large windows: a power of two in [128, 4096] (checked by the caller)
-  static const cudaError_t ok1 = cudaFuncSetAttribute(fftcc_rows_fwd_kernel,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      static_cast<int>(2 * fft_slots(kLineElems) * sizeof(float2)));
+  // large windows: a power of two in [128, 4096] (checked by the caller). Up to 512 the
+  // row kernels write and read the work buffer transposed (runs of kTrRun rows), so the
+  // two transpose kernels drop out; above, a block holds fewer rows (and four-row runs
+  // measured slower than the transposes at 1024).
+  const int line_bytes = static_cast<int>(2 * fft_slots(kLineElems) * sizeof(float2));
+  static const cudaError_t ok1 = cudaFuncSetAttribute(fftcc_rows_fwd_kernel<false>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, line_bytes);
+  static const cudaError_t ok1t = cudaFuncSetAttribute(fftcc_rows_fwd_kernel<true>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, line_bytes);
   static const cudaError_t ok2 = cudaFuncSetAttribute(fftcc_pairs_kernel,
                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       static_cast<int>(2 * fft_slots(2 * kLineElems) * sizeof(float2)));
-  static const cudaError_t ok3 = cudaFuncSetAttribute(fftcc_rows_inv_kernel,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      static_cast<int>(2 * fft_slots(kLineElems) * sizeof(float2)));
-  if (ok1 != cudaSuccess) return ok1;
-  if (ok2 != cudaSuccess) return ok2;
-  if (ok3 != cudaSuccess) return ok3;
+  static const cudaError_t ok3 = cudaFuncSetAttribute(fftcc_rows_inv_kernel<false>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, line_bytes);
+  static const cudaError_t ok3t = cudaFuncSetAttribute(fftcc_rows_inv_kernel<true>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, line_bytes);
+  for (cudaError_t ok : {ok1, ok1t, ok2, ok3, ok3t})
+    if (ok != cudaSuccess) return ok;
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.nonflat, 0, sizeof(int32_t) * 2 * a.n, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.norms, 0, sizeof(double) * 2 * a.n, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(a.keys, 0, sizeof(unsigned long long) * a.n, s)) != cudaSuccess) return e;
   const unsigned nw = static_cast<unsigned>(a.n);
   const int rows = kLineElems / L;
-  const size_t line_smem = 2 * fft_slots(kLineElems) * sizeof(float2);
-  fftcc_rows_fwd_kernel<<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
+  const bool tr = rows >= kTrRun;
+  const size_t line_smem = static_cast<size_t>(line_bytes);
   const int T = L / kTransposeTile;
-  fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
+  if (tr) {
+    fftcc_rows_fwd_kernel<true><<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
+  } else {
+    fftcc_rows_fwd_kernel<false><<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
+    fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
+  }
   const int units = L <= kLineElems / 2 ? kLineElems / 2 / L : 1;
   const int nunits = L / 2 + 1;
   const size_t pair_smem = 2 * sizeof(float2) * fft_slots(2 * units * L);
   fftcc_pairs_kernel<<<dim3(nw, (nunits + units - 1) / units), kLineThreads, pair_smem, s>>>(a);
-  fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
-  fftcc_rows_inv_kernel<<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
+  if (tr) {
+    fftcc_rows_inv_kernel<true><<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
+  } else {
+    fftcc_transpose_kernel<<<dim3(nw, T * T), kTransposeTile * 8, 0, s>>>(a);
+    fftcc_rows_inv_kernel<false><<<dim3(nw, L / rows), kLineThreads, line_smem, s>>>(a);
+  }
   fftcc_finish_kernel<<<(nw + 255) / 256, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
