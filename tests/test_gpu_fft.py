@@ -152,6 +152,30 @@ def test_gray_types_over_windows_match_oracle(pkg, dtype, L):
     assert ties <= 2
 
 
+@pytest.mark.parametrize("scale", [1e-12, 1e-6, 1e6, 1e12])
+def test_extreme_gray_ranges_match_oracle(pkg, scale):
+    """Floating-point gray levels far from the usual range (scaled by 1e-12 .. 1e12):
+    Eq. 1 does not depend on the scale, and the tensor-core windows (31, 32 px) take
+    their power-of-two operand scales from the data, so they must give the oracle's
+    result at any scale where the FP32 window sums of squares stay finite and normal."""
+    W, H = 300, 280
+    fld = synth.affine_field(W, H, u0=1.7, v0=-2.4, exx=2e-3, eyy=-1e-3, exy=5e-4)
+    ref = _speckle(W, H, 41, dtype="f64") * scale
+    dfm = _speckle(W, H, 41, fld=fld, dtype="f64", tag=2) * scale
+    c = pkg.Correlation(ref, dfm, None, 21, 10, "affine")
+    for L, subpixel in ((31, True), (32, True), (64, True)):
+        rng = np.random.default_rng(7 + L)
+        origins = _random_origins(rng, W, H, L, 30, spread=8)
+        gu, gv, gp = _gpu_windows(pkg, c, L, origins, subpixel)
+        ora = _oracle_windows(ref, dfm, L, origins, subpixel)
+        for k, (ou, ov, opk, tie, R) in enumerate(ora):
+            if tie:
+                continue
+            assert abs(gu[k] - ou) < 1e-4 and abs(gv[k] - ov) < 1e-4, (L, k, gu[k], ou, gv[k], ov)
+            assert abs(gp[k] - opk) < 2e-5, (L, k, gp[k], opk)
+    c.close()
+
+
 def test_flat_and_skipped_windows(pkg):
     W, H = 400, 360
     ref = _speckle(W, H, 5)
