@@ -1193,14 +1193,17 @@ __global__ void __launch_bounds__(kLineThreads, 3) fftcc_pairs_kernel(FftccArgs 
     atomicAdd(&a.norms[2 * w], static_cast<double>(nf));
     atomicAdd(&a.norms[2 * w + 1], static_cast<double>(ng));
   }
-  float2* R = fft_lines<true>(Y, X, L, lines, L, 1, a.tw_pow2);
+  // the cross power is Hermitian (P(-k) = conj P(k)), so the mirror row's inverse
+  // transform is the conjugate of row u's: only the even lines are transformed back
+  float2* R = fft_lines<true>(Y, X, L, lines / 2, 2 * L, 1, a.tw_pow2);
   for (int e = threadIdx.x; e < lines * L; e += kLineThreads) {
     const int line = e >> lg, y = e & (L - 1);
     const int u = u0 + (line >> 1);
     if (u >= nunits) continue;
     if ((line & 1) && (u == 0 || 2 * u == L)) continue;   // a self-paired row is written once
     const int row = (line & 1) ? (L - u) & (L - 1) : u;
-    base[static_cast<int64_t>(row) * L + y] = R[fsl(e)];
+    const float2 r = R[fsl((line & ~1) * L + y)];
+    base[static_cast<int64_t>(row) * L + y] = (line & 1) ? make_float2(r.x, -r.y) : r;
   }
 }
 
@@ -1237,11 +1240,32 @@ __global__ void __launch_bounds__(kLineThreads, 3) fftcc_rows_inv_kernel(FftccAr
     for (int e = threadIdx.x; e < rows * L; e += kLineThreads) P[fsl(e)] = src[e];
   }
   __syncthreads();
-  const float2* R = fft_lines<true>(P, Q, L, rows, L, 1, a.tw_pow2);
   unsigned long long best = 0ull;
-  for (int e = threadIdx.x; e < rows * L; e += kLineThreads) {
-    const unsigned long long k = peak_key(R[fsl(e)].x, y0 * L + e);
-    best = k > best ? k : best;
+  if (rows >= 2) {
+    // every row transforms back to real values: rows 2l and 2l + 1 go through one
+    // transform as row 2l + i row 2l + 1, whose result holds them as real and
+    // imaginary parts
+    const int lg = __ffs(L) - 1;
+    for (int e = threadIdx.x; e < (rows / 2) * L; e += kLineThreads) {
+      const int l = e >> lg, x = e & (L - 1);
+      const float2 p0 = P[fsl(2 * l * L + x)], p1 = P[fsl((2 * l + 1) * L + x)];
+      Q[fsl(e)] = make_float2(p0.x - p1.y, p0.y + p1.x);
+    }
+    __syncthreads();
+    const float2* R = fft_lines<true>(Q, P, L, rows / 2, L, 1, a.tw_pow2);
+    for (int e = threadIdx.x; e < (rows / 2) * L; e += kLineThreads) {
+      const int l = e >> lg, x = e & (L - 1);
+      const float2 v = R[fsl(e)];
+      const unsigned long long k0 = peak_key(v.x, (y0 + 2 * l) * L + x), k1 = peak_key(v.y, (y0 + 2 * l + 1) * L + x);
+      best = k0 > best ? k0 : best;
+      best = k1 > best ? k1 : best;
+    }
+  } else {
+    const float2* R = fft_lines<true>(P, Q, L, rows, L, 1, a.tw_pow2);
+    for (int e = threadIdx.x; e < rows * L; e += kLineThreads) {
+      const unsigned long long k = peak_key(R[fsl(e)].x, y0 * L + e);
+      best = k > best ? k : best;
+    }
   }
   best = block_max_key(best, s_key);
   if (threadIdx.x == 0) atomicMax(&a.keys[w], best);
