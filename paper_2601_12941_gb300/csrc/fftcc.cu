@@ -632,13 +632,15 @@ __device__ __forceinline__ void split_h2(float x0, float x1, float s, uint32_t& 
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// 2^E with E = 13 - floor(log2(m)): m scaled by it lies in [2^13, 2^14); 1 for m = 0
+// The exponent E = 13 - floor(log2 m), clamped to [-100, 100] (0 for m = 0): m 2^E lies
+// in [2^13, 2^14)
 __device__ __forceinline__ int f16_scale_exp(float m) {
   if (!(m > 0.f)) return 0;
   const int e = static_cast<int>((__float_as_uint(m) >> 23) & 0xffu) - 127;
   const int E = 13 - e;
   return E < -100 ? -100 : (E > 100 ? 100 : E);
 }
+// 2^E as a float, -126 <= E <= 127
 __device__ __forceinline__ float pow2f(int E) { return __uint_as_float(static_cast<uint32_t>(127 + E) << 23); }
 
 __device__ __forceinline__ float warp_max(float v) {
