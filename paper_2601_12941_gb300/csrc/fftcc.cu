@@ -25,6 +25,7 @@
 //     (packed 64-bit keys: the larger R, ties to the lower row-major index).
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <cuda_fp16.h>
 
@@ -628,8 +629,8 @@ __device__ __forceinline__ void split_h2(float x0, float x1, float s, uint32_t& 
   const __half2 h = __floats2half2_rn(y0, y1);
   const float2 hf = __half22float2(h);
   const __half2 l = __floats2half2_rn(y0 - hf.x, y1 - hf.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
+  memcpy(&hi, &h, sizeof(hi));
+  memcpy(&lo, &l, sizeof(lo));
 }
 
 // The exponent E = 13 - floor(log2 m), clamped to [-100, 100] (0 for m = 0): m 2^E lies
