@@ -11,7 +11,9 @@
 // separably from shared-memory tiles. A window with missing points is fitted
 // from its normal equations (grid units, unit-diagonal scaling, elimination
 // without exchanges); a scaled pivot at or below 1e-5 leaves the point without
-// strain (NaN). Arithmetic in FP32 on displacements taken relative to the centre.
+// strain (NaN). Arithmetic in FP32 on displacement offsets: from a reference point of
+// the tile for the separable filter (whose slope weights sum to zero, so the reference
+// drops out), from the centre, formed in FP64 and rounded once, for the general fit.
 #include <math.h>
 
 #include "dic_internal.cuh"
@@ -184,7 +186,8 @@ constexpr int kSmallHalf = 4, kMaxHalf = 15;
 // Block of kTileX x kTileY grid points. The block stages the displacements of its
 // points and of a halo of h = (window - 1) / 2 points as FP32 offsets from one
 // accepted point of the tile, the first in row-major order (points outside the grid
-// or not accepted become NaN), then applies the full-window slope filter separably:
+// or not accepted become NaN), and as the FP64 values (for the general fit), then
+// applies the full-window slope filter separably:
 // along each staged row the sums sum_i i d, sum_i d and sum_i i^2 d over the window's
 // columns, then down each point's column the x slope sum_j (a + b j^2) (sum_i i d)_j
 // and the y slope sum_j j (a (sum_i d)_j + b (sum_i i^2 d)_j). A NaN anywhere in a
