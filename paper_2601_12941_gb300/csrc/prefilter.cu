@@ -35,10 +35,9 @@ struct Taps {
   T h[29];
 };
 
+// truncation radius of the FIR form (FP64; the FP32 path runs the recursions)
 template <typename T>
 constexpr int taps_radius();
-template <>
-constexpr int taps_radius<float>() { return 14; }
 template <>
 constexpr int taps_radius<double>() { return 28; }
 
@@ -59,8 +58,6 @@ Taps<T> make_taps() {
 // G + 2K inputs and produces G outputs from it
 template <typename T>
 struct OutputsPerThread;
-template <>
-struct OutputsPerThread<float> { static constexpr int kValue = 4; };
 template <>
 struct OutputsPerThread<double> { static constexpr int kValue = 2; };
 
@@ -164,31 +161,34 @@ template <>
 struct GrayBytes<DIC_F64> { static constexpr int kValue = 8; };
 
 // element i of 16 gray-level bytes as FP32, exactly (integers through the
-// 2^23 exponent: 0x4B000000 | n is the float 2^23 + n)
+// 2^23 exponent: 0x4B000000 | n is the float 2^23 + n); FP64 gray levels arrive
+// already rounded to FP32 (see RowRun)
 template <int DT>
 __device__ __forceinline__ float unpack(const uint4& w, int i) {
-  const uint32_t word = i * GrayBytes<DT>::kValue < 4 ? w.x : i * GrayBytes<DT>::kValue < 8 ? w.y
-                        : i * GrayBytes<DT>::kValue < 12 ? w.z : w.w;
+  constexpr int B = DT == DIC_F64 ? 4 : GrayBytes<DT>::kValue;   // bytes per element as held
+  const uint32_t word = i * B < 4 ? w.x : i * B < 8 ? w.y : i * B < 12 ? w.z : w.w;
   if constexpr (DT == DIC_U8) {
     return __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7440u + (i & 3))) - 8388608.0f;
   } else if constexpr (DT == DIC_U16) {
     return __uint_as_float(__byte_perm(word, 0x4B000000u, (i & 1) ? 0x7432u : 0x7410u)) - 8388608.0f;
   } else if constexpr (DT == DIC_BF16) {
     return __uint_as_float(__byte_perm(word, 0u, (i & 1) ? 0x3244u : 0x1044u));
-  } else if constexpr (DT == DIC_F32) {
+  } else {   // F32, and F64 (held as FP32 values, see RowRun)
     return __uint_as_float(word);
-  } else {
-    const uint64_t bits = (i & 1) ? (static_cast<uint64_t>(w.w) << 32 | w.z) : (static_cast<uint64_t>(w.y) << 32 | w.x);
-    return static_cast<float>(__longlong_as_double(static_cast<long long>(bits)));
   }
 }
 
 // x-pass item: 64 gray levels of one row, columns xa .. xa + 63 (mirrored into the
 // image where they leave it); held as raw 16-byte words when the row allows
-// aligned vector loads
+// aligned vector loads. FP64 gray levels are rounded to FP32 as they arrive (the
+// recursions run in FP32), which keeps the run at 16 words.
+template <int DT>
+struct RowBytes {
+  static constexpr int kValue = DT == DIC_F64 ? 4 : GrayBytes<DT>::kValue;
+};
 template <int DT>
 struct RowRun {
-  static constexpr int kVec = 64 * GrayBytes<DT>::kValue / 16;
+  static constexpr int kVec = 64 * RowBytes<DT>::kValue / 16;
   uint4 w[kVec];
 };
 
@@ -197,10 +197,29 @@ __device__ __forceinline__ void load_run(RowRun<DT>& run, const PrefilterArgs<fl
                                          int y) {
   const int gy = static_cast<int>(mirror_index(y, a.H));
   const char* row = static_cast<const char*>(a.src.data) + static_cast<int64_t>(gy) * a.src.stride;
-  if (fast) {
+  if (fast && DT == DIC_F64) {
+    const double2* src = reinterpret_cast<const double2*>(row + static_cast<int64_t>(xa) * 8);
+#pragma unroll 4
+    for (int v = 0; v < RowRun<DT>::kVec; ++v) {
+      const double2 p = src[2 * v], q = src[2 * v + 1];
+      run.w[v] = make_uint4(__float_as_uint(static_cast<float>(p.x)), __float_as_uint(static_cast<float>(p.y)),
+                            __float_as_uint(static_cast<float>(q.x)), __float_as_uint(static_cast<float>(q.y)));
+    }
+  } else if (fast) {
     const uint4* src = reinterpret_cast<const uint4*>(row + static_cast<int64_t>(xa) * GrayBytes<DT>::kValue);
 #pragma unroll
     for (int v = 0; v < RowRun<DT>::kVec; ++v) run.w[v] = src[v];
+  } else if (DT == DIC_F64) {
+#pragma unroll
+    for (int v = 0; v < RowRun<DT>::kVec; ++v) {
+      uint32_t q[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t gx = mirror_index(xa + 4 * v + e, a.W);
+        q[e] = __float_as_uint(static_cast<float>(reinterpret_cast<const double*>(row)[gx]));
+      }
+      run.w[v] = make_uint4(q[0], q[1], q[2], q[3]);
+    }
   } else {
     // edge strips: element by element through the mirror, repacked into words
     constexpr int EPV = 16 / GrayBytes<DT>::kValue;
@@ -231,7 +250,7 @@ __device__ __forceinline__ void x_recursions(const RowRun<DT>& run, float z, flo
 #pragma unroll
   for (int j = 0; j < kPfRun; ++j) {
     const int e = j + 2;
-    const float x = unpack<DT>(run.w[e * GrayBytes<DT>::kValue / 16], e % (16 / GrayBytes<DT>::kValue));
+    const float x = unpack<DT>(run.w[e * RowBytes<DT>::kValue / 16], e % (16 / RowBytes<DT>::kValue));
     acc = j == 0 ? x : fmaf(z, acc, x);
     if (j >= kPfLead) q[j - kPfLead] = acc;
   }
