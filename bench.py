@@ -737,6 +737,13 @@ def variants_leg(ref, dfm, w, seeds, stream, steps=2):
     return out
 
 
+def fft_launches(levels):
+    """Kernel launches of one FFT field: per level the origins, the correlation and the
+    MAD filter, the correlation taking 4 launches at 128-512 px (rows, paired columns,
+    inverse rows, finish) and 6 above (two transposes more); one status launch."""
+    return 1 + 3 * len(levels) + sum(3 if L <= 512 else 5 for L in levels if L > 64)
+
+
 def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel_reps=3):
     """Multi-window FFT initialiser (Sec. 2.2, Eq. 1; MAD) on the 1 Gpx pair with the
     SEM study's settings (Sec. 4): subset 31, step 15, maximum displacement 2000 px
@@ -802,8 +809,7 @@ def fft_leg(ref, dfm, stream, S=31, step=15, D=2000, border=None, reps=3, kernel
     tc_achieved = tc_flops / (k / 1e3) / 1e12
     f16_peak = MEASURED.get("bf16_tflops", 1912.3)
     levels = g["windows"]
-    # origins, fftcc, MAD per level (fftcc: 4 launches for 128-512 px, 6 above); status
-    launches = 1 + 3 * len(levels) + sum(3 if L <= 512 else 5 for L in levels if L > 64)
+    launches = fft_launches(levels)
     c.close()
     del roi
     return {"workload": "sem_fft_%d_u8: %dx%d u8 pair, subset %d, step %d, max displacement %d px, %d px border "
